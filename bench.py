@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Throughput of the beyond-Limber FFTLog C_ell hot path on GB300.
+
+Metric: C_ell evaluations per second, one evaluation = the 120 spectra x 103 ell of one
+parameter point of the N5K-shaped workload (10 clustering + 5 lensing windows, N_FFT = 2048,
+N_k = 1024, N_I = 150 k-knots), forward + VJP (the whole hot path: FFTLog, Gamma-ratio
+contraction with k-interpolation, k-quadrature and their reverse mode).  Inputs are seeded,
+synthetic and resident in HBM when the timed region starts; L2 is flushed (256 MB write)
+before every timed step.  Under torchrun every rank evaluates its own parameter points (weak
+scaling, no collective on the data path) and the slowest rank's time counts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 3xtf32|bf16x6|fp64]
+                    [--walkers B] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (NumPy/SciPy on the host cores) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "C_ell evals/s (120 spectra×103 ℓ), fwd & fwd+grad, vs FP64 GPU path at 1e-4 rel"
+WORKLOAD = ("N5K-shaped: 15 tracers (10 Gaussian clustering + 5 Smail lensing bins), 120 spectra, "
+            "103 log-spaced ell in [2,2000], N_FFT=2048, N_k=1024 in [1e-4,10] h/Mpc, N_I=150 k-knots, "
+            "D(k,z)=(1+z)^-1(1+0.01 ln(k/0.1)); one evaluation = forward + VJP")
+
+# measured peaks (MEASURED_PEAKS.json written by the pool driver); FP64 derived below
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM (FMA-loop probe: 1.19 TF/s at 2070 MHz)
+TF32_OVER_BF16 = 1.1 / 2.25                      # nominal dense ratio
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "3xtf32", "bf16x6"])
+    ap.add_argument("--walkers", type=int, default=1, help="parameter points per step per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ inputs ----
+
+def make_inputs(walkers: int, rank: int):
+    from workloads import make_workload
+    if walkers <= 1 and rank == 0:
+        w = make_workload("n5k_vjp")
+        return w, w.C_bar[None] if w.C_bar.ndim == 3 else w.C_bar
+    w = make_workload("walkers", seed=20250528 + rank, n_walkers=walkers)
+    w.ell_lists = None  # every walker evaluates the full 103-ell set for the headline metric
+    rng = np.random.default_rng(99 + rank)
+    cbar = rng.standard_normal((walkers, len(w.ells), w.n_tr, w.n_tr))
+    return w, cbar
+
+
+def n_walk(w):
+    return 1 if w.W.ndim == 2 else w.W.shape[0]
+
+
+# ---------------------------------------------------------------- roofline ----
+
+def algorithmic_work(w, walkers):
+    """Algorithmic FLOPs per launch of each kernel ('Measurement')."""
+    n_h = w.N // 2 + 1
+    ntr, nk, nl, ni, N = w.n_tr, len(w.k), len(w.ells), len(w.knots), w.N
+    contraction = 4.0 * n_h * ntr * nk * nl * walkers          # Re sum_n of complex products
+    fft = 2.5 * N * np.log2(N) * ntr * ni * walkers             # real FFT of length N per row
+    return {
+        "contract fp64": ("alu", contraction),
+        "contract adj fp64": ("alu", contraction),
+        "contract tc": ("tensor", contraction),
+        "contract adj tc": ("tensor", contraction),
+        "fftlog": ("alu", fft),
+        "fftlog adj": ("alu", fft),
+    }
+
+
+def roofline(stats, w, walkers, precision, peaks, src):
+    if not stats:
+        return None
+    name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
+    work = algorithmic_work(w, walkers)
+    bound, flops = work.get(name, ("alu", None))
+    avg_s = ms / launches / 1e3
+    if flops is None:
+        return {"kernel": name, "bound": None, "avg_ms": ms / launches, "note": "no algorithmic count"}
+    if bound == "tensor":
+        products = 3 if precision == "3xtf32" else 6
+        tflops = flops * products / avg_s / 1e12
+        if precision == "3xtf32":
+            peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+            unit_note = "tf32 peak = measured bf16 burst x nominal tf32/bf16 ratio"
+        else:
+            peak = peaks["bf16_tflops"]
+            unit_note = "bf16 burst peak"
+        return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": tflops / peak, "traffic": None, "avg_ms": ms / launches, "launches": launches,
+                "peak_source": "%s (%s)" % (src, unit_note),
+                "useful_tflops": flops / avg_s / 1e12}
+    tflops = flops / avg_s / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "avg_ms": ms / launches, "launches": launches,
+            "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; FMA probe 1.19 TF/s)"}
+
+
+# ------------------------------------------------------------------ clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle ----
+
+def oracle_eval(w, cbar, g=None):
+    from oracle import fftlog as O
+    if g is None:
+        g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
+    W = w.W if w.W.ndim == 2 else w.W[0]
+    P = w.P if w.P.ndim == 1 else w.P[0]
+    A = w.amp if w.amp.ndim == 1 else w.amp[0]
+    f = O.forward(g, W, w.D, P, A, w.B)
+    O.vjp(g, f, cbar[0], W, w.D, P, A, w.B)
+    return g, f
+
+
+def cpu_baseline(w, cbar, n_eval=2):
+    from oracle import fftlog as O
+    g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
+    for b in np.unique(w.fft_bias):
+        g.mtable(b)  # the paper excludes the Gamma-ratio precomputation from its timings
+    t0 = time.perf_counter()
+    f = None
+    for _ in range(n_eval):
+        _, f = oracle_eval(w, cbar, g)
+    dt = time.perf_counter() - t0
+    return {"value": n_eval / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d full forward+VJP evaluations of one parameter point (Gamma/phase tables "
+                      "precomputed, as the paper excludes them), NumPy/SciPy FP64, BLAS threads = all cores"
+                      % n_eval}, f
+
+
+# ----------------------------------------------------------------- our arm ----
+
+def run_ours(args, rank, world, device):
+    import torch
+    import paper_2505_22718_gb300 as swcl
+
+    torch.cuda.set_device(device)
+    dev = torch.device("cuda", device)
+    prec = swcl.PRECISIONS[args.precision]
+    w, cbar = make_inputs(args.walkers, rank)
+    nw = n_walk(w)
+    stream = torch.cuda.current_stream(dev)
+    ctx = swcl.Context(device, 0, stream.cuda_stream)
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    ctx.set_grids(w.chi_min, w.chi_max, w.N, w.k, w.ells, w.knots)
+    ctx.set_tracers(w.kind, w.fft_bias)
+    W_d, D_d = t(w.W), t(w.D)
+    P_d, A_d = t(w.P), t(w.amp)
+    ctx.set_windows(W_d, D_d, None if w.B is None else t(w.B))
+    ctx.set_power(P_d, A_d)
+    C_d = torch.empty((nw * len(w.ells), w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
+    Cb_d = t(cbar.reshape(C_d.shape))
+    Pb_d = torch.empty((nw, len(w.k)), dtype=torch.float64, device=dev)
+    Ab_d = torch.empty((nw, w.n_tr), dtype=torch.float64, device=dev)
+    Wb_d = torch.empty((nw, w.n_tr, w.N), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(p=prec):
+        swcl.swcl_compute_cl(ctx.ptr, p, C_d)
+        n1 = ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
+        swcl.swcl_vjp(ctx.ptr, p, Cb_d, Pb_d, Ab_d, Wb_d)
+        return n1 + ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
+
+    def fwd(p=prec):
+        swcl.swcl_compute_cl(ctx.ptr, p, C_d)
+        return ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
+
+    def timed(fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        if profile:
+            swcl.swcl_profile_reset(ctx.ptr)
+            swcl.swcl_profile_enable(ctx.ptr, True)
+        evs = []
+        launches = 0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches += fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        stats = None
+        if profile:
+            stats = swcl.swcl_profile_read(ctx.ptr)
+            swcl.swcl_profile_enable(ctx.ptr, False)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+            torch.distributed.barrier()
+        return ms, launches, stats
+
+    out = {}
+    clocks = ClockSampler(device) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms, launches, stats = timed(step, args.steps, args.warmup, profile=True)
+    clk = clocks.stop() if clocks else None
+    ms_step = ms / args.steps
+    value = nw * world / (ms_step / 1e3)
+    out["value"] = value
+    out["ms_per_step"] = ms_step
+    out["gpu_launches"] = launches
+    out["clocks"] = clk
+    out["kernel_ms"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in (stats or {}).items()}
+    peaks, src = load_peaks()
+    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src)
+    msf, _, _ = timed(fwd, args.steps, max(3, args.warmup // 2))
+    out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",
+                       "ms_per_step": msf / args.steps}
+    if not args.no_fp64_compare and args.precision != "fp64":
+        k64 = max(3, args.steps // 4)
+        ms64, _, _ = timed(lambda: step(swcl.SWCL_FP64), k64, 2)
+        out["fp64_gpu_path"] = {"value": nw * world / (ms64 / k64 / 1e3), "unit": "evals/s",
+                                "ms_per_step": ms64 / k64}
+    # result of this precision (rank 0, walker 0) for the accuracy check against the oracle
+    step()
+    torch.cuda.synchronize(dev)
+    out["_C0"] = C_d[:len(w.ells)].cpu().numpy()
+
+    # end to end through the public API with pinned host buffers
+    if not args.no_e2e:
+        def pinned(a):
+            h = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            h.numpy()[...] = a
+            return h
+        W_h, D_h, P_h, A_h = pinned(w.W), pinned(w.D), pinned(w.P), pinned(w.amp)
+        B_h = None if w.B is None else pinned(w.B)
+        Cb_h = pinned(cbar.reshape(C_d.shape))
+        C_h = torch.empty(C_d.shape, dtype=torch.float64, pin_memory=True)
+        Pb_h = torch.empty(Pb_d.shape, dtype=torch.float64, pin_memory=True)
+        Ab_h = torch.empty(Ab_d.shape, dtype=torch.float64, pin_memory=True)
+        Wb_h = torch.empty(Wb_d.shape, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            swcl.swcl_set_windows(ctx.ptr, nw, W_h, D_h, B_h)
+            swcl.swcl_set_power(ctx.ptr, nw, P_h, A_h)
+            swcl.swcl_compute_cl(ctx.ptr, prec, C_h)
+            swcl.swcl_vjp(ctx.ptr, prec, Cb_h, Pb_h, Ab_h, Wb_h)
+
+        for _ in range(max(2, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([el], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            el = float(tt.item())
+        h2d = sum(x.numel() * 8 for x in (W_h, D_h, P_h, A_h, Cb_h) if x is not None)
+        h2d += 0 if B_h is None else B_h.numel() * 8
+        d2h = sum(x.numel() * 8 for x in (C_h, Pb_h, Ab_h, Wb_h))
+        out["e2e"] = {"value": nw * world * args.steps / el, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+    ctx.close()
+    return out, w, cbar
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w, cbar = make_inputs(1, 0)
+        from oracle import fftlog as O
+        g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
+        for b in np.unique(w.fft_bias):
+            g.mtable(b)
+        for _ in range(args.warmup):
+            oracle_eval(w, cbar, g)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle_eval(w, cbar, g)
+        dt = time.perf_counter() - t0
+        v = args.steps / dt
+        line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": WORKLOAD, "walkers_per_gpu": 1, "precision": "fp64 oracle"},
+                "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": "one full forward+VJP evaluation per step (tables precomputed)"},
+                "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    out, w, cbar = run_ours(args, rank, world, local)
+    if rank == 0:
+        cpu = None
+        acc = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu, f = cpu_baseline(w if n_walk(w) == 1 else w, cbar[:1] if cbar.ndim == 4 else cbar)
+            if n_walk(w) == 1:
+                Co = f["C"]
+                C0 = out["_C0"]
+                dg = np.abs(np.einsum("lii->li", Co))
+                floor = 1e-3 * np.sqrt(dg[:, :, None] * dg[:, None, :])
+                acc = {"max_norm_err_vs_oracle": float(np.max(np.abs(C0 - Co) / np.maximum(np.abs(Co), floor))),
+                       "gate": 1e-10 if args.precision == "fp64" else 1e-4}
+        dtype = {"fp64": "f64", "3xtf32": "tf32x3 (f32 accumulate) + f64 FFT/k-sum",
+                 "bf16x6": "bf16x6 (f32 accumulate) + f64 FFT/k-sum"}[args.precision]
+        line = {"metric": METRIC, "value": out["value"], "unit": "evals/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "walkers_per_gpu": n_walk(w), "precision": args.precision,
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": "walkers sharded across ranks" if world > 1 else "1 GPU"},
+                "roofline": out["roofline"], "cpu_baseline": cpu, "e2e": out.get("e2e"),
+                "clocks": out["clocks"], "gpu_launches": out["gpu_launches"],
+                "fwd_only": out["fwd_only"], "fp64_gpu_path": out.get("fp64_gpu_path"),
+                "accuracy": acc, "kernel_ms": out["kernel_ms"]}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * swiftcl.h -- C ABI of the GB300 (sm_103a) beyond-Limber FFTLog C_ell library.
+ *
+ * The library computes the angular power spectra of arXiv:2505.22718 (SwiftCl):
+ *
+ *   a1  FFTLog of every window at every k-knot (Sec. 3.1-3.2, Eq. 3.2-3.3):
+ *         c_{i,a,n} = T_c(n) chi_min^{-i eta_n} (1/N) sum_{m<N} g_m e^{-2 pi i n m/N},
+ *         g_m = W_i(chi_m) chi_m^{s_i - b_i} T_chi(m) D(kappa_a, chi_m) B_i(kappa_a, chi_m),
+ *         n = 0..N/2, chi_m = chi_min exp(m L/N), L = ln(chi_max/chi_min), eta_n = 2 pi n/L.
+ *   a2  the Gamma-ratio table of Eq. 3.4 (denominator Gamma((l+2-p)/2)):
+ *         M_{l,n} = sqrt(pi) 2^{p-1} Gamma((l+1+p)/2) / Gamma((l+2-p)/2),  p = b_i + i eta_n.
+ *   a3  the contraction with k-interpolation (Eq. 3.3-3.5, Sec. 3.2):
+ *         Delta_i(l, k_q) = pi_i(l) k_q^{t_i-1-b_i} Re sum_{n=0}^{N/2} w_n c_{i,n}(k_q) M_{l,n} e^{-i eta_n ln k_q},
+ *         c_{i,n}(k_q) = sum_a lambda_a(k_q) c_{i,a,n} (4-point Lagrange in ln k), w_0 = w_{N/2} = 1, else 2.
+ *   a4  the k-quadrature of Eq. 2.1:
+ *         C_l^{ij} = A_i A_j sum_q u_q Delta_i(l,k_q) Delta_j(l,k_q),  u_q = (2/pi) w_q k_q^2 P(k_q),
+ *         w_q = k_q (ln k_{q+1} - ln k_{q-1})/2 (trapezoid in ln k, half intervals at the ends).
+ *   a5  the vector-Jacobian product of a1-a4 with respect to P(k), the amplitudes A_i and the
+ *       window samples W_i(chi_m).
+ *
+ * Tracer kinds: SWCL_DENSITY (s = 0, t = 0, pi = 1; Eq. 2.6) and SWCL_LENSING
+ * (s = -2, t = -2, pi = sqrt((l+2)!/(l-2)!); Eq. 2.14).
+ *
+ * Conventions
+ *  - Every call returns an int status: SWCL_OK (0) or a negative SWCL_ERR_* code.  No call
+ *    aborts, exits or throws across the ABI.  swcl_last_error() returns a message for the
+ *    last failing call on a context.
+ *  - Pointers are caller-owned.  Input arrays may live in host memory or in device memory
+ *    of the context's GPU (unified addressing decides which); set_* calls copy them into
+ *    library-owned device buffers, so the caller may free or reuse its arrays once the call
+ *    returns.  Outputs are written into caller buffers (host or device).
+ *  - All arrays are dense, row-major, FP64 (double) unless stated.
+ *  - Work is queued on the context's stream.  Calls that take host output pointers
+ *    synchronise that stream before returning; calls with device outputs do not
+ *    (swcl_sync waits and reports deferred device errors).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SWIFTCL_H
+#define SWIFTCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swcl_ctx swcl_ctx;
+
+/* status codes */
+#define SWCL_OK               0
+#define SWCL_ERR_INVALID_ARG (-1)  /* a size, pointer or value outside its documented range */
+#define SWCL_ERR_UNSUPPORTED (-2)  /* valid request this build does not implement */
+#define SWCL_ERR_OOM_BUDGET  (-3)  /* the request does not fit the context's memory budget */
+#define SWCL_ERR_CUDA        (-4)  /* a CUDA runtime call failed (message has the CUDA error) */
+#define SWCL_ERR_TIMEOUT     (-5)  /* a bounded device wait gave up */
+#define SWCL_ERR_NONFINITE   (-6)  /* an input or output contains NaN or Inf */
+#define SWCL_ERR_STATE       (-7)  /* call out of order (e.g. compute before set_grids) */
+
+/* tracer kinds */
+#define SWCL_DENSITY 0
+#define SWCL_LENSING 1
+
+/* arithmetic of the contraction (a3) and of the k-quadrature (a4) */
+#define SWCL_FP64        0  /* FP64 CUDA cores throughout */
+#define SWCL_3XTF32      1  /* tcgen05 kind::tf32, hi/lo split, 3 products, FP32 accumulate */
+#define SWCL_SPLIT_BF16  2  /* tcgen05 kind::f16 (bf16), 3-term split, 6 products, FP32 accumulate */
+
+/* swcl_query keys */
+#define SWCL_Q_WORKSPACE_BYTES 1  /* device bytes the context holds now */
+#define SWCL_Q_RECOMPUTE       2  /* 1 if the VJP recomputes Delta instead of storing it */
+#define SWCL_Q_N_HALF          3  /* N/2 + 1 */
+#define SWCL_Q_KERNEL_LAUNCHES 4  /* kernels launched by the last compute/vjp call */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the device memory the
+ * context may hold (0 = no bound).  `stream` is a cudaStream_t (NULL = the context creates
+ * its own non-blocking stream).  On success *out receives the context. */
+int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* stream);
+
+/* Release every device buffer of the context and the context itself (NULL is accepted). */
+int swcl_destroy(swcl_ctx* ctx);
+
+/* Grids (Sec. 3.1-3.2, Appendix A).  chi grid: N points chi_min exp(m L/N), chi_max excluded;
+ * N a power of two, 16 <= N <= 8192.  k[N_k]: strictly increasing, > 0, N_k >= 2.
+ * ells[N_ell]: integers >= 0 (>= 2 for lensing tracers).  knots[N_I]: strictly increasing, > 0,
+ * N_I >= 1 (one knot = scale-independent growth).  Drops tracers and windows set before. */
+int swcl_set_grids(swcl_ctx* ctx, double chi_min, double chi_max, int N,
+                   const double* k, int N_k, const int* ells, int N_ell,
+                   const double* knots, int N_I);
+
+/* Tracers.  kind[N_tr] (SWCL_DENSITY / SWCL_LENSING), fft_bias[N_tr] = b_i with
+ * -ell_min - 1 < b_i < 1 (Eq. 3.4 range), taper_chi[N_tr][N] and taper_c[N_tr][N/2+1] optional
+ * smoothing of the tails (Sec. 3.1; NULL = none).  Builds the Gamma-ratio (a2) and phase tables. */
+int swcl_set_tracers(swcl_ctx* ctx, int N_tr, const int* kind, const double* fft_bias,
+                     const double* taper_chi, const double* taper_c);
+
+/* Windows for n_walk parameter points (n_walk >= 1).  W[n_walk][N_tr][N] window samples on the
+ * chi grid; D[N_I][N] growth at the knots (NULL = 1); B[N_tr][N_I][N] k,z-dependent bias at the
+ * knots (NULL = 1).  Window samples may differ per walker; D and B are shared. */
+int swcl_set_windows(swcl_ctx* ctx, int n_walk, const double* W, const double* D, const double* B);
+
+/* Power spectrum and amplitudes: P[n_walk][N_k] = P(k_q, z_fid) (Eq. 2.3), amp[n_walk][N_tr] = A_i
+ * (linear bias for density, amplitude for lensing). */
+int swcl_set_power(swcl_ctx* ctx, int n_walk, const double* P, const double* amp);
+
+/* Optional ragged multipole lists: walker w uses master-list entries
+ * ell_idx[offsets[w] .. offsets[w+1]), strictly increasing.  offsets == NULL restores "all ells for
+ * every walker".  Outputs of compute/vjp are then packed walker after walker. */
+int swcl_set_ell_lists(swcl_ctx* ctx, const int* offsets, const int* ell_idx);
+
+/* Forward pass a1-a4 for every walker.  C_out[sum_w n_ell(w)][N_tr][N_tr] (full symmetric
+ * matrices, C^{ij} = C^{ji} bit for bit). */
+int swcl_compute_cl(swcl_ctx* ctx, int precision, double* C_out);
+
+/* Vector-Jacobian product (a5) of the last swcl_compute_cl for the same precision.
+ * C_bar has the layout of C_out.  Outputs (each may be NULL to skip):
+ * P_bar[n_walk][N_k], amp_bar[n_walk][N_tr], W_bar[n_walk][N_tr][N]. */
+int swcl_vjp(swcl_ctx* ctx, int precision, const double* C_bar,
+             double* P_bar, double* amp_bar, double* W_bar);
+
+/* Per-kernel device timing.  While enabled, every kernel the context launches is bracketed by
+ * CUDA events on the context stream (a few microseconds of overhead per launch).
+ * swcl_profile_read synchronises the stream and returns, for up to max_entries kernels,
+ * a NUL-terminated name (32 bytes per entry in names[max_entries][32]), the launch count and the
+ * total device milliseconds accumulated since the last reset; *n_entries receives the count.
+ * swcl_profile_reset clears the accumulators. */
+int swcl_profile_enable(swcl_ctx* ctx, int enable);
+int swcl_profile_read(swcl_ctx* ctx, int max_entries, char* names, int64_t* launches, double* ms,
+                      int* n_entries);
+int swcl_profile_reset(swcl_ctx* ctx);
+
+/* Stage read-back for element-wise testing of each step.  Copies an internal array of the last
+ * compute into out (host or device), as FP64 values (complex arrays as interleaved re, im):
+ *   SWCL_DBG_COEF   a1 c[n_walk][N_tr][N_I][N/2+1] complex
+ *   SWCL_DBG_DELTA  a3 Delta[n_walk][N_ell][N_tr][N_k] (mixed paths: FP32 values widened)
+ *   SWCL_DBG_GTAB   a2 w_n pi(l) M_{l,n} per tracer class [n_cls][N_ell][N/2+1] complex
+ *   SWCL_DBG_PHASE  e^{-i eta_n ln k_q} [N_k][N/2+1] complex
+ *   SWCL_DBG_UNIT   a4 unit-amplitude C [n_walk][N_ell][N_tr][N_tr]
+ * *count receives the number of doubles written (out may be NULL to query it). */
+#define SWCL_DBG_COEF  1
+#define SWCL_DBG_DELTA 2
+#define SWCL_DBG_GTAB  3
+#define SWCL_DBG_PHASE 4
+#define SWCL_DBG_UNIT  5
+int swcl_debug_read(swcl_ctx* ctx, int what, double* out, int64_t* count);
+
+/* Wait for queued work; returns any deferred device error. */
+int swcl_sync(swcl_ctx* ctx);
+
+/* Query a SWCL_Q_* value into *value. */
+int swcl_query(swcl_ctx* ctx, int key, int64_t* value);
+
+/* Message of the last failing call on ctx ("" if none; static storage of the context). */
+const char* swcl_last_error(swcl_ctx* ctx);
+
+/* Static description of a status code. */
+const char* swcl_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWIFTCL_H */

@@ -25,6 +25,9 @@ R5  The k-interpolation of Sec. 3.2 is local 4-point Lagrange in ln k on the
 R6  The k-integral of Eq. (2.1) "over all N_k points" (Sec. 3.2) is the
     trapezoid rule in ln k: int dk g = int dlnk k g, w_q = k_q h_q with
     h_q = (ln k_{q+1} - ln k_{q-1})/2 and half intervals at the ends.
+R8  The Gamma-ratio table is evaluated from log-Gammas at the smallest ell of each parity and
+    carried to larger ell by the exact two-step recurrence of Gamma(z+1) = z Gamma(z)
+    (see bessel_power_integral).
 R7  Source functions: density Delta = int W D j_ell (Eq. 2.6, the linear bias
     b_1 is the tracer amplitude); lensing Delta = sqrt((l+2)!/(l-2)!) k^-2
     int W chi^-2 D j_ell (Eq. 2.14).  A per-tracer amplitude A_i multiplies
@@ -117,11 +120,37 @@ def bessel_power_integral(ells, p):
 
     Eq. (3.4) at k = 1 with reading R1; valid for -ell-1 < Re p < 1.
     Returns the table [len(ells), len(p)].
+
+    Evaluation (reading R8): the Gamma ratio is formed from log-Gammas only at the smallest
+    requested ell of each parity; larger ell follow from the exact identity Gamma(z+1) = z Gamma(z),
+        I_{ell+2}(p) = I_ell(p) (ell + 1 + p) / (ell + 2 - p),
+    applied one step at a time.  A direct difference of log-Gammas of size ~ (ell/2) ln(ell/2)
+    would lose ~1e-12 of relative accuracy at ell ~ 2000 to cancellation; the recurrence keeps
+    the table within ~1e-14 (checked against 50-digit values in the tests).
     """
-    l = np.asarray(ells, dtype=np.float64)[:, None]
-    p = np.asarray(p, dtype=np.complex128)[None, :]
-    lg = loggamma(0.5 * (l + 1.0 + p)) - loggamma(0.5 * (l + 2.0 - p))
-    return np.sqrt(np.pi) * np.exp((p - 1.0) * np.log(2.0) + lg)
+    ells = np.asarray(ells, dtype=np.int64)
+    p = np.asarray(p, dtype=np.complex128)
+    out = np.empty((len(ells), len(p)), dtype=np.complex128)
+    for parity in (0, 1):
+        sel = np.nonzero(ells % 2 == parity)[0]
+        if len(sel) == 0:
+            continue
+        l0 = int(ells[sel].min())
+        cur = np.sqrt(np.pi) * np.exp((p - 1.0) * np.log(2.0)
+                                      + loggamma(0.5 * (l0 + 1.0 + p)) - loggamma(0.5 * (l0 + 2.0 - p)))
+        want = {int(ells[j]): [] for j in sel}
+        for j in sel:
+            want[int(ells[j])].append(j)
+        l = l0
+        lmax = int(ells[sel].max())
+        while True:
+            for j in want.get(l, ()):
+                out[j] = cur
+            if l >= lmax:
+                break
+            cur = cur * (l + 1.0 + p) / (l + 2.0 - p)
+            l += 2
+    return out
 
 
 # ------------------------------------------------------ k-interpolation ----

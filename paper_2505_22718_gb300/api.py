@@ -1,0 +1,239 @@
+"""Thin Python binding of the swiftcl C ABI (include/swiftcl.h).
+
+Argument marshalling only: every function forwards to the C symbol of the same name.  Arrays
+may be numpy arrays (host memory) or torch tensors (host or CUDA memory of the context's
+device); they must be C-contiguous and of the documented dtype (float64 / int32).  A failing
+call raises SwiftClError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+SWCL_OK = 0
+SWCL_DENSITY, SWCL_LENSING = 0, 1
+SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16 = 0, 1, 2
+SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES = 1, 2, 3, 4
+PRECISIONS = {"fp64": SWCL_FP64, "3xtf32": SWCL_3XTF32, "bf16x6": SWCL_SPLIT_BF16}
+
+
+class SwiftClError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("swiftcl status %d (%s): %s" % (status, strerror(status), msg))
+        self.status = status
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive) for a numpy array / torch tensor / None."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError("tensor must be contiguous %s" % want)
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def strerror(status: int) -> str:
+    return _lib.load().swcl_strerror(status).decode()
+
+
+def _check(ctx, status):
+    if status != SWCL_OK:
+        msg = _lib.load().swcl_last_error(ctx).decode() if ctx else ""
+        raise SwiftClError(status, msg)
+
+
+def swcl_create(device: int = 0, mem_budget_bytes: int = 0, stream=None):
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    st = lib.swcl_create(ctypes.byref(out), device, mem_budget_bytes,
+                         ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return out
+
+
+def swcl_destroy(ctx):
+    _check(None, _lib.load().swcl_destroy(ctx))
+
+
+def swcl_set_grids(ctx, chi_min, chi_max, N, k, ells, knots):
+    pk, a = _ptr(k, np.float64)
+    pe, b = _ptr(ells, np.int32)
+    pn, c = _ptr(knots, np.float64)
+    _check(ctx, _lib.load().swcl_set_grids(ctx, chi_min, chi_max, N, pk, len(a), pe, len(b), pn, len(c)))
+
+
+def swcl_set_tracers(ctx, kind, fft_bias, taper_chi=None, taper_c=None):
+    pk, a = _ptr(kind, np.int32)
+    pb, _b = _ptr(fft_bias, np.float64)
+    pt, _t = _ptr(taper_chi, np.float64)
+    pc, _c = _ptr(taper_c, np.float64)
+    _check(ctx, _lib.load().swcl_set_tracers(ctx, len(a), pk, pb, pt, pc))
+
+
+def swcl_set_windows(ctx, n_walk, W, D=None, B=None):
+    pw, _w = _ptr(W, np.float64)
+    pd, _d = _ptr(D, np.float64)
+    pb, _b = _ptr(B, np.float64)
+    _check(ctx, _lib.load().swcl_set_windows(ctx, n_walk, pw, pd, pb))
+
+
+def swcl_set_power(ctx, n_walk, P, amp):
+    pp, _p = _ptr(P, np.float64)
+    pa, _a = _ptr(amp, np.float64)
+    _check(ctx, _lib.load().swcl_set_power(ctx, n_walk, pp, pa))
+
+
+def swcl_set_ell_lists(ctx, offsets=None, ell_idx=None):
+    po, _o = _ptr(offsets, np.int32)
+    pi, _i = _ptr(ell_idx, np.int32)
+    _check(ctx, _lib.load().swcl_set_ell_lists(ctx, po, pi))
+
+
+def swcl_compute_cl(ctx, precision, C_out):
+    pc, keep = _ptr(C_out, np.float64)
+    if keep is not C_out:
+        raise TypeError("C_out must be a contiguous float64 array or tensor (written in place)")
+    _check(ctx, _lib.load().swcl_compute_cl(ctx, precision, pc))
+
+
+def swcl_vjp(ctx, precision, C_bar, P_bar=None, amp_bar=None, W_bar=None):
+    outs = []
+    for o in (P_bar, amp_bar, W_bar):
+        p, keep = _ptr(o, np.float64)
+        if o is not None and keep is not o:
+            raise TypeError("VJP outputs must be contiguous float64 arrays or tensors")
+        outs.append(p)
+    pc, _c = _ptr(C_bar, np.float64)
+    _check(ctx, _lib.load().swcl_vjp(ctx, precision, pc, *outs))
+
+
+def swcl_profile_enable(ctx, enable=True):
+    _check(ctx, _lib.load().swcl_profile_enable(ctx, 1 if enable else 0))
+
+
+def swcl_profile_reset(ctx):
+    _check(ctx, _lib.load().swcl_profile_reset(ctx))
+
+
+def swcl_profile_read(ctx, max_entries=64):
+    """{kernel name: (launches, total device ms)} accumulated since the last reset."""
+    names = ctypes.create_string_buffer(32 * max_entries)
+    launches = (ctypes.c_int64 * max_entries)()
+    ms = (ctypes.c_double * max_entries)()
+    n = ctypes.c_int()
+    _check(ctx, _lib.load().swcl_profile_read(ctx, max_entries, names, launches, ms, ctypes.byref(n)))
+    out = {}
+    for i in range(min(n.value, max_entries)):
+        nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+SWCL_DBG_COEF, SWCL_DBG_DELTA, SWCL_DBG_GTAB, SWCL_DBG_PHASE, SWCL_DBG_UNIT = 1, 2, 3, 4, 5
+
+
+def swcl_debug_read(ctx, what):
+    """Internal array of the last compute as a flat float64 numpy array (complex interleaved)."""
+    lib = _lib.load()
+    n = ctypes.c_int64()
+    _check(ctx, lib.swcl_debug_read(ctx, what, None, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.float64)
+    _check(ctx, lib.swcl_debug_read(ctx, what, ctypes.c_void_p(out.ctypes.data), ctypes.byref(n)))
+    return out
+
+
+def swcl_sync(ctx):
+    _check(ctx, _lib.load().swcl_sync(ctx))
+
+
+def swcl_query(ctx, key):
+    v = ctypes.c_int64()
+    _check(ctx, _lib.load().swcl_query(ctx, key, ctypes.byref(v)))
+    return v.value
+
+
+def swcl_last_error(ctx) -> str:
+    return _lib.load().swcl_last_error(ctx).decode()
+
+
+class Context:
+    """Owning wrapper: one swcl_ctx on one device."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None):
+        self.ptr = swcl_create(device, mem_budget_bytes, stream)
+        self.n_tr = self.n_ell = self.n_k = self.N = 0
+        self.n_walk = 1
+        self.n_out = 0
+
+    def close(self):
+        if self.ptr:
+            swcl_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_grids(self, chi_min, chi_max, N, k, ells, knots):
+        swcl_set_grids(self.ptr, chi_min, chi_max, N, k, ells, knots)
+        self.N, self.n_k, self.n_ell = N, len(k), len(ells)
+        self.n_out = self.n_walk * self.n_ell
+
+    def set_tracers(self, kind, fft_bias, taper_chi=None, taper_c=None):
+        swcl_set_tracers(self.ptr, kind, fft_bias, taper_chi, taper_c)
+        self.n_tr = len(kind)
+
+    def set_windows(self, W, D=None, B=None):
+        n_walk = 1 if W.ndim == 2 else W.shape[0]
+        swcl_set_windows(self.ptr, n_walk, W, D, B)
+        self.n_walk = n_walk
+        self.n_out = n_walk * self.n_ell
+
+    def set_power(self, P, amp):
+        n_walk = 1 if P.ndim == 1 else P.shape[0]
+        swcl_set_power(self.ptr, n_walk, P, amp)
+        self.n_walk = n_walk
+        self.n_out = n_walk * self.n_ell
+
+    def set_ell_lists(self, lists=None):
+        if lists is None:
+            swcl_set_ell_lists(self.ptr, None, None)
+            self.n_out = self.n_walk * self.n_ell
+            return
+        off = np.zeros(len(lists) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(x) for x in lists])
+        idx = np.concatenate([np.asarray(x, dtype=np.int32) for x in lists]) if lists else np.zeros(0, np.int32)
+        swcl_set_ell_lists(self.ptr, off, idx)
+        self.n_out = int(off[-1])
+
+    def compute_cl(self, precision=SWCL_FP64, out=None):
+        if out is None:
+            out = np.empty((self.n_out, self.n_tr, self.n_tr))
+        swcl_compute_cl(self.ptr, precision, out)
+        return out
+
+    def vjp(self, C_bar, precision=SWCL_FP64, want_W=True):
+        P_bar = np.empty((self.n_walk, self.n_k))
+        amp_bar = np.empty((self.n_walk, self.n_tr))
+        W_bar = np.empty((self.n_walk, self.n_tr, self.N)) if want_W else None
+        swcl_vjp(self.ptr, precision, C_bar, P_bar, amp_bar, W_bar)
+        return P_bar, amp_bar, W_bar
+
+    def query(self, key):
+        return swcl_query(self.ptr, key)
+
+    def sync(self):
+        swcl_sync(self.ptr)

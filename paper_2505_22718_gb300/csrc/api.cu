@@ -1,0 +1,711 @@
+// C ABI of the library (include/swiftcl.h): argument checking, device buffers, and the
+// sequence of kernels for the forward pass (a1-a4) and the VJP (a5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <utility>
+
+#include "swcl_internal.h"
+
+using swcl::cplx;
+using swcl::DevBuf;
+
+namespace swcl {
+
+int fail(swcl_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(swcl_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SWCL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ensure(swcl_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.p && b.bytes >= bytes) return SWCL_OK;
+  size_t freed = b.p ? b.bytes : 0;
+  if (c->budget && c->held - freed + bytes > c->budget)
+    return fail(c, SWCL_ERR_OOM_BUDGET,
+                "memory budget exceeded: need " + std::to_string(c->held - freed + bytes) +
+                    " bytes, budget " + std::to_string(c->budget));
+  if (b.p) {
+    cudaFree(b.p);
+    c->held -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return cuda_fail(c, e, "cudaMalloc");
+  }
+  b.bytes = bytes;
+  c->held += bytes;
+  return SWCL_OK;
+}
+
+void release(swcl_ctx* c, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    c->held -= b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes) {
+  int st = ensure(c, dst, bytes);
+  if (st) return st;
+  cudaError_t e = cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync (input)");
+  if (!is_device_ptr(src)) {
+    e = cudaStreamSynchronize(c->stream);  // the caller may free a host array on return
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  }
+  return SWCL_OK;
+}
+
+int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (dst == src || bytes == 0) return SWCL_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync (output)");
+  if (!is_device_ptr(dst)) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  }
+  return SWCL_OK;
+}
+
+static cudaEvent_t take_event(swcl_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_begin(swcl_ctx* c) {
+  if (!c->prof) return;
+  c->ev_open = take_event(c);
+  if (c->ev_open) cudaEventRecord(c->ev_open, c->stream);
+}
+
+void prof_end(swcl_ctx* c, const char* name) {
+  if (!c->prof || !c->ev_open) return;
+  cudaEvent_t b = take_event(c);
+  if (!b) return;
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back({name, c->ev_open, b});
+  c->ev_open = nullptr;
+}
+
+static int prof_flush(swcl_ctx* c) {
+  if (c->pending.empty()) return SWCL_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    swcl_ctx::Stat* st = nullptr;
+    for (auto& s : c->stats)
+      if (s.name == p.name) st = &s;
+    if (!st) {
+      c->stats.push_back(swcl_ctx::Stat{p.name, 0, 0.0});
+      st = &c->stats.back();
+    }
+    st->launches += 1;
+    st->ms += ms;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  return SWCL_OK;
+}
+
+}  // namespace swcl
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define SWCL_TRY_CUDA(ctx, expr, what)                    \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return swcl::cuda_fail(ctx, _e, what); \
+  } while (0)
+
+#define SWCL_TRY(expr)            \
+  do {                            \
+    int _s = (expr);              \
+    if (_s != SWCL_OK) return _s; \
+  } while (0)
+
+#define SWCL_LAUNCH(ctx, expr, what)  \
+  do {                                \
+    ++(ctx)->last_launches;           \
+    swcl::prof_begin(ctx);            \
+    cudaError_t _le = (expr);         \
+    swcl::prof_end(ctx, what);        \
+    if (_le != cudaSuccess) return swcl::cuda_fail(ctx, _le, what); \
+  } while (0)
+
+int64_t out_count(const swcl_ctx* c) {
+  return c->ragged ? c->n_out_ell : (int64_t)c->n_walk * c->N_ell;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* swcl_strerror(int s) {
+  switch (s) {
+    case SWCL_OK: return "ok";
+    case SWCL_ERR_INVALID_ARG: return "invalid argument";
+    case SWCL_ERR_UNSUPPORTED: return "unsupported";
+    case SWCL_ERR_OOM_BUDGET: return "memory budget exceeded";
+    case SWCL_ERR_CUDA: return "CUDA error";
+    case SWCL_ERR_TIMEOUT: return "device wait timed out";
+    case SWCL_ERR_NONFINITE: return "non-finite value";
+    case SWCL_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* swcl_last_error(swcl_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* stream) {
+  if (!out) return SWCL_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return SWCL_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  swcl_ctx* c = new swcl_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SWCL_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return SWCL_OK;
+}
+
+int swcl_destroy(swcl_ctx* c) {
+  if (!c) return SWCL_OK;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->d_k, &c->d_ells, &c->d_knots, &c->d_wk2, &c->d_interp_j0,
+                    &c->d_interp_w, &c->d_twiddle, &c->d_phase, &c->d_knot_qrange,
+                    &c->d_cls_of, &c->d_chipow, &c->d_psi, &c->d_gtab, &c->d_kpow, &c->d_W,
+                    &c->d_D, &c->d_B, &c->d_P, &c->d_amp, &c->d_off, &c->d_idx, &c->ws_coef,
+                    &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar, &c->ws_Cbar,
+                    &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status};
+  for (DevBuf* b : bufs) swcl::release(c, *b);
+  for (auto& t : c->tc) {
+    swcl::release(c, t.bfwd);
+    swcl::release(c, t.bvjp);
+    swcl::release(c, t.phase32);
+  }
+  for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return SWCL_OK;
+}
+
+int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const double* k, int N_k,
+                   const int* ells, int N_ell, const double* knots, int N_I) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!(chi_min > 0) || !(chi_max > chi_min) || !std::isfinite(chi_max))
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 0 < chi_min < chi_max");
+  if (N < 16 || N > 8192 || (N & (N - 1)))
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "N must be a power of two in [16, 8192]");
+  if (!k || N_k < 2 || !ells || N_ell < 1 || !knots || N_I < 1)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need k (N_k >= 2), ells (N_ell >= 1), knots (N_I >= 1)");
+  std::vector<double> kh(N_k), knh(N_I);
+  std::vector<int> eh(N_ell);
+  SWCL_TRY_CUDA(c, cudaMemcpy(kh.data(), k, sizeof(double) * N_k, cudaMemcpyDefault), "copy k");
+  SWCL_TRY_CUDA(c, cudaMemcpy(knh.data(), knots, sizeof(double) * N_I, cudaMemcpyDefault), "copy knots");
+  SWCL_TRY_CUDA(c, cudaMemcpy(eh.data(), ells, sizeof(int) * N_ell, cudaMemcpyDefault), "copy ells");
+  for (int q = 0; q < N_k; ++q)
+    if (!(kh[q] > 0) || !std::isfinite(kh[q]) || (q && !(kh[q] > kh[q - 1])))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "k must be finite, positive, strictly increasing");
+  for (int a = 0; a < N_I; ++a)
+    if (!(knh[a] > 0) || !std::isfinite(knh[a]) || (a && !(knh[a] > knh[a - 1])))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "knots must be finite, positive, strictly increasing");
+  for (int l = 0; l < N_ell; ++l)
+    if (eh[l] < 0 || eh[l] > 100000) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell out of range");
+  c->have_grids = c->have_tracers = c->have_windows = c->have_power = false;
+  c->ragged = false;
+  for (auto& t : c->tc) t.ready = false;
+  c->N = N;
+  c->n_h = N / 2 + 1;
+  c->N_k = N_k;
+  c->N_ell = N_ell;
+  c->N_I = N_I;
+  c->chi_min = chi_min;
+  c->chi_max = chi_max;
+  c->L = std::log(chi_max / chi_min);
+  c->k_h = kh;
+  c->knots_h = knh;
+  c->ells_h = eh;
+  c->last_fwd_precision = -1;
+  SWCL_TRY(swcl::copy_in(c, c->d_k, kh.data(), sizeof(double) * N_k));
+  SWCL_TRY(swcl::copy_in(c, c->d_knots, knh.data(), sizeof(double) * N_I));
+  SWCL_TRY(swcl::copy_in(c, c->d_ells, eh.data(), sizeof(int) * N_ell));
+  SWCL_TRY(swcl::ensure(c, c->d_wk2, sizeof(double) * N_k));
+  SWCL_TRY(swcl::ensure(c, c->d_interp_j0, sizeof(int) * N_k));
+  SWCL_TRY(swcl::ensure(c, c->d_interp_w, sizeof(double) * 4 * N_k));
+  SWCL_TRY(swcl::ensure(c, c->d_twiddle, sizeof(cplx) * N));
+  SWCL_TRY(swcl::ensure(c, c->d_phase, sizeof(cplx) * (size_t)N_k * c->n_h));
+  c->last_launches = 0;
+  SWCL_LAUNCH(c, swcl::launch_fft_twiddles((cplx*)c->d_twiddle.p, N, c->stream), "twiddles");
+  SWCL_LAUNCH(c, swcl::launch_phase_table((cplx*)c->d_phase.p, (const double*)c->d_k.p, N_k,
+                                          c->n_h, c->L, c->stream), "phase table");
+  SWCL_LAUNCH(c, swcl::launch_interp_weights((int*)c->d_interp_j0.p, (double*)c->d_interp_w.p,
+                                             (const double*)c->d_k.p, N_k,
+                                             (const double*)c->d_knots.p, N_I, c->stream),
+              "interp weights");
+  SWCL_LAUNCH(c, swcl::launch_quad_weights((double*)c->d_wk2.p, (const double*)c->d_k.p, N_k,
+                                           c->stream), "quad weights");
+  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "set_grids");
+  c->have_grids = true;
+  return SWCL_OK;
+}
+
+int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_bias,
+                     const double* taper_chi, const double* taper_c) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->have_grids) return swcl::fail(c, SWCL_ERR_STATE, "set_grids first");
+  if (N_tr < 1 || N_tr > 64 || !kind || !fft_bias)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 1 <= N_tr <= 64, kind and fft_bias");
+  std::vector<int> kh(N_tr);
+  std::vector<double> bh(N_tr);
+  SWCL_TRY_CUDA(c, cudaMemcpy(kh.data(), kind, sizeof(int) * N_tr, cudaMemcpyDefault), "copy kind");
+  SWCL_TRY_CUDA(c, cudaMemcpy(bh.data(), fft_bias, sizeof(double) * N_tr, cudaMemcpyDefault), "copy bias");
+  int lmin = c->ells_h[0];
+  for (int l : c->ells_h) lmin = l < lmin ? l : lmin;
+  for (int i = 0; i < N_tr; ++i) {
+    if (kh[i] != SWCL_DENSITY && kh[i] != SWCL_LENSING)
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "tracer kind must be SWCL_DENSITY or SWCL_LENSING");
+    if (kh[i] == SWCL_LENSING && lmin < 2)
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "lensing tracers need every ell >= 2");
+    if (!(bh[i] < 1.0) || !(bh[i] > -(double)lmin - 1.0))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "fft_bias must satisfy -ell_min - 1 < b < 1 (Eq. 3.4)");
+  }
+  // classes: distinct (kind, b)
+  std::vector<std::pair<int, double>> cls;
+  std::vector<int> cls_of(N_tr);
+  for (int i = 0; i < N_tr; ++i) {
+    int found = -1;
+    for (size_t j = 0; j < cls.size(); ++j)
+      if (cls[j].first == kh[i] && cls[j].second == bh[i]) found = (int)j;
+    if (found < 0) {
+      found = (int)cls.size();
+      cls.push_back({kh[i], bh[i]});
+    }
+    cls_of[i] = found;
+  }
+  c->have_tracers = false;
+  for (auto& t : c->tc) t.ready = false;
+  c->last_fwd_precision = -1;
+  c->N_tr = N_tr;
+  c->n_cls = (int)cls.size();
+  c->kind_h = kh;
+  c->bias_h = bh;
+  c->cls_of_h = cls_of;
+  const int N = c->N, n_h = c->n_h;
+  SWCL_TRY(swcl::copy_in(c, c->d_cls_of, cls_of.data(), sizeof(int) * N_tr));
+  SWCL_TRY(swcl::ensure(c, c->d_chipow, sizeof(double) * N_tr * N));
+  SWCL_TRY(swcl::ensure(c, c->d_psi, sizeof(cplx) * N_tr * n_h));
+  SWCL_TRY(swcl::ensure(c, c->d_kpow, sizeof(double) * N_tr * c->N_k));
+  SWCL_TRY(swcl::ensure(c, c->d_gtab, sizeof(cplx) * c->n_cls * (size_t)c->N_ell * n_h));
+  DevBuf tchi, tcn;
+  if (taper_chi) SWCL_TRY(swcl::copy_in(c, tchi, taper_chi, sizeof(double) * N_tr * N));
+  if (taper_c) SWCL_TRY(swcl::copy_in(c, tcn, taper_c, sizeof(double) * N_tr * n_h));
+  int st = SWCL_OK;
+  for (int i = 0; i < N_tr && st == SWCL_OK; ++i) {
+    cudaError_t e = swcl::launch_tracer_tables(
+        (double*)c->d_chipow.p + (size_t)i * N, (cplx*)c->d_psi.p + (size_t)i * n_h,
+        (double*)c->d_kpow.p + (size_t)i * c->N_k, (const double*)c->d_k.p, c->N_k, N,
+        c->chi_min, c->L, bh[i], kh[i], taper_chi ? (const double*)tchi.p + (size_t)i * N : nullptr,
+        taper_c ? (const double*)tcn.p + (size_t)i * n_h : nullptr, c->stream);
+    if (e != cudaSuccess) st = swcl::cuda_fail(c, e, "tracer tables");
+  }
+  for (int j = 0; j < c->n_cls && st == SWCL_OK; ++j) {
+    cudaError_t e = swcl::launch_gamma_table((cplx*)c->d_gtab.p + (size_t)j * c->N_ell * n_h,
+                                             (const int*)c->d_ells.p, c->N_ell, n_h, c->L,
+                                             cls[j].second, cls[j].first, c->stream);
+    if (e != cudaSuccess) st = swcl::cuda_fail(c, e, "gamma table");
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  swcl::release(c, tchi);
+  swcl::release(c, tcn);
+  if (st) return st;
+  if (e != cudaSuccess) return swcl::cuda_fail(c, e, "set_tracers");
+  c->have_tracers = true;
+  return SWCL_OK;
+}
+
+int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, const double* B) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->have_tracers) return swcl::fail(c, SWCL_ERR_STATE, "set_grids and set_tracers first");
+  if (n_walk < 1 || !W) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need n_walk >= 1 and W");
+  if (c->have_power && c->n_walk != n_walk)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_power");
+  const int N = c->N;
+  SWCL_TRY(swcl::copy_in(c, c->d_W, W, sizeof(double) * (size_t)n_walk * c->N_tr * N));
+  if (D) {
+    SWCL_TRY(swcl::copy_in(c, c->d_D, D, sizeof(double) * (size_t)c->N_I * N));
+  } else {
+    std::vector<double> ones((size_t)c->N_I * N, 1.0);
+    SWCL_TRY(swcl::copy_in(c, c->d_D, ones.data(), sizeof(double) * ones.size()));
+  }
+  c->have_B = B != nullptr;
+  if (B) SWCL_TRY(swcl::copy_in(c, c->d_B, B, sizeof(double) * (size_t)c->N_tr * c->N_I * N));
+  c->n_walk = n_walk;
+  c->have_windows = true;
+  c->last_fwd_precision = -1;
+  if (c->ragged && (int)c->off_h.size() != n_walk + 1) c->ragged = false;
+  return SWCL_OK;
+}
+
+int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->have_tracers) return swcl::fail(c, SWCL_ERR_STATE, "set_grids and set_tracers first");
+  if (n_walk < 1 || !P || !amp) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need n_walk >= 1, P, amp");
+  if (c->have_windows && c->n_walk != n_walk)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_windows");
+  SWCL_TRY(swcl::copy_in(c, c->d_P, P, sizeof(double) * (size_t)n_walk * c->N_k));
+  SWCL_TRY(swcl::copy_in(c, c->d_amp, amp, sizeof(double) * (size_t)n_walk * c->N_tr));
+  c->n_walk = n_walk;
+  c->have_power = true;
+  c->last_fwd_precision = -1;
+  return SWCL_OK;
+}
+
+int swcl_set_ell_lists(swcl_ctx* c, const int* offsets, const int* ell_idx) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->have_windows && !c->have_power)
+    return swcl::fail(c, SWCL_ERR_STATE, "set_windows or set_power first (they fix n_walk)");
+  if (!offsets) {
+    c->ragged = false;
+    return SWCL_OK;
+  }
+  if (!ell_idx) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell_idx is NULL");
+  std::vector<int> off(c->n_walk + 1);
+  SWCL_TRY_CUDA(c, cudaMemcpy(off.data(), offsets, sizeof(int) * off.size(), cudaMemcpyDefault), "copy offsets");
+  if (off[0] != 0) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (int w = 0; w < c->n_walk; ++w)
+    if (off[w + 1] < off[w]) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "offsets must be nondecreasing");
+  std::vector<int> idx(off.back());
+  if (!idx.empty())
+    SWCL_TRY_CUDA(c, cudaMemcpy(idx.data(), ell_idx, sizeof(int) * idx.size(), cudaMemcpyDefault), "copy ell_idx");
+  for (int w = 0; w < c->n_walk; ++w)
+    for (int o = off[w]; o < off[w + 1]; ++o) {
+      if (idx[o] < 0 || idx[o] >= c->N_ell)
+        return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell_idx entry outside the master list");
+      if (o > off[w] && idx[o] <= idx[o - 1])
+        return swcl::fail(c, SWCL_ERR_INVALID_ARG, "each walker's ell_idx must be strictly increasing");
+    }
+  c->off_h = off;
+  c->idx_h = idx;
+  SWCL_TRY(swcl::copy_in(c, c->d_off, off.data(), sizeof(int) * off.size()));
+  SWCL_TRY(swcl::copy_in(c, c->d_idx, idx.empty() ? off.data() : idx.data(),
+                         sizeof(int) * (idx.empty() ? 1 : idx.size())));
+  c->n_out_ell = off.back();
+  c->ragged = true;
+  return SWCL_OK;
+}
+
+static int check_ready(swcl_ctx* c, int precision) {
+  if (!c->have_grids || !c->have_tracers || !c->have_windows || !c->have_power)
+    return swcl::fail(c, SWCL_ERR_STATE, "set_grids, set_tracers, set_windows and set_power first");
+  if (precision != SWCL_FP64 && precision != SWCL_3XTF32 && precision != SWCL_SPLIT_BF16)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown precision");
+  return SWCL_OK;
+}
+
+int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(check_ready(c, precision));
+  if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
+  c->last_launches = 0;
+  const int nw = c->n_walk, N_tr = c->N_tr, N_I = c->N_I, n_h = c->n_h, N = c->N;
+  const int N_k = c->N_k, N_ell = c->N_ell;
+  const size_t nrow = (size_t)nw * N_tr;
+  SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
+  const size_t nd = nrow * N_ell * N_k;
+  SWCL_TRY(swcl::ensure(c, c->ws_delta, nd * (precision == SWCL_FP64 ? sizeof(double) : sizeof(float))));
+  SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
+  SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
+                                         (const double*)c->d_chipow.p, (const double*)c->d_D.p,
+                                         c->have_B ? (const double*)c->d_B.p : nullptr,
+                                         (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p, nw,
+                                         N_tr, N_I, N, c->stream), "fftlog");
+  if (precision == SWCL_FP64) {
+    SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
+                                              (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
+                                              (const int*)c->d_cls_of.p, (const double*)c->d_kpow.p,
+                                              (const int*)c->d_interp_j0.p,
+                                              (const double*)c->d_interp_w.p, nw, N_tr, N_I, n_h,
+                                              N_k, N_ell, c->stream), "contract fp64");
+    SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
+                                          (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
+                                          N_tr, N_k, N_ell, c->stream), "k-quadrature fp64");
+  } else {
+    SWCL_TRY(swcl::compute_delta_tc(c, precision));
+    SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
+                                         (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
+                                         N_tr, N_k, N_ell, c->stream), "k-quadrature f32");
+  }
+  const int64_t n_out = out_count(c);
+  const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
+  double* dst = C_out;
+  bool dev_out = swcl::is_device_ptr(C_out);
+  if (!dev_out) {
+    SWCL_TRY(swcl::ensure(c, c->ws_C, cbytes));
+    dst = (double*)c->ws_C.p;
+  }
+  SWCL_LAUNCH(c, swcl::launch_scale_pack(dst, (const double*)c->ws_U.p, (const double*)c->d_amp.p,
+                                         c->ragged ? (const int*)c->d_off.p : nullptr,
+                                         c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
+                                         N_ell, n_out, c->stream), "scale/pack");
+  c->last_fwd_precision = precision;
+  if (!dev_out) SWCL_TRY(swcl::copy_out(c, C_out, dst, cbytes));
+  return SWCL_OK;
+}
+
+int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, double* amp_bar,
+             double* W_bar) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(check_ready(c, precision));
+  if (!C_bar) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_bar is NULL");
+  if (c->last_fwd_precision != precision)
+    return swcl::fail(c, SWCL_ERR_STATE, "call swcl_compute_cl with the same precision first");
+  c->last_launches = 0;
+  const int nw = c->n_walk, N_tr = c->N_tr, N_I = c->N_I, n_h = c->n_h, N = c->N;
+  const int N_k = c->N_k, N_ell = c->N_ell;
+  const int64_t n_out = out_count(c);
+  const size_t nrow = (size_t)nw * N_tr;
+  const bool fp64 = precision == SWCL_FP64;
+  // cotangent on the device
+  const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
+  const double* cb = C_bar;
+  if (!swcl::is_device_ptr(C_bar)) {
+    SWCL_TRY(swcl::copy_in(c, c->ws_C, C_bar, cbytes));
+    cb = (const double*)c->ws_C.p;
+  }
+  SWCL_TRY(swcl::ensure(c, c->ws_Cbar, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
+  SWCL_TRY(swcl::ensure(c, c->ws_dbar, nrow * N_ell * N_k * (fp64 ? sizeof(double) : sizeof(float))));
+  SWCL_TRY(swcl::ensure(c, c->ws_cbar, sizeof(cplx) * nrow * N_I * n_h));
+  SWCL_TRY(swcl::ensure(c, c->ws_outP, sizeof(double) * nw * (size_t)N_k));
+  SWCL_TRY(swcl::ensure(c, c->ws_outA, sizeof(double) * nrow));
+  const size_t wbytes = sizeof(double) * nrow * N;
+  SWCL_TRY(swcl::ensure(c, c->ws_outW, wbytes + swcl::fftlog_adj_scratch_bytes(nw, N_tr, N_I, N)));
+  SWCL_LAUNCH(c, swcl::launch_unpack_sym((double*)c->ws_Cbar.p, cb,
+                                         c->ragged ? (const int*)c->d_off.p : nullptr,
+                                         c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
+                                         N_ell, n_out, c->stream), "unpack cotangent");
+  double* Pb = P_bar && swcl::is_device_ptr(P_bar) ? P_bar : (double*)c->ws_outP.p;
+  double* Ab = amp_bar && swcl::is_device_ptr(amp_bar) ? amp_bar : (double*)c->ws_outA.p;
+  if (fp64) {
+    SWCL_LAUNCH(c, swcl::launch_delta_bar<double>((double*)c->ws_dbar.p, Pb,
+                                                  (const double*)c->ws_delta.p,
+                                                  (const double*)c->ws_Cbar.p,
+                                                  (const double*)c->d_amp.p, (const double*)c->d_P.p,
+                                                  (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
+                                                  c->stream), "delta_bar fp64");
+  } else {
+    SWCL_LAUNCH(c, swcl::launch_delta_bar<float>((float*)c->ws_dbar.p, Pb,
+                                                 (const float*)c->ws_delta.p,
+                                                 (const double*)c->ws_Cbar.p,
+                                                 (const double*)c->d_amp.p, (const double*)c->d_P.p,
+                                                 (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
+                                                 c->stream), "delta_bar f32");
+  }
+  SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
+                                      (const double*)c->d_amp.p, nw, N_tr, N_ell, c->stream),
+              "amp_bar");
+  if (W_bar) {
+    if (fp64) {
+      SWCL_LAUNCH(c, swcl::launch_contract_fp64_adj((cplx*)c->ws_cbar.p, (const double*)c->ws_dbar.p,
+                                                    (const cplx*)c->d_phase.p,
+                                                    (const cplx*)c->d_gtab.p,
+                                                    (const int*)c->d_cls_of.p,
+                                                    (const double*)c->d_kpow.p,
+                                                    (const int*)c->d_interp_j0.p,
+                                                    (const double*)c->d_interp_w.p, nw, N_tr, N_I,
+                                                    n_h, N_k, N_ell, c->stream), "contract adj fp64");
+    } else {
+      SWCL_TRY(swcl::contract_adj_tc(c, precision));
+    }
+    double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
+    double* scratch = (double*)((char*)c->ws_outW.p + wbytes);
+    SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
+                                           (const double*)c->d_chipow.p, (const double*)c->d_D.p,
+                                           c->have_B ? (const double*)c->d_B.p : nullptr,
+                                           (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
+                                           nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
+    ++c->last_launches;  // the chunk reduction
+    SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
+  }
+  if (P_bar) SWCL_TRY(swcl::copy_out(c, P_bar, Pb, sizeof(double) * nw * (size_t)N_k));
+  if (amp_bar) SWCL_TRY(swcl::copy_out(c, amp_bar, Ab, sizeof(double) * nrow));
+  return SWCL_OK;
+}
+
+int swcl_profile_enable(swcl_ctx* c, int enable) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!enable) {
+    int st = swcl::prof_flush(c);
+    c->prof = false;
+    return st;
+  }
+  c->prof = true;
+  return SWCL_OK;
+}
+
+int swcl_profile_reset(swcl_ctx* c) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  int st = swcl::prof_flush(c);
+  c->stats.clear();
+  return st;
+}
+
+int swcl_profile_read(swcl_ctx* c, int max_entries, char* names, int64_t* launches, double* ms,
+                      int* n_entries) {
+  if (!c || max_entries < 0 || !n_entries) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  int st = swcl::prof_flush(c);
+  if (st) return st;
+  int n = (int)c->stats.size();
+  *n_entries = n;
+  for (int i = 0; i < n && i < max_entries; ++i) {
+    if (names) {
+      std::strncpy(names + 32 * i, c->stats[i].name.c_str(), 31);
+      names[32 * i + 31] = 0;
+    }
+    if (launches) launches[i] = c->stats[i].launches;
+    if (ms) ms[i] = c->stats[i].ms;
+  }
+  return SWCL_OK;
+}
+
+namespace {
+__global__ void k_widen(double* out, const float* in, long n) {
+  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (double)in[t];
+}
+}  // namespace
+
+int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
+  if (!c || !count) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  const void* src = nullptr;
+  int64_t n = 0;
+  bool widen = false;
+  switch (what) {
+    case SWCL_DBG_COEF:
+      src = c->ws_coef.p; n = 2LL * c->n_walk * c->N_tr * c->N_I * c->n_h; break;
+    case SWCL_DBG_DELTA:
+      src = c->ws_delta.p; n = (int64_t)c->n_walk * c->N_ell * c->N_tr * c->N_k;
+      widen = c->last_fwd_precision != SWCL_FP64; break;
+    case SWCL_DBG_GTAB:
+      src = c->d_gtab.p; n = 2LL * c->n_cls * c->N_ell * c->n_h; break;
+    case SWCL_DBG_PHASE:
+      src = c->d_phase.p; n = 2LL * c->N_k * c->n_h; break;
+    case SWCL_DBG_UNIT:
+      src = c->ws_U.p; n = (int64_t)c->n_walk * c->N_ell * c->N_tr * c->N_tr; break;
+    default:
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown debug array");
+  }
+  *count = n;
+  if (!out) return SWCL_OK;
+  if (!src) return swcl::fail(c, SWCL_ERR_STATE, "array not computed yet");
+  if (what == SWCL_DBG_DELTA && c->last_fwd_precision < 0)
+    return swcl::fail(c, SWCL_ERR_STATE, "no forward pass yet");
+  if (widen) {
+    DevBuf tmp;
+    SWCL_TRY(swcl::ensure(c, tmp, sizeof(double) * n));
+    k_widen<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((double*)tmp.p, (const float*)src, n);
+    int st = swcl::copy_out(c, out, tmp.p, sizeof(double) * n);
+    cudaStreamSynchronize(c->stream);
+    swcl::release(c, tmp);
+    return st;
+  }
+  SWCL_TRY(swcl::copy_out(c, out, src, sizeof(double) * n));
+  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "debug read");
+  return SWCL_OK;
+}
+
+int swcl_sync(swcl_ctx* c) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return swcl::cuda_fail(c, e, "swcl_sync");
+  return SWCL_OK;
+}
+
+int swcl_query(swcl_ctx* c, int key, int64_t* value) {
+  if (!c || !value) return SWCL_ERR_INVALID_ARG;
+  switch (key) {
+    case SWCL_Q_WORKSPACE_BYTES: *value = (int64_t)c->held; return SWCL_OK;
+    case SWCL_Q_RECOMPUTE: *value = 0; return SWCL_OK;
+    case SWCL_Q_N_HALF: *value = c->n_h; return SWCL_OK;
+    case SWCL_Q_KERNEL_LAUNCHES: *value = c->last_launches; return SWCL_OK;
+    default: return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown query key");
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// a1: FFTLog coefficients of every window at every k-knot (Sec. 3.1-3.2, Eq. 3.2-3.3), FP64,
+// and the adjoint used by the VJP.
+//
+// One CTA transforms one or more rows (walker, tracer, knot).  The real length-N sequence
+// g_m = W_i(chi_m) * chipow_i[m] * D_a[m] * B_ia[m] is packed as N/2 complex points
+// z_j = g_{2j} + i g_{2j+1}, transformed by a radix-4 (plus one radix-2) Stockham FFT in shared
+// memory, and unpacked to X_n = sum_m g_m e^{-2 pi i n m/N}, n = 0..N/2.  The coefficient is
+// c_n = psi_i[n] X_n with psi = T_c chi_min^{-i eta_n}/N.  Twiddles come from a table
+// e^{-2 pi i t/N}, t < N, so the only FP64 arithmetic is the butterflies themselves.
+#include "swcl_internal.h"
+
+namespace swcl {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+__device__ __forceinline__ cplx cmulc(cplx a, cplx b) {  // a * conj(b)
+  return {fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y)};
+}
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
+
+// Forward DFT of n2 = N/2 points held in buffers a/b (ping-pong) for `rows` rows laid out
+// row-major with stride n2; returns the buffer holding the result.  Stockham autosort:
+// pass with radix R and span Ns maps j -> (j/Ns)*Ns*R + j%Ns with twiddle
+// e^{-2 pi i (j%Ns) r / (Ns R)} = tw[(j%Ns) r (N/(Ns R))].
+__device__ cplx* stockham(cplx* a, cplx* b, int n2, int rows, const cplx* __restrict__ tw,
+                          int N) {
+  int lg = 31 - __clz(n2);
+  int Ns = 1;
+  if (lg & 1) {
+    // radix-2 pass, trivial twiddles (Ns = 1)
+    int nb = n2 / 2;
+    for (int g = threadIdx.x; g < rows * nb; g += blockDim.x) {
+      int r = g / nb, j = g - r * nb;
+      const cplx* x = a + r * n2;
+      cplx* y = b + r * n2;
+      cplx v0 = x[j], v1 = x[j + nb];
+      y[2 * j] = cadd(v0, v1);
+      y[2 * j + 1] = csub(v0, v1);
+    }
+    __syncthreads();
+    cplx* t = a; a = b; b = t;
+    Ns = 2;
+  }
+  int nb = n2 / 4;
+  for (; Ns < n2; Ns *= 4) {
+    int tstep = N / (Ns * 4);
+    for (int g = threadIdx.x; g < rows * nb; g += blockDim.x) {
+      int r = g / nb, j = g - r * nb;
+      const cplx* x = a + r * n2;
+      cplx* y = b + r * n2;
+      int jm = j & (Ns - 1);
+      cplx v0 = x[j], v1 = x[j + nb], v2 = x[j + 2 * nb], v3 = x[j + 3 * nb];
+      if (Ns > 1) {
+        int t1 = jm * tstep;
+        v1 = cmul(v1, tw[t1]);
+        v2 = cmul(v2, tw[2 * t1]);
+        v3 = cmul(v3, tw[3 * t1]);
+      }
+      // 4-point DFT (e^{-2 pi i/4} = -i)
+      cplx s02 = cadd(v0, v2), d02 = csub(v0, v2);
+      cplx s13 = cadd(v1, v3), d13 = csub(v1, v3);
+      cplx md13 = {d13.y, -d13.x};  // -i * d13
+      int o = (j - jm) * 4 + jm;
+      y[o] = cadd(s02, s13);
+      y[o + Ns] = cadd(d02, md13);
+      y[o + 2 * Ns] = csub(s02, s13);
+      y[o + 3 * Ns] = csub(d02, md13);
+    }
+    __syncthreads();
+    cplx* t = a; a = b; b = t;
+  }
+  return a;
+}
+
+// rows per CTA: enough independent transforms to give every thread work
+__host__ __device__ inline int rows_per_cta(int N) {
+  int n2 = N / 2;
+  int r = (4 * kThreads) / n2;
+  return r < 1 ? 1 : r;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_fftlog_fwd(cplx* __restrict__ coef, const double* __restrict__ W,
+             const double* __restrict__ chipow, const double* __restrict__ D,
+             const double* __restrict__ B, const cplx* __restrict__ psi,
+             const cplx* __restrict__ tw, int n_walk, int N_tr, int N_I, int N) {
+  extern __shared__ cplx smem[];
+  const int n2 = N / 2, n_h = N / 2 + 1;
+  const int R = rows_per_cta(N);
+  const long total_rows = (long)n_walk * N_tr * N_I;
+  const long row0 = (long)blockIdx.x * R;
+  int rows = (int)min((long)R, total_rows - row0);
+  cplx* a = smem;
+  cplx* b = smem + R * n2;
+  // load and pack
+  for (int g = threadIdx.x; g < rows * n2; g += blockDim.x) {
+    int r = g / n2, j = g - r * n2;
+    long row = row0 + r;
+    int ka = (int)(row % N_I);
+    long wi = row / N_I;  // walker * N_tr + tracer
+    int i = (int)(wi % N_tr);
+    const double* w = W + wi * N;
+    const double* cp = chipow + (size_t)i * N;
+    const double* d = D + (size_t)ka * N;
+    int m = 2 * j;
+    double g0 = w[m] * cp[m] * d[m];
+    double g1 = w[m + 1] * cp[m + 1] * d[m + 1];
+    if (B) {
+      const double* bb = B + ((size_t)i * N_I + ka) * N;
+      g0 *= bb[m];
+      g1 *= bb[m + 1];
+    }
+    a[r * n2 + j] = {g0, g1};
+  }
+  __syncthreads();
+  cplx* Z = stockham(a, b, n2, rows, tw, N);
+  // unpack: X_n = E_n + e^{-2 pi i n/N} O_n, E = (Z_n + conj Z_{n2-n})/2, O = (Z_n - conj Z_{n2-n})/(2i)
+  for (int g = threadIdx.x; g < rows * n_h; g += blockDim.x) {
+    int r = g / n_h, n = g - r * n_h;
+    long row = row0 + r;
+    int i = (int)((row / N_I) % N_tr);
+    const cplx* z = Z + r * n2;
+    cplx zn = z[n == n2 ? 0 : n];
+    cplx zc = cconj(z[n == 0 ? 0 : n2 - n]);
+    cplx e = {0.5 * (zn.x + zc.x), 0.5 * (zn.y + zc.y)};
+    cplx dlt = {0.5 * (zn.x - zc.x), 0.5 * (zn.y - zc.y)};
+    cplx o = {dlt.y, -dlt.x};  // dlt / i
+    cplx x = cadd(e, cmul(tw[n], o));
+    coef[row * n_h + n] = cmul(psi[(size_t)i * n_h + n], x);
+  }
+}
+
+// Adjoint.  For row (w, i, a): Y_n = conj(psi_n) cbar_n, H_0 = Re Y_0, H_{N/2} = Re Y_{N/2},
+// H_n = Y_n / 2 otherwise; gbar_m = sum_{n<N} H_n e^{+2 pi i n m/N} (Hermitian H), computed as
+// x_{2j} + i x_{2j+1} = sum_n (E_n + i O_n) e^{+2 pi i n j/(N/2)} with
+// E_n = H_n + conj H_{n2-n}, O_n = (H_n - conj H_{n2-n}) e^{+2 pi i n/N}; the inverse transform is
+// conj(FFT(conj(.))).  Each CTA sums gbar * chipow * D_a * B_ia over a chunk of knots of one
+// (walker, tracer) into scratch[chunk][w*N_tr+i][m].
+constexpr int kKnotChunk = 16;
+
+__global__ void __launch_bounds__(kThreads)
+k_fftlog_adj(double* __restrict__ scratch, const cplx* __restrict__ cbar,
+             const double* __restrict__ chipow, const double* __restrict__ D,
+             const double* __restrict__ B, const cplx* __restrict__ psi,
+             const cplx* __restrict__ tw, int n_walk, int N_tr, int N_I, int N) {
+  extern __shared__ cplx smem[];
+  const int n2 = N / 2, n_h = N / 2 + 1;
+  cplx* a = smem;
+  cplx* b = smem + n2;
+  double* acc = reinterpret_cast<double*>(smem + 2 * n2);
+  const int wi = blockIdx.y;          // walker * N_tr + tracer
+  const int i = wi % N_tr;
+  const int chunk = blockIdx.x;
+  const int a0 = chunk * kKnotChunk;
+  const int a1 = min(N_I, a0 + kKnotChunk);
+  for (int m = threadIdx.x; m < N; m += blockDim.x) acc[m] = 0.0;
+  const cplx* ps = psi + (size_t)i * n_h;
+  for (int ka = a0; ka < a1; ++ka) {
+    const cplx* cb = cbar + ((size_t)wi * N_I + ka) * n_h;
+    for (int n = threadIdx.x; n < n2; n += blockDim.x) {
+      // H_n and conj H_{n2-n}
+      cplx y = cmulc(cb[n], ps[n]);           // cbar * conj(psi) ... conj(psi) cbar
+      cplx h = (n == 0) ? cplx{y.x, 0.0} : cplx{0.5 * y.x, 0.5 * y.y};
+      int m = n2 - n;
+      cplx ym = cmulc(cb[m], ps[m]);
+      cplx hm = (m == n2) ? cplx{ym.x, 0.0} : cplx{0.5 * ym.x, 0.5 * ym.y};
+      cplx hmc = cconj(hm);
+      cplx e = cadd(h, hmc);
+      cplx d = csub(h, hmc);
+      cplx o = cmulc(d, tw[n]);                // * e^{+2 pi i n/N}
+      // Z = E + i O, store conj(Z) for the forward transform
+      cplx z = {e.x - o.y, e.y + o.x};
+      a[n] = cconj(z);
+    }
+    __syncthreads();
+    cplx* Z = stockham(a, b, n2, 1, tw, N);
+    const double* cp = chipow + (size_t)i * N;
+    const double* d = D + (size_t)ka * N;
+    const double* bb = B ? B + ((size_t)i * N_I + ka) * N : nullptr;
+    for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+      cplx v = cconj(Z[j]);
+      int m = 2 * j;
+      double f0 = cp[m] * d[m], f1 = cp[m + 1] * d[m + 1];
+      if (bb) { f0 *= bb[m]; f1 *= bb[m + 1]; }
+      acc[m] = fma(v.x, f0, acc[m]);
+      acc[m + 1] = fma(v.y, f1, acc[m + 1]);
+    }
+    __syncthreads();
+  }
+  double* out = scratch + ((size_t)chunk * n_walk * N_tr + wi) * N;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) out[m] = acc[m];
+}
+
+__global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restrict__ scratch,
+                             long per_chunk, int nchunk) {
+  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per_chunk) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += scratch[(size_t)c * per_chunk + t];
+  W_bar[t] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_fftlog_fwd(cplx* coef, const double* W, const double* chipow,
+                              const double* D, const double* B, const cplx* psi,
+                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                              cudaStream_t s) {
+  int R = rows_per_cta(N);
+  long rows = (long)n_walk * N_tr * N_I;
+  long grid = (rows + R - 1) / R;
+  size_t smem = (size_t)2 * R * (N / 2) * sizeof(cplx);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fftlog_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_fftlog_fwd<<<(unsigned)grid, kThreads, smem, s>>>(coef, W, chipow, D, B, psi, twiddle,
+                                                       n_walk, N_tr, N_I, N);
+  return cudaGetLastError();
+}
+
+size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N) {
+  int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
+  return (size_t)nchunk * n_walk * N_tr * N * sizeof(double);
+}
+
+cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
+                              const double* D, const double* B, const cplx* psi,
+                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                              double* scratch, cudaStream_t s) {
+  int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
+  size_t smem = (size_t)(N / 2) * 2 * sizeof(cplx) + (size_t)N * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fftlog_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g(nchunk, n_walk * N_tr);
+  k_fftlog_adj<<<g, kThreads, smem, s>>>(scratch, cbar, chipow, D, B, psi, twiddle, n_walk, N_tr,
+                                          N_I, N);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  long per = (long)n_walk * N_tr * N;
+  k_sum_chunks<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(W_bar, scratch, per, nchunk);
+  return cudaGetLastError();
+}
+
+}  // namespace swcl

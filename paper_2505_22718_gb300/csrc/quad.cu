@@ -1,0 +1,281 @@
+// a4: the k-quadrature of Eq. 2.1, C_l^{ij} = A_i A_j sum_q u_q Delta_i(l,q) Delta_j(l,q),
+// u_q = wk2[q] P(k_q), and the reductions of its reverse mode (a5):
+//   Pbar_q   = wk2[q] sum_l sum_i A_i Delta_i T_i,   T_i = sum_j S_ij A_j Delta_j,
+//   Dbar_i   = 2 A_i u_q T_i,
+//   Abar_i   = 2 sum_l sum_j S_ij A_j U_ij            (U = C at unit amplitudes),
+// with S = (Cbar + Cbar^T)/2 (zero for multipoles outside a walker's list).
+//
+// The unit-amplitude spectra U are formed per (walker, multipole) by one CTA; each unordered
+// pair (i <= j) is summed once over k and written to both (i,j) and (j,i), so C is symmetric
+// bit for bit.  Delta in FP32 (mixed paths): the products and partial sums over 32 k points are
+// FP32, the per-pair total over k is FP64.
+#include "swcl_internal.h"
+
+namespace swcl {
+namespace {
+
+constexpr int QT = 256;    // threads
+constexpr int QC = 128;    // k points staged per step
+
+template <typename T>
+__global__ void __launch_bounds__(QT)
+k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __restrict__ P,
+       const double* __restrict__ wk2, int N_tr, int N_k, int N_ell) {
+  extern __shared__ double qsm[];
+  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][QC]
+  __shared__ double us[QC];
+  __shared__ double red[QT];
+  const int l = blockIdx.x;
+  const int w = blockIdx.y;
+  const int npair = N_tr * (N_tr + 1) / 2;
+  const T* dl = delta + ((size_t)w * N_ell + l) * N_tr * N_k;
+  const double* Pw = P + (size_t)w * N_k;
+  // thread -> (pair slot, k-group)
+  const int ngroups = max(1, QT / npair);
+  const int group = threadIdx.x / npair;
+  for (int p0 = 0; p0 < npair; p0 += QT) {
+    int p = p0 + (ngroups > 1 ? (threadIdx.x % npair) : threadIdx.x);
+    bool active = (ngroups > 1) ? (group < ngroups) : (p < npair);
+    int pi = 0, pj = 0;
+    if (active && p < npair) {
+      // unordered pair index -> (i <= j)
+      int r = p, ii = 0;
+      while (r >= N_tr - ii) { r -= N_tr - ii; ++ii; }
+      pi = ii; pj = ii + r;
+    }
+    double acc = 0.0;
+    for (int qb = 0; qb < N_k; qb += QC) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < N_tr * QC; e += QT) {
+        int t = e / QC, qq = e - t * QC;
+        int q = qb + qq;
+        Ds[t * QC + qq] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
+      }
+      for (int e = threadIdx.x; e < QC; e += QT) {
+        int q = qb + e;
+        us[e] = (q < N_k) ? wk2[q] * Pw[q] : 0.0;
+      }
+      __syncthreads();
+      if (active && p < npair) {
+        const T* di = Ds + pi * QC;
+        const T* dj = Ds + pj * QC;
+        int qs = (ngroups > 1) ? group : 0;
+        int qstep = (ngroups > 1) ? ngroups : 1;
+        if (sizeof(T) == 4) {
+          // FP32 products and partial sums of 32 points, FP64 total
+          for (int c0 = qs * 32; c0 < QC; c0 += qstep * 32) {
+            float part = 0.0f;
+#pragma unroll 8
+            for (int qq = c0; qq < c0 + 32; ++qq)
+              part = fmaf((float)di[qq] * (float)us[qq], (float)dj[qq], part);
+            acc += (double)part;
+          }
+        } else {
+          for (int qq = qs; qq < QC; qq += qstep)
+            acc = fma((double)di[qq] * us[qq], (double)dj[qq], acc);
+        }
+      }
+    }
+    // combine k-groups
+    __syncthreads();
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (active && p < npair && (ngroups == 1 || group == 0)) {
+      double s = acc;
+      if (ngroups > 1)
+        for (int g = 1; g < ngroups; ++g) s += red[g * npair + (threadIdx.x % npair)];
+      double* out = U + ((size_t)w * N_ell + l) * N_tr * N_tr;
+      out[pi * N_tr + pj] = s;
+      out[pj * N_tr + pi] = s;
+    }
+    if (ngroups > 1) break;
+  }
+}
+
+// C[o][i][j] = A_i A_j U[w][l][i][j] for the packed (walker, listed multipole) outputs.
+__global__ void k_scale_pack(double* __restrict__ C, const double* __restrict__ U,
+                             const double* __restrict__ amp, const int* __restrict__ off,
+                             const int* __restrict__ idx, int n_walk, int N_tr, int N_ell,
+                             long n_out) {
+  long o = blockIdx.x;
+  if (o >= n_out) return;
+  int w, l;
+  if (off) {
+    // walker of output o: largest w with off[w] <= o
+    int lo = 0, hi = n_walk;
+    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (off[mid] <= o) lo = mid; else hi = mid; }
+    w = lo;
+    l = idx[o];
+  } else {
+    w = (int)(o / N_ell);
+    l = (int)(o % N_ell);
+  }
+  const double* u = U + ((size_t)w * N_ell + l) * N_tr * N_tr;
+  const double* A = amp + (size_t)w * N_tr;
+  for (int e = threadIdx.x; e < N_tr * N_tr; e += blockDim.x) {
+    int i = e / N_tr, j = e - i * N_tr;
+    double ai = A[i], aj = A[j];
+    double s = (i <= j) ? ai * aj : aj * ai;
+    C[o * N_tr * N_tr + e] = s * u[e];
+  }
+}
+
+// Cbar_full[w][l] = (Cbar + Cbar^T)/2 on listed multipoles, 0 elsewhere.
+__global__ void k_unpack_sym(double* __restrict__ Cf, const double* __restrict__ Cb,
+                             const int* __restrict__ off, const int* __restrict__ idx,
+                             int n_walk, int N_tr, int N_ell, long n_out) {
+  long o = blockIdx.x;
+  if (o >= n_out) return;
+  int w, l;
+  if (off) {
+    int lo = 0, hi = n_walk;
+    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (off[mid] <= o) lo = mid; else hi = mid; }
+    w = lo;
+    l = idx[o];
+  } else {
+    w = (int)(o / N_ell);
+    l = (int)(o % N_ell);
+  }
+  const double* s = Cb + o * N_tr * N_tr;
+  double* d = Cf + ((size_t)w * N_ell + l) * N_tr * N_tr;
+  for (int e = threadIdx.x; e < N_tr * N_tr; e += blockDim.x) {
+    int i = e / N_tr, j = e - i * N_tr;
+    d[e] = 0.5 * (s[i * N_tr + j] + s[j * N_tr + i]);
+  }
+}
+
+// amp_bar[w][i] = 2 sum_l sum_j S_ij A_j U_ij
+__global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ Cf,
+                          const double* __restrict__ U, const double* __restrict__ amp,
+                          int N_tr, int N_ell) {
+  const int w = blockIdx.y;
+  const int i = blockIdx.x;
+  __shared__ double red[256];
+  double s = 0.0;
+  const double* A = amp + (size_t)w * N_tr;
+  for (int e = threadIdx.x; e < N_ell * N_tr; e += blockDim.x) {
+    int l = e / N_tr, j = e - l * N_tr;
+    size_t base = (((size_t)w * N_ell + l) * N_tr + i) * N_tr + j;
+    s = fma(Cf[base] * A[j], U[base], s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) abar[(size_t)w * N_tr + i] = 2.0 * red[0];
+}
+
+// One thread per (walker, k point); loop over multipoles with S_l staged in shared memory.
+constexpr int DT = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(DT)
+k_delta_bar(T* __restrict__ dbar, double* __restrict__ Pbar, const T* __restrict__ delta,
+            const double* __restrict__ Cf, const double* __restrict__ amp,
+            const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
+            int N_ell) {
+  extern __shared__ double dsm[];
+  double* S = dsm;                        // [N_tr][N_tr]  S_ij A_j
+  double* Dl = dsm + N_tr * N_tr;         // [N_tr][DT]
+  const int w = blockIdx.y;
+  const int q = blockIdx.x * DT + threadIdx.x;
+  const double* A = amp + (size_t)w * N_tr;
+  const double uq = (q < N_k) ? wk2[q] * P[(size_t)w * N_k + q] : 0.0;
+  double pacc = 0.0;
+  for (int l = 0; l < N_ell; ++l) {
+    __syncthreads();
+    const double* cf = Cf + ((size_t)w * N_ell + l) * N_tr * N_tr;
+    for (int e = threadIdx.x; e < N_tr * N_tr; e += DT) S[e] = cf[e] * A[e % N_tr];
+    const T* dl = delta + ((size_t)w * N_ell + l) * N_tr * N_k;
+    for (int t = 0; t < N_tr; ++t)
+      Dl[t * DT + threadIdx.x] = (q < N_k) ? (double)dl[(size_t)t * N_k + q] : 0.0;
+    __syncthreads();
+    if (q < N_k) {
+      T* db = dbar + ((size_t)w * N_ell + l) * N_tr * N_k;
+      for (int ii = 0; ii < N_tr; ++ii) {
+        double t = 0.0;
+        for (int j = 0; j < N_tr; ++j) t = fma(S[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
+        pacc = fma(A[ii] * Dl[ii * DT + threadIdx.x], t, pacc);
+        db[(size_t)ii * N_k + q] = (T)(2.0 * A[ii] * uq * t);
+      }
+    }
+  }
+  if (q < N_k) Pbar[(size_t)w * N_k + q] = wk2[q] * pacc;
+}
+
+}  // namespace
+
+cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
+                             int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s) {
+  size_t smem = (size_t)N_tr * QC * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_quad<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g(N_ell, n_walk);
+  k_quad<double><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
+                            int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s) {
+  size_t smem = (size_t)N_tr * QC * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_quad<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g(N_ell, n_walk);
+  k_quad<float><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
+                              const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
+                              cudaStream_t s) {
+  if (n_out == 0) return cudaSuccess;
+  k_scale_pack<<<(unsigned)n_out, 128, 0, s>>>(C, U, amp, off, idx, n_walk, N_tr, N_ell, n_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_sym(double* Cf, const double* Cb, const int* off, const int* idx,
+                              int n_walk, int N_tr, int N_ell, int64_t n_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(Cf, 0, (size_t)n_walk * N_ell * N_tr * N_tr * sizeof(double), s);
+  if (e != cudaSuccess || n_out == 0) return e;
+  k_unpack_sym<<<(unsigned)n_out, 128, 0, s>>>(Cf, Cb, off, idx, n_walk, N_tr, N_ell, n_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amp_bar(double* amp_bar, const double* Cf, const double* U, const double* amp,
+                           int n_walk, int N_tr, int N_ell, cudaStream_t s) {
+  dim3 g(N_tr, n_walk);
+  k_amp_bar<<<g, 256, 0, s>>>(amp_bar, Cf, U, amp, N_tr, N_ell);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cf,
+                             const double* amp, const double* P, const double* wk2, int n_walk,
+                             int N_tr, int N_k, int N_ell, cudaStream_t s) {
+  size_t smem = (size_t)(N_tr * N_tr + N_tr * DT) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g((N_k + DT - 1) / DT, n_walk);
+  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, P_bar, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_delta_bar<double>(double*, double*, const double*, const double*,
+                                              const double*, const double*, const double*, int,
+                                              int, int, int, cudaStream_t);
+template cudaError_t launch_delta_bar<float>(float*, double*, const float*, const double*,
+                                             const double*, const double*, const double*, int,
+                                             int, int, int, cudaStream_t);
+
+}  // namespace swcl

@@ -1,0 +1,174 @@
+// Internal declarations of the swiftcl library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/swiftcl.h"
+
+namespace swcl {
+
+struct cplx { double x, y; };
+
+// Device buffer with a byte count, owned by the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-precision operand tables for the tensor-core contraction.
+struct TcTables {
+  bool ready = false;
+  DevBuf bfwd;     // forward B operand, per class: [cls][Lpad][Kpad] (hi plane then lo plane(s))
+  DevBuf bvjp;     // transposed operand for the VJP, per class: [cls][Kpad_rows][Lk]
+  DevBuf phase32;  // float2 phase table [N_k][n_h]
+  int Lpad = 0, Kpad = 0, Lk = 0, nsplit = 0;
+};
+
+// a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
+int compute_delta_tc(swcl_ctx* c, int precision);
+int contract_adj_tc(swcl_ctx* c, int precision);
+
+}  // namespace swcl
+
+struct swcl_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;      // 0 = unbounded
+  size_t held = 0;        // device bytes held
+  std::string err;
+  int64_t last_launches = 0;
+
+  // grids
+  bool have_grids = false;
+  int N = 0, n_h = 0, N_k = 0, N_ell = 0, N_I = 0;
+  double chi_min = 0, chi_max = 0, L = 0;
+  std::vector<int> ells_h;
+  std::vector<double> k_h, knots_h;
+  swcl::DevBuf d_k, d_ells, d_knots, d_wk2;   // wk2 = (2/pi) w_q k_q^2
+  swcl::DevBuf d_interp_j0, d_interp_w;       // [N_k] int, [N_k][4] double
+  swcl::DevBuf d_twiddle;                     // FFT twiddles e^{-2 pi i t/N}, t < N  (cplx)
+  swcl::DevBuf d_phase;                       // [N_k][n_h] cplx  e^{-i eta_n ln k_q}
+  swcl::DevBuf d_knot_qrange;                 // [N_I][2] int: first/last q whose stencil uses knot a
+
+  // tracers
+  bool have_tracers = false;
+  int N_tr = 0, n_cls = 0;
+  std::vector<int> kind_h, cls_of_h;
+  std::vector<double> bias_h;
+  swcl::DevBuf d_cls_of;                      // [N_tr] int
+  swcl::DevBuf d_chipow;                      // [N_tr][N] chi^{s-b} T_chi
+  swcl::DevBuf d_psi;                         // [N_tr][n_h] cplx  T_c chi_min^{-i eta}/N
+  swcl::DevBuf d_gtab;                        // [n_cls][N_ell][n_h] cplx  w_n pi(l) M_{l,n}
+  swcl::DevBuf d_kpow;                        // [N_tr][N_k] k^{t-1-b}
+  swcl::TcTables tc[3];
+
+  // windows / power
+  int n_walk = 0;
+  bool have_windows = false, have_power = false, have_B = false;
+  swcl::DevBuf d_W, d_D, d_B, d_P, d_amp;
+
+  // ragged ell lists
+  bool ragged = false;
+  std::vector<int> off_h, idx_h;
+  swcl::DevBuf d_off, d_idx;
+  int64_t n_out_ell = 0;                      // sum_w n_ell(w)
+
+  // workspaces
+  swcl::DevBuf ws_coef;      // [n_walk][N_tr][N_I][n_h] cplx
+  swcl::DevBuf ws_delta;     // FP64: [n_walk][N_ell][N_tr][N_k] double; mixed: float
+  swcl::DevBuf ws_U;         // [n_walk][N_ell][N_tr][N_tr] double, unit-amplitude C
+  swcl::DevBuf ws_C;         // [n_out][N_tr][N_tr] double, device staging for host outputs
+  swcl::DevBuf ws_cbar;      // [n_walk][N_tr][N_I][n_h] cplx
+  swcl::DevBuf ws_dbar;      // FP64: like ws_delta
+  swcl::DevBuf ws_Cbar;      // [n_walk][N_ell][N_tr][N_tr] double, symmetrised, zero off-list
+  swcl::DevBuf ws_outP, ws_outA, ws_outW;   // device staging of VJP outputs
+  swcl::DevBuf ws_status;    // device status word(s)
+  int last_fwd_precision = -1;
+
+  // per-kernel timing (swcl_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { const char* name; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  cudaEvent_t ev_open = nullptr;
+  struct Stat { std::string name; int64_t launches = 0; double ms = 0.0; };
+  std::vector<Stat> stats;
+};
+
+// ---------------------------------------------------------------- helpers ----
+namespace swcl {
+
+int fail(swcl_ctx* c, int code, const std::string& msg);
+int cuda_fail(swcl_ctx* c, cudaError_t e, const char* what);
+int ensure(swcl_ctx* c, DevBuf& b, size_t bytes);
+void release(swcl_ctx* c, DevBuf& b);
+bool is_device_ptr(const void* p);
+int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes);
+int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes);
+void prof_begin(swcl_ctx* c);
+void prof_end(swcl_ctx* c, const char* name);
+
+// ------------------------------------------------------------ launchers ----
+// tables (tables.cu)
+cudaError_t launch_fft_twiddles(cplx* tw, int N, cudaStream_t s);
+cudaError_t launch_phase_table(cplx* phase, const double* k, int N_k, int n_h, double L,
+                               cudaStream_t s);
+cudaError_t launch_interp_weights(int* j0, double* w, const double* k, int N_k,
+                                  const double* knots, int N_I, cudaStream_t s);
+cudaError_t launch_quad_weights(double* wk2, const double* k, int N_k, cudaStream_t s);
+cudaError_t launch_gamma_table(cplx* gtab, const int* ells, int N_ell, int n_h, double L,
+                               double b, int kind, cudaStream_t s);
+cudaError_t launch_tracer_tables(double* chipow, cplx* psi, double* kpow, const double* k,
+                                 int N_k, int N, double chi_min, double L, double b, int kind,
+                                 const double* taper_chi, const double* taper_c,
+                                 cudaStream_t s);
+
+// a1 FFTLog (fft.cu)
+cudaError_t launch_fftlog_fwd(cplx* coef, const double* W, const double* chipow,
+                              const double* D, const double* B, const cplx* psi,
+                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                              cudaStream_t s);
+// adjoint: W_bar[w][i][m] = chipow_i[m] sum_a D_a[m] B_ia[m] Re sum_n conj(psi_n) cbar_n e^{+2pi i n m/N}
+cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
+                              const double* D, const double* B, const cplx* psi,
+                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                              double* scratch, cudaStream_t s);
+size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
+
+// a3 FP64 contraction (contract_fp64.cu)
+cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
+                                 const cplx* gtab, const int* cls_of, const double* kpow,
+                                 const int* j0, const double* lw, int n_walk, int N_tr,
+                                 int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
+cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx* phase,
+                                     const cplx* gtab, const int* cls_of, const double* kpow,
+                                     const int* j0, const double* lw, int n_walk, int N_tr,
+                                     int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
+
+// a4 k-quadrature and VJP reductions (quad.cu)
+cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
+                             int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s);
+cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
+                            int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s);
+cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
+                              const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
+                              cudaStream_t s);
+cudaError_t launch_unpack_sym(double* Cbar_full, const double* Cbar, const int* off,
+                              const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
+                              cudaStream_t s);
+cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const double* U,
+                           const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s);
+template <typename T>
+cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cbar_full,
+                             const double* amp, const double* P, const double* wk2, int n_walk,
+                             int N_tr, int N_k, int N_ell, cudaStream_t s);
+
+// a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
+int compute_delta_tc(swcl_ctx* c, int precision);
+int contract_adj_tc(swcl_ctx* c, int precision);
+
+}  // namespace swcl
