@@ -144,6 +144,37 @@ int swcl_profile_reset(swcl_ctx* ctx);
 #define SWCL_DBG_UNIT  5
 int swcl_debug_read(swcl_ctx* ctx, int what, double* out, int64_t* count);
 
+/* FFTLog coefficients (a1) without a context and without allocating device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate device
+ * memory, e.g. a JAX/XLA process that has pre-reserved the GPU's memory for its own arena, a
+ * plugin confined to another framework's workspace, or a loop that must not pay for (or risk
+ * the failure of) a cudaMalloc.  It never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Arguments as for swcl_set_grids / swcl_set_tracers / swcl_set_windows, except:
+ *   kind[N_tr], fft_bias[N_tr]      host arrays;
+ *   taper_chi, taper_c, W, D, B     device arrays of the current device (taper_*, B may be NULL;
+ *                                   D is required);
+ *   coef                            device output [n_walk][N_tr][N_I][N/2+1] complex
+ *                                   (interleaved re, im) -- the same values swcl_compute_cl
+ *                                   produces for the same inputs (SWCL_DBG_COEF);
+ *   stream                          cudaStream_t the work is queued on (NULL = legacy stream).
+ * Work runs on the current CUDA device.  The twiddle, chi-power and phase tables the kernel reads
+ * live in one static device array of SWCL_NOALLOC_SCRATCH_BYTES per device, held by every GPU
+ * that loads the library until the process exits.  Requests whose tables exceed it,
+ * 16 N + 8 N_tr N + 16 N_tr (N/2+1) bytes (each term rounded up to 256), return
+ * SWCL_ERR_OOM_BUDGET; bad sizes or pointers return SWCL_ERR_INVALID_ARG; a failing launch
+ * returns SWCL_ERR_CUDA.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call rewrites
+ * the tables it reads, so nothing from an earlier call leaks into a later one, but all calls share
+ * the one array: calls that overlap on the GPU (different streams, or host threads) race.
+ */
+#define SWCL_NOALLOC_SCRATCH_BYTES (4u << 20)
+int swcl_fftlog_noalloc(int n_walk, int N_tr, int N_I, int N, double chi_min, double chi_max,
+                        const int* kind, const double* fft_bias, const double* taper_chi,
+                        const double* taper_c, const double* W, const double* D, const double* B,
+                        double* coef, void* stream);
+
 /* Wait for queued work; returns any deferred device error. */
 int swcl_sync(swcl_ctx* ctx);
 

@@ -28,6 +28,9 @@ SIGNATURES = {
     "swcl_vjp": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "swcl_sync": (c_int, [c_void_p]),
     "swcl_debug_read": (c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_int64)]),
+    "swcl_fftlog_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p]),
     "swcl_profile_enable": (c_int, [c_void_p, c_int]),
     "swcl_profile_read": (c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_int64),
                                   ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),

@@ -153,6 +153,21 @@ def swcl_debug_read(ctx, what):
     return out
 
 
+def swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, kind, fft_bias, taper_chi, taper_c,
+                        W, D, B, coef, stream=None):
+    """FFTLog coefficients without a context or any device allocation (see include/swiftcl.h).
+
+    kind, fft_bias: host arrays; taper_chi, taper_c, W, D, B, coef: CUDA tensors of the current
+    device (taper_*, B may be None).  Returns the status code (0 = ok) instead of raising, so a
+    caller can test the size limit."""
+    pk, _k = _ptr(np.asarray(kind, dtype=np.int32), np.int32)
+    pb, _b = _ptr(np.asarray(fft_bias, dtype=np.float64), np.float64)
+    args = [_ptr(x, np.float64) for x in (taper_chi, taper_c, W, D, B, coef)]
+    return _lib.load().swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, pk, pb,
+                                           *[a[0] for a in args],
+                                           ctypes.c_void_p(stream) if stream else None)
+
+
 def swcl_sync(ctx):
     _check(ctx, _lib.load().swcl_sync(ctx))
 
