@@ -1,7 +1,9 @@
 // C ABI of the library (include/swiftcl.h): argument checking, device buffers, and the
 // sequence of kernels for the forward pass (a1-a4) and the VJP (a5).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <utility>
@@ -219,6 +221,15 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
     }
     c->own_stream = true;
   }
+  // device status word raised by bounded waits in the tensor-core kernels
+  if (swcl::ensure(c, c->ws_status, 16) != SWCL_OK ||
+      cudaMemset(c->ws_status.p, 0, 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    swcl::release(c, c->ws_status);
+    delete c;
+    return SWCL_ERR_CUDA;
+  }
   *out = c;
   return SWCL_OK;
 }
@@ -232,12 +243,15 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_cls_of, &c->d_chipow, &c->d_psi, &c->d_gtab, &c->d_kpow, &c->d_W,
                     &c->d_D, &c->d_B, &c->d_P, &c->d_amp, &c->d_off, &c->d_idx, &c->ws_coef,
                     &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar, &c->ws_Cbar,
-                    &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status};
+                    &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status, &c->tc_lw32,
+                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
     swcl::release(c, t.bvjp);
     swcl::release(c, t.phase32);
+    swcl::release(c, t.tile_alo);
+    swcl::release(c, t.knot_qt);
   }
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -272,7 +286,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
     if (eh[l] < 0 || eh[l] > 100000) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell out of range");
   c->have_grids = c->have_tracers = c->have_windows = c->have_power = false;
   c->ragged = false;
-  for (auto& t : c->tc) t.ready = false;
+  for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->N = N;
   c->n_h = N / 2 + 1;
   c->N_k = N_k;
@@ -344,7 +358,7 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
     cls_of[i] = found;
   }
   c->have_tracers = false;
-  for (auto& t : c->tc) t.ready = false;
+  for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->last_fwd_precision = -1;
   c->N_tr = N_tr;
   c->n_cls = (int)cls.size();
@@ -461,10 +475,24 @@ int swcl_set_ell_lists(swcl_ctx* c, const int* offsets, const int* ell_idx) {
   return SWCL_OK;
 }
 
+// Reads (and clears) the device status word the tensor-core kernels raise on a wait timeout.
+static int check_status(swcl_ctx* c) {
+  if (!c->ws_status.p) return SWCL_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, c->ws_status.p, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return swcl::cuda_fail(c, e, "status read");
+  if (h) {
+    cudaMemset(c->ws_status.p, 0, sizeof(int));
+    return swcl::fail(c, SWCL_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on an mbarrier");
+  }
+  return SWCL_OK;
+}
+
 static int check_ready(swcl_ctx* c, int precision) {
   if (!c->have_grids || !c->have_tracers || !c->have_windows || !c->have_power)
     return swcl::fail(c, SWCL_ERR_STATE, "set_grids, set_tracers, set_windows and set_power first");
-  if (precision != SWCL_FP64 && precision != SWCL_3XTF32 && precision != SWCL_SPLIT_BF16)
+  if (precision != SWCL_FP64 && precision != SWCL_3XTF32 && precision != SWCL_SPLIT_BF16 &&
+      precision != SWCL_TF32X6)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown precision");
   return SWCL_OK;
 }
@@ -483,12 +511,12 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   const size_t nd = nrow * N_ell * N_k;
   SWCL_TRY(swcl::ensure(c, c->ws_delta, nd * (precision == SWCL_FP64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
-  SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
-                                         (const double*)c->d_chipow.p, (const double*)c->d_D.p,
-                                         c->have_B ? (const double*)c->d_B.p : nullptr,
-                                         (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p, nw,
-                                         N_tr, N_I, N, c->stream), "fftlog");
   if (precision == SWCL_FP64) {
+    SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
+                                           (const double*)c->d_chipow.p, (const double*)c->d_D.p,
+                                           c->have_B ? (const double*)c->d_B.p : nullptr,
+                                           (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
+                                           nw, N_tr, N_I, N, c->stream), "fftlog");
     SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
                                               (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
                                               (const int*)c->d_cls_of.p, (const double*)c->d_kpow.p,
@@ -499,6 +527,11 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                           (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
                                           N_tr, N_k, N_ell, c->stream), "k-quadrature fp64");
   } else {
+    SWCL_LAUNCH(c, swcl::launch_fftlog_fwd_df((float4*)c->ws_coef.p, (const double*)c->d_W.p,
+                                               (const double*)c->d_chipow.p, (const double*)c->d_D.p,
+                                               c->have_B ? (const double*)c->d_B.p : nullptr,
+                                               (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
+                                               nw, N_tr, N_I, N, c->stream), "fftlog");
     SWCL_TRY(swcl::compute_delta_tc(c, precision));
     SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                          (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
@@ -517,7 +550,10 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
                                          N_ell, n_out, c->stream), "scale/pack");
   c->last_fwd_precision = precision;
-  if (!dev_out) SWCL_TRY(swcl::copy_out(c, C_out, dst, cbytes));
+  if (!dev_out) {
+    SWCL_TRY(swcl::copy_out(c, C_out, dst, cbytes));
+    SWCL_TRY(check_status(c));
+  }
   return SWCL_OK;
 }
 
@@ -646,6 +682,14 @@ __global__ void k_widen(double* out, const float* in, long n) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) out[t] = (double)in[t];
 }
+__global__ void k_join_df(double* out, const float4* in, long n) {
+  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const float4 v = in[t];
+    out[2 * t] = (double)v.x + (double)v.z;
+    out[2 * t + 1] = (double)v.y + (double)v.w;
+  }
+}
 }  // namespace
 
 int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
@@ -654,10 +698,11 @@ int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
   c->err.clear();
   const void* src = nullptr;
   int64_t n = 0;
-  bool widen = false;
+  bool widen = false, dfpair = false;
   switch (what) {
     case SWCL_DBG_COEF:
-      src = c->ws_coef.p; n = 2LL * c->n_walk * c->N_tr * c->N_I * c->n_h; break;
+      src = c->ws_coef.p; n = 2LL * c->n_walk * c->N_tr * c->N_I * c->n_h;
+      dfpair = c->last_fwd_precision > SWCL_FP64; break;
     case SWCL_DBG_DELTA:
       src = c->ws_delta.p; n = (int64_t)c->n_walk * c->N_ell * c->N_tr * c->N_k;
       widen = c->last_fwd_precision != SWCL_FP64; break;
@@ -675,6 +720,16 @@ int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
   if (!src) return swcl::fail(c, SWCL_ERR_STATE, "array not computed yet");
   if (what == SWCL_DBG_DELTA && c->last_fwd_precision < 0)
     return swcl::fail(c, SWCL_ERR_STATE, "no forward pass yet");
+  if (dfpair) {
+    // double-float pairs (re_hi, im_hi, re_lo, im_lo) -> (re, im)
+    DevBuf tmp;
+    SWCL_TRY(swcl::ensure(c, tmp, sizeof(double) * n));
+    k_join_df<<<(unsigned)((n / 2 + 255) / 256), 256, 0, c->stream>>>((double*)tmp.p, (const float4*)src, n / 2);
+    int st = swcl::copy_out(c, out, tmp.p, sizeof(double) * n);
+    cudaStreamSynchronize(c->stream);
+    swcl::release(c, tmp);
+    return st;
+  }
   if (widen) {
     DevBuf tmp;
     SWCL_TRY(swcl::ensure(c, tmp, sizeof(double) * n));
@@ -694,7 +749,7 @@ int swcl_sync(swcl_ctx* c) {
   DeviceGuard g(c->device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return swcl::cuda_fail(c, e, "swcl_sync");
-  return SWCL_OK;
+  return check_status(c);
 }
 
 int swcl_query(swcl_ctx* c, int key, int64_t* value) {

@@ -85,8 +85,16 @@ __host__ __device__ inline int rows_per_cta(int N) {
   return r < 1 ? 1 : r;
 }
 
+__device__ __forceinline__ void store_coef(cplx* p, cplx v) { *p = v; }
+// double-float pair (re_hi, im_hi, re_lo, im_lo): hi = fl32(v), lo = fl32(v - hi)
+__device__ __forceinline__ void store_coef(float4* p, cplx v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  *p = make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+
+template <typename CT>
 __global__ void __launch_bounds__(kThreads)
-k_fftlog_fwd(cplx* __restrict__ coef, const double* __restrict__ W,
+k_fftlog_fwd(CT* __restrict__ coef, const double* __restrict__ W,
              const double* __restrict__ chipow, const double* __restrict__ D,
              const double* __restrict__ B, const cplx* __restrict__ psi,
              const cplx* __restrict__ tw, int n_walk, int N_tr, int N_I, int N) {
@@ -132,7 +140,7 @@ k_fftlog_fwd(cplx* __restrict__ coef, const double* __restrict__ W,
     cplx dlt = {0.5 * (zn.x - zc.x), 0.5 * (zn.y - zc.y)};
     cplx o = {dlt.y, -dlt.x};  // dlt / i
     cplx x = cadd(e, cmul(tw[n], o));
-    coef[row * n_h + n] = cmul(psi[(size_t)i * n_h + n], x);
+    store_coef(coef + row * n_h + n, cmul(psi[(size_t)i * n_h + n], x));
   }
 }
 
@@ -208,22 +216,36 @@ __global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restric
 
 }  // namespace
 
-cudaError_t launch_fftlog_fwd(cplx* coef, const double* W, const double* chipow,
-                              const double* D, const double* B, const cplx* psi,
-                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
-                              cudaStream_t s) {
+template <typename CT>
+static cudaError_t fftlog_fwd(CT* coef, const double* W, const double* chipow, const double* D,
+                              const double* B, const cplx* psi, const cplx* twiddle, int n_walk,
+                              int N_tr, int N_I, int N, cudaStream_t s) {
   int R = rows_per_cta(N);
   long rows = (long)n_walk * N_tr * N_I;
   long grid = (rows + R - 1) / R;
   size_t smem = (size_t)2 * R * (N / 2) * sizeof(cplx);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_fftlog_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fftlog_fwd<CT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_fftlog_fwd<<<(unsigned)grid, kThreads, smem, s>>>(coef, W, chipow, D, B, psi, twiddle,
-                                                       n_walk, N_tr, N_I, N);
+  k_fftlog_fwd<CT><<<(unsigned)grid, kThreads, smem, s>>>(coef, W, chipow, D, B, psi, twiddle,
+                                                           n_walk, N_tr, N_I, N);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fftlog_fwd(cplx* coef, const double* W, const double* chipow,
+                              const double* D, const double* B, const cplx* psi,
+                              const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                              cudaStream_t s) {
+  return fftlog_fwd(coef, W, chipow, D, B, psi, twiddle, n_walk, N_tr, N_I, N, s);
+}
+
+cudaError_t launch_fftlog_fwd_df(float4* coef, const double* W, const double* chipow,
+                                  const double* D, const double* B, const cplx* psi,
+                                  const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                                  cudaStream_t s) {
+  return fftlog_fwd(coef, W, chipow, D, B, psi, twiddle, n_walk, N_tr, N_I, N, s);
 }
 
 size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N) {

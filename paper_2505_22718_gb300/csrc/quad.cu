@@ -7,8 +7,9 @@
 //
 // The unit-amplitude spectra U are formed per (walker, multipole) by one CTA; each unordered
 // pair (i <= j) is summed once over k and written to both (i,j) and (j,i), so C is symmetric
-// bit for bit.  Delta in FP32 (mixed paths): the products and partial sums over 32 k points are
-// FP32, the per-pair total over k is FP64.
+// bit for bit.  Delta in FP32 (mixed paths): the products are FP32, the partial sums over 32 k
+// points are compensated FP32 sums (TwoSum; the rounding of each addition is carried in a second
+// float), and the per-pair total over k is FP64.
 #include "swcl_internal.h"
 
 namespace swcl {
@@ -24,6 +25,7 @@ k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __rest
   extern __shared__ double qsm[];
   T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][QC]
   __shared__ double us[QC];
+  __shared__ float usf[QC];
   __shared__ double red[QT];
   const int l = blockIdx.x;
   const int w = blockIdx.y;
@@ -54,6 +56,7 @@ k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __rest
       for (int e = threadIdx.x; e < QC; e += QT) {
         int q = qb + e;
         us[e] = (q < N_k) ? wk2[q] * Pw[q] : 0.0;
+        usf[e] = (float)us[e];
       }
       __syncthreads();
       if (active && p < npair) {
@@ -62,13 +65,18 @@ k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __rest
         int qs = (ngroups > 1) ? group : 0;
         int qstep = (ngroups > 1) ? ngroups : 1;
         if (sizeof(T) == 4) {
-          // FP32 products and partial sums of 32 points, FP64 total
+          // FP32 products, compensated FP32 partial sums of 32 points, FP64 total
           for (int c0 = qs * 32; c0 < QC; c0 += qstep * 32) {
-            float part = 0.0f;
+            float sum = 0.0f, comp = 0.0f;
 #pragma unroll 8
-            for (int qq = c0; qq < c0 + 32; ++qq)
-              part = fmaf((float)di[qq] * (float)us[qq], (float)dj[qq], part);
-            acc += (double)part;
+            for (int qq = c0; qq < c0 + 32; ++qq) {
+              const float t = ((float)di[qq] * usf[qq]) * (float)dj[qq];
+              const float sn = sum + t;
+              const float bp = sn - sum;
+              comp += (sum - (sn - bp)) + (t - bp);
+              sum = sn;
+            }
+            acc += (double)sum + (double)comp;
           }
         } else {
           for (int qq = qs; qq < QC; qq += qstep)

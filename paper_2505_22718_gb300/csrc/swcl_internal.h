@@ -20,11 +20,14 @@ struct DevBuf {
 
 // Per-precision operand tables for the tensor-core contraction.
 struct TcTables {
-  bool ready = false;
-  DevBuf bfwd;     // forward B operand, per class: [cls][Lpad][Kpad] (hi plane then lo plane(s))
-  DevBuf bvjp;     // transposed operand for the VJP, per class: [cls][Kpad_rows][Lk]
-  DevBuf phase32;  // float2 phase table [N_k][n_h]
-  int Lpad = 0, Kpad = 0, Lk = 0, nsplit = 0;
+  bool ready = false;      // forward operand tables built for the current grids/tracers
+  bool adj_ready = false;  // VJP operand tables built
+  DevBuf bfwd;      // forward B image [cls][l tile][K-block][plane][NT x 128 B]
+  DevBuf bvjp;      // VJP B image [cls][column tile][K-block][plane][128 x 128 B]
+  DevBuf phase32;   // float2 phase table [n_h][N_k] (transposed)
+  DevBuf tile_alo;  // [n_qt] first knot touched by each 128-point k tile
+  DevBuf knot_qt;   // [N_I][2] first/last k tile touching each knot
+  int R = 0;        // knot slots per k tile
 };
 
 // a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
@@ -64,7 +67,9 @@ struct swcl_ctx {
   swcl::DevBuf d_psi;                         // [N_tr][n_h] cplx  T_c chi_min^{-i eta}/N
   swcl::DevBuf d_gtab;                        // [n_cls][N_ell][n_h] cplx  w_n pi(l) M_{l,n}
   swcl::DevBuf d_kpow;                        // [N_tr][N_k] k^{t-1-b}
-  swcl::TcTables tc[3];
+  swcl::TcTables tc[4];
+  swcl::DevBuf tc_lw32;                       // [N_k][4] float interpolation weights
+  swcl::DevBuf tc_kpow32;                     // [N_tr][N_k] float k^{t-1-b}
 
   // windows / power
   int n_walk = 0;
@@ -87,6 +92,8 @@ struct swcl_ctx {
   swcl::DevBuf ws_Cbar;      // [n_walk][N_ell][N_tr][N_tr] double, symmetrised, zero off-list
   swcl::DevBuf ws_outP, ws_outA, ws_outW;   // device staging of VJP outputs
   swcl::DevBuf ws_status;    // device status word(s)
+  swcl::DevBuf ws_aimg;      // VJP: split Dbar image (tensor-core A operand)
+  swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   int last_fwd_precision = -1;
 
   // per-kernel timing (swcl_profile_*)
@@ -132,6 +139,12 @@ cudaError_t launch_fftlog_fwd(cplx* coef, const double* W, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
                               cudaStream_t s);
+// same coefficients as double-float pairs (re_hi, im_hi, re_lo, im_lo), the input of the
+// tensor-core contraction
+cudaError_t launch_fftlog_fwd_df(float4* coef, const double* W, const double* chipow,
+                                  const double* D, const double* B, const cplx* psi,
+                                  const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
+                                  cudaStream_t s);
 // adjoint: W_bar[w][i][m] = chipow_i[m] sum_a D_a[m] B_ia[m] Re sum_n conj(psi_n) cbar_n e^{+2pi i n m/N}
 cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
