@@ -53,10 +53,10 @@ def load_peaks():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "3xtf32", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x9", choices=["fp64", "3xtf32", "tf32x6", "bf16x9"])
     ap.add_argument("--walkers", type=int, default=1, help="parameter points per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -110,9 +110,9 @@ def roofline(stats, w, walkers, precision, peaks, src):
     if flops is None:
         return {"kernel": name, "bound": None, "avg_ms": ms / launches, "note": "no algorithmic count"}
     if bound == "tensor":
-        products = 3 if precision == "3xtf32" else 6
+        products = {"3xtf32": 3, "tf32x6": 6, "bf16x9": 9}[precision]
         tflops = flops * products / avg_s / 1e12
-        if precision == "3xtf32":
+        if precision != "bf16x9":
             peak = peaks["bf16_tflops"] * TF32_OVER_BF16
             unit_note = "tf32 peak = measured bf16 burst x nominal tf32/bf16 ratio"
         else:
@@ -408,8 +408,10 @@ def main():
                 floor = 1e-3 * np.sqrt(dg[:, :, None] * dg[:, None, :])
                 acc = {"max_norm_err_vs_oracle": float(np.max(np.abs(C0 - Co) / np.maximum(np.abs(Co), floor))),
                        "gate": 1e-10 if args.precision == "fp64" else 1e-4}
-        dtype = {"fp64": "f64", "3xtf32": "tf32x3 (f32 accumulate) + f64 FFT/k-sum",
-                 "bf16x6": "bf16x6 (f32 accumulate) + f64 FFT/k-sum"}[args.precision]
+        dtype = {"fp64": "f64",
+                 "3xtf32": "tf32x3 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum",
+                 "tf32x6": "tf32x6 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum",
+                 "bf16x9": "bf16x9 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum"}[args.precision]
         line = {"metric": METRIC, "value": out["value"], "unit": "evals/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,

@@ -244,7 +244,7 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_D, &c->d_B, &c->d_P, &c->d_amp, &c->d_off, &c->d_idx, &c->ws_coef,
                     &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar, &c->ws_Cbar,
                     &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status, &c->tc_lw32,
-                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart};
+                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -590,6 +590,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                          c->ragged ? (const int*)c->d_off.p : nullptr,
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
                                          N_ell, n_out, c->stream), "unpack cotangent");
+  SWCL_TRY(swcl::ensure(c, c->ws_pbpart, swcl::delta_bar_scratch_bytes(nw, N_k, N_ell)));
   double* Pb = P_bar && swcl::is_device_ptr(P_bar) ? P_bar : (double*)c->ws_outP.p;
   double* Ab = amp_bar && swcl::is_device_ptr(amp_bar) ? amp_bar : (double*)c->ws_outA.p;
   if (fp64) {
@@ -598,14 +599,16 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                   (const double*)c->ws_Cbar.p,
                                                   (const double*)c->d_amp.p, (const double*)c->d_P.p,
                                                   (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
-                                                  c->stream), "delta_bar fp64");
+                                                  (double*)c->ws_pbpart.p, c->stream), "delta_bar fp64");
+    ++c->last_launches;  // the P_bar chunk reduction
   } else {
     SWCL_LAUNCH(c, swcl::launch_delta_bar<float>((float*)c->ws_dbar.p, Pb,
                                                  (const float*)c->ws_delta.p,
                                                  (const double*)c->ws_Cbar.p,
                                                  (const double*)c->d_amp.p, (const double*)c->d_P.p,
                                                  (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
-                                                 c->stream), "delta_bar f32");
+                                                 (double*)c->ws_pbpart.p, c->stream), "delta_bar f32");
+    ++c->last_launches;  // the P_bar chunk reduction
   }
   SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
                                       (const double*)c->d_amp.p, nw, N_tr, N_ell, c->stream),

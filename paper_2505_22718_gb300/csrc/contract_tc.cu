@@ -9,8 +9,9 @@
 // for every k point and would not average out in the k-sum, stays below 2^-44; the interpolation
 // and phase product run in FP32 (errors that vary from k point to k point) and the FP32 result
 // is split exactly into tf32/bf16 planes.  Warp roles: warps 0-7 form A in shared memory (interpolation, phase,
-// split) and later drain the accumulator; thread 0 also streams the pre-split B image with
-// cp.async.bulk; warp 8 owns TMEM and one of its threads issues tcgen05.mma.  All waits are
+// split) and drain the accumulator; thread 0 also streams the pre-split B image with
+// cp.async.bulk and, once all warps have handed over a K-block, issues its tcgen05.mma
+// instructions; warp 0 owns the TMEM allocation.  All waits are
 // bounded; a timeout raises a status word the host reports as SWCL_ERR_TIMEOUT.
 #include <algorithm>
 
@@ -23,11 +24,13 @@ namespace {
 using namespace tc;
 
 constexpr int kProducers = 256;
-constexpr int kThreadsTc = kProducers + 32;
+constexpr int kThreadsTc = kProducers;   // two warpgroups: the full register file is available
+
+constexpr uint32_t kCoefSmem = 16 * 1024;   // staged knot coefficients of one K-block
 
 struct SmemLayout {
   int stages;
-  uint32_t stage_bytes, a_bytes, b_plane_bytes, bar_off, total;
+  uint32_t stage_bytes, a_bytes, b_plane_bytes, coef_off, bar_off, total;
 };
 
 template <class P>
@@ -37,7 +40,8 @@ __host__ __device__ inline SmemLayout smem_layout(int NT, int stages) {
   s.a_bytes = P::kPlanesA * kPlaneA;
   s.b_plane_bytes = NT * kRowBytes;
   s.stage_bytes = s.a_bytes + P::kPlanesB * s.b_plane_bytes;
-  s.bar_off = stages * s.stage_bytes;
+  s.coef_off = stages * s.stage_bytes;
+  s.bar_off = s.coef_off + kCoefSmem;
   s.total = s.bar_off + 8 * (3 * stages + 5) + 16 + 1024;  // barriers, tmem slot, abort, align
   return s;
 }
@@ -124,7 +128,7 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 8) tmem_alloc(smem_u32(tmem_slot), tmem_cols);
+  if (warp == 0) tmem_alloc(smem_u32(tmem_slot), tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -135,7 +139,7 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
   const uint32_t b_bytes = P::kPlanesB * L.b_plane_bytes;
   const uint8_t* bsrc = bimg + (size_t)(cls * n_lt + lt) * n_kb * b_bytes;
 
-  if (warp < 8) {
+  {
     // ------------------------------------------------------------ producers ----
     // Each thread also owns one accumulator row (k point) and half of the multipole columns:
     // after every K-block it adds the tensor core's short partial sums (one K-block each,
@@ -151,6 +155,52 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
     for (int t = 0; t < 64; ++t) acc[t] = 0.0f;
     int last_round[4] = {-1, -1, -1, -1};   // thread 0: last round whose B copy was issued
     const float4* cf = coefdf + (size_t)wi * N_I * n_h;
+
+    // Formation: thread tid forms row prow (fixed) and the 16-byte chunks phalf, phalf+2, ...
+    const int prow = tid & (kMTile - 1);
+    const int phalf = tid >> 7;
+    const int pq = q0 + prow;
+    const bool plive = pq < N_k;
+    int jq = 0, rmax = 0;
+    float wr[4] = {0.f, 0.f, 0.f, 0.f};
+    if (plive) {
+      jq = j0[pq];
+      const float4 wq = *reinterpret_cast<const float4*>(lw32 + (size_t)pq * 4);
+      wr[0] = wq.x; wr[1] = wq.y; wr[2] = wq.z; wr[3] = wq.w;
+      rmax = min(4, N_I - jq);
+    }
+    // The knots this tile touches are staged in shared memory once per K-block (every row of a
+    // warp reads the same few knots); the loads of K-block kb+1 (knots and phases) are issued
+    // into registers right after K-block kb is handed to the tensor core.  A tile spanning too many knots reads them from global memory.
+    const int a_lo = j0[q0];
+    const int a_hi = min(N_I - 1, j0[min(q0 + kMTile, N_k) - 1] + 3);
+    const int span = a_hi - a_lo + 1;
+    const bool staged = span * CPK * 16 <= (int)kCoefSmem;
+    float4* Cs = reinterpret_cast<float4*>(base + L.coef_off);
+    float4 cpre[4];
+    float2 epre[4 * 4];
+    auto prefetch = [&](int kbn) {
+      if (staged) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = tid + kProducers * u;
+          cpre[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e < span * CPK) {
+            const int kn = e / CPK, off = e - kn * CPK;
+            const int n = kbn * CPK + off;
+            if (n < n_h) cpre[u] = cf[(size_t)(a_lo + kn) * n_h + n];
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int cc = 0; cc < CPC; ++cc) {
+          const int n = kbn * CPK + (phalf + 2 * c) * CPC + cc;
+          epre[c * CPC + cc] = (plive && n < n_h) ? phaseT[(size_t)n * N_k + pq] : make_float2(0.f, 0.f);
+        }
+    };
+    prefetch(0);
 
     auto drain = [&](int kd) -> bool {
       const int b = kd & 1;
@@ -172,97 +222,16 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
       return true;
     };
 
-    bool ok = true;
-    for (int kb = 0; kb < n_kb && ok; ++kb) {
-      const int s = kb % S;
-      const int r = kb / S;
-      uint8_t* st = base + s * L.stage_bytes;
-      if (r > 0 && !mbar_wait(smem_u32(&bars[2 * S + s]), (r - 1) & 1, abort_flag)) { ok = false; break; }
-      if (tid == 0) {
-        mbar_arrive_tx(smem_u32(&bars[S + s]), b_bytes);
-        bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)kb * b_bytes, b_bytes,
-                 smem_u32(&bars[S + s]));
-        last_round[s] = r;
-      }
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
-        const int id = tid + kProducers * c;
-        const int row = id & (kMTile - 1);
-        const int chunk = id >> 7;           // 0..7: 16-byte column of the 128-byte row
-        const int q = q0 + row;
-        float v[2 * 4];
-#pragma unroll
-        for (int t = 0; t < 2 * CPC; ++t) v[t] = 0.0f;
-        if (q < N_k) {
-          const int jq = j0[q];
-          const float4 wq = *reinterpret_cast<const float4*>(lw32 + (size_t)q * 4);
-          const float wr[4] = {wq.x, wq.y, wq.z, wq.w};
-          const int rmax = min(4, N_I - jq);
-#pragma unroll
-          for (int cc = 0; cc < CPC; ++cc) {
-            const int n = kb * CPK + chunk * CPC + cc;
-            if (n < n_h) {
-              // sum_r lw_r (c_hi + c_lo): low parts first, then the high parts
-              float4 cv[4];
-#pragma unroll
-              for (int rr = 0; rr < 4; ++rr)
-                cv[rr] = rr < rmax ? cf[(size_t)(jq + rr) * n_h + n] : make_float4(0.f, 0.f, 0.f, 0.f);
-              float xr = 0.0f, xi = 0.0f;
-#pragma unroll
-              for (int rr = 0; rr < 4; ++rr) {
-                xr = fmaf(wr[rr], cv[rr].z, xr);
-                xi = fmaf(wr[rr], cv[rr].w, xi);
-              }
-#pragma unroll
-              for (int rr = 0; rr < 4; ++rr) {
-                xr = fmaf(wr[rr], cv[rr].x, xr);
-                xi = fmaf(wr[rr], cv[rr].y, xi);
-              }
-              const float2 e = phaseT[(size_t)n * N_k + q];
-              v[2 * cc] = fmaf(xr, e.x, -xi * e.y);
-              v[2 * cc + 1] = fmaf(xr, e.y, xi * e.x);
-            }
-          }
-        }
-        store_split<P>(st, core_offset(row, chunk * 16), v);
-      }
-      fence_proxy_async();
-      mbar_arrive(smem_u32(&bars[s]));
-      if (kb >= 1 && !drain(kb - 1)) ok = false;
-    }
-    if (ok) ok = drain(n_kb - 1);
-    // ----------------------------------------------------------- epilogue ----
-    const int q = q0 + row_acc;
-    if (ok && q < N_k) {
-      const float kp = kpow32[(size_t)i * N_k + q];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c < my_chunks) {
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int l = l0 + (c_begin + c) * 16 + t;
-            if (l < N_ell) delta[(((size_t)w * N_ell + l) * N_tr + i) * N_k + q] = kp * acc[c * 16 + t];
-          }
-        }
-      }
-    }
-    if (tid == 0 && *abort_flag) {
-      // bulk copies still in flight after an abort land before the CTA exits
-      for (int s = 0; s < S; ++s)
-        if (last_round[s] >= 0) mbar_wait_drain(smem_u32(&bars[S + s]), last_round[s] & 1);
-      atomicExch(status, 1);
-    }
-  } else if (lane == 0) {
-    // ---------------------------------------------------------------- MMA ----
-    const uint32_t idesc = P::idesc(kMTile, NT);
-    for (int kb = 0; kb < n_kb; ++kb) {
+    // tcgen05.mma for K-block kb, issued by thread 0 once all producers have handed it over
+    auto issue = [&](int kb) -> bool {
       const int s = kb % S;
       const int r = kb / S;
       const int b = kb & 1;
-      if (kb >= 2 && !mbar_wait(smem_u32(&accempty[b]), ((kb >> 1) - 1) & 1, abort_flag)) break;
-      if (!mbar_wait(smem_u32(&bars[s]), r & 1, abort_flag)) break;
-      if (!mbar_wait(smem_u32(&bars[S + s]), r & 1, abort_flag)) break;
+      if (kb >= 2 && !mbar_wait(smem_u32(&accempty[b]), ((kb >> 1) - 1) & 1, abort_flag)) return false;
+      if (!mbar_wait(smem_u32(&bars[s]), r & 1, abort_flag)) return false;
+      if (!mbar_wait(smem_u32(&bars[S + s]), r & 1, abort_flag)) return false;
       tc_fence_after();
+      const uint32_t idesc = P::idesc(kMTile, NT);
       const uint32_t a0 = smem_u32(base + s * L.stage_bytes);
       const uint32_t b0 = a0 + L.a_bytes;
       const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
@@ -282,14 +251,112 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
       }
       mma_commit(smem_u32(&bars[2 * S + s]));
       mma_commit(smem_u32(&accfull[b]));
+      return true;
+    };
+
+    // After a failed (timed-out) wait a thread skips all remaining work but still executes every
+    // named barrier of the loop, so no thread is left waiting on a barrier that cannot complete.
+    bool ok = true;
+    for (int kb = 0; kb < n_kb; ++kb) {
+      const int s = kb % S;
+      const int r = kb / S;
+      uint8_t* st = base + s * L.stage_bytes;
+      if (staged) {
+        // every producer has finished reading the previous K-block's knots
+        asm volatile("bar.sync 1, %0;" ::"r"(kProducers) : "memory");
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = tid + kProducers * u;
+          if (ok && e < span * CPK) Cs[e] = cpre[u];
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kProducers) : "memory");
+      }
+      if (!ok) continue;
+      if (r > 0 && !mbar_wait(smem_u32(&bars[2 * S + s]), (r - 1) & 1, abort_flag)) { ok = false; continue; }
+      if (tid == 0) {
+        mbar_arrive_tx(smem_u32(&bars[S + s]), b_bytes);
+        bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)kb * b_bytes, b_bytes,
+                 smem_u32(&bars[S + s]));
+        last_round[s] = r;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int chunk = phalf + 2 * c;     // 0..7: 16-byte column of the 128-byte row
+        float v[2 * 4];
+#pragma unroll
+        for (int t = 0; t < 2 * CPC; ++t) v[t] = 0.0f;
+        if (plive) {
+#pragma unroll
+          for (int cc = 0; cc < CPC; ++cc) {
+            const int nl = chunk * CPC + cc;
+            const int n = kb * CPK + nl;
+            if (n < n_h) {
+              // sum_r lw_r (c_hi + c_lo): low parts first, then the high parts
+              float4 cv[4];
+#pragma unroll
+              for (int rr = 0; rr < 4; ++rr) {
+                if (rr < rmax)
+                  cv[rr] = staged ? Cs[(jq - a_lo + rr) * CPK + nl] : cf[(size_t)(jq + rr) * n_h + n];
+                else
+                  cv[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+              float xr = 0.0f, xi = 0.0f;
+#pragma unroll
+              for (int rr = 0; rr < 4; ++rr) {
+                xr = fmaf(wr[rr], cv[rr].z, xr);
+                xi = fmaf(wr[rr], cv[rr].w, xi);
+              }
+#pragma unroll
+              for (int rr = 0; rr < 4; ++rr) {
+                xr = fmaf(wr[rr], cv[rr].x, xr);
+                xi = fmaf(wr[rr], cv[rr].y, xi);
+              }
+              const float2 e = epre[c * CPC + cc];
+              v[2 * cc] = fmaf(xr, e.x, -xi * e.y);
+              v[2 * cc + 1] = fmaf(xr, e.y, xi * e.x);
+            }
+          }
+        }
+        store_split<P>(st, core_offset(prow, chunk * 16), v);
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&bars[s]));
+      if (tid == 0 && !issue(kb)) ok = false;
+      // next K-block's knots and phases: in flight during the drain and the barrier waits
+      if (kb + 1 < n_kb) prefetch(kb + 1);
+      if (kb >= 1 && !drain(kb - 1)) ok = false;
     }
-    mma_commit(smem_u32(done));
-    // every issued MMA has completed before TMEM is released
-    mbar_wait_drain(smem_u32(done), 0);
+    if (ok) ok = drain(n_kb - 1);
+    // ----------------------------------------------------------- epilogue ----
+    const int q = q0 + row_acc;
+    if (ok && q < N_k) {
+      const float kp = kpow32[(size_t)i * N_k + q];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < my_chunks) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int l = l0 + (c_begin + c) * 16 + t;
+            if (l < N_ell) delta[(((size_t)w * N_ell + l) * N_tr + i) * N_k + q] = kp * acc[c * 16 + t];
+          }
+        }
+      }
+    }
+    if (tid == 0) {
+      // every issued MMA has completed before TMEM is released
+      mma_commit(smem_u32(done));
+      mbar_wait_drain(smem_u32(done), 0);
+      if (*abort_flag) {
+        // bulk copies still in flight after an abort land before the CTA exits
+        for (int s = 0; s < S; ++s)
+          if (last_round[s] >= 0) mbar_wait_drain(smem_u32(&bars[S + s]), last_round[s] & 1);
+        atomicExch(status, 1);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, tmem_cols);
   }

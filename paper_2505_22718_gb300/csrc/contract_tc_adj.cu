@@ -142,8 +142,9 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
     }
     // ---------------------------------------------------------------- epilogue ----
     // all MMAs are complete (last drain) and every stage has been consumed: reuse stage memory
-    float2* V = reinterpret_cast<float2*>(base);                       // [128 rows][64]
-    int* tj0 = reinterpret_cast<int*>(base + kMTile * 64 * sizeof(float2));
+    constexpr int VS = kMTile + 1;                                    // padded row stride
+    float2* V = reinterpret_cast<float2*>(base);                       // [64 columns][VS]
+    int* tj0 = reinterpret_cast<int*>(base + 64 * VS * sizeof(float2));
     float4* tlw = reinterpret_cast<float4*>(tj0 + kMTile);
     asm volatile("bar.sync 1, %0;" ::"r"(kWarps * 32) : "memory");
     {
@@ -162,7 +163,7 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
             const float2 e = phaseT[(size_t)n * N_k + q];
             v = make_float2(fmaf(xr, e.x, xi * e.y), fmaf(xi, e.x, -xr * e.y));   // X conj(E)
           }
-          V[row_acc * 64 + m] = v;
+          V[m * VS + row_acc] = v;
         }
       }
       if (half == 0) {
@@ -184,17 +185,21 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
         const int n = ct * (kCT / 2) + m;
         if (n >= n_h) continue;
         float sr = 0.f, si = 0.f;
-        for (int r = 0; r < kMTile; ++r) {
+        // first row whose stencil can hold knot a (j0 >= a - 3; j0 is nondecreasing in q)
+        int lo = 0, hi = kMTile;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (tj0[mid] < a - 3) lo = mid + 1; else hi = mid;
+        }
+        for (int r = lo; r < kMTile; ++r) {
           const int jr = tj0[r];
-          if (jr > a) break;                 // j0 is nondecreasing in q
+          if (jr > a) break;
           const int d = a - jr;
-          if (d <= 3) {
-            const float4 lw = tlw[r];
-            const float l = d == 0 ? lw.x : d == 1 ? lw.y : d == 2 ? lw.z : lw.w;
-            const float2 v = V[r * 64 + m];
-            sr = fmaf(l, v.x, sr);
-            si = fmaf(l, v.y, si);
-          }
+          const float4 lw = tlw[r];
+          const float l = d == 0 ? lw.x : d == 1 ? lw.y : d == 2 ? lw.z : lw.w;
+          const float2 v = V[m * VS + r];
+          sr = fmaf(l, v.x, sr);
+          si = fmaf(l, v.y, si);
         }
         out[(size_t)ka * n_h + n] = make_float2(sr, si);
       }
@@ -409,7 +414,7 @@ int run_adjoint(swcl_ctx* c, int precision) {
   AdjLayout L = adj_layout<P>(stages);
   while (stages > 2 && L.total > 227 * 1024) L = adj_layout<P>(--stages);
   if (L.total > 227 * 1024) return fail(c, SWCL_ERR_UNSUPPORTED, "VJP tile does not fit shared memory");
-  if (L.total < (uint32_t)(kMTile * 64 * sizeof(float2) + kMTile * (sizeof(int) + sizeof(float4)) + 1024))
+  if (L.total < (uint32_t)(64 * (kMTile + 1) * sizeof(float2) + kMTile * (sizeof(int) + sizeof(float4)) + 1024))
     return fail(c, SWCL_ERR_UNSUPPORTED, "VJP epilogue staging does not fit");
   cudaError_t e = cudaFuncSetAttribute(k_contract_tc_adj<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);

@@ -175,42 +175,71 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
   if (threadIdx.x == 0) abar[(size_t)w * N_tr + i] = 2.0 * red[0];
 }
 
-// One thread per (walker, k point); loop over multipoles with S_l staged in shared memory.
+// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, chunk of LC multipoles,
+// walker); one thread per k point.  S_l A_j is staged per multipole chunk in shared memory (in the
+// arithmetic type T: FP32 for the mixed paths, FP64 for the FP64 path), Delta_j(l, q) in a
+// per-thread shared column.  The P_bar partial of each multipole chunk is a compensated sum
+// (TwoSum) written as FP64 to pbar_part[chunk][w][q]; k_pbar_reduce adds the chunks.
 constexpr int DT = 128;
+constexpr int LC = 8;
+
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {
+  const T sn = s + x;
+  const T bp = sn - s;
+  c += (s - (sn - bp)) + (x - bp);
+  s = sn;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(DT)
-k_delta_bar(T* __restrict__ dbar, double* __restrict__ Pbar, const T* __restrict__ delta,
+k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __restrict__ delta,
             const double* __restrict__ Cf, const double* __restrict__ amp,
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
-            int N_ell) {
-  extern __shared__ double dsm[];
-  double* S = dsm;                        // [N_tr][N_tr]  S_ij A_j
-  double* Dl = dsm + N_tr * N_tr;         // [N_tr][DT]
-  const int w = blockIdx.y;
+            int N_ell, int n_walk) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* S = reinterpret_cast<T*>(dsm_raw);            // [LC][N_tr][N_tr]  S_ij A_j
+  T* Dl = S + LC * N_tr * N_tr;                    // [N_tr][DT]
+  const int w = blockIdx.z;
+  const int lc = blockIdx.y;
   const int q = blockIdx.x * DT + threadIdx.x;
+  const int l0 = lc * LC;
+  const int nl = min(LC, N_ell - l0);
   const double* A = amp + (size_t)w * N_tr;
-  const double uq = (q < N_k) ? wk2[q] * P[(size_t)w * N_k + q] : 0.0;
-  double pacc = 0.0;
-  for (int l = 0; l < N_ell; ++l) {
+  for (int e = threadIdx.x; e < nl * N_tr * N_tr; e += DT) {
+    const int ll = e / (N_tr * N_tr), r = e - ll * N_tr * N_tr;
+    S[e] = (T)(Cf[((size_t)w * N_ell + l0 + ll) * N_tr * N_tr + r] * A[r % N_tr]);
+  }
+  const T two_u = (q < N_k) ? (T)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : T(0);
+  T ps = 0, pc = 0;
+  for (int ll = 0; ll < nl; ++ll) {
     __syncthreads();
-    const double* cf = Cf + ((size_t)w * N_ell + l) * N_tr * N_tr;
-    for (int e = threadIdx.x; e < N_tr * N_tr; e += DT) S[e] = cf[e] * A[e % N_tr];
-    const T* dl = delta + ((size_t)w * N_ell + l) * N_tr * N_k;
+    const T* dl = delta + ((size_t)w * N_ell + l0 + ll) * N_tr * N_k;
     for (int t = 0; t < N_tr; ++t)
-      Dl[t * DT + threadIdx.x] = (q < N_k) ? (double)dl[(size_t)t * N_k + q] : 0.0;
+      Dl[t * DT + threadIdx.x] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
     __syncthreads();
     if (q < N_k) {
-      T* db = dbar + ((size_t)w * N_ell + l) * N_tr * N_k;
+      const T* Sl = S + ll * N_tr * N_tr;
+      T* db = dbar + ((size_t)w * N_ell + l0 + ll) * N_tr * N_k;
       for (int ii = 0; ii < N_tr; ++ii) {
-        double t = 0.0;
-        for (int j = 0; j < N_tr; ++j) t = fma(S[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
-        pacc = fma(A[ii] * Dl[ii * DT + threadIdx.x], t, pacc);
-        db[(size_t)ii * N_k + q] = (T)(2.0 * A[ii] * uq * t);
+        T t = 0;
+        for (int j = 0; j < N_tr; ++j) t = fma(Sl[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
+        const T ai = (T)A[ii];
+        two_sum_acc(ps, pc, ai * Dl[ii * DT + threadIdx.x] * t);
+        db[(size_t)ii * N_k + q] = two_u * ai * t;
       }
     }
   }
-  if (q < N_k) Pbar[(size_t)w * N_k + q] = wk2[q] * pacc;
+  if (q < N_k) pbar_part[((size_t)lc * n_walk + w) * N_k + q] = (double)ps + (double)pc;
+}
+
+__global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restrict__ part,
+                              const double* __restrict__ wk2, int n_chunk, int n_walk, int N_k) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n_walk * N_k) return;
+  double s = 0.0;
+  for (int c = 0; c < n_chunk; ++c) s += part[(size_t)c * n_walk * N_k + t];
+  Pbar[t] = wk2[t % N_k] * s;
 }
 
 }  // namespace
@@ -267,23 +296,32 @@ cudaError_t launch_amp_bar(double* amp_bar, const double* Cf, const double* U, c
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cf,
                              const double* amp, const double* P, const double* wk2, int n_walk,
-                             int N_tr, int N_k, int N_ell, cudaStream_t s) {
-  size_t smem = (size_t)(N_tr * N_tr + N_tr * DT) * sizeof(double);
+                             int N_tr, int N_k, int N_ell, double* scratch, cudaStream_t s) {
+  const size_t smem = (size_t)(LC * N_tr * N_tr + N_tr * DT) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 g((N_k + DT - 1) / DT, n_walk);
-  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, P_bar, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell);
+  const int n_chunk = (N_ell + LC - 1) / LC;
+  dim3 g((N_k + DT - 1) / DT, n_chunk, n_walk);
+  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell, n_walk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long n = (long)n_walk * N_k;
+  k_pbar_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P_bar, scratch, wk2, n_chunk, n_walk, N_k);
   return cudaGetLastError();
+}
+
+size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell) {
+  return sizeof(double) * (size_t)((N_ell + LC - 1) / LC) * n_walk * N_k;
 }
 
 template cudaError_t launch_delta_bar<double>(double*, double*, const double*, const double*,
                                               const double*, const double*, const double*, int,
-                                              int, int, int, cudaStream_t);
+                                              int, int, int, double*, cudaStream_t);
 template cudaError_t launch_delta_bar<float>(float*, double*, const float*, const double*,
                                              const double*, const double*, const double*, int,
-                                             int, int, int, cudaStream_t);
+                                             int, int, int, double*, cudaStream_t);
 
 }  // namespace swcl

@@ -94,6 +94,7 @@ struct swcl_ctx {
   swcl::DevBuf ws_status;    // device status word(s)
   swcl::DevBuf ws_aimg;      // VJP: split Dbar image (tensor-core A operand)
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
+  swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
   int last_fwd_precision = -1;
 
   // per-kernel timing (swcl_profile_*)
@@ -178,7 +179,8 @@ cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const doubl
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cbar_full,
                              const double* amp, const double* P, const double* wk2, int n_walk,
-                             int N_tr, int N_k, int N_ell, cudaStream_t s);
+                             int N_tr, int N_k, int N_ell, double* scratch, cudaStream_t s);
+size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
 
 // a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
 int compute_delta_tc(swcl_ctx* c, int precision);
