@@ -121,6 +121,18 @@ int swcl_compute_cl(swcl_ctx* ctx, int precision, double* C_out);
 int swcl_vjp(swcl_ctx* ctx, int precision, const double* C_bar,
              double* P_bar, double* amp_bar, double* W_bar);
 
+/* Batched evaluation as one CUDA-graph replay.  Runs swcl_compute_cl for every walker and, when
+ * C_bar is not NULL, swcl_vjp with the given outputs (P_bar, amp_bar, W_bar may be NULL), with all
+ * of their kernels captured once into a CUDA graph on the context's stream and replayed on later
+ * calls with the same arguments, precision and sizes.  Walkers, their parameter arrays and
+ * ragged multipole lists are those of the last swcl_set_* calls (Sec. 4.3 runs many parameter
+ * points of one survey setup; SwiftCl batches them with vmap).  All pointers must be device
+ * pointers of the context's GPU.  The first call of a configuration also runs it once outside
+ * the graph (building tables and buffers) and captures; a change of any set_* size, of the
+ * precision or of a pointer re-captures.  Calls are asynchronous on the context stream. */
+int swcl_compute_batched(swcl_ctx* ctx, int precision, double* C_out, const double* C_bar,
+                         double* P_bar, double* amp_bar, double* W_bar);
+
 /* Per-kernel device timing.  While enabled, every kernel the context launches is bracketed by
  * CUDA events on the context stream (a few microseconds of overhead per launch).
  * swcl_profile_read synchronises the stream and returns, for up to max_entries kernels,

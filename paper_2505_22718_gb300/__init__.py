@@ -13,5 +13,13 @@ from .api import (  # noqa: F401
     swcl_set_power, swcl_set_ell_lists, swcl_compute_cl, swcl_vjp, swcl_sync, swcl_query,
     swcl_profile_enable, swcl_profile_read, swcl_profile_reset, swcl_debug_read,
     SWCL_DBG_COEF, SWCL_DBG_DELTA, SWCL_DBG_GTAB, SWCL_DBG_PHASE, SWCL_DBG_UNIT,
-    swcl_last_error, strerror, swcl_fftlog_noalloc,
+    swcl_last_error, strerror, swcl_fftlog_noalloc, swcl_compute_batched,
 )
+
+
+def __getattr__(name):
+    # the torch wrapper is imported lazily so that the ctypes binding works without torch
+    if name == "AngularPowerSpectrum":
+        from .autograd import AngularPowerSpectrum
+        return AngularPowerSpectrum
+    raise AttributeError(name)

@@ -118,6 +118,16 @@ def swcl_vjp(ctx, precision, C_bar, P_bar=None, amp_bar=None, W_bar=None):
     _check(ctx, _lib.load().swcl_vjp(ctx, precision, pc, *outs))
 
 
+def swcl_compute_batched(ctx, precision, C_out, C_bar=None, P_bar=None, amp_bar=None, W_bar=None):
+    """Forward (+ VJP when C_bar is given) for all walkers as one CUDA-graph replay; device
+    tensors only."""
+    ptrs = []
+    for a in (C_out, C_bar, P_bar, amp_bar, W_bar):
+        p, _k = _ptr(a, np.float64)
+        ptrs.append(p)
+    _check(ctx, _lib.load().swcl_compute_batched(ctx, precision, *ptrs))
+
+
 def swcl_profile_enable(ctx, enable=True):
     _check(ctx, _lib.load().swcl_profile_enable(ctx, 1 if enable else 0))
 

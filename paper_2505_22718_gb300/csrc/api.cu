@@ -38,6 +38,8 @@ int ensure(swcl_ctx* c, DevBuf& b, size_t bytes) {
     b.p = nullptr;
     b.bytes = 0;
   }
+  if (c->capturing)
+    return fail(c, SWCL_ERR_STATE, "device buffer would grow during graph capture");
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -45,6 +47,7 @@ int ensure(swcl_ctx* c, DevBuf& b, size_t bytes) {
   }
   b.bytes = bytes;
   c->held += bytes;
+  ++c->alloc_gen;
   return SWCL_OK;
 }
 
@@ -101,13 +104,13 @@ static cudaEvent_t take_event(swcl_ctx* c) {
 }
 
 void prof_begin(swcl_ctx* c) {
-  if (!c->prof) return;
+  if (!c->prof || c->capturing) return;
   c->ev_open = take_event(c);
   if (c->ev_open) cudaEventRecord(c->ev_open, c->stream);
 }
 
 void prof_end(swcl_ctx* c, const char* name) {
-  if (!c->prof || !c->ev_open) return;
+  if (!c->prof || c->capturing || !c->ev_open) return;
   cudaEvent_t b = take_event(c);
   if (!b) return;
   cudaEventRecord(b, c->stream);
@@ -255,6 +258,7 @@ int swcl_destroy(swcl_ctx* c) {
   }
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SWCL_OK;
@@ -265,6 +269,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   c->err.clear();
+  ++c->alloc_gen;
   if (!(chi_min > 0) || !(chi_max > chi_min) || !std::isfinite(chi_max))
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 0 < chi_min < chi_max");
   if (N < 16 || N > 8192 || (N & (N - 1)))
@@ -327,6 +332,7 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   c->err.clear();
+  ++c->alloc_gen;
   if (!c->have_grids) return swcl::fail(c, SWCL_ERR_STATE, "set_grids first");
   if (N_tr < 1 || N_tr > 64 || !kind || !fft_bias)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 1 <= N_tr <= 64, kind and fft_bias");
@@ -414,6 +420,7 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
     std::vector<double> ones((size_t)c->N_I * N, 1.0);
     SWCL_TRY(swcl::copy_in(c, c->d_D, ones.data(), sizeof(double) * ones.size()));
   }
+  if (c->have_B != (B != nullptr) || c->n_walk != n_walk) ++c->alloc_gen;  // new graph needed
   c->have_B = B != nullptr;
   if (B) SWCL_TRY(swcl::copy_in(c, c->d_B, B, sizeof(double) * (size_t)c->N_tr * c->N_I * N));
   c->n_walk = n_walk;
@@ -431,6 +438,7 @@ int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) 
   if (n_walk < 1 || !P || !amp) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need n_walk >= 1, P, amp");
   if (c->have_windows && c->n_walk != n_walk)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_windows");
+  if (c->n_walk != n_walk) ++c->alloc_gen;
   SWCL_TRY(swcl::copy_in(c, c->d_P, P, sizeof(double) * (size_t)n_walk * c->N_k));
   SWCL_TRY(swcl::copy_in(c, c->d_amp, amp, sizeof(double) * (size_t)n_walk * c->N_tr));
   c->n_walk = n_walk;
@@ -443,6 +451,7 @@ int swcl_set_ell_lists(swcl_ctx* c, const int* offsets, const int* ell_idx) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   c->err.clear();
+  ++c->alloc_gen;
   if (!c->have_windows && !c->have_power)
     return swcl::fail(c, SWCL_ERR_STATE, "set_windows or set_power first (they fix n_walk)");
   if (!offsets) {
@@ -638,6 +647,62 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   }
   if (P_bar) SWCL_TRY(swcl::copy_out(c, P_bar, Pb, sizeof(double) * nw * (size_t)N_k));
   if (amp_bar) SWCL_TRY(swcl::copy_out(c, amp_bar, Ab, sizeof(double) * nrow));
+  return SWCL_OK;
+}
+
+int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double* C_bar,
+                         double* P_bar, double* amp_bar, double* W_bar) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(check_ready(c, precision));
+  const void* ptrs[5] = {C_out, C_bar, P_bar, amp_bar, W_bar};
+  for (const void* p : ptrs)
+    if (p && !swcl::is_device_ptr(p))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "swcl_compute_batched takes device pointers only");
+  if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
+  auto run = [&]() -> int {
+    int st = swcl_compute_cl(c, precision, C_out);
+    if (st == SWCL_OK && C_bar) st = swcl_vjp(c, precision, C_bar, P_bar, amp_bar, W_bar);
+    return st;
+  };
+  bool same = c->graph_exec && c->graph_key.precision == precision &&
+              c->graph_key.alloc_gen == c->alloc_gen;
+  for (int t = 0; t < 5 && same; ++t) same = c->graph_key.ptrs[t] == ptrs[t];
+  if (!same) {
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    // run once outside the graph: builds tables, sizes every buffer
+    SWCL_TRY(run());
+    const int64_t gen = c->alloc_gen;
+    cudaGraph_t graph = nullptr;
+    SWCL_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->capturing = true;
+    const int64_t launches_before = c->last_launches;
+    int st = run();
+    c->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (st != SWCL_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "end capture");
+    (void)launches_before;
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return swcl::cuda_fail(c, e, "graph instantiate");
+    }
+    c->graph_key.precision = precision;
+    c->graph_key.alloc_gen = gen;
+    for (int t = 0; t < 5; ++t) c->graph_key.ptrs[t] = ptrs[t];
+    c->graph_launches = c->last_launches;
+  }
+  SWCL_TRY_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+  c->last_launches = c->graph_launches;
   return SWCL_OK;
 }
 

@@ -97,6 +97,17 @@ struct swcl_ctx {
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
   int last_fwd_precision = -1;
 
+  // CUDA graph of the batched call (swcl_compute_batched)
+  cudaGraphExec_t graph_exec = nullptr;
+  struct GraphKey {
+    int precision = -1;
+    const void* ptrs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t alloc_gen = -1;
+  } graph_key;
+  int64_t alloc_gen = 0;      // bumped whenever a device buffer is (re)allocated or sizes change
+  bool capturing = false;
+  int64_t graph_launches = 0; // kernels in the captured graph
+
   // per-kernel timing (swcl_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
