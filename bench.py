@@ -66,15 +66,19 @@ def parse():
 
 # ------------------------------------------------------------------ inputs ----
 
-def make_inputs(walkers: int, rank: int):
+def make_inputs(walkers: int, rank: int, world: int):
+    """This rank's parameter points: walkers per GPU x world in all (weak scaling), the rank's
+    contiguous block from paper_2505_22718_gb300.sharding.shard."""
     from workloads import make_workload
-    if walkers <= 1 and rank == 0:
+    from paper_2505_22718_gb300.sharding import shard
+    if walkers <= 1 and world == 1:
         w = make_workload("n5k_vjp")
         return w, w.C_bar[None] if w.C_bar.ndim == 3 else w.C_bar
-    w = make_workload("walkers", seed=20250528 + rank, n_walkers=walkers)
+    first, count = shard(walkers * world, world, rank)
+    w = make_workload("walkers", n_walkers=count, first_walker=first)
     w.ell_lists = None  # every walker evaluates the full 103-ell set for the headline metric
-    rng = np.random.default_rng(99 + rank)
-    cbar = rng.standard_normal((walkers, len(w.ells), w.n_tr, w.n_tr))
+    rng = np.random.default_rng([99, first])
+    cbar = rng.standard_normal((count, len(w.ells), w.n_tr, w.n_tr))
     return w, cbar
 
 
@@ -217,11 +221,12 @@ def cpu_baseline(w, cbar, n_eval=2):
 def run_ours(args, rank, world, device):
     import torch
     import paper_2505_22718_gb300 as swcl
+    from paper_2505_22718_gb300.sharding import max_over_ranks
 
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
     prec = swcl.PRECISIONS[args.precision]
-    w, cbar = make_inputs(args.walkers, rank)
+    w, cbar = make_inputs(args.walkers, rank, world)
     nw = n_walk(w)
     # one dedicated stream: the library's kernels, the L2 flush and the timing events are
     # all ordered on it
@@ -285,9 +290,7 @@ def run_ours(args, rank, world, device):
             swcl.swcl_profile_enable(ctx.ptr, False)
         ms = sum(a.elapsed_time(b) for a, b in evs)
         if world > 1:
-            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+            ms = max_over_ranks(ms, dev)
             torch.distributed.barrier()
         return ms, launches, stats
 
@@ -360,9 +363,7 @@ def run_ours(args, rank, world, device):
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         if world > 1:
-            tt = torch.tensor([el], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            el = float(tt.item())
+            el = max_over_ranks(el, dev)
         h2d = sum(x.numel() * 8 for x in (W_h, D_h, P_h, A_h, Cb_h) if x is not None)
         h2d += 0 if B_h is None else B_h.numel() * 8
         d2h = sum(x.numel() * 8 for x in (C_h, Pb_h, Ab_h, Wb_h))
@@ -380,7 +381,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        w, cbar = make_inputs(1, 0)
+        w, cbar = make_inputs(1, 0, 1)
         from oracle import fftlog as O
         g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
         for b in np.unique(w.fft_bias):

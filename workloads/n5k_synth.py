@@ -276,7 +276,7 @@ def window_rows(meta: dict, shifts=None):
     return _windows(cosmo, meta["chi"], meta["gauss"], meta["lens_edges"], shifts)
 
 
-def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256) -> Workload:
+def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256, first_walker: int = 0) -> Workload:
     rng = np.random.default_rng(seed)
     cosmo = Cosmology(0.3)
     if name == "tiny2":
@@ -321,19 +321,24 @@ def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256) -> Work
     meta = dict(omega_m=0.3, chi=chi, gauss=gauss, lens_edges=list(lens_edges))
     A = 3.5e6 * rng.uniform(0.9, 1.1)
     if name == "walkers":
+        # each walker draws from its own stream (seed, global index), so any contiguous block of
+        # walkers (one rank's shard) can be generated on its own
         nw = n_walkers
-        amps = 3.5e6 * rng.uniform(0.9, 1.1, nw)
-        tilts = rng.uniform(0.94, 0.99, nw)
-        biases = rng.uniform(1.0, 2.5, (nw, ng))
-        shifts = rng.uniform(-0.02, 0.02, (nw, ng + nl))
+        amps, tilts, biases, shifts, lists = [], [], [], [], []
+        for wg in range(first_walker, first_walker + nw):
+            r = np.random.default_rng([seed, wg])
+            amps.append(3.5e6 * r.uniform(0.9, 1.1))
+            tilts.append(r.uniform(0.94, 0.99))
+            biases.append(r.uniform(1.0, 2.5, ng))
+            shifts.append(r.uniform(-0.02, 0.02, ng + nl))
+            m = int(r.integers(50, len(ells) + 1))
+            lists.append(np.sort(r.choice(len(ells), size=m, replace=False)).astype(np.int32))
+        amps, tilts = np.array(amps), np.array(tilts)
+        biases, shifts = np.array(biases), np.array(shifts)
         W = np.stack([_windows(cosmo, chi, gauss, lens_edges, shifts[w]) for w in range(nw)])
         P = np.stack([power_spectrum(k, amps[w], tilts[w]) for w in range(nw)])
         amp = np.concatenate([biases, np.ones((nw, nl))], axis=1)
-        lists = []
-        for w in range(nw):
-            m = int(rng.integers(50, len(ells) + 1))
-            lists.append(np.sort(rng.choice(len(ells), size=m, replace=False)).astype(np.int32))
-        meta.update(shifts=shifts, amps=amps, tilts=tilts)
+        meta.update(shifts=shifts, amps=amps, tilts=tilts, first_walker=first_walker)
         return Workload(name, N, CHI_MIN, CHI_MAX, k, ells, knots, kind, fft_bias, W, D, B, P, amp,
                         None, lists, meta)
     W = _windows(cosmo, chi, gauss, lens_edges)
