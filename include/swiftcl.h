@@ -74,6 +74,7 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_Q_RECOMPUTE       2  /* 1 if the VJP recomputes Delta instead of storing it */
 #define SWCL_Q_N_HALF          3  /* N/2 + 1 */
 #define SWCL_Q_KERNEL_LAUNCHES 4  /* kernels launched by the last compute/vjp call */
+#define SWCL_Q_PROFILE_RANK    5  /* rank r of the knot profiles D*B used (0 = one FFT per knot) */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the device memory the
  * context may hold (0 = no bound).  `stream` is a cudaStream_t (NULL = the context creates
@@ -97,7 +98,12 @@ int swcl_set_grids(swcl_ctx* ctx, double chi_min, double chi_max, int N,
 int swcl_set_tracers(swcl_ctx* ctx, int N_tr, const int* kind, const double* fft_bias,
                      const double* taper_chi, const double* taper_c);
 
-/* Windows for n_walk parameter points (n_walk >= 1).  W[n_walk][N_tr][N] window samples on the
+/* Windows for n_walk parameter points (n_walk >= 1).  The FFTLog input of tracer i at knot a is
+ * W_i chi^{s_i - b_i} D_a B_ia; when the knot profiles D_a B_ia are numerically of rank r <= 4
+ * (row residuals below 1e-14 of the largest row after r steps of pivoted Gram-Schmidt), the
+ * library transforms r basis profiles per tracer instead of N_I knots and carries the
+ * interpolation weights through the basis (exact by linearity, up to rounding; set the environment
+ * variable SWCL_PER_KNOT_FFT=1 before creating a context to always transform every knot).  W[n_walk][N_tr][N] window samples on the
  * chi grid; D[N_I][N] growth at the knots (NULL = 1); B[N_tr][N_I][N] k,z-dependent bias at the
  * knots (NULL = 1).  Window samples may differ per walker; D and B are shared. */
 int swcl_set_windows(swcl_ctx* ctx, int n_walk, const double* W, const double* D, const double* B);

@@ -141,9 +141,34 @@ static int prof_flush(swcl_ctx* c) {
   return SWCL_OK;
 }
 
+Stencil stencil(const swcl_ctx* c) {
+  Stencil v;
+  if (c->lr_basis) {
+    v.j0 = (const int*)c->lr_j0.p;
+    v.w = (const double*)c->lr_w.p;
+    v.w_ts = c->have_B ? (long)c->N_k * 4 : 0;
+    v.NI = c->have_B ? 4 : c->lr_true_rank;
+    v.D = c->have_B ? (const double*)c->lr_ones.p : (const double*)c->lr_Q.p;
+    v.B = c->have_B ? (const double*)c->lr_Q.p : nullptr;
+  } else {
+    v.j0 = (const int*)c->d_interp_j0.p;
+    v.w = (const double*)c->d_interp_w.p;
+    v.w_ts = 0;
+    v.NI = c->N_I;
+    v.D = (const double*)c->d_D.p;
+    v.B = c->have_B ? (const double*)c->d_B.p : nullptr;
+  }
+  return v;
+}
+
 }  // namespace swcl
 
 namespace {
+
+__global__ void k_differs(int* flag, const double* a, const double* b, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    if (a[t] != b[t]) { *flag = 1; return; }
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -224,6 +249,8 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
     }
     c->own_stream = true;
   }
+  // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
+  if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
   // device status word raised by bounded waits in the tensor-core kernels
   if (swcl::ensure(c, c->ws_status, 16) != SWCL_OK ||
       cudaMemset(c->ws_status.p, 0, 16) != cudaSuccess) {
@@ -247,7 +274,9 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_D, &c->d_B, &c->d_P, &c->d_amp, &c->d_off, &c->d_idx, &c->ws_coef,
                     &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar, &c->ws_Cbar,
                     &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status, &c->tc_lw32,
-                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart};
+                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
+                    &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
+                    &c->lr_j0, &c->lr_ones};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -290,6 +319,8 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
   for (int l = 0; l < N_ell; ++l)
     if (eh[l] < 0 || eh[l] > 100000) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell out of range");
   c->have_grids = c->have_tracers = c->have_windows = c->have_power = false;
+  c->lr_dirty = true;
+  c->lr_basis = false;
   c->ragged = false;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->N = N;
@@ -366,6 +397,8 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   c->have_tracers = false;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->last_fwd_precision = -1;
+  c->lr_dirty = true;
+  c->lr_basis = false;
   c->N_tr = N_tr;
   c->n_cls = (int)cls.size();
   c->kind_h = kh;
@@ -414,15 +447,41 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_power");
   const int N = c->N;
   SWCL_TRY(swcl::copy_in(c, c->d_W, W, sizeof(double) * (size_t)n_walk * c->N_tr * N));
+  // D and B: the knot profiles are re-factorised (low-rank mode) only when their values change
+  const size_t dn = (size_t)c->N_I * N, bn = B ? (size_t)c->N_tr * c->N_I * N : 0;
+  const bool had_prev = c->have_windows && c->have_B == (B != nullptr) && c->d_D.p &&
+                        c->d_prev.p && c->d_prev.bytes >= sizeof(double) * (dn + bn);
+  if (had_prev) {
+    cudaError_t e = cudaMemcpyAsync(c->d_prev.p, c->d_D.p, sizeof(double) * dn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && bn)
+      e = cudaMemcpyAsync((double*)c->d_prev.p + dn, c->d_B.p, sizeof(double) * bn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "keep previous D");
+  }
   if (D) {
-    SWCL_TRY(swcl::copy_in(c, c->d_D, D, sizeof(double) * (size_t)c->N_I * N));
+    SWCL_TRY(swcl::copy_in(c, c->d_D, D, sizeof(double) * dn));
   } else {
-    std::vector<double> ones((size_t)c->N_I * N, 1.0);
+    std::vector<double> ones(dn, 1.0);
     SWCL_TRY(swcl::copy_in(c, c->d_D, ones.data(), sizeof(double) * ones.size()));
   }
   if (c->have_B != (B != nullptr) || c->n_walk != n_walk) ++c->alloc_gen;  // new graph needed
   c->have_B = B != nullptr;
-  if (B) SWCL_TRY(swcl::copy_in(c, c->d_B, B, sizeof(double) * (size_t)c->N_tr * c->N_I * N));
+  if (B) SWCL_TRY(swcl::copy_in(c, c->d_B, B, sizeof(double) * bn));
+  if (had_prev && !c->lr_dirty) {
+    SWCL_TRY(swcl::ensure(c, c->d_flag, sizeof(int)));
+    int flag = 0;
+    SWCL_TRY_CUDA(c, cudaMemsetAsync(c->d_flag.p, 0, sizeof(int), c->stream), "flag");
+    k_differs<<<152, 256, 0, c->stream>>>((int*)c->d_flag.p, (const double*)c->d_D.p,
+                                           (const double*)c->d_prev.p, (long)dn);
+    if (bn)
+      k_differs<<<152, 256, 0, c->stream>>>((int*)c->d_flag.p, (const double*)c->d_B.p,
+                                             (const double*)c->d_prev.p + dn, (long)bn);
+    SWCL_TRY_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag read");
+    SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "flag sync");
+    if (flag) c->lr_dirty = true;
+  } else {
+    c->lr_dirty = true;
+  }
+  SWCL_TRY(swcl::ensure(c, c->d_prev, sizeof(double) * (dn + bn)));
   c->n_walk = n_walk;
   c->have_windows = true;
   c->last_fwd_precision = -1;
@@ -512,8 +571,14 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   c->err.clear();
   SWCL_TRY(check_ready(c, precision));
   if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
+  if (c->lr_dirty) {
+    if (c->capturing) return swcl::fail(c, SWCL_ERR_STATE, "knot profiles changed during capture");
+    SWCL_TRY(swcl::factor_profiles(c));
+    c->lr_dirty = false;
+  }
   c->last_launches = 0;
-  const int nw = c->n_walk, N_tr = c->N_tr, N_I = c->N_I, n_h = c->n_h, N = c->N;
+  const swcl::Stencil sv = swcl::stencil(c);
+  const int nw = c->n_walk, N_tr = c->N_tr, N_I = sv.NI, n_h = c->n_h, N = c->N;
   const int N_k = c->N_k, N_ell = c->N_ell;
   const size_t nrow = (size_t)nw * N_tr;
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
@@ -522,23 +587,20 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
   if (precision == SWCL_FP64) {
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
-                                           (const double*)c->d_chipow.p, (const double*)c->d_D.p,
-                                           c->have_B ? (const double*)c->d_B.p : nullptr,
+                                           (const double*)c->d_chipow.p, sv.D, sv.B,
                                            (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                            nw, N_tr, N_I, N, c->stream), "fftlog");
     SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
                                               (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
                                               (const int*)c->d_cls_of.p, (const double*)c->d_kpow.p,
-                                              (const int*)c->d_interp_j0.p,
-                                              (const double*)c->d_interp_w.p, nw, N_tr, N_I, n_h,
+                                              sv.j0, sv.w, sv.w_ts, nw, N_tr, N_I, n_h,
                                               N_k, N_ell, c->stream), "contract fp64");
     SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                           (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
                                           N_tr, N_k, N_ell, c->stream), "k-quadrature fp64");
   } else {
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd_df((float4*)c->ws_coef.p, (const double*)c->d_W.p,
-                                               (const double*)c->d_chipow.p, (const double*)c->d_D.p,
-                                               c->have_B ? (const double*)c->d_B.p : nullptr,
+                                               (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
     SWCL_TRY(swcl::compute_delta_tc(c, precision));
@@ -576,7 +638,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   if (c->last_fwd_precision != precision)
     return swcl::fail(c, SWCL_ERR_STATE, "call swcl_compute_cl with the same precision first");
   c->last_launches = 0;
-  const int nw = c->n_walk, N_tr = c->N_tr, N_I = c->N_I, n_h = c->n_h, N = c->N;
+  const swcl::Stencil sv = swcl::stencil(c);
+  const int nw = c->n_walk, N_tr = c->N_tr, N_I = sv.NI, n_h = c->n_h, N = c->N;
   const int N_k = c->N_k, N_ell = c->N_ell;
   const int64_t n_out = out_count(c);
   const size_t nrow = (size_t)nw * N_tr;
@@ -629,8 +692,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                     (const cplx*)c->d_gtab.p,
                                                     (const int*)c->d_cls_of.p,
                                                     (const double*)c->d_kpow.p,
-                                                    (const int*)c->d_interp_j0.p,
-                                                    (const double*)c->d_interp_w.p, nw, N_tr, N_I,
+                                                    sv.j0, sv.w, sv.w_ts, nw, N_tr, N_I,
                                                     n_h, N_k, N_ell, c->stream), "contract adj fp64");
     } else {
       SWCL_TRY(swcl::contract_adj_tc(c, precision));
@@ -638,8 +700,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
     double* scratch = (double*)((char*)c->ws_outW.p + wbytes);
     SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
-                                           (const double*)c->d_chipow.p, (const double*)c->d_D.p,
-                                           c->have_B ? (const double*)c->d_B.p : nullptr,
+                                           (const double*)c->d_chipow.p, sv.D, sv.B,
                                            (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                            nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
     ++c->last_launches;  // the chunk reduction
@@ -770,7 +831,20 @@ int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
   switch (what) {
     case SWCL_DBG_COEF:
       src = c->ws_coef.p; n = 2LL * c->n_walk * c->N_tr * c->N_I * c->n_h;
-      dfpair = c->last_fwd_precision > SWCL_FP64; break;
+      dfpair = c->last_fwd_precision > SWCL_FP64;
+      if (c->lr_basis) {
+        *count = n;
+        if (!out) return SWCL_OK;
+        if (c->last_fwd_precision < 0) return swcl::fail(c, SWCL_ERR_STATE, "no forward pass yet");
+        DevBuf tmp;
+        SWCL_TRY(swcl::ensure(c, tmp, sizeof(double) * n));
+        int st = swcl::expand_basis_coefficients(c, tmp.p, dfpair);
+        if (st == SWCL_OK) st = swcl::copy_out(c, out, tmp.p, sizeof(double) * n);
+        cudaStreamSynchronize(c->stream);
+        swcl::release(c, tmp);
+        return st;
+      }
+      break;
     case SWCL_DBG_DELTA:
       src = c->ws_delta.p; n = (int64_t)c->n_walk * c->N_ell * c->N_tr * c->N_k;
       widen = c->last_fwd_precision != SWCL_FP64; break;
@@ -827,6 +901,7 @@ int swcl_query(swcl_ctx* c, int key, int64_t* value) {
     case SWCL_Q_RECOMPUTE: *value = 0; return SWCL_OK;
     case SWCL_Q_N_HALF: *value = c->n_h; return SWCL_OK;
     case SWCL_Q_KERNEL_LAUNCHES: *value = c->last_launches; return SWCL_OK;
+    case SWCL_Q_PROFILE_RANK: *value = c->lr_basis ? c->lr_true_rank : 0; return SWCL_OK;
     default: return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown query key");
   }
 }

@@ -19,8 +19,8 @@ __global__ void __launch_bounds__(NT)
 k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
                 const cplx* __restrict__ phase, const cplx* __restrict__ gtab,
                 const int* __restrict__ cls_of, const double* __restrict__ kpow,
-                const int* __restrict__ j0, const double* __restrict__ lw, int N_tr, int N_I,
-                int n_h, int N_k, int N_ell) {
+                const int* __restrict__ j0, const double* __restrict__ lw, long lw_ts, int N_tr,
+                int N_I, int n_h, int N_k, int N_ell) {
   __shared__ cplx Xs[BN][BQ + 1];
   __shared__ cplx Gs[BN][BL + 1];
   const int q0 = blockIdx.x * BQ;
@@ -30,6 +30,7 @@ k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
   const int w = wi / N_tr;
   const cplx* cf = coef + (size_t)wi * N_I * n_h;
   const cplx* G = gtab + (size_t)cls_of[i] * N_ell * n_h;
+  lw += (size_t)i * lw_ts;
   const int tq = threadIdx.x & 15;   // 4 consecutive q
   const int tl = threadIdx.x >> 4;   // 8 multipoles strided by 16
   double acc[4][8];
@@ -51,7 +52,7 @@ k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           double wr = wq[r];
-          if (wr != 0.0) {
+          if (s + r < N_I && wr != 0.0) {
             cplx c = cf[(size_t)(s + r) * n_h + n];
             re = fma(wr, c.x, re);
             im = fma(wr, c.y, im);
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(NT)
 k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
                     const cplx* __restrict__ phase, const cplx* __restrict__ gtab,
                     const int* __restrict__ cls_of, const double* __restrict__ kpow,
-                    const int* __restrict__ j0, const double* __restrict__ lw, int N_tr,
-                    int N_I, int n_h, int N_k, int N_ell) {
+                    const int* __restrict__ j0, const double* __restrict__ lw, long lw_ts,
+                    int N_tr, int N_I, int n_h, int N_k, int N_ell) {
   __shared__ double Ds[AL][AQ + 1];
   __shared__ cplx Gs[AL][AN + 1];
   __shared__ cplx V[AQ][AN + 1];
@@ -116,6 +117,7 @@ k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
   const int i = wi % N_tr;
   const int w = wi / N_tr;
   const cplx* G = gtab + (size_t)cls_of[i] * N_ell * n_h;
+  lw += (size_t)i * lw_ts;
   // thread micro-tile: 2 q x 4 n
   const int tn = threadIdx.x & 7;    // n = tn + 8 b
   const int tq = threadIdx.x >> 3;   // q = tq + 32 a
@@ -220,23 +222,24 @@ k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
 
 cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
                                  const cplx* gtab, const int* cls_of, const double* kpow,
-                                 const int* j0, const double* lw, int n_walk, int N_tr,
-                                 int N_I, int n_h, int N_k, int N_ell, cudaStream_t s) {
+                                 const int* j0, const double* lw, long lw_ts, int n_walk,
+                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, cudaStream_t s) {
   dim3 g((N_k + BQ - 1) / BQ, (N_ell + BL - 1) / BL, n_walk * N_tr);
-  k_contract_fp64<<<g, NT, 0, s>>>(delta, coef, phase, gtab, cls_of, kpow, j0, lw, N_tr, N_I,
-                                    n_h, N_k, N_ell);
+  k_contract_fp64<<<g, NT, 0, s>>>(delta, coef, phase, gtab, cls_of, kpow, j0, lw, lw_ts, N_tr,
+                                    N_I, n_h, N_k, N_ell);
   return cudaGetLastError();
 }
 
 cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx* phase,
                                      const cplx* gtab, const int* cls_of, const double* kpow,
-                                     const int* j0, const double* lw, int n_walk, int N_tr,
-                                     int N_I, int n_h, int N_k, int N_ell, cudaStream_t s) {
+                                     const int* j0, const double* lw, long lw_ts, int n_walk,
+                                     int N_tr, int N_I, int n_h, int N_k, int N_ell,
+                                     cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cbar, 0, (size_t)n_walk * N_tr * N_I * n_h * sizeof(cplx), s);
   if (e != cudaSuccess) return e;
   dim3 g((N_k + AQ - 1) / AQ, (n_h + AN - 1) / AN, n_walk * N_tr);
-  k_contract_fp64_adj<<<g, NT, 0, s>>>(cbar, dbar, phase, gtab, cls_of, kpow, j0, lw, N_tr, N_I,
-                                        n_h, N_k, N_ell);
+  k_contract_fp64_adj<<<g, NT, 0, s>>>(cbar, dbar, phase, gtab, cls_of, kpow, j0, lw, lw_ts, N_tr,
+                                        N_I, n_h, N_k, N_ell);
   return cudaGetLastError();
 }
 

@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
               const float2* __restrict__ phaseT, const uint8_t* __restrict__ bimg,
               const int* __restrict__ cls_of, const float* __restrict__ kpow32,
-              const int* __restrict__ j0, const float* __restrict__ lw32, int N_tr, int N_I,
-              int n_h, int N_k, int N_ell, int NT, int n_lt, int n_qt, int n_kb, int stages,
-              uint32_t tmem_cols, int* __restrict__ status) {
+              const int* __restrict__ j0, const float* __restrict__ lw32, long lw_ts, int N_tr,
+              int N_I, int n_h, int N_k, int N_ell, int NT, int n_lt, int n_qt, int n_kb,
+              int stages, uint32_t tmem_cols, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const SmemLayout L = smem_layout<P>(NT, stages);
@@ -165,7 +165,7 @@ k_contract_tc(float* __restrict__ delta, const float4* __restrict__ coefdf,
     float wr[4] = {0.f, 0.f, 0.f, 0.f};
     if (plive) {
       jq = j0[pq];
-      const float4 wq = *reinterpret_cast<const float4*>(lw32 + (size_t)pq * 4);
+      const float4 wq = *reinterpret_cast<const float4*>(lw32 + (size_t)i * lw_ts + (size_t)pq * 4);
       wr[0] = wq.x; wr[1] = wq.y; wr[2] = wq.z; wr[3] = wq.w;
       rmax = min(4, N_I - jq);
     }
@@ -444,7 +444,9 @@ int prepare_tables(swcl_ctx* c, int precision, int& NT, int& n_lt, int& n_kb) {
   if (st) return st;
   st = ensure(c, T.phase32, sizeof(float2) * (size_t)c->N_k * n_h);
   if (st) return st;
-  st = ensure(c, c->tc_lw32, sizeof(float) * 4 * (size_t)c->N_k);
+  const Stencil sv = stencil(c);
+  const long n_lw = 4L * c->N_k * (sv.w_ts ? c->N_tr : 1);
+  st = ensure(c, c->tc_lw32, sizeof(float) * n_lw);
   if (st) return st;
   st = ensure(c, c->tc_kpow32, sizeof(float) * (size_t)c->N_tr * c->N_k);
   if (st) return st;
@@ -453,9 +455,7 @@ int prepare_tables(swcl_ctx* c, int precision, int& NT, int& n_lt, int& n_kb) {
       (uint8_t*)T.bfwd.p, (const cplx*)c->d_gtab.p, c->n_cls, c->N_ell, n_h, NT, n_lt, n_kb);
   dim3 gt((n_h + 31) / 32, (c->N_k + 31) / 32), bt(32, 8);
   k_phase_t<<<gt, bt, 0, c->stream>>>((float2*)T.phase32.p, (const cplx*)c->d_phase.p, c->N_k, n_h);
-  long nl = 4L * c->N_k;
-  k_to_f32<<<(unsigned)((nl + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_lw32.p,
-                                                               (const double*)c->d_interp_w.p, nl);
+  k_to_f32<<<(unsigned)((n_lw + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_lw32.p, sv.w, n_lw);
   long nk = (long)c->N_tr * c->N_k;
   k_to_f32<<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_kpow32.p,
                                                                (const double*)c->d_kpow.p, nk);
@@ -467,6 +467,7 @@ int prepare_tables(swcl_ctx* c, int precision, int& NT, int& n_lt, int& n_kb) {
 
 template <class P>
 int run_forward(swcl_ctx* c, int precision) {
+  const Stencil sv = stencil(c);
   int NT, n_lt, n_kb;
   int st = prepare_tables<P>(c, precision, NT, n_lt, n_kb);
   if (st) return st;
@@ -489,8 +490,8 @@ int run_forward(swcl_ctx* c, int precision) {
   k_contract_tc<P><<<(unsigned)grid, kThreadsTc, L.total, c->stream>>>(
       (float*)c->ws_delta.p, (const float4*)c->ws_coef.p, (const float2*)c->tc[precision].phase32.p,
       (const uint8_t*)c->tc[precision].bfwd.p, (const int*)c->d_cls_of.p,
-      (const float*)c->tc_kpow32.p, (const int*)c->d_interp_j0.p, (const float*)c->tc_lw32.p,
-      c->N_tr, c->N_I, c->n_h, c->N_k, c->N_ell, NT, n_lt, n_qt, n_kb, stages, tmem_cols,
+      (const float*)c->tc_kpow32.p, sv.j0, (const float*)c->tc_lw32.p, sv.w_ts, c->N_tr, sv.NI,
+      c->n_h, c->N_k, c->N_ell, NT, n_lt, n_qt, n_kb, stages, tmem_cols,
       (int*)c->ws_status.p);
   e = cudaGetLastError();
   prof_end(c, "contract tc");

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThr, 1)
 k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
                   const uint8_t* __restrict__ bimgT, const int* __restrict__ cls_of,
                   const float* __restrict__ kpow32, const int* __restrict__ j0,
-                  const float* __restrict__ lw32, const float2* __restrict__ phaseT,
+                  const float* __restrict__ lw32, long lw_ts, const float2* __restrict__ phaseT,
                   const int* __restrict__ tile_alo, int N_tr, int N_I, int n_h, int N_k, int n_ct,
                   int n_qt, int n_kb, int R, int stages, uint32_t tmem_cols,
                   int* __restrict__ status) {
@@ -168,7 +168,7 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
       }
       if (half == 0) {
         tj0[row_acc] = q < N_k ? j0[q] : 0x7fffffff;
-        tlw[row_acc] = q < N_k ? *reinterpret_cast<const float4*>(lw32 + (size_t)q * 4)
+        tlw[row_acc] = q < N_k ? *reinterpret_cast<const float4*>(lw32 + (size_t)i * lw_ts + (size_t)q * 4)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
@@ -360,7 +360,8 @@ __global__ void k_knot_reduce(cplx* __restrict__ cbar, const float2* __restrict_
 template <class P>
 int run_adjoint(swcl_ctx* c, int precision) {
   TcTables& T = c->tc[precision];
-  const int N_tr = c->N_tr, n_h = c->n_h, N_k = c->N_k, N_ell = c->N_ell, N_I = c->N_I;
+  const Stencil sv = stencil(c);
+  const int N_tr = c->N_tr, n_h = c->n_h, N_k = c->N_k, N_ell = c->N_ell, N_I = sv.NI;
   const int n_qt = (N_k + kMTile - 1) / kMTile;
   const int n_ct = (2 * n_h + kCT - 1) / kCT;
   const int n_kb = (N_ell + P::kKb - 1) / P::kKb;
@@ -369,7 +370,7 @@ int run_adjoint(swcl_ctx* c, int precision) {
   if (!T.adj_ready) {
     // knot ranges of the k tiles (j0 is nondecreasing in q)
     std::vector<int> j0(N_k);
-    cudaError_t e = cudaMemcpy(j0.data(), c->d_interp_j0.p, sizeof(int) * N_k, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(j0.data(), sv.j0, sizeof(int) * N_k, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "read interpolation stencils");
     std::vector<int> alo(n_qt), kq(2 * N_I);
     int R = 1;
@@ -424,8 +425,8 @@ int run_adjoint(swcl_ctx* c, int precision) {
   ++c->last_launches;
   k_contract_tc_adj<P><<<(unsigned)grid, kThr, L.total, c->stream>>>(
       (float2*)c->ws_cpart.p, (const uint8_t*)c->ws_aimg.p, (const uint8_t*)T.bvjp.p,
-      (const int*)c->d_cls_of.p, (const float*)c->tc_kpow32.p, (const int*)c->d_interp_j0.p,
-      (const float*)c->tc_lw32.p, (const float2*)T.phase32.p, (const int*)T.tile_alo.p, N_tr, N_I,
+      (const int*)c->d_cls_of.p, (const float*)c->tc_kpow32.p, sv.j0,
+      (const float*)c->tc_lw32.p, sv.w_ts, (const float2*)T.phase32.p, (const int*)T.tile_alo.p, N_tr, N_I,
       n_h, N_k, n_ct, n_qt, n_kb, T.R, stages, 4 * kCT, (int*)c->ws_status.p);
   e = cudaGetLastError();
   prof_end(c, "contract adj tc");

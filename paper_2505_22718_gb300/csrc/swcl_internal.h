@@ -34,6 +34,17 @@ struct TcTables {
 int compute_delta_tc(swcl_ctx* c, int precision);
 int contract_adj_tc(swcl_ctx* c, int precision);
 
+// The k-interpolation stencil and FFT profiles the kernels use: the N_I knots with 4-point
+// Lagrange weights, or (basis mode) r low-rank profiles with weights mu.
+struct Stencil {
+  const int* j0;        // [N_k] first row of each k point's stencil
+  const double* w;      // [n_w][N_k][4] weights
+  long w_ts;            // tracer stride of w in doubles (0 = shared)
+  int NI;               // stencil rows ("knots") per tracer
+  const double* D;      // FFT profile rows [NI][N]
+  const double* B;      // per-tracer factor [N_tr][NI][N] or null
+};
+
 }  // namespace swcl
 
 struct swcl_ctx {
@@ -75,6 +86,16 @@ struct swcl_ctx {
   int n_walk = 0;
   bool have_windows = false, have_power = false, have_B = false;
   swcl::DevBuf d_W, d_D, d_B, d_P, d_amp;
+  swcl::DevBuf d_prev;        // previous D (and B) for change detection
+  swcl::DevBuf d_flag;        // device int flag
+
+  // low-rank knot profiles (lowrank.cu)
+  bool lr_dirty = true;       // D/B/grids changed since the last factorisation
+  bool lr_disabled = false;   // environment override SWCL_PER_KNOT_FFT=1
+  bool lr_basis = false;      // basis mode active
+  int lr_rank = 0;            // stencil rows used in basis mode
+  int lr_true_rank = 0;
+  swcl::DevBuf lr_res, lr_norms, lr_Q, lr_coef, lr_w, lr_j0, lr_ones;
 
   // ragged ell lists
   bool ragged = false;
@@ -128,6 +149,9 @@ void release(swcl_ctx* c, DevBuf& b);
 bool is_device_ptr(const void* p);
 int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes);
 int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes);
+Stencil stencil(const swcl_ctx* c);
+int factor_profiles(swcl_ctx* c);
+int expand_basis_coefficients(swcl_ctx* c, void* out, bool df_input);
 void prof_begin(swcl_ctx* c);
 void prof_end(swcl_ctx* c, const char* name);
 
@@ -167,12 +191,13 @@ size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
 // a3 FP64 contraction (contract_fp64.cu)
 cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
                                  const cplx* gtab, const int* cls_of, const double* kpow,
-                                 const int* j0, const double* lw, int n_walk, int N_tr,
-                                 int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
+                                 const int* j0, const double* lw, long lw_ts, int n_walk,
+                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
 cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx* phase,
                                      const cplx* gtab, const int* cls_of, const double* kpow,
-                                     const int* j0, const double* lw, int n_walk, int N_tr,
-                                     int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
+                                     const int* j0, const double* lw, long lw_ts, int n_walk,
+                                     int N_tr, int N_I, int n_h, int N_k, int N_ell,
+                                     cudaStream_t s);
 
 // a4 k-quadrature and VJP reductions (quad.cu)
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
@@ -192,9 +217,5 @@ cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const doubl
                              const double* amp, const double* P, const double* wk2, int n_walk,
                              int N_tr, int N_k, int N_ell, double* scratch, cudaStream_t s);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
-
-// a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
-int compute_delta_tc(swcl_ctx* c, int precision);
-int contract_adj_tc(swcl_ctx* c, int precision);
 
 }  // namespace swcl
