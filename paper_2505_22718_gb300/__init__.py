@@ -9,7 +9,7 @@ from .api import (  # noqa: F401
     Context, SwiftClError, PRECISIONS,
     SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16, SWCL_TF32X6, SWCL_DENSITY, SWCL_LENSING,
     SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES,
-    SWCL_Q_PROFILE_RANK,
+    SWCL_Q_PROFILE_RANK, SWCL_Q_TILE_FWD, SWCL_Q_TILE_ADJ,
     swcl_create, swcl_destroy, swcl_set_grids, swcl_set_tracers, swcl_set_windows,
     swcl_set_power, swcl_set_ell_lists, swcl_compute_cl, swcl_vjp, swcl_sync, swcl_query,
     swcl_profile_enable, swcl_profile_read, swcl_profile_reset, swcl_debug_read,

@@ -17,7 +17,7 @@ SWCL_OK = 0
 SWCL_DENSITY, SWCL_LENSING = 0, 1
 SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16, SWCL_TF32X6 = 0, 1, 2, 3
 SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES = 1, 2, 3, 4
-SWCL_Q_PROFILE_RANK = 5
+SWCL_Q_PROFILE_RANK, SWCL_Q_TILE_FWD, SWCL_Q_TILE_ADJ = 5, 6, 7
 PRECISIONS = {"fp64": SWCL_FP64, "3xtf32": SWCL_3XTF32, "bf16x9": SWCL_SPLIT_BF16, "tf32x6": SWCL_TF32X6}
 
 

@@ -251,6 +251,7 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   }
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
+  if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
   // device status word raised by bounded waits in the tensor-core kernels
   if (swcl::ensure(c, c->ws_status, 16) != SWCL_OK ||
       cudaMemset(c->ws_status.p, 0, 16) != cudaSuccess) {
@@ -276,7 +277,8 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status, &c->tc_lw32,
                     &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
-                    &c->lr_j0, &c->lr_ones};
+                    &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
+                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -323,6 +325,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
   c->lr_basis = false;
   c->ragged = false;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
+  c->bt_ready = false;
   c->N = N;
   c->n_h = N / 2 + 1;
   c->N_k = N_k;
@@ -396,6 +399,7 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   }
   c->have_tracers = false;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
+  c->bt_ready = false;
   c->last_fwd_precision = -1;
   c->lr_dirty = true;
   c->lr_basis = false;
@@ -556,6 +560,12 @@ static int check_status(swcl_ctx* c) {
   return SWCL_OK;
 }
 
+// Basis mode with split-bf16 products runs a3 and its transpose as GEMMs against the constant
+// phase operand (basis_tc.cu); the other forms use the knot-stencil kernels with the basis view.
+static bool use_basis_gemm(const swcl_ctx* c, int precision) {
+  return precision == SWCL_SPLIT_BF16 && c->lr_basis && !c->bt_disabled;
+}
+
 static int check_ready(swcl_ctx* c, int precision) {
   if (!c->have_grids || !c->have_tracers || !c->have_windows || !c->have_power)
     return swcl::fail(c, SWCL_ERR_STATE, "set_grids, set_tracers, set_windows and set_power first");
@@ -603,7 +613,10 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                                (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
-    SWCL_TRY(swcl::compute_delta_tc(c, precision));
+    if (use_basis_gemm(c, precision))
+      SWCL_TRY(swcl::basis_forward(c, 0, N_ell));
+    else
+      SWCL_TRY(swcl::compute_delta_tc(c, precision));
     SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                          (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
                                          N_tr, N_k, N_ell, c->stream), "k-quadrature f32");
@@ -695,7 +708,10 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                     sv.j0, sv.w, sv.w_ts, nw, N_tr, N_I,
                                                     n_h, N_k, N_ell, c->stream), "contract adj fp64");
     } else {
-      SWCL_TRY(swcl::contract_adj_tc(c, precision));
+      if (use_basis_gemm(c, precision))
+        SWCL_TRY(swcl::basis_adjoint(c, 0, N_ell, false));
+      else
+        SWCL_TRY(swcl::contract_adj_tc(c, precision));
     }
     double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
     double* scratch = (double*)((char*)c->ws_outW.p + wbytes);
@@ -902,6 +918,8 @@ int swcl_query(swcl_ctx* c, int key, int64_t* value) {
     case SWCL_Q_N_HALF: *value = c->n_h; return SWCL_OK;
     case SWCL_Q_KERNEL_LAUNCHES: *value = c->last_launches; return SWCL_OK;
     case SWCL_Q_PROFILE_RANK: *value = c->lr_basis ? c->lr_true_rank : 0; return SWCL_OK;
+    case SWCL_Q_TILE_FWD: *value = c->bt_nt_fwd; return SWCL_OK;
+    case SWCL_Q_TILE_ADJ: *value = c->bt_nt_adj; return SWCL_OK;
     default: return swcl::fail(c, SWCL_ERR_INVALID_ARG, "unknown query key");
   }
 }

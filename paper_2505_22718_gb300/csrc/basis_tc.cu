@@ -1,0 +1,843 @@
+// a3 and its transpose (a5) on the tensor cores in basis mode, where the knot profiles are low
+// rank (lowrank.cu): both become GEMMs against one constant operand, the phase table
+// E_{q,n} = e^{-i eta_n ln k_q}.
+//
+// With r basis profiles of FFTLog coefficients F_{w,i,s,n} (Eq. 3.3) and weights
+// mu_{i,q,s} = sum_a lambda_{q,a} coef_{i,a,s} (the k-interpolation of Sec. 3.2 carried through the
+// basis), Eq. 3.4-3.5 read
+//   Delta_i(l, q) = kpow_i[q] sum_s mu_{i,q,s} Re sum_n E_{q,n} H_{w,i,l,s,n},
+//   H_{w,i,l,s,n} = F_{w,i,s,n} G_{cls(i)}[l][n],   G = w_n pi_i(l) M_{l,n}.
+// Forward GEMM: rows q, columns (w, i, l, s) (s fastest), K = (n, re/im) interleaved:
+//   A[q][2n] = Re E, A[q][2n+1] = Im E;  B[j][2n] = Re H, B[j][2n+1] = -Im H.
+// The reverse mode of the same expression is
+//   Fbar_{w,i,s,n} = sum_l conj(G[l][n]) Y_{w,i,s,l,n},
+//   Y_{w,i,s,l,n} = sum_q conj(E_{q,n}) kpow_i[q] mu_{i,q,s} Dbar_i(l, q),
+// the adjoint GEMM: rows (n, re/im), columns (w, i, s, l) (l fastest), K = q:
+//   A[2n][q] = Re E, A[2n+1][q] = -Im E;  B[j][q] = kpow mu Dbar;
+// its epilogue multiplies by conj(G) and sums over l.
+//
+// Compensated products with FP32 accumulation (the 5th-generation tensor cores take bf16 operands
+// here): the constant operand is split once from FP64 into 4 bf16 planes; the forward B operand
+// H is formed in double-float arithmetic from double-float F and G and split into 4 planes; the
+// adjoint B operand is an FP32 product split exactly into 3 planes.  Products with pa + pb <= 3
+// are issued (10 forward, 9 adjoint).  The tensor core accumulates one 32-deep K-block at a
+// time, the leading product and the corrections in separate TMEM slots (double-buffered); eight
+// drain warps add each K-block's partial sums into FP32 registers with round-to-nearest.
+//
+// Warp roles: warp 0 streams both operand images into a shared-memory ring with cp.async.bulk;
+// warp 1 owns TMEM and issues tcgen05.mma; warps 2-9 drain TMEM (two warps per 32-lane quarter,
+// each with half of the columns) and run the epilogue.  All waits are bounded; a timeout raises
+// the context's status word (SWCL_ERR_TIMEOUT).
+#include <algorithm>
+#include <cuda_bf16.h>
+
+#include "swcl_internal.h"
+#include "tc_common.cuh"
+
+namespace swcl {
+namespace {
+
+using namespace tc;
+
+constexpr int kK = 32;                  // K elements (bf16) per 64-byte operand row
+constexpr int kRow = 64;                // bytes per operand row and K-block
+constexpr int kM = 128;                 // rows per CTA (TMEM lanes)
+constexpr int kPlaneM = kM * kRow;      // 8 KB: one plane of the A operand per K-block
+constexpr int kDrain = 256;             // drain threads (warps 2-9)
+constexpr int kThreads = 64 + kDrain;   // warp 0 copies, warp 1 MMA
+constexpr int kMaxNT = 128;
+constexpr int kHalf = kMaxNT / 2;       // columns per drain thread at most
+constexpr int kMaxStages = 6;
+
+// A operand 4 planes, B operand 4 planes: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0) (0,3) (1,2) (2,1) (3,0)
+struct A4B4 {
+  static constexpr int kPlanesA = 4, kPlanesB = 4, kProducts = 10;
+  __host__ __device__ static constexpr int pa(int t) {
+    return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : t == 7 ? 1 : t == 8 ? 2 : t == 9 ? 3 : 0;
+  }
+  __host__ __device__ static constexpr int pb(int t) {
+    return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : t == 6 ? 3 : t == 7 ? 2 : t == 8 ? 1 : 0;
+  }
+};
+// A operand 4 planes, B operand 3 planes: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0) (1,2) (2,1) (3,0)
+struct A4B3 {
+  static constexpr int kPlanesA = 4, kPlanesB = 3, kProducts = 9;
+  __host__ __device__ static constexpr int pa(int t) {
+    return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : t == 6 ? 1 : t == 7 ? 2 : t == 8 ? 3 : 0;
+  }
+  __host__ __device__ static constexpr int pb(int t) {
+    return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : t == 6 ? 2 : t == 7 ? 1 : 0;
+  }
+};
+
+// D f32, A/B bf16, K-major A and B, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of (row r, byte kb) in one [rows x 64 B] plane, canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices of 128 contiguous bytes, K-adjacent cores 128 B apart
+// (LBO), 8-row groups 512 B apart (SBO).
+__host__ __device__ inline uint32_t off64(int r, int kbyte) {
+  return (uint32_t)((((r >> 3) * 4 + (kbyte >> 4)) << 7) + ((r & 7) << 4) + (kbyte & 15));
+}
+__device__ __forceinline__ uint64_t desc64(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+}
+
+// 32 lanes x 16 columns of 32-bit TMEM words without waiting: the registers are valid after
+// tmem_wait_ld(); reg_fence() keeps their uses behind the wait.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void reg_fence(uint32_t (&r)[16]) {
+#pragma unroll
+  for (int t = 0; t < 16; ++t) asm volatile("" : "+r"(r[t]));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+struct Layout {
+  uint32_t a_bytes, b_bytes, stage, bar_off, total;
+  int stages;
+};
+template <class P>
+__host__ __device__ inline Layout layout(int NT, int stages) {
+  Layout L;
+  L.stages = stages;
+  L.a_bytes = P::kPlanesA * kPlaneM;
+  L.b_bytes = P::kPlanesB * NT * kRow;
+  L.stage = L.a_bytes + L.b_bytes;
+  L.bar_off = stages * L.stage;
+  L.total = L.bar_off + 8 * (3 * stages + 1) + 16 + 1024;
+  return L;
+}
+
+struct GemmShape {
+  int n_mt, n_kb, NT, stages;
+  uint32_t tmem_cols;
+};
+
+// ------------------------------------------------------------------ epilogues ----
+
+// Forward: Delta[w][l][i][q] = sum_s kmu[i][s][q] Z[q][(w, i, l, s)]
+struct EpiFwd {
+  float* delta;
+  const float* kmu;     // [N_tr][4][N_k]
+  int N_k, N_tr, n_l, r, n_cols;
+  // row m, this thread's columns j0 .. j0 + nc - 1 (j0 is a multiple of r)
+  __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
+    if (m >= N_k) return;
+    float v = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c) {
+      if (c < nc) {
+        const int j = j0 + c;
+        if (j < n_cols) {
+          const int s = j % r, g = j / r;
+          const int l = g % n_l, wi = g / n_l;
+          const int i = wi % N_tr, w = wi / N_tr;
+          v = fmaf(kmu[((size_t)i * 4 + s) * N_k + m], acc[c], v);
+          if (s == r - 1) {
+            delta[(((size_t)w * n_l + l) * N_tr + i) * N_k + m] = v;
+            v = 0.0f;
+          }
+        }
+      }
+    }
+  }
+};
+
+// Adjoint: Fbar[(w, i, s)][n] += sum_l conj(G[l][n]) Y[(n, re/im)][(w, i, s, l)]; the lanes of
+// rows 2n (Re Y) and 2n+1 (Im Y) are neighbours and combine with one shuffle.
+struct EpiAdj {
+  cplx* cbar;           // [n_walk][N_tr][NI][n_h]
+  const float2* g32;    // [n_cls][N_ell][n_h]
+  const int* cls_of;
+  int n_h, N_tr, N_ell, l_lo, n_l, r, NI, n_cols;
+  __device__ __forceinline__ void flush(int g, int n, int t, float are, float aim) const {
+    const float re = are + __shfl_xor_sync(0xffffffffu, are, 1);
+    const float im = aim + __shfl_xor_sync(0xffffffffu, aim, 1);
+    if (t == 0 && n < n_h) {
+      const int wi = g / r, s = g % r;
+      cplx* dst = cbar + ((size_t)wi * NI + s) * n_h + n;
+      atomicAdd(&dst->x, (double)re);
+      atomicAdd(&dst->y, (double)im);
+    }
+  }
+  __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
+    const int n = m >> 1, t = m & 1;
+    const bool live = n < n_h;
+    float are = 0.0f, aim = 0.0f;
+    int gcur = -1;
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c) {
+      if (c < nc) {
+        const int j = j0 + c;           // the same for every lane: branches below are uniform
+        if (j < n_cols) {
+          const int l = j % n_l, g = j / n_l;
+          if (g != gcur) {
+            if (gcur >= 0) flush(gcur, n, t, are, aim);
+            gcur = g;
+            are = 0.0f;
+            aim = 0.0f;
+          }
+          const int i = (g / r) % N_tr;
+          const float2 G = live ? g32[((size_t)cls_of[i] * N_ell + l_lo + l) * n_h + n]
+                                : make_float2(0.0f, 0.0f);
+          const float y = acc[c];
+          if (t == 0) {
+            are = fmaf(G.x, y, are);
+            aim = fmaf(-G.y, y, aim);
+          } else {
+            are = fmaf(G.y, y, are);
+            aim = fmaf(G.x, y, aim);
+          }
+        }
+      }
+    }
+    if (gcur >= 0) flush(gcur, n, t, are, aim);
+  }
+};
+
+// ------------------------------------------------------------------- GEMM ----
+
+template <class P, class Epi>
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
+             Epi epi, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int NT = sh.NT, S = sh.stages, n_kb = sh.n_kb;
+  const Layout L = layout<P>(NT, S);
+  // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
+  // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
+  // the TMEM buffer the K-block accumulates into (1 + kDrain arrivals); mmadone[s] when the
+  // K-block's MMAs are done (one commit), which frees the stage for the copy warp and the
+  // accumulator for the drain warps.  The MMA thread waits once and commits once per K-block:
+  // a single thread issues tcgen05.mma only about as fast as the tensor core executes a
+  // 128 x 96 x 16 product, so its own time between MMAs is the critical resource.
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
+  uint64_t* full = bars;
+  uint64_t* mmadone = bars + S;
+  uint64_t* ready = bars + 2 * S;
+  uint64_t* done = bars + 3 * S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x % sh.n_mt;
+  const int nt = blockIdx.x / sh.n_mt;
+  const int stride = (NT + 31) & ~31;   // TMEM columns per accumulator slot
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1 + kDrain);
+      mbar_init(smem_u32(&mmadone[s]), 1);
+      mbar_init(smem_u32(&ready[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), sh.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- copies ----
+      // Issues the copies of K-block `next` as soon as its stage is free and forwards landed
+      // K-blocks (ready -> full) in order; both without blocking on either condition.
+      const uint8_t* asrc = aimg + (size_t)mt * n_kb * L.a_bytes;
+      const uint8_t* bsrc = bimg + (size_t)nt * n_kb * L.b_bytes;
+      int next = 0, fwd = 0;
+      long idle = 0;
+      while (fwd < n_kb) {
+        bool progress = false;
+        if (next < n_kb) {
+          const int s = next % S, r = next / S;
+          if (r == 0 || mbar_try_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
+            uint8_t* st = base + s * L.stage;
+            mbar_arrive_tx(smem_u32(&ready[s]), L.stage);
+            bulk_g2s(smem_u32(st), asrc + (size_t)next * L.a_bytes, L.a_bytes, smem_u32(&ready[s]));
+            bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)next * L.b_bytes, L.b_bytes,
+                     smem_u32(&ready[s]));
+            ++next;
+            progress = true;
+          }
+        }
+        if (fwd < next && mbar_try_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
+          mbar_arrive(smem_u32(&full[fwd % S]));
+          ++fwd;
+          progress = true;
+        }
+        if (progress) {
+          idle = 0;
+        } else if (++idle > kSpinLimit || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      // copies still in flight (issued, not forwarded) land before the CTA exits
+      for (int kb = fwd; kb < next; ++kb) mbar_wait_drain(smem_u32(&ready[kb % S]), (kb / S) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA ----
+      const uint32_t idesc = idesc_bf16(kM, NT);
+      const uint32_t b_plane = NT * kRow;
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int s = kb % S, r = kb / S, b = kb & 1;
+        if (!mbar_wait(smem_u32(&full[s]), r & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(base + s * L.stage);
+        const uint64_t da = desc64(a0), db = desc64(a0 + L.a_bytes);
+        const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
+        const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+#pragma unroll
+        for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+          for (int t = 0; t < P::kProducts; ++t) {
+            // descriptor start addresses advance in 16-byte units
+            const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+            const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+            const bool lead = (t == 0);
+            const bool first = (j == 0) && (t <= 1);
+            mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+          }
+        }
+        mma_commit(smem_u32(&mmadone[s]));
+      }
+      // every issued MMA has completed before TMEM is released
+      mma_commit(smem_u32(done));
+      mbar_wait_drain(smem_u32(done), 0);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ drain ----
+    const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31 for this warp
+    const int half = (warp - 2) >> 2;    // column half
+    const int row = quarter * 32 + lane;
+    const int nch = NT / 16;
+    const int nch0 = (nch + 1) / 2;
+    const int c_begin = half ? nch0 : 0;
+    const int my = half ? nch - nch0 : nch0;   // 16-column chunks of this thread (<= 4)
+    float acc[kHalf];
+#pragma unroll
+    for (int t = 0; t < kHalf; ++t) acc[t] = 0.0f;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    // the first two K-blocks find their accumulator buffers empty
+    mbar_arrive(smem_u32(&full[0]));
+    if (n_kb > 1) mbar_arrive(smem_u32(&full[1 % S]));
+    bool ok = true;
+    for (int kb = 0; kb < n_kb && ok; ++kb) {
+      const int b = kb & 1;
+      if (!mbar_wait(smem_u32(&mmadone[kb % S]), (kb / S) & 1, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
+      const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
+      // two chunks (main and correction slots) in flight per wait
+#pragma unroll
+      for (int g = 0; g < kHalf / 16; g += 2) {
+        if (g < my) {
+          uint32_t m0[16], r0[16], m1[16], r1[16];
+          const bool two = g + 1 < my;
+          tmem_ld16_async(slot_m + g * 16, m0);
+          tmem_ld16_async(slot_c + g * 16, r0);
+          if (two) {
+            tmem_ld16_async(slot_m + (g + 1) * 16, m1);
+            tmem_ld16_async(slot_c + (g + 1) * 16, r1);
+          }
+          tmem_wait_ld();
+          reg_fence(m0);
+          reg_fence(r0);
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            acc[g * 16 + t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+          if (two) {
+            reg_fence(m1);
+            reg_fence(r1);
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+              acc[(g + 1) * 16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+          }
+        }
+      }
+      tc_fence_before();
+      // buffer b is free for K-block kb + 2
+      if (kb + 2 < n_kb) mbar_arrive(smem_u32(&full[(kb + 2) % S]));
+    }
+    // every lane of a drain warp reaches the epilogue (its shuffles need the full warp)
+    const bool all_ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+    if (all_ok) epi(mt * kM + row, nt * NT + c_begin * 16, acc, my * 16);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(status, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, sh.tmem_cols);
+  }
+}
+
+// -------------------------------------------------------------- operand images ----
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// FP64 value -> n bf16 planes, each the rounded remainder of the previous ones
+template <int NP>
+__device__ __forceinline__ void split_f64(double x, __nv_bfloat16 (&p)[NP]) {
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    p[k] = __float2bfloat16_rn((float)x);
+    x -= (double)bf(p[k]);
+  }
+}
+// double-float (hi + lo) -> 4 bf16 planes
+__device__ __forceinline__ void split_df(float hi, float lo, __nv_bfloat16 (&p)[4]) {
+  p[0] = __float2bfloat16_rn(hi);
+  float r = (hi - bf(p[0])) + lo;
+  p[1] = __float2bfloat16_rn(r);
+  r -= bf(p[1]);
+  p[2] = __float2bfloat16_rn(r);
+  r -= bf(p[2]);
+  p[3] = __float2bfloat16_rn(r);
+}
+// FP32 -> 3 bf16 planes (exact)
+__device__ __forceinline__ void split_f32(float x, __nv_bfloat16 (&p)[3]) {
+  p[0] = __float2bfloat16_rn(x);
+  const float r = x - bf(p[0]);
+  p[1] = __float2bfloat16_rn(r);
+  p[2] = __float2bfloat16_rn(r - bf(p[1]));
+}
+
+template <int NP>
+__device__ __forceinline__ void store_planes(uint8_t* dst, uint32_t plane_bytes, uint32_t off,
+                                             const __nv_bfloat16 (&v)[8][NP]) {
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) o[u] = v[u][p];
+    *reinterpret_cast<uint4*>(dst + (size_t)p * plane_bytes + off) = *reinterpret_cast<const uint4*>(o);
+  }
+}
+
+// Forward A image [mt][kb][4 planes][128 rows x 64 B]: (q, 2n + t) = Re/Im E_{q,n}
+__global__ void k_eimg_fwd(uint8_t* __restrict__ img, const cplx* __restrict__ phase, int N_k,
+                           int n_h, int n_mt, int n_kb) {
+  const long total = (long)n_mt * n_kb * kM * 4;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long t = e;
+    const int ch = (int)(t % 4); t /= 4;
+    const int row = (int)(t % kM); t /= kM;
+    const int kb = (int)(t % n_kb); t /= n_kb;
+    const int mt = (int)t;
+    const int q = mt * kM + row;
+    __nv_bfloat16 v[8][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int n = (kb * kK + ch * 8) / 2 + u;
+      cplx E = {0.0, 0.0};
+      if (q < N_k && n < n_h) E = phase[(size_t)q * n_h + n];
+      split_f64<4>(E.x, v[2 * u]);
+      split_f64<4>(E.y, v[2 * u + 1]);
+    }
+    store_planes<4>(img + ((size_t)mt * n_kb + kb) * 4 * kPlaneM, kPlaneM, off64(row, ch * 16), v);
+  }
+}
+
+// Adjoint A image [mt][kb][4 planes][128 rows x 64 B]: (2n + t, q) = Re E_{q,n}, -Im E_{q,n}
+__global__ void k_eimg_adj(uint8_t* __restrict__ img, const cplx* __restrict__ phase, int N_k,
+                           int n_h, int n_mt, int n_kb) {
+  const long total = (long)n_mt * n_kb * kM * 4;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long t = e;
+    const int row = (int)(t % kM); t /= kM;
+    const int ch = (int)(t % 4); t /= 4;
+    const int kb = (int)(t % n_kb); t /= n_kb;
+    const int mt = (int)t;
+    const int m = mt * kM + row;
+    const int n = m >> 1;
+    __nv_bfloat16 v[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = kb * kK + ch * 8 + u;
+      double x = 0.0;
+      if (q < N_k && n < n_h) {
+        const cplx E = phase[(size_t)q * n_h + n];
+        x = (m & 1) ? -E.y : E.x;
+      }
+      split_f64<4>(x, v[u]);
+    }
+    store_planes<4>(img + ((size_t)mt * n_kb + kb) * 4 * kPlaneM, kPlaneM, off64(row, ch * 16), v);
+  }
+}
+
+// double-float copy (re_hi, im_hi, re_lo, im_lo) and FP32 copy of the Gamma-ratio table
+__global__ void k_gtab_split(float4* __restrict__ gdf, float2* __restrict__ g32,
+                             const cplx* __restrict__ gtab, long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const cplx g = gtab[e];
+    const float rh = (float)g.x, ih = (float)g.y;
+    gdf[e] = make_float4(rh, ih, (float)(g.x - (double)rh), (float)(g.y - (double)ih));
+    g32[e] = make_float2(rh, ih);
+  }
+}
+
+// kmu[i][s][q] = kpow_i[q] mu_{p(i), q, s}  (p = i with per-tracer profiles, else 0)
+__global__ void k_kmu(float* __restrict__ kmu, const double* __restrict__ kpow,
+                      const double* __restrict__ mu, int N_tr, int N_k, int r, int per_tracer) {
+  const long total = (long)N_tr * 4 * N_k;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % N_k);
+    const int s = (int)((e / N_k) % 4);
+    const int i = (int)(e / (4L * N_k));
+    const int p = per_tracer ? i : 0;
+    kmu[e] = s < r ? (float)(kpow[(size_t)i * N_k + q] * mu[((size_t)p * N_k + q) * 4 + s]) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (a_hi + a_lo)(b_hi + b_lo) - (c_hi + c_lo)(d_hi + d_lo) in double-float (sgn = -1), or + (sgn = 1)
+__device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, float ch, float cl,
+                                        float dh, float dl, float sgn, float& hi, float& lo) {
+  float p1, e1, p2, e2;
+  two_prod(ah, bh, p1, e1);
+  two_prod(ch, dh, p2, e2);
+  e1 = fmaf(ah, bl, fmaf(al, bh, e1));
+  e2 = fmaf(ch, dl, fmaf(cl, dh, e2));
+  float s, es;
+  two_sum(p1, sgn * p2, s, es);
+  const float l = es + e1 + sgn * e2;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+
+// Forward B image [nt][kb][4 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
+// (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
+__global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
+                       const float4* __restrict__ gdf, const int* __restrict__ cls_of, int N_tr,
+                       int N_ell, int n_h, int l_lo, int n_l, int r, int NI, int n_cols, int NT,
+                       int n_nt, int n_kb) {
+  const long total = (long)n_nt * n_kb * NT * 4;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long t = e;
+    const int ch = (int)(t % 4); t /= 4;
+    const int row = (int)(t % NT); t /= NT;
+    const int kb = (int)(t % n_kb); t /= n_kb;
+    const int nt = (int)t;
+    const int j = nt * NT + row;
+    __nv_bfloat16 v[8][4];
+    const bool live = j < n_cols;
+    int s = 0, l = 0, wi = 0, i = 0;
+    if (live) {
+      s = j % r;
+      const int g = j / r;
+      l = g % n_l;
+      wi = g / n_l;
+      i = wi % N_tr;
+    }
+    const float4* Fr = F + ((size_t)wi * NI + s) * n_h;
+    const float4* Gr = gdf + ((size_t)(live ? cls_of[i] : 0) * N_ell + l_lo + l) * n_h;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int n = (kb * kK + ch * 8) / 2 + u;
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      if (live && n < n_h) {
+        const float4 f = Fr[n], g = Gr[n];
+        // Re = fr gr - fi gi, Im = fr gi + fi gr
+        df_dot2(f.x, f.z, g.x, g.z, f.y, f.w, g.y, g.w, -1.0f, rh, rl);
+        df_dot2(f.x, f.z, g.y, g.w, f.y, f.w, g.x, g.z, 1.0f, ih, il);
+      }
+      split_df(rh, rl, v[2 * u]);
+      split_df(-ih, -il, v[2 * u + 1]);
+    }
+    store_planes<4>(img + ((size_t)nt * n_kb + kb) * 4 * NT * kRow, NT * kRow,
+                    off64(row, ch * 16), v);
+  }
+}
+
+// Adjoint B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, s, l) (l fastest),
+// (j, q) = kmu[i][s][q] Dbar[w][l][i][q]
+__global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
+                       const float* __restrict__ kmu, int N_tr, int N_k, int n_l, int r,
+                       int n_cols, int NT, int n_nt, int n_kb) {
+  const long total = (long)n_nt * n_kb * NT * 4;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long t = e;
+    const int ch = (int)(t % 4); t /= 4;
+    const int row = (int)(t % NT); t /= NT;
+    const int kb = (int)(t % n_kb); t /= n_kb;
+    const int nt = (int)t;
+    const int j = nt * NT + row;
+    const bool live = j < n_cols;
+    int l = 0, s = 0, i = 0, w = 0;
+    if (live) {
+      l = j % n_l;
+      const int g = j / n_l;
+      s = g % r;
+      const int wi = g / r;
+      i = wi % N_tr;
+      w = wi / N_tr;
+    }
+    const float* drow = dbar + (((size_t)w * n_l + l) * N_tr + i) * N_k;
+    const float* krow = kmu + ((size_t)i * 4 + s) * N_k;
+    __nv_bfloat16 v[8][3];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = kb * kK + ch * 8 + u;
+      const float x = (live && q < N_k) ? krow[q] * drow[q] : 0.0f;
+      split_f32(x, v[u]);
+    }
+    store_planes<3>(img + ((size_t)nt * n_kb + kb) * 3 * NT * kRow, NT * kRow,
+                    off64(row, ch * 16), v);
+  }
+}
+
+unsigned grid_for(long total) {
+  return (unsigned)std::max<long>(1, std::min<long>((total + 255) / 256, 152L * 32));
+}
+
+template <class P>
+int shape_for(swcl_ctx* c, int NT, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
+  int stages = kMaxStages;
+  Layout L = layout<P>(NT, stages);
+  while (stages > 2 && L.total > 227 * 1024) L = layout<P>(NT, --stages);
+  if (L.total > 227 * 1024) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
+  const int stride = (NT + 31) & ~31;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(4 * stride)) cols <<= 1;
+  sh = GemmShape{n_mt, n_kb, NT, stages, cols};
+  smem = L.total;
+  return SWCL_OK;
+}
+
+template <class P, class Epi>
+cudaError_t launch_gemm(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                        uint32_t smem, int n_nt, const Epi& epi) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gemm_basis<P, Epi><<<(unsigned)(sh.n_mt * n_nt), kThreads, smem, c->stream>>>(
+      a, b, sh, epi, (int*)c->ws_status.p);
+  return cudaGetLastError();
+}
+
+// candidate column tiles: multiples of 16; in forward tiles each drain thread's column range
+// (whole 16-column chunks, split in two halves) holds whole groups of r basis columns
+std::vector<int> nt_candidates(int r, bool need_groups) {
+  std::vector<int> v;
+  for (int nt = 32; nt <= kMaxNT; nt += 16) {
+    const int half0 = 16 * ((nt / 16 + 1) / 2);
+    if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt);
+  }
+  return v;
+}
+
+int basis_rank(swcl_ctx* c) { return c->lr_true_rank; }
+
+}  // namespace
+
+// Constant operands of basis mode: the two phase images, the FP32/double-float Gamma tables and
+// kpow * mu.  Rebuilt whenever the grids, tracers or knot profiles change.
+int basis_prepare(swcl_ctx* c) {
+  if (c->bt_ready) return SWCL_OK;
+  const int N_k = c->N_k, n_h = c->n_h;
+  const int r = basis_rank(c);
+  int st;
+  c->bt_f_mt = (N_k + kM - 1) / kM;
+  c->bt_f_kb = (2 * n_h + kK - 1) / kK;
+  c->bt_a_mt = (2 * n_h + kM - 1) / kM;
+  c->bt_a_kb = (N_k + kK - 1) / kK;
+  const size_t ef = (size_t)c->bt_f_mt * c->bt_f_kb * 4 * kPlaneM;
+  const size_t ea = (size_t)c->bt_a_mt * c->bt_a_kb * 4 * kPlaneM;
+  if ((st = ensure(c, c->bt_eimg_f, ef))) return st;
+  if ((st = ensure(c, c->bt_eimg_a, ea))) return st;
+  const long ng = (long)c->n_cls * c->N_ell * n_h;
+  if ((st = ensure(c, c->bt_gdf, sizeof(float4) * ng))) return st;
+  if ((st = ensure(c, c->bt_g32, sizeof(float2) * ng))) return st;
+  if ((st = ensure(c, c->bt_kmu, sizeof(float) * (size_t)c->N_tr * 4 * N_k))) return st;
+  long tot = (long)c->bt_f_mt * c->bt_f_kb * kM * 4;
+  k_eimg_fwd<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_eimg_f.p, (const cplx*)c->d_phase.p,
+                                                   N_k, n_h, c->bt_f_mt, c->bt_f_kb);
+  tot = (long)c->bt_a_mt * c->bt_a_kb * kM * 4;
+  k_eimg_adj<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_eimg_a.p, (const cplx*)c->d_phase.p,
+                                                   N_k, n_h, c->bt_a_mt, c->bt_a_kb);
+  k_gtab_split<<<grid_for(ng), 256, 0, c->stream>>>((float4*)c->bt_gdf.p, (float2*)c->bt_g32.p,
+                                                    (const cplx*)c->d_gtab.p, ng);
+  k_kmu<<<grid_for((long)c->N_tr * 4 * N_k), 256, 0, c->stream>>>(
+      (float*)c->bt_kmu.p, (const double*)c->d_kpow.p, (const double*)c->lr_w.p, c->N_tr, N_k, r,
+      c->have_B ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis operand tables");
+  c->bt_nt_fwd = c->bt_nt_adj = 0;
+  c->bt_ready = true;
+  return SWCL_OK;
+}
+
+namespace {
+
+int build_h(swcl_ctx* c, int NT, int n_nt, int l_lo, int n_l) {
+  const Stencil sv = stencil(c);
+  const int r = basis_rank(c);
+  const int n_cols = c->n_walk * c->N_tr * n_l * r;
+  int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * 4 * NT * kRow);
+  if (st) return st;
+  const long tot = (long)n_nt * c->bt_f_kb * NT * 4;
+  k_himg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p,
+                                               (const float4*)c->bt_gdf.p, (const int*)c->d_cls_of.p,
+                                               c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r, sv.NI,
+                                               n_cols, NT, n_nt, c->bt_f_kb);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward operand");
+}
+
+int build_d(swcl_ctx* c, int NT, int n_nt, int n_l) {
+  const int r = basis_rank(c);
+  const int n_cols = c->n_walk * c->N_tr * r * n_l;
+  int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * 3 * NT * kRow);
+  if (st) return st;
+  const long tot = (long)n_nt * c->bt_a_kb * NT * 4;
+  k_dimg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p,
+                                               (const float*)c->bt_kmu.p, c->N_tr, c->N_k, n_l, r,
+                                               n_cols, NT, n_nt, c->bt_a_kb);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint operand");
+}
+
+// one counted (and, when profiling, timed) launch
+template <class F>
+int counted(swcl_ctx* c, const char* name, F f) {
+  ++c->last_launches;
+  prof_begin(c);
+  const int st = f();
+  prof_end(c, name);
+  return st;
+}
+
+// Times each candidate tile (operand build excluded) and keeps the fastest.
+template <class Run>
+int autotune(swcl_ctx* c, const std::vector<int>& cands, Run run, int& best) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return fail(c, SWCL_ERR_CUDA, "autotune events");
+  float best_ms = 1e30f;
+  best = cands.front();
+  int st = SWCL_OK;
+  for (int NT : cands) {
+    if ((st = run(NT, true))) break;           // operand build + one warm-up launch
+    cudaEventRecord(a, c->stream);
+    for (int rep = 0; rep < 3 && st == SWCL_OK; ++rep) st = run(NT, false);
+    cudaEventRecord(b, c->stream);
+    if (st) break;
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_ms) { best_ms = ms; best = NT; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
+
+}  // namespace
+
+// Delta (FP32, [n_walk][n_l][N_tr][N_k]) for multipoles [l_lo, l_lo + n_l) from the basis
+// coefficients in ws_coef (double-float).
+int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
+  int st = basis_prepare(c);
+  if (st) return st;
+  const int r = basis_rank(c);
+  const int n_cols = c->n_walk * c->N_tr * n_l * r;
+  auto run = [&](int NT, bool build) -> int {
+    const int n_nt = (n_cols + NT - 1) / NT;
+    if (build && (st = build_h(c, NT, n_nt, l_lo, n_l))) return st;
+    GemmShape sh;
+    uint32_t smem;
+    if ((st = shape_for<A4B4>(c, NT, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
+    EpiFwd epi{(float*)c->ws_delta.p, (const float*)c->bt_kmu.p, c->N_k, c->N_tr, n_l, r, n_cols};
+    cudaError_t e = launch_gemm<A4B4>(c, (const uint8_t*)c->bt_eimg_f.p,
+                                      (const uint8_t*)c->bt_himg.p, sh, smem, n_nt, epi);
+    return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward GEMM");
+  };
+  if (c->bt_nt_fwd == 0) {
+    if (c->capturing) c->bt_nt_fwd = nt_candidates(r, true).back();
+    else if ((st = autotune(c, nt_candidates(r, true), run, c->bt_nt_fwd))) return st;
+  }
+  const int NT = c->bt_nt_fwd;
+  const int n_nt = (n_cols + NT - 1) / NT;
+  if ((st = counted(c, "basis operand fwd", [&] { return build_h(c, NT, n_nt, l_lo, n_l); })))
+    return st;
+  return counted(c, "basis gemm fwd", [&] { return run(NT, false); });
+}
+
+// ws_cbar (FP64 complex, [n_walk][N_tr][NI][n_h], zeroed here) from ws_dbar (FP32,
+// [n_walk][n_l][N_tr][N_k]) for multipoles [l_lo, l_lo + n_l); accumulate = keep ws_cbar.
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
+  int st = basis_prepare(c);
+  if (st) return st;
+  const Stencil sv = stencil(c);
+  const int r = basis_rank(c);
+  const int n_cols = c->n_walk * c->N_tr * r * n_l;
+  const size_t cbytes = sizeof(cplx) * (size_t)c->n_walk * c->N_tr * sv.NI * c->n_h;
+  auto run = [&](int NT, bool build) -> int {
+    const int n_nt = (n_cols + NT - 1) / NT;
+    if (build && (st = build_d(c, NT, n_nt, n_l))) return st;
+    GemmShape sh;
+    uint32_t smem;
+    if ((st = shape_for<A4B3>(c, NT, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
+    EpiAdj epi{(cplx*)c->ws_cbar.p, (const float2*)c->bt_g32.p, (const int*)c->d_cls_of.p,
+               c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
+    cudaError_t e = launch_gemm<A4B3>(c, (const uint8_t*)c->bt_eimg_a.p,
+                                      (const uint8_t*)c->bt_dimg.p, sh, smem, n_nt, epi);
+    return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint GEMM");
+  };
+  if (c->bt_nt_adj == 0) {
+    if (c->capturing) {
+      c->bt_nt_adj = 128;
+    } else {
+      // the tuning launches accumulate into ws_cbar, which is cleared below
+      if ((st = autotune(c, nt_candidates(r, false), run, c->bt_nt_adj))) return st;
+      if (accumulate) return fail(c, SWCL_ERR_STATE, "basis adjoint tuned inside an accumulation");
+    }
+  }
+  if (!accumulate) {
+    cudaError_t e = cudaMemsetAsync(c->ws_cbar.p, 0, cbytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear cbar");
+  }
+  const int NT = c->bt_nt_adj;
+  const int n_nt = (n_cols + NT - 1) / NT;
+  if ((st = counted(c, "basis operand adj", [&] { return build_d(c, NT, n_nt, n_l); }))) return st;
+  return counted(c, "basis gemm adj", [&] { return run(NT, false); });
+}
+
+}  // namespace swcl

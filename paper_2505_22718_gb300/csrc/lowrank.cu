@@ -232,6 +232,7 @@ int factor_profiles(swcl_ctx* c) {
   c->lr_true_rank = rank;
   c->lr_basis = true;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;   // stencil weights changed
+  c->bt_ready = false;
   ++c->alloc_gen;
   return SWCL_OK;
 }

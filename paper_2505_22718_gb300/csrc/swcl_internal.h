@@ -33,6 +33,10 @@ struct TcTables {
 // a3 on tensor cores (contract_tc.cu): fills ws_delta (float) / ws_cbar for the context
 int compute_delta_tc(swcl_ctx* c, int precision);
 int contract_adj_tc(swcl_ctx* c, int precision);
+// a3 / a5 in basis mode as GEMMs against the constant phase operand (basis_tc.cu)
+int basis_prepare(swcl_ctx* c);
+int basis_forward(swcl_ctx* c, int l_lo, int n_l);
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate);
 
 // The k-interpolation stencil and FFT profiles the kernels use: the N_I knots with 4-point
 // Lagrange weights, or (basis mode) r low-rank profiles with weights mu.
@@ -96,6 +100,16 @@ struct swcl_ctx {
   int lr_rank = 0;            // stencil rows used in basis mode
   int lr_true_rank = 0;
   swcl::DevBuf lr_res, lr_norms, lr_Q, lr_coef, lr_w, lr_j0, lr_ones;
+
+  // basis-mode tensor-core GEMMs (basis_tc.cu)
+  bool bt_ready = false;       // constant operands built for the current grids/tracers/profiles
+  bool bt_disabled = false;    // environment override SWCL_BASIS_GEMM=0
+  int bt_f_mt = 0, bt_f_kb = 0, bt_a_mt = 0, bt_a_kb = 0;
+  int bt_nt_fwd = 0, bt_nt_adj = 0;   // autotuned column tiles (0 = not tuned yet)
+  swcl::DevBuf bt_eimg_f, bt_eimg_a;  // phase images: forward A [q][(n,re/im)], adjoint A [(n,re/im)][q]
+  swcl::DevBuf bt_gdf, bt_g32;        // Gamma-ratio table as double-float and FP32
+  swcl::DevBuf bt_kmu;                // [N_tr][4][N_k] float kpow * mu
+  swcl::DevBuf bt_himg, bt_dimg;      // per-call B images (forward H, adjoint kpow mu Dbar)
 
   // ragged ell lists
   bool ragged = false;

@@ -1,0 +1,122 @@
+"""Basis-mode tensor-core GEMMs (bf16 compensated products against the constant phase operand):
+parity with the FP64 oracle at the mixed-precision gate, agreement with the knot-stencil
+tensor-core kernels, autotuned tiles, rank > 1 and per-tracer profiles."""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import lib_context, make_ragged_case, max_rel, norm_err, oracle_walker
+
+pytestmark = pytest.mark.gpu
+
+GATE_C, GATE_G = 1e-4, 5e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _context(w, tapers=None, basis=True):
+    old = os.environ.get("SWCL_BASIS_GEMM")
+    os.environ["SWCL_BASIS_GEMM"] = "1" if basis else "0"
+    try:
+        return lib_context(w, tapers)
+    finally:
+        if old is None:
+            del os.environ["SWCL_BASIS_GEMM"]
+        else:
+            os.environ["SWCL_BASIS_GEMM"] = old
+
+
+def _fwd_vjp(ctx, Cb):
+    import paper_2505_22718_gb300 as S
+    C = ctx.compute_cl(S.SWCL_SPLIT_BF16)
+    g = ctx.vjp(Cb, S.SWCL_SPLIT_BF16)
+    return C, g
+
+
+def test_n5k_against_oracle_and_stencil_kernels(wl):
+    import paper_2505_22718_gb300 as S
+    w = wl("n5k_vjp")
+    ctx = _context(w)
+    C, (Pb, Ab, Wb) = _fwd_vjp(ctx, w.C_bar)
+    assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 1
+    nt_f, nt_a = ctx.query(S.SWCL_Q_TILE_FWD), ctx.query(S.SWCL_Q_TILE_ADJ)
+    assert nt_f in range(32, 129, 16) and nt_a in range(32, 129, 16)
+    f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=w.C_bar)
+    e = (norm_err(C, f["C"]), max_rel(Pb[0], Pbo), max_rel(Ab[0], Abo), max_rel(Wb[0], Wbo))
+    print("basis GEMM n5k: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e  tiles %d/%d" % (e + (nt_f, nt_a)))
+    assert e[0] < GATE_C and max(e[1:]) < GATE_G
+    assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
+    d = S.swcl_debug_read(ctx.ptr, S.SWCL_DBG_DELTA).reshape(f["delta"].shape)
+    rel = np.abs(d - f["delta"]) / np.abs(f["delta"]).max(axis=2, keepdims=True)
+    assert rel.max() < 1e-4
+    # the knot-stencil tensor-core kernels on the same inputs
+    ctx2 = _context(w, basis=False)
+    C2, (Pb2, Ab2, Wb2) = _fwd_vjp(ctx2, w.C_bar)
+    assert ctx2.query(S.SWCL_Q_TILE_FWD) == 0
+    assert norm_err(C, C2) < 2 * GATE_C
+    assert max_rel(Wb, Wb2) < 2 * GATE_G
+
+
+def test_repeat_is_stable(wl):
+    """A second forward/VJP on the same context (tuned tiles, rebuilt operands) agrees closely;
+    the adjoint's atomics may reorder FP64 additions."""
+    w = wl("n5k_vjp")
+    ctx = _context(w)
+    C1, g1 = _fwd_vjp(ctx, w.C_bar)
+    C2, g2 = _fwd_vjp(ctx, w.C_bar)
+    assert np.array_equal(C1, C2)
+    for a, b in zip(g1, g2):
+        assert max_rel(a, b) < 1e-12
+
+
+def test_per_tracer_profiles_walkers_tapers():
+    """B_i(k, z) (per-tracer rank-1 profiles), tapers, 333 k, 37 ells, 3 walkers, ragged lists."""
+    import paper_2505_22718_gb300 as S
+    w, tapers = make_ragged_case()
+    ctx = _context(w, tapers)
+    C = ctx.compute_cl(S.SWCL_SPLIT_BF16)
+    rng = np.random.default_rng(5)
+    Cb = rng.standard_normal(C.shape)
+    Pb, Ab, Wb = ctx.vjp(Cb, S.SWCL_SPLIT_BF16)
+    assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 1 and ctx.query(S.SWCL_Q_TILE_FWD) > 0
+    o = 0
+    for wk, lst in enumerate(w.ell_lists):
+        n = len(lst)
+        Cbw = np.zeros((len(w.ells), 7, 7))
+        Cbw[lst] = Cb[o:o + n]
+        f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, tapers, C_bar=Cbw)
+        assert norm_err(C[o:o + n], f["C"][lst]) < GATE_C
+        assert max_rel(Pb[wk], Pbo) < GATE_G
+        assert max_rel(Ab[wk], Abo) < GATE_G
+        assert max_rel(Wb[wk], Wbo) < GATE_G
+        o += n
+
+
+def test_rank_two_profiles():
+    """D(k, z) of rank 2: r = 2 basis columns per (tracer, multipole) in the forward tile."""
+    import copy
+
+    import paper_2505_22718_gb300 as S
+    from workloads import make_workload
+    w = copy.copy(make_workload("n5k"))
+    tr = [0, 3, 9, 10, 14]
+    w.W, w.kind, w.fft_bias, w.amp = w.W[tr], w.kind[tr], w.fft_bias[tr], w.amp[tr]
+    z = (1.0 + 0.01 * np.log(w.knots[0] / 0.1)) / w.D[0] - 1.0
+    lk = np.log(w.knots / 0.1)
+    w.D = (1.0 / (1.0 + z))[None, :] * (1.0 + 0.01 * lk[:, None] * (1.0 + z[None, :]))
+    w.ell_lists = None
+    ctx = _context(w)
+    C = ctx.compute_cl(S.SWCL_SPLIT_BF16)
+    Cb = np.random.default_rng(8).standard_normal(C.shape)
+    Pb, Ab, Wb = ctx.vjp(Cb, S.SWCL_SPLIT_BF16)
+    assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 2
+    assert ctx.query(S.SWCL_Q_TILE_FWD) % 2 == 0
+    f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=Cb)
+    assert norm_err(C, f["C"]) < GATE_C
+    assert max_rel(Pb[0], Pbo) < GATE_G
+    assert max_rel(Wb[0], Wbo) < GATE_G
