@@ -75,8 +75,10 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_Q_N_HALF          3  /* N/2 + 1 */
 #define SWCL_Q_KERNEL_LAUNCHES 4  /* kernels launched by the last compute/vjp call */
 #define SWCL_Q_PROFILE_RANK    5  /* rank r of the knot profiles D*B used (0 = one FFT per knot) */
-#define SWCL_Q_TILE_FWD        6  /* autotuned column tile of the basis-mode forward GEMM (0 = none yet) */
-#define SWCL_Q_TILE_ADJ        7  /* autotuned column tile of the basis-mode adjoint GEMM (0 = none yet) */
+#define SWCL_Q_TILE_FWD        6  /* autotuned tile of the basis-mode forward GEMM (0 = none yet):
+                                     column tile in bits 0-7, bit 8 set for the variant that runs
+                                     two CTAs per SM */
+#define SWCL_Q_TILE_ADJ        7  /* the same for the basis-mode adjoint GEMM */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the device memory the
  * context may hold (0 = no bound).  `stream` is a cudaStream_t (NULL = the context creates

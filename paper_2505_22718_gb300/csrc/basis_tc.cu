@@ -25,8 +25,8 @@
 // drain warps add each K-block's partial sums into FP32 registers with round-to-nearest.
 //
 // Warp roles: warp 0 streams both operand images into a shared-memory ring with cp.async.bulk;
-// warp 1 owns TMEM and issues tcgen05.mma; warps 2-9 drain TMEM (two warps per 32-lane quarter,
-// each with half of the columns) and run the epilogue.  All waits are bounded; a timeout raises
+// warp 1 owns TMEM and issues tcgen05.mma; the remaining 4 or 8 warps drain TMEM (with 8, two
+// warps per 32-lane quarter, each with half of the columns) and run the epilogue.  All waits are bounded; a timeout raises
 // the context's status word (SWCL_ERR_TIMEOUT).
 #include <algorithm>
 #include <cuda_bf16.h>
@@ -43,8 +43,10 @@ constexpr int kK = 32;                  // K elements (bf16) per 64-byte operand
 constexpr int kRow = 64;                // bytes per operand row and K-block
 constexpr int kM = 128;                 // rows per CTA (TMEM lanes)
 constexpr int kPlaneM = kM * kRow;      // 8 KB: one plane of the A operand per K-block
-constexpr int kDrain = 256;             // drain threads (warps 2-9)
-constexpr int kThreads = 64 + kDrain;   // warp 0 copies, warp 1 MMA
+// Two variants: DW = 8 drain warps (one CTA per SM, column tiles up to 128) and DW = 4 (tiles
+// up to 64, two CTAs per SM: two MMA-issuing threads share the SM's tensor core, which pays when
+// one thread alone cannot issue small MMAs as fast as the tensor core runs them).
+__host__ __device__ constexpr int threads_for(int DW) { return 64 + 32 * DW; }
 constexpr int kMaxNT = 128;
 constexpr int kHalf = kMaxNT / 2;       // columns per drain thread at most
 constexpr int kMaxStages = 6;
@@ -144,20 +146,33 @@ struct EpiFwd {
   // row m, this thread's columns j0 .. j0 + nc - 1 (j0 is a multiple of r)
   __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
     if (m >= N_k) return;
+    // column j = ((w N_tr + i) n_l + l) r + s, walked incrementally
+    int s = j0 % r, g = j0 / r;
+    int l = g % n_l, wi = g / n_l;
+    int icur = -1;
+    float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f;
     float v = 0.0f;
 #pragma unroll
     for (int c = 0; c < kHalf; ++c) {
-      if (c < nc) {
-        const int j = j0 + c;
-        if (j < n_cols) {
-          const int s = j % r, g = j / r;
-          const int l = g % n_l, wi = g / n_l;
-          const int i = wi % N_tr, w = wi / N_tr;
-          v = fmaf(kmu[((size_t)i * 4 + s) * N_k + m], acc[c], v);
-          if (s == r - 1) {
-            delta[(((size_t)w * n_l + l) * N_tr + i) * N_k + m] = v;
-            v = 0.0f;
-          }
+      if (c < nc && j0 + c < n_cols) {
+        const int i = wi % N_tr;
+        if (i != icur) {
+          icur = i;
+          const float* kr = kmu + (size_t)i * 4 * N_k + m;
+          k0 = __ldg(kr);
+          if (r > 1) k1 = __ldg(kr + N_k);
+          if (r > 2) k2 = __ldg(kr + 2 * N_k);
+          if (r > 3) k3 = __ldg(kr + 3 * N_k);
+        }
+        const float km = s == 0 ? k0 : s == 1 ? k1 : s == 2 ? k2 : k3;
+        v = fmaf(km, acc[c], v);
+        if (s == r - 1) {
+          delta[(((size_t)(wi / N_tr) * n_l + l) * N_tr + i) * N_k + m] = v;
+          v = 0.0f;
+        }
+        if (++s == r) {
+          s = 0;
+          if (++l == n_l) { l = 0; ++wi; }
         }
       }
     }
@@ -184,42 +199,43 @@ struct EpiAdj {
   __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
     const int n = m >> 1, t = m & 1;
     const bool live = n < n_h;
+    const int nn = live ? n : 0;
     float are = 0.0f, aim = 0.0f;
-    int gcur = -1;
+    // column j = ((w N_tr + i) r + s) n_l + l, walked incrementally; the same for every lane,
+    // so the group changes (shuffles) are warp-uniform
+    int l = j0 % n_l, g = j0 / n_l;
+    const float2* grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
+    int gcur = g;
 #pragma unroll
     for (int c = 0; c < kHalf; ++c) {
-      if (c < nc) {
-        const int j = j0 + c;           // the same for every lane: branches below are uniform
-        if (j < n_cols) {
-          const int l = j % n_l, g = j / n_l;
-          if (g != gcur) {
-            if (gcur >= 0) flush(gcur, n, t, are, aim);
-            gcur = g;
-            are = 0.0f;
-            aim = 0.0f;
-          }
-          const int i = (g / r) % N_tr;
-          const float2 G = live ? g32[((size_t)cls_of[i] * N_ell + l_lo + l) * n_h + n]
-                                : make_float2(0.0f, 0.0f);
-          const float y = acc[c];
-          if (t == 0) {
-            are = fmaf(G.x, y, are);
-            aim = fmaf(-G.y, y, aim);
-          } else {
-            are = fmaf(G.y, y, are);
-            aim = fmaf(G.x, y, aim);
-          }
+      if (c < nc && j0 + c < n_cols) {
+        if (g != gcur) {
+          flush(gcur, n, t, are, aim);
+          gcur = g;
+          are = 0.0f;
+          aim = 0.0f;
+          grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
         }
+        const float2 G = __ldg(grow + (size_t)l * n_h);
+        const float y = live ? acc[c] : 0.0f;
+        if (t == 0) {
+          are = fmaf(G.x, y, are);
+          aim = fmaf(-G.y, y, aim);
+        } else {
+          are = fmaf(G.y, y, are);
+          aim = fmaf(G.x, y, aim);
+        }
+        if (++l == n_l) { l = 0; ++g; }
       }
     }
-    if (gcur >= 0) flush(gcur, n, t, are, aim);
+    if (nc > 0 && j0 < n_cols) flush(gcur, n, t, are, aim);
   }
 };
 
 // ------------------------------------------------------------------- GEMM ----
 
-template <class P, class Epi>
-__global__ void __launch_bounds__(kThreads, 1)
+template <class P, class Epi, int DW>
+__global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
@@ -228,7 +244,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   const Layout L = layout<P>(NT, S);
   // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
   // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
-  // the TMEM buffer the K-block accumulates into (1 + kDrain arrivals); mmadone[s] when the
+  // the TMEM buffer the K-block accumulates into (1 + 32 DW arrivals); mmadone[s] when the
   // K-block's MMAs are done (one commit), which frees the stage for the copy warp and the
   // accumulator for the drain warps.  The MMA thread waits once and commits once per K-block:
   // a single thread issues tcgen05.mma only about as fast as the tensor core executes a
@@ -248,7 +264,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&full[s]), 1 + kDrain);
+      mbar_init(smem_u32(&full[s]), 1 + 32 * DW);
       mbar_init(smem_u32(&mmadone[s]), 1);
       mbar_init(smem_u32(&ready[s]), 1);
     }
@@ -336,10 +352,10 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   } else {
     // ------------------------------------------------------------ drain ----
     const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31 for this warp
-    const int half = (warp - 2) >> 2;    // column half
+    const int half = DW == 8 ? (warp - 2) >> 2 : 0;   // column half (DW = 8)
     const int row = quarter * 32 + lane;
     const int nch = NT / 16;
-    const int nch0 = (nch + 1) / 2;
+    const int nch0 = DW == 8 ? (nch + 1) / 2 : nch;
     const int c_begin = half ? nch0 : 0;
     const int my = half ? nch - nch0 : nch0;   // 16-column chunks of this thread (<= 4)
     float acc[kHalf];
@@ -627,12 +643,18 @@ unsigned grid_for(long total) {
   return (unsigned)std::max<long>(1, std::min<long>((total + 255) / 256, 152L * 32));
 }
 
+// Tile configuration code: column tile NT in bits 0-7, bit 8 = the two-CTAs-per-SM variant.
+constexpr int kPair = 256;
+
 template <class P>
-int shape_for(swcl_ctx* c, int NT, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
+int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
+  const int NT = code & 255;
+  const bool pair = code & kPair;
+  const uint32_t cap = pair ? 113 * 1024 : 227 * 1024;
   int stages = kMaxStages;
   Layout L = layout<P>(NT, stages);
-  while (stages > 2 && L.total > 227 * 1024) L = layout<P>(NT, --stages);
-  if (L.total > 227 * 1024) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
+  while (stages > 2 && L.total > cap) L = layout<P>(NT, --stages);
+  if (L.total > cap) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
   while (cols < (uint32_t)(4 * stride)) cols <<= 1;
@@ -641,25 +663,35 @@ int shape_for(swcl_ctx* c, int NT, int n_mt, int n_kb, GemmShape& sh, uint32_t& 
   return SWCL_OK;
 }
 
-template <class P, class Epi>
-cudaError_t launch_gemm(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
-                        uint32_t smem, int n_nt, const Epi& epi) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi>,
+template <class P, class Epi, int DW>
+cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                           uint32_t smem, int n_nt, const Epi& epi) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi><<<(unsigned)(sh.n_mt * n_nt), kThreads, smem, c->stream>>>(
+  k_gemm_basis<P, Epi, DW><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
       a, b, sh, epi, (int*)c->ws_status.p);
   return cudaGetLastError();
 }
 
-// candidate column tiles: multiples of 16; in forward tiles each drain thread's column range
-// (whole 16-column chunks, split in two halves) holds whole groups of r basis columns
-std::vector<int> nt_candidates(int r, bool need_groups) {
+template <class P, class Epi>
+cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* b,
+                        const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
+  return (code & kPair) ? launch_variant<P, Epi, 4>(c, a, b, sh, smem, n_nt, epi)
+                        : launch_variant<P, Epi, 8>(c, a, b, sh, smem, n_nt, epi);
+}
+
+// Candidate tile codes: column tiles that are multiples of 16; in forward tiles each drain
+// thread's column range (whole 16-column chunks; split in two halves with eight drain warps)
+// holds whole groups of r basis columns.
+std::vector<int> tile_candidates(int r, bool need_groups) {
   std::vector<int> v;
   for (int nt = 32; nt <= kMaxNT; nt += 16) {
     const int half0 = 16 * ((nt / 16 + 1) / 2);
     if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt);
   }
+  for (int nt = 32; nt <= 64; nt += 16)
+    if (!need_groups || nt % r == 0) v.push_back(nt | kPair);
   return v;
 }
 
@@ -747,22 +779,23 @@ int counted(swcl_ctx* c, const char* name, F f) {
 // Times each candidate tile (operand build excluded) and keeps the fastest.
 template <class Run>
 int autotune(swcl_ctx* c, const std::vector<int>& cands, Run run, int& best) {
+  // each candidate: operand build + one warm-up launch, then three timed launches
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
     return fail(c, SWCL_ERR_CUDA, "autotune events");
   float best_ms = 1e30f;
   best = cands.front();
   int st = SWCL_OK;
-  for (int NT : cands) {
-    if ((st = run(NT, true))) break;           // operand build + one warm-up launch
+  for (int code : cands) {
+    if ((st = run(code, true))) break;
     cudaEventRecord(a, c->stream);
-    for (int rep = 0; rep < 3 && st == SWCL_OK; ++rep) st = run(NT, false);
+    for (int rep = 0; rep < 3 && st == SWCL_OK; ++rep) st = run(code, false);
     cudaEventRecord(b, c->stream);
     if (st) break;
     cudaEventSynchronize(b);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
-    if (ms < best_ms) { best_ms = ms; best = NT; }
+    if (ms < best_ms) { best_ms = ms; best = code; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -778,26 +811,27 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
   if (st) return st;
   const int r = basis_rank(c);
   const int n_cols = c->n_walk * c->N_tr * n_l * r;
-  auto run = [&](int NT, bool build) -> int {
+  auto run = [&](int code, bool build) -> int {
+    const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
     if (build && (st = build_h(c, NT, n_nt, l_lo, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
-    if ((st = shape_for<A4B4>(c, NT, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
+    if ((st = shape_for<A4B4>(c, code, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
     EpiFwd epi{(float*)c->ws_delta.p, (const float*)c->bt_kmu.p, c->N_k, c->N_tr, n_l, r, n_cols};
-    cudaError_t e = launch_gemm<A4B4>(c, (const uint8_t*)c->bt_eimg_f.p,
+    cudaError_t e = launch_gemm<A4B4>(c, code, (const uint8_t*)c->bt_eimg_f.p,
                                       (const uint8_t*)c->bt_himg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward GEMM");
   };
   if (c->bt_nt_fwd == 0) {
-    if (c->capturing) c->bt_nt_fwd = nt_candidates(r, true).back();
-    else if ((st = autotune(c, nt_candidates(r, true), run, c->bt_nt_fwd))) return st;
+    if (c->capturing) c->bt_nt_fwd = 96 % r == 0 ? 96 : 64;
+    else if ((st = autotune(c, tile_candidates(r, true), run, c->bt_nt_fwd))) return st;
   }
-  const int NT = c->bt_nt_fwd;
+  const int code = c->bt_nt_fwd, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
   if ((st = counted(c, "basis operand fwd", [&] { return build_h(c, NT, n_nt, l_lo, n_l); })))
     return st;
-  return counted(c, "basis gemm fwd", [&] { return run(NT, false); });
+  return counted(c, "basis gemm fwd", [&] { return run(code, false); });
 }
 
 // ws_cbar (FP64 complex, [n_walk][N_tr][NI][n_h], zeroed here) from ws_dbar (FP32,
@@ -809,24 +843,25 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
   const int r = basis_rank(c);
   const int n_cols = c->n_walk * c->N_tr * r * n_l;
   const size_t cbytes = sizeof(cplx) * (size_t)c->n_walk * c->N_tr * sv.NI * c->n_h;
-  auto run = [&](int NT, bool build) -> int {
+  auto run = [&](int code, bool build) -> int {
+    const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
     if (build && (st = build_d(c, NT, n_nt, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
-    if ((st = shape_for<A4B3>(c, NT, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
+    if ((st = shape_for<A4B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
     EpiAdj epi{(cplx*)c->ws_cbar.p, (const float2*)c->bt_g32.p, (const int*)c->d_cls_of.p,
                c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
-    cudaError_t e = launch_gemm<A4B3>(c, (const uint8_t*)c->bt_eimg_a.p,
+    cudaError_t e = launch_gemm<A4B3>(c, code, (const uint8_t*)c->bt_eimg_a.p,
                                       (const uint8_t*)c->bt_dimg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint GEMM");
   };
   if (c->bt_nt_adj == 0) {
     if (c->capturing) {
-      c->bt_nt_adj = 128;
+      c->bt_nt_adj = 96;
     } else {
       // the tuning launches accumulate into ws_cbar, which is cleared below
-      if ((st = autotune(c, nt_candidates(r, false), run, c->bt_nt_adj))) return st;
+      if ((st = autotune(c, tile_candidates(r, false), run, c->bt_nt_adj))) return st;
       if (accumulate) return fail(c, SWCL_ERR_STATE, "basis adjoint tuned inside an accumulation");
     }
   }
@@ -834,10 +869,10 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
     cudaError_t e = cudaMemsetAsync(c->ws_cbar.p, 0, cbytes, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "clear cbar");
   }
-  const int NT = c->bt_nt_adj;
+  const int code = c->bt_nt_adj, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
   if ((st = counted(c, "basis operand adj", [&] { return build_d(c, NT, n_nt, n_l); }))) return st;
-  return counted(c, "basis gemm adj", [&] { return run(NT, false); });
+  return counted(c, "basis gemm adj", [&] { return run(code, false); });
 }
 
 }  // namespace swcl

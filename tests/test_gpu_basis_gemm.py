@@ -44,11 +44,14 @@ def test_n5k_against_oracle_and_stencil_kernels(wl):
     ctx = _context(w)
     C, (Pb, Ab, Wb) = _fwd_vjp(ctx, w.C_bar)
     assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 1
-    nt_f, nt_a = ctx.query(S.SWCL_Q_TILE_FWD), ctx.query(S.SWCL_Q_TILE_ADJ)
+    code_f, code_a = ctx.query(S.SWCL_Q_TILE_FWD), ctx.query(S.SWCL_Q_TILE_ADJ)
+    nt_f, nt_a = code_f & 255, code_a & 255
     assert nt_f in range(32, 129, 16) and nt_a in range(32, 129, 16)
+    assert code_f >> 8 in (0, 1) and code_a >> 8 in (0, 1)
+    assert (code_f < 256 or nt_f <= 64) and (code_a < 256 or nt_a <= 64)
     f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=w.C_bar)
     e = (norm_err(C, f["C"]), max_rel(Pb[0], Pbo), max_rel(Ab[0], Abo), max_rel(Wb[0], Wbo))
-    print("basis GEMM n5k: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e  tiles %d/%d" % (e + (nt_f, nt_a)))
+    print("basis GEMM n5k: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e  tile codes %d/%d" % (e + (code_f, code_a)))
     assert e[0] < GATE_C and max(e[1:]) < GATE_G
     assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
     d = S.swcl_debug_read(ctx.ptr, S.SWCL_DBG_DELTA).reshape(f["delta"].shape)
@@ -115,7 +118,7 @@ def test_rank_two_profiles():
     Cb = np.random.default_rng(8).standard_normal(C.shape)
     Pb, Ab, Wb = ctx.vjp(Cb, S.SWCL_SPLIT_BF16)
     assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 2
-    assert ctx.query(S.SWCL_Q_TILE_FWD) % 2 == 0
+    assert (ctx.query(S.SWCL_Q_TILE_FWD) & 255) % 2 == 0
     f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=Cb)
     assert norm_err(C, f["C"]) < GATE_C
     assert max_rel(Pb[0], Pbo) < GATE_G
