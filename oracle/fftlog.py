@@ -76,14 +76,15 @@ def ell_prefactor(ells, kind: int) -> np.ndarray:
 
 # ------------------------------------------------------------- FFTLog ------
 
-def fftlog_coefficients(F, chi_min, chi_max, b, taper_chi=None, taper_c=None):
+def fftlog_coefficients(F, chi_min, chi_max, b, taper_chi=None, taper_c=None, fft="direct"):
     """Two-sided FFTLog coefficients c_n, n = -N/2..N/2, of real samples F[..., m].
 
     Eq. (3.2) with readings R2-R4:
         c_n = T_c(|n|) chi_min^{-i eta_n} (1/N) sum_{m<N} F(chi_m) chi_m^{-b} T_chi(m) e^{-2 pi i n m/N},
     and c_{+-N/2} halved, so that F(chi) = sum_n c_n chi^{b + i eta_n} (Eq. 3.1) on the grid.
-    The DFT is the plain O(N^2) sum, written as a product with the DFT matrix
-    whose phases use the exact integer residue (n m mod N).
+    fft="direct": the plain O(N^2) sum, written as a product with the DFT matrix whose phases
+    use the exact integer residue (n m mod N).  fft="numpy": the same sum by numpy.fft (a library
+    step for large N; the pins check it against the direct sum), with c_{-n} read from bin N - n.
     """
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[-1]
@@ -93,10 +94,15 @@ def fftlog_coefficients(F, chi_min, chi_max, b, taper_chi=None, taper_c=None):
     g = F * chi ** (-b)
     if taper_chi is not None:
         g = g * taper_chi
-    m = np.arange(N)
-    resid = np.mod(np.outer(m, n), N)                 # (n m) mod N, exact
-    dft = np.exp(-2j * np.pi * resid / N)             # [N, N+1]
-    c = (g @ dft) / N
+    if fft == "numpy":
+        c = np.fft.fft(g, axis=-1)[..., np.mod(n, N)] / N
+    elif fft == "direct":
+        m = np.arange(N)
+        resid = np.mod(np.outer(m, n), N)             # (n m) mod N, exact
+        dft = np.exp(-2j * np.pi * resid / N)         # [N, N+1]
+        c = (g @ dft) / N
+    else:
+        raise ValueError("fft must be 'direct' or 'numpy'")
     c = c * np.exp(-1j * eta * np.log(chi_min))       # chi_min^{-i eta_n}
     if taper_c is not None:
         c = c * taper_c[np.abs(n)]
@@ -214,8 +220,9 @@ def source_samples(W, D, B, chi, kind):
 class Grids:
     """Everything that depends on the grids only (the paper's precomputation, Sec. 3.2)."""
 
-    def __init__(self, N, chi_min, chi_max, k, ells, knots, kind, fft_bias):
+    def __init__(self, N, chi_min, chi_max, k, ells, knots, kind, fft_bias, fft="direct"):
         self.N = int(N)
+        self.fft = fft                                            # see fftlog_coefficients
         self.chi_min, self.chi_max = float(chi_min), float(chi_max)
         self.L = np.log(self.chi_max / self.chi_min)
         self.chi = chi_grid(self.chi_min, self.chi_max, self.N)
@@ -247,7 +254,7 @@ def window_coefficients(g: Grids, W, D, B=None, taper_chi=None, taper_c=None):
     for i in range(F.shape[0]):
         tc = None if taper_chi is None else taper_chi[i]
         tn = None if taper_c is None else taper_c[i]
-        out.append(fftlog_coefficients(F[i], g.chi_min, g.chi_max, g.fft_bias[i], tc, tn))
+        out.append(fftlog_coefficients(F[i], g.chi_min, g.chi_max, g.fft_bias[i], tc, tn, g.fft))
     return np.array(out)                                          # [N_tr, N_I, N+1]
 
 
@@ -321,9 +328,10 @@ def vjp(g: Grids, fwd: dict, C_bar, W, D, P, amp, B=None, taper_chi=None, taper_
 
     N = g.N
     n, eta = g.n, g.eta
-    m = np.arange(N)
-    resid = np.mod(np.outer(m, n), N)
-    dft = np.exp(-2j * np.pi * resid / N)                       # [N, N+1]
+    if g.fft == "direct":
+        m = np.arange(N)
+        resid = np.mod(np.outer(m, n), N)
+        dft = np.exp(-2j * np.pi * resid / N)                   # [N, N+1]
     chi_phase = np.exp(-1j * eta * np.log(g.chi_min))
     F_bar_all = []
     W_bar = np.zeros((coef.shape[0], N))
@@ -346,8 +354,15 @@ def vjp(g: Grids, fwd: dict, C_bar, W, D, P, amp, B=None, taper_chi=None, taper_
         if taper_c is not None:
             c_bar = c_bar * taper_c[i][np.abs(n)]
         c_bar = c_bar * np.conj(chi_phase)
-        # c = (g @ dft)/N for real g:  g_bar_m = Re sum_n conj(dft_mn) ... in the real-pair sense
-        g_bar = np.real(np.conj(c_bar) @ dft.T).astype(np.float64) / N  # [N_I, N]
+        # c = (g @ dft)/N for real g: in the real-pair sense g_bar_m = Re sum_n conj(c_bar_n) dft_mn / N
+        if g.fft == "direct":
+            g_bar = np.real(np.conj(c_bar) @ dft.T).astype(np.float64) / N  # [N_I, N]
+        else:
+            # the same sum by numpy.fft: conj(c_bar_n) into bin n mod N (both Nyquist terms in N/2)
+            X = np.zeros(c_bar.shape[:-1] + (N,), dtype=np.complex128)
+            for col, nn in enumerate(n):
+                X[..., nn % N] += np.conj(c_bar[..., col])
+            g_bar = np.real(np.fft.fft(X, axis=-1)) / N
         F_bar = g_bar * g.chi ** (-b)
         if taper_chi is not None:
             F_bar = F_bar * taper_chi[i]

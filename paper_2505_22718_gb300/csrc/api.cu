@@ -575,6 +575,59 @@ static int check_ready(swcl_ctx* c, int precision) {
   return SWCL_OK;
 }
 
+// Multipoles per chunk of Delta: all of them, unless the memory budget cannot hold Delta and
+// Dbar (and, in basis mode, the per-call GEMM operands) for every multipole at once.  Then the
+// forward pass contracts and integrates chunk by chunk, and the VJP recomputes each chunk's
+// Delta before its reverse mode.  Returns 0 when not even 8 multipoles fit.
+static int plan_ell_chunk(swcl_ctx* c, int precision) {
+  const int N_ell = c->N_ell;
+  const bool fp64 = precision == SWCL_FP64;
+  const bool basis = use_basis_gemm(c, precision);
+  if (!c->budget || (!fp64 && !basis)) return N_ell;   // knot-stencil tensor-core forms: whole
+  const swcl::Stencil sv = swcl::stencil(c);
+  const size_t nw = c->n_walk, nrow = nw * c->N_tr, ntr2 = (size_t)c->N_tr * c->N_tr;
+  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float));
+  if (basis) per_l += swcl::basis_bytes_per_ell(c);
+  // workspace that does not scale with the chunk
+  size_t fixed = 2 * sizeof(cplx) * nrow * sv.NI * c->n_h              // coefficients, cbar
+                 + 2 * sizeof(double) * nw * N_ell * ntr2               // U, symmetrised cotangent
+                 + sizeof(double) * out_count(c) * ntr2                 // output staging
+                 + sizeof(double) * nrow * c->N
+                 + swcl::fftlog_adj_scratch_bytes(c->n_walk, c->N_tr, sv.NI, c->N)
+                 + swcl::delta_bar_scratch_bytes(c->n_walk, c->N_k, N_ell)
+                 + sizeof(double) * (nw * c->N_k + nrow);
+  if (basis) fixed += swcl::basis_fixed_bytes(c);
+  const DevBuf* ws[] = {&c->ws_coef, &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar,
+                        &c->ws_Cbar, &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_pbpart,
+                        &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
+                        &c->bt_himg, &c->bt_dimg};
+  size_t ws_now = 0;
+  for (const DevBuf* b : ws) ws_now += b->bytes;
+  const size_t other = c->held - ws_now;     // tables, inputs
+  if (other + fixed + per_l * N_ell <= c->budget) return N_ell;
+  if (other + fixed + per_l * 8 > c->budget) return 0;
+  const size_t n = (c->budget - other - fixed) / per_l;
+  return (int)std::min<size_t>(N_ell, std::max<size_t>(8, n / 8 * 8));
+}
+
+// Delta for multipoles [l_lo, l_lo + n_l) into ws_delta ([n_walk][n_l][N_tr][N_k])
+static int contract_chunk(swcl_ctx* c, int precision, int l_lo, int n_l) {
+  const swcl::Stencil sv = swcl::stencil(c);
+  if (precision == SWCL_FP64) {
+    SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
+                                              (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
+                                              (const int*)c->d_cls_of.p, (const double*)c->d_kpow.p,
+                                              sv.j0, sv.w, sv.w_ts, c->n_walk, c->N_tr, sv.NI,
+                                              c->n_h, c->N_k, c->N_ell, l_lo, n_l, c->stream),
+                "contract fp64");
+    return SWCL_OK;
+  }
+  if (use_basis_gemm(c, precision)) return swcl::basis_forward(c, l_lo, n_l);
+  if (l_lo != 0 || n_l != c->N_ell)
+    return swcl::fail(c, SWCL_ERR_OOM_BUDGET, "the knot-stencil tensor-core form needs Delta for every multipole");
+  return swcl::compute_delta_tc(c, precision);
+}
+
 int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -591,36 +644,36 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   const int nw = c->n_walk, N_tr = c->N_tr, N_I = sv.NI, n_h = c->n_h, N = c->N;
   const int N_k = c->N_k, N_ell = c->N_ell;
   const size_t nrow = (size_t)nw * N_tr;
+  const bool fp64 = precision == SWCL_FP64;
+  const int n_lc = plan_ell_chunk(c, precision);
+  if (n_lc == 0)
+    return swcl::fail(c, SWCL_ERR_OOM_BUDGET, "memory budget too small for 8 multipoles of Delta");
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
-  const size_t nd = nrow * N_ell * N_k;
-  SWCL_TRY(swcl::ensure(c, c->ws_delta, nd * (precision == SWCL_FP64 ? sizeof(double) : sizeof(float))));
+  SWCL_TRY(swcl::ensure(c, c->ws_delta, nrow * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
-  if (precision == SWCL_FP64) {
+  if (fp64)
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
                                            (const double*)c->d_chipow.p, sv.D, sv.B,
                                            (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                            nw, N_tr, N_I, N, c->stream), "fftlog");
-    SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
-                                              (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
-                                              (const int*)c->d_cls_of.p, (const double*)c->d_kpow.p,
-                                              sv.j0, sv.w, sv.w_ts, nw, N_tr, N_I, n_h,
-                                              N_k, N_ell, c->stream), "contract fp64");
-    SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
-                                          (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                          N_tr, N_k, N_ell, c->stream), "k-quadrature fp64");
-  } else {
+  else
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd_df((float4*)c->ws_coef.p, (const double*)c->d_W.p,
                                                (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
-    if (use_basis_gemm(c, precision))
-      SWCL_TRY(swcl::basis_forward(c, 0, N_ell));
+  for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
+    const int n_l = std::min(n_lc, N_ell - l_lo);
+    SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
+    if (fp64)
+      SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
+                                            (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
+                                            N_tr, N_k, N_ell, l_lo, n_l, c->stream), "k-quadrature fp64");
     else
-      SWCL_TRY(swcl::compute_delta_tc(c, precision));
-    SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
-                                         (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                         N_tr, N_k, N_ell, c->stream), "k-quadrature f32");
+      SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
+                                           (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
+                                           N_tr, N_k, N_ell, l_lo, n_l, c->stream), "k-quadrature f32");
   }
+  c->ell_chunk = n_lc;
   const int64_t n_out = out_count(c);
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
   double* dst = C_out;
@@ -657,6 +710,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   const int64_t n_out = out_count(c);
   const size_t nrow = (size_t)nw * N_tr;
   const bool fp64 = precision == SWCL_FP64;
+  const int n_lc = c->ell_chunk;
+  const bool recompute = n_lc < N_ell;
   // cotangent on the device
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
   const double* cb = C_bar;
@@ -665,7 +720,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     cb = (const double*)c->ws_C.p;
   }
   SWCL_TRY(swcl::ensure(c, c->ws_Cbar, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
-  SWCL_TRY(swcl::ensure(c, c->ws_dbar, nrow * N_ell * N_k * (fp64 ? sizeof(double) : sizeof(float))));
+  SWCL_TRY(swcl::ensure(c, c->ws_dbar, nrow * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_cbar, sizeof(cplx) * nrow * N_I * n_h));
   SWCL_TRY(swcl::ensure(c, c->ws_outP, sizeof(double) * nw * (size_t)N_k));
   SWCL_TRY(swcl::ensure(c, c->ws_outA, sizeof(double) * nrow));
@@ -678,27 +733,30 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   SWCL_TRY(swcl::ensure(c, c->ws_pbpart, swcl::delta_bar_scratch_bytes(nw, N_k, N_ell)));
   double* Pb = P_bar && swcl::is_device_ptr(P_bar) ? P_bar : (double*)c->ws_outP.p;
   double* Ab = amp_bar && swcl::is_device_ptr(amp_bar) ? amp_bar : (double*)c->ws_outA.p;
-  if (fp64) {
-    SWCL_LAUNCH(c, swcl::launch_delta_bar<double>((double*)c->ws_dbar.p, Pb,
-                                                  (const double*)c->ws_delta.p,
-                                                  (const double*)c->ws_Cbar.p,
-                                                  (const double*)c->d_amp.p, (const double*)c->d_P.p,
-                                                  (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
-                                                  (double*)c->ws_pbpart.p, c->stream), "delta_bar fp64");
-    ++c->last_launches;  // the P_bar chunk reduction
-  } else {
-    SWCL_LAUNCH(c, swcl::launch_delta_bar<float>((float*)c->ws_dbar.p, Pb,
-                                                 (const float*)c->ws_delta.p,
-                                                 (const double*)c->ws_Cbar.p,
-                                                 (const double*)c->d_amp.p, (const double*)c->d_P.p,
-                                                 (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
-                                                 (double*)c->ws_pbpart.p, c->stream), "delta_bar f32");
-    ++c->last_launches;  // the P_bar chunk reduction
-  }
   SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
                                       (const double*)c->d_amp.p, nw, N_tr, N_ell, c->stream),
               "amp_bar");
-  if (W_bar) {
+  for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
+    const int n_l = std::min(n_lc, N_ell - l_lo);
+    const bool accumulate = l_lo > 0;
+    if (recompute) SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
+    if (fp64)
+      SWCL_LAUNCH(c, swcl::launch_delta_bar<double>((double*)c->ws_dbar.p,
+                                                    (const double*)c->ws_delta.p,
+                                                    (const double*)c->ws_Cbar.p,
+                                                    (const double*)c->d_amp.p, (const double*)c->d_P.p,
+                                                    (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
+                                                    l_lo, n_l, (double*)c->ws_pbpart.p, c->stream),
+                  "delta_bar fp64");
+    else
+      SWCL_LAUNCH(c, swcl::launch_delta_bar<float>((float*)c->ws_dbar.p,
+                                                   (const float*)c->ws_delta.p,
+                                                   (const double*)c->ws_Cbar.p,
+                                                   (const double*)c->d_amp.p, (const double*)c->d_P.p,
+                                                   (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
+                                                   l_lo, n_l, (double*)c->ws_pbpart.p, c->stream),
+                  "delta_bar f32");
+    if (!W_bar) continue;
     if (fp64) {
       SWCL_LAUNCH(c, swcl::launch_contract_fp64_adj((cplx*)c->ws_cbar.p, (const double*)c->ws_dbar.p,
                                                     (const cplx*)c->d_phase.p,
@@ -706,13 +764,18 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                     (const int*)c->d_cls_of.p,
                                                     (const double*)c->d_kpow.p,
                                                     sv.j0, sv.w, sv.w_ts, nw, N_tr, N_I,
-                                                    n_h, N_k, N_ell, c->stream), "contract adj fp64");
+                                                    n_h, N_k, N_ell, l_lo, n_l, accumulate,
+                                                    c->stream), "contract adj fp64");
+    } else if (use_basis_gemm(c, precision)) {
+      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate));
     } else {
-      if (use_basis_gemm(c, precision))
-        SWCL_TRY(swcl::basis_adjoint(c, 0, N_ell, false));
-      else
-        SWCL_TRY(swcl::contract_adj_tc(c, precision));
+      SWCL_TRY(swcl::contract_adj_tc(c, precision));   // whole multipole range (no chunks)
     }
+  }
+  SWCL_LAUNCH(c, swcl::launch_pbar_reduce(Pb, (const double*)c->ws_pbpart.p,
+                                          (const double*)c->d_wk2.p, nw, N_k, N_ell, c->stream),
+              "P_bar reduce");
+  if (W_bar) {
     double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
     double* scratch = (double*)((char*)c->ws_outW.p + wbytes);
     SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
@@ -914,7 +977,7 @@ int swcl_query(swcl_ctx* c, int key, int64_t* value) {
   if (!c || !value) return SWCL_ERR_INVALID_ARG;
   switch (key) {
     case SWCL_Q_WORKSPACE_BYTES: *value = (int64_t)c->held; return SWCL_OK;
-    case SWCL_Q_RECOMPUTE: *value = 0; return SWCL_OK;
+    case SWCL_Q_RECOMPUTE: *value = c->ell_chunk > 0 && c->ell_chunk < c->N_ell ? 1 : 0; return SWCL_OK;
     case SWCL_Q_N_HALF: *value = c->n_h; return SWCL_OK;
     case SWCL_Q_KERNEL_LAUNCHES: *value = c->last_launches; return SWCL_OK;
     case SWCL_Q_PROFILE_RANK: *value = c->lr_basis ? c->lr_true_rank : 0; return SWCL_OK;

@@ -699,6 +699,20 @@ int basis_rank(swcl_ctx* c) { return c->lr_true_rank; }
 
 }  // namespace
 
+size_t basis_fixed_bytes(const swcl_ctx* c) {
+  const size_t f_mt = (c->N_k + kM - 1) / kM, f_kb = (2 * c->n_h + kK - 1) / kK;
+  const size_t a_mt = (2 * c->n_h + kM - 1) / kM, a_kb = (c->N_k + kK - 1) / kK;
+  const size_t ng = (size_t)c->n_cls * c->N_ell * c->n_h;
+  return (f_mt * f_kb + a_mt * a_kb) * 4 * kPlaneM + ng * (sizeof(float4) + sizeof(float2)) +
+         sizeof(float) * (size_t)c->N_tr * 4 * c->N_k +
+         (size_t)kMaxNT * (f_kb * 4 + a_kb * 3) * kRow;   // column padding of the last tile
+}
+
+size_t basis_bytes_per_ell(const swcl_ctx* c) {
+  const size_t f_kb = (2 * c->n_h + kK - 1) / kK, a_kb = (c->N_k + kK - 1) / kK;
+  return (size_t)c->n_walk * c->N_tr * std::max(1, c->lr_true_rank) * (f_kb * 4 + a_kb * 3) * kRow;
+}
+
 // Constant operands of basis mode: the two phase images, the FP32/double-float Gamma tables and
 // kpow * mu.  Rebuilt whenever the grids, tracers or knot profiles change.
 int basis_prepare(swcl_ctx* c) {

@@ -20,7 +20,8 @@ k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
                 const cplx* __restrict__ phase, const cplx* __restrict__ gtab,
                 const int* __restrict__ cls_of, const double* __restrict__ kpow,
                 const int* __restrict__ j0, const double* __restrict__ lw, long lw_ts, int N_tr,
-                int N_I, int n_h, int N_k, int N_ell) {
+                int N_I, int n_h, int N_k, int N_ell, int l_lo, int n_l) {
+  // multipoles [l_lo, l_lo + n_l) into delta[w][l - l_lo][i][q]
   __shared__ cplx Xs[BN][BQ + 1];
   __shared__ cplx Gs[BN][BL + 1];
   const int q0 = blockIdx.x * BQ;
@@ -66,7 +67,7 @@ k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
     for (int e = threadIdx.x; e < BL * BN; e += NT) {
       int nn = e % BN, ll = e / BN;
       int l = l0 + ll, n = n0 + nn;
-      Gs[nn][ll] = (l < N_ell && n < n_h) ? G[(size_t)l * n_h + n] : cplx{0.0, 0.0};
+      Gs[nn][ll] = (l < n_l && n < n_h) ? G[(size_t)(l_lo + l) * n_h + n] : cplx{0.0, 0.0};
     }
     __syncthreads();
 #pragma unroll
@@ -87,8 +88,8 @@ k_contract_fp64(double* __restrict__ delta, const cplx* __restrict__ coef,
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     int l = l0 + tl + 16 * b;
-    if (l >= N_ell) continue;
-    double* out = delta + (((size_t)w * N_ell + l) * N_tr + i) * N_k;
+    if (l >= n_l) continue;
+    double* out = delta + (((size_t)w * n_l + l) * N_tr + i) * N_k;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       int q = q0 + tq * 4 + a;
@@ -107,7 +108,8 @@ k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
                     const cplx* __restrict__ phase, const cplx* __restrict__ gtab,
                     const int* __restrict__ cls_of, const double* __restrict__ kpow,
                     const int* __restrict__ j0, const double* __restrict__ lw, long lw_ts,
-                    int N_tr, int N_I, int n_h, int N_k, int N_ell) {
+                    int N_tr, int N_I, int n_h, int N_k, int N_ell, int l_lo, int n_l) {
+  // dbar holds multipoles [l_lo, l_lo + n_l); cbar accumulates (zeroed by the caller)
   __shared__ double Ds[AL][AQ + 1];
   __shared__ cplx Gs[AL][AN + 1];
   __shared__ cplx V[AQ][AN + 1];
@@ -126,17 +128,17 @@ k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) { ar[a][b] = 0.0; ai[a][b] = 0.0; }
-  for (int l0 = 0; l0 < N_ell; l0 += AL) {
+  for (int l0 = 0; l0 < n_l; l0 += AL) {
     for (int e = threadIdx.x; e < AL * AQ; e += NT) {
       int ql = e % AQ, ll = e / AQ;
       int q = q0 + ql, l = l0 + ll;
-      Ds[ll][ql] = (q < N_k && l < N_ell)
-                       ? dbar[(((size_t)w * N_ell + l) * N_tr + i) * N_k + q] : 0.0;
+      Ds[ll][ql] = (q < N_k && l < n_l)
+                       ? dbar[(((size_t)w * n_l + l) * N_tr + i) * N_k + q] : 0.0;
     }
     for (int e = threadIdx.x; e < AL * AN; e += NT) {
       int nn = e % AN, ll = e / AN;
       int n = nb + nn, l = l0 + ll;
-      Gs[ll][nn] = (n < n_h && l < N_ell) ? G[(size_t)l * n_h + n] : cplx{0.0, 0.0};
+      Gs[ll][nn] = (n < n_h && l < n_l) ? G[(size_t)(l_lo + l) * n_h + n] : cplx{0.0, 0.0};
     }
     __syncthreads();
 #pragma unroll
@@ -223,23 +225,26 @@ k_contract_fp64_adj(cplx* __restrict__ cbar, const double* __restrict__ dbar,
 cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
                                  const cplx* gtab, const int* cls_of, const double* kpow,
                                  const int* j0, const double* lw, long lw_ts, int n_walk,
-                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, cudaStream_t s) {
-  dim3 g((N_k + BQ - 1) / BQ, (N_ell + BL - 1) / BL, n_walk * N_tr);
+                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, int l_lo,
+                                 int n_l, cudaStream_t s) {
+  dim3 g((N_k + BQ - 1) / BQ, (n_l + BL - 1) / BL, n_walk * N_tr);
   k_contract_fp64<<<g, NT, 0, s>>>(delta, coef, phase, gtab, cls_of, kpow, j0, lw, lw_ts, N_tr,
-                                    N_I, n_h, N_k, N_ell);
+                                    N_I, n_h, N_k, N_ell, l_lo, n_l);
   return cudaGetLastError();
 }
 
 cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx* phase,
                                      const cplx* gtab, const int* cls_of, const double* kpow,
                                      const int* j0, const double* lw, long lw_ts, int n_walk,
-                                     int N_tr, int N_I, int n_h, int N_k, int N_ell,
-                                     cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(cbar, 0, (size_t)n_walk * N_tr * N_I * n_h * sizeof(cplx), s);
-  if (e != cudaSuccess) return e;
+                                     int N_tr, int N_I, int n_h, int N_k, int N_ell, int l_lo,
+                                     int n_l, bool accumulate, cudaStream_t s) {
+  if (!accumulate) {
+    cudaError_t e = cudaMemsetAsync(cbar, 0, (size_t)n_walk * N_tr * N_I * n_h * sizeof(cplx), s);
+    if (e != cudaSuccess) return e;
+  }
   dim3 g((N_k + AQ - 1) / AQ, (n_h + AN - 1) / AN, n_walk * N_tr);
   k_contract_fp64_adj<<<g, NT, 0, s>>>(cbar, dbar, phase, gtab, cls_of, kpow, j0, lw, lw_ts, N_tr,
-                                        N_I, n_h, N_k, N_ell);
+                                        N_I, n_h, N_k, N_ell, l_lo, n_l);
   return cudaGetLastError();
 }
 

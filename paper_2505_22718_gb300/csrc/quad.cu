@@ -21,16 +21,17 @@ constexpr int QC = 128;    // k points staged per step
 template <typename T>
 __global__ void __launch_bounds__(QT)
 k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __restrict__ P,
-       const double* __restrict__ wk2, int N_tr, int N_k, int N_ell) {
+       const double* __restrict__ wk2, int N_tr, int N_k, int N_ell, int l_lo, int n_l) {
   extern __shared__ double qsm[];
   T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][QC]
   __shared__ double us[QC];
   __shared__ float usf[QC];
   __shared__ double red[QT];
-  const int l = blockIdx.x;
+  // Delta holds multipoles [l_lo, l_lo + n_l) of each walker; U all N_ell
+  const int l = l_lo + blockIdx.x;
   const int w = blockIdx.y;
   const int npair = N_tr * (N_tr + 1) / 2;
-  const T* dl = delta + ((size_t)w * N_ell + l) * N_tr * N_k;
+  const T* dl = delta + ((size_t)w * n_l + blockIdx.x) * N_tr * N_k;
   const double* Pw = P + (size_t)w * N_k;
   // thread -> (pair slot, k-group)
   const int ngroups = max(1, QT / npair);
@@ -179,7 +180,9 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
 // walker); one thread per k point.  S_l A_j is staged per multipole chunk in shared memory (in the
 // arithmetic type T: FP32 for the mixed paths, FP64 for the FP64 path), Delta_j(l, q) in a
 // per-thread shared column.  The P_bar partial of each multipole chunk is a compensated sum
-// (TwoSum) written as FP64 to pbar_part[chunk][w][q]; k_pbar_reduce adds the chunks.
+// (TwoSum) written as FP64 to pbar_part[chunk][w][q]; k_pbar_reduce adds the chunks.  A launch
+// covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a multipole chunk
+// when Delta is recomputed chunk by chunk); the reduction runs once after the last chunk.
 constexpr int DT = 128;
 constexpr int LC = 8;
 
@@ -196,15 +199,16 @@ __global__ void __launch_bounds__(DT)
 k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __restrict__ delta,
             const double* __restrict__ Cf, const double* __restrict__ amp,
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
-            int N_ell, int n_walk) {
+            int N_ell, int n_walk, int l_lo, int n_l) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   T* S = reinterpret_cast<T*>(dsm_raw);            // [LC][N_tr][N_tr]  S_ij A_j
   T* Dl = S + LC * N_tr * N_tr;                    // [N_tr][DT]
   const int w = blockIdx.z;
-  const int lc = blockIdx.y;
+  // Delta and Dbar hold multipoles [l_lo, l_lo + n_l) (l_lo a multiple of LC); Cf all N_ell
+  const int lc = l_lo / LC + blockIdx.y;
   const int q = blockIdx.x * DT + threadIdx.x;
   const int l0 = lc * LC;
-  const int nl = min(LC, N_ell - l0);
+  const int nl = min(LC, l_lo + n_l - l0);
   const double* A = amp + (size_t)w * N_tr;
   for (int e = threadIdx.x; e < nl * N_tr * N_tr; e += DT) {
     const int ll = e / (N_tr * N_tr), r = e - ll * N_tr * N_tr;
@@ -214,13 +218,13 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
   T ps = 0, pc = 0;
   for (int ll = 0; ll < nl; ++ll) {
     __syncthreads();
-    const T* dl = delta + ((size_t)w * N_ell + l0 + ll) * N_tr * N_k;
+    const T* dl = delta + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
     for (int t = 0; t < N_tr; ++t)
       Dl[t * DT + threadIdx.x] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
     __syncthreads();
     if (q < N_k) {
       const T* Sl = S + ll * N_tr * N_tr;
-      T* db = dbar + ((size_t)w * N_ell + l0 + ll) * N_tr * N_k;
+      T* db = dbar + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
       for (int ii = 0; ii < N_tr; ++ii) {
         T t = 0;
         for (int j = 0; j < N_tr; ++j) t = fma(Sl[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
@@ -244,30 +248,30 @@ __global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restric
 
 }  // namespace
 
-cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
-                             int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s) {
-  size_t smem = (size_t)N_tr * QC * sizeof(double);
+template <typename T>
+cudaError_t launch_quad(double* U, const T* delta, const double* P, const double* wk2, int n_walk,
+                        int N_tr, int N_k, int N_ell, int l_lo, int n_l, cudaStream_t s) {
+  size_t smem = (size_t)N_tr * QC * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_quad<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 g(N_ell, n_walk);
-  k_quad<double><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell);
+  dim3 g(n_l, n_walk);
+  k_quad<T><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell, l_lo, n_l);
   return cudaGetLastError();
 }
 
+cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
+                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
+                             cudaStream_t s) {
+  return launch_quad<double>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
+}
+
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
-                            int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s) {
-  size_t smem = (size_t)N_tr * QC * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_quad<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 g(N_ell, n_walk);
-  k_quad<float><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell);
-  return cudaGetLastError();
+                            int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
+                            cudaStream_t s) {
+  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
 }
 
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
@@ -294,20 +298,24 @@ cudaError_t launch_amp_bar(double* amp_bar, const double* Cf, const double* U, c
 }
 
 template <typename T>
-cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cf,
-                             const double* amp, const double* P, const double* wk2, int n_walk,
-                             int N_tr, int N_k, int N_ell, double* scratch, cudaStream_t s) {
+cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const double* amp,
+                             const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
+                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s) {
   const size_t smem = (size_t)(LC * N_tr * N_tr + N_tr * DT) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  dim3 g((N_k + DT - 1) / DT, (n_l + LC - 1) / LC, n_walk);
+  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell,
+                                     n_walk, l_lo, n_l);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
+                               int n_walk, int N_k, int N_ell, cudaStream_t s) {
   const int n_chunk = (N_ell + LC - 1) / LC;
-  dim3 g((N_k + DT - 1) / DT, n_chunk, n_walk);
-  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell, n_walk);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const long n = (long)n_walk * N_k;
   k_pbar_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P_bar, scratch, wk2, n_chunk, n_walk, N_k);
   return cudaGetLastError();
@@ -317,11 +325,11 @@ size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell) {
   return sizeof(double) * (size_t)((N_ell + LC - 1) / LC) * n_walk * N_k;
 }
 
-template cudaError_t launch_delta_bar<double>(double*, double*, const double*, const double*,
+template cudaError_t launch_delta_bar<double>(double*, const double*, const double*,
                                               const double*, const double*, const double*, int,
-                                              int, int, int, double*, cudaStream_t);
-template cudaError_t launch_delta_bar<float>(float*, double*, const float*, const double*,
-                                             const double*, const double*, const double*, int,
-                                             int, int, int, double*, cudaStream_t);
+                                              int, int, int, int, int, double*, cudaStream_t);
+template cudaError_t launch_delta_bar<float>(float*, const float*, const double*, const double*,
+                                             const double*, const double*, int, int, int, int,
+                                             int, int, double*, cudaStream_t);
 
 }  // namespace swcl

@@ -37,6 +37,8 @@ int contract_adj_tc(swcl_ctx* c, int precision);
 int basis_prepare(swcl_ctx* c);
 int basis_forward(swcl_ctx* c, int l_lo, int n_l);
 int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate);
+size_t basis_fixed_bytes(const swcl_ctx* c);     // constant operands of basis mode
+size_t basis_bytes_per_ell(const swcl_ctx* c);   // per-call operand images per multipole
 
 // The k-interpolation stencil and FFT profiles the kernels use: the N_I knots with 4-point
 // Lagrange weights, or (basis mode) r low-rank profiles with weights mu.
@@ -131,6 +133,7 @@ struct swcl_ctx {
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
   int last_fwd_precision = -1;
+  int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
 
   // CUDA graph of the batched call (swcl_compute_batched)
   cudaGraphExec_t graph_exec = nullptr;
@@ -206,18 +209,22 @@ size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
 cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
                                  const cplx* gtab, const int* cls_of, const double* kpow,
                                  const int* j0, const double* lw, long lw_ts, int n_walk,
-                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, cudaStream_t s);
+                                 int N_tr, int N_I, int n_h, int N_k, int N_ell, int l_lo,
+                                 int n_l, cudaStream_t s);
 cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx* phase,
                                      const cplx* gtab, const int* cls_of, const double* kpow,
                                      const int* j0, const double* lw, long lw_ts, int n_walk,
-                                     int N_tr, int N_I, int n_h, int N_k, int N_ell,
-                                     cudaStream_t s);
+                                     int N_tr, int N_I, int n_h, int N_k, int N_ell, int l_lo,
+                                     int n_l, bool accumulate, cudaStream_t s);
 
-// a4 k-quadrature and VJP reductions (quad.cu)
+// a4 k-quadrature and VJP reductions (quad.cu).  Delta and Dbar buffers hold the multipoles
+// l_lo .. l_lo + n_l - 1 ([n_walk][n_l][N_tr][N_k]); U and Cbar_full all N_ell.
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
-                             int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s);
+                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
+                             cudaStream_t s);
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
-                            int n_walk, int N_tr, int N_k, int N_ell, cudaStream_t s);
+                            int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
+                            cudaStream_t s);
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
                               cudaStream_t s);
@@ -226,10 +233,14 @@ cudaError_t launch_unpack_sym(double* Cbar_full, const double* Cbar, const int* 
                               cudaStream_t s);
 cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const double* U,
                            const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s);
+// Dbar for the chunk (l_lo a multiple of 8) and its partial sums of P_bar in scratch (indexed by
+// the global 8-multipole chunk); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
 template <typename T>
-cudaError_t launch_delta_bar(T* dbar, double* P_bar, const T* delta, const double* Cbar_full,
-                             const double* amp, const double* P, const double* wk2, int n_walk,
-                             int N_tr, int N_k, int N_ell, double* scratch, cudaStream_t s);
+cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, const double* amp,
+                             const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
+                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s);
+cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
+                               int n_walk, int N_k, int N_ell, cudaStream_t s);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
 
 }  // namespace swcl

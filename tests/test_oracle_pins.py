@@ -305,3 +305,36 @@ def test_vjp_against_central_differences(wl):
         fd = (L(Wp, P, amp) - L(Wm, P, amp)) / (2 * hz)
         chain = np.sum(Wb * (Wp - Wm)) / (2 * hz)
         assert abs(fd - chain) <= 1e-6 * abs(fd), (t, fd, chain)
+
+
+def test_numpy_fft_matches_direct_sum():
+    """Eq. 3.2 evaluated by numpy.fft (the large-workload option) equals the direct DFT sum, for
+    the coefficients (both Nyquist bins, tapers, non-unit chi_min) and for the reverse mode."""
+    rng = np.random.default_rng(17)
+    N, chi_min, chi_max = 64, 3.0, 3.0e4
+    F = rng.standard_normal((5, N))
+    tchi = rng.uniform(0.5, 1.0, N)
+    tc = rng.uniform(0.5, 1.0, N // 2 + 1)
+    for b in (-0.3, -1.5):
+        c1 = O.fftlog_coefficients(F, chi_min, chi_max, b, tchi, tc, fft="direct")
+        c2 = O.fftlog_coefficients(F, chi_min, chi_max, b, tchi, tc, fft="numpy")
+        assert np.max(np.abs(c1 - c2)) < 1e-13 * np.max(np.abs(c1))
+    # reverse mode through both DFT forms
+    k = np.geomspace(1e-3, 1.0, 40)
+    ells = np.array([2, 7, 30])
+    knots = np.geomspace(1e-3, 1.0, 6)
+    kind = np.array([0, 1])
+    bias = np.array([-0.3, -1.5])
+    chi = O.chi_grid(chi_min, chi_max, N)
+    W = np.exp(-0.5 * ((np.log(chi) - rng.uniform(5, 7, 2)[:, None]) / 0.4) ** 2)
+    D = 1.0 + 0.01 * rng.standard_normal((len(knots), N))
+    P = rng.uniform(1.0, 2.0, len(k))
+    amp = np.array([1.3, 1.0])
+    Cb = rng.standard_normal((len(ells), 2, 2))
+    out = []
+    for fft in ("direct", "numpy"):
+        g = O.Grids(N, chi_min, chi_max, k, ells, knots, kind, bias, fft=fft)
+        f = O.forward(g, W, D, P, amp)
+        out.append((f["C"],) + tuple(O.vjp(g, f, Cb, W, D, P, amp)[:3]))
+    for a, b in zip(out[0], out[1]):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
