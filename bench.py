@@ -9,7 +9,7 @@ synthetic and resident in HBM when the timed region starts; L2 is flushed (256 M
 before every timed step.  Under torchrun every rank evaluates its own parameter points (weak
 scaling, no collective on the data path) and the slowest rank's time counts.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 3xtf32|bf16x6|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x9|tf32x6|3xtf32|fp64]
                     [--walkers B] [--impl ours|reference]
 
 --impl reference times the FP64 oracle (NumPy/SciPy on the host cores) on the same workload.
@@ -88,47 +88,74 @@ def n_walk(w):
 
 # ---------------------------------------------------------------- roofline ----
 
-def algorithmic_work(w, walkers):
-    """Algorithmic FLOPs per launch of each kernel ('Measurement')."""
+def algorithmic_work(w, walkers, rank):
+    """Algorithmic FLOPs per launch of each kernel and, for tensor-core kernels, the number of
+    compensated products each useful multiply-add costs ('Measurement')."""
     n_h = w.N // 2 + 1
     ntr, nk, nl, ni, N = w.n_tr, len(w.k), len(w.ells), len(w.knots), w.N
     contraction = 4.0 * n_h * ntr * nk * nl * walkers          # Re sum_n of complex products
-    fft = 2.5 * N * np.log2(N) * ntr * ni * walkers             # real FFT of length N per row
+    rows = rank if rank else ni                                 # FFT rows per tracer
+    fft = 2.5 * N * np.log2(N) * ntr * rows * walkers           # real FFT of length N per row
     return {
-        "contract fp64": ("alu", contraction),
-        "contract adj fp64": ("alu", contraction),
-        "contract tc": ("tensor", contraction),
-        "contract adj tc": ("tensor", contraction),
-        "fftlog": ("alu", fft),
-        "fftlog adj": ("alu", fft),
+        "contract fp64": ("alu", contraction, 1),
+        "contract adj fp64": ("alu", contraction, 1),
+        "contract tc": ("tensor", contraction, None),
+        "contract adj tc": ("tensor", contraction, None),
+        "basis gemm fwd": ("tensor", contraction, 10),
+        "basis gemm adj": ("tensor", contraction, 9),
+        "fftlog": ("alu", fft, 1),
+        "fftlog adj": ("alu", fft, 1),
     }
 
 
-def roofline(stats, w, walkers, precision, peaks, src):
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel at the
+# benchmark workload (one walker), from the ncu capture summarised in profiles/, valid only for
+# the kernel source it was taken from (sha256 of the file; otherwise reported as null).
+TRAFFIC = {}
+
+
+def traffic_for(name, walkers):
+    import hashlib
+    t = TRAFFIC.get(name)
+    if not t:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["src"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes"] * walkers
+
+
+def roofline(stats, w, walkers, precision, peaks, src, rank):
     if not stats:
         return None
     name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
-    work = algorithmic_work(w, walkers)
-    bound, flops = work.get(name, ("alu", None))
+    work = algorithmic_work(w, walkers, rank)
+    bound, flops, products = work.get(name, ("alu", None, 1))
     avg_s = ms / launches / 1e3
     if flops is None:
         return {"kernel": name, "bound": None, "avg_ms": ms / launches, "note": "no algorithmic count"}
     if bound == "tensor":
-        products = {"3xtf32": 3, "tf32x6": 6, "bf16x9": 9}[precision]
+        if products is None:
+            products = {"3xtf32": 3, "tf32x6": 6, "bf16x9": 9}[precision]
         tflops = flops * products / avg_s / 1e12
-        if precision != "bf16x9":
+        if precision in ("3xtf32", "tf32x6") and not name.startswith("basis"):
             peak = peaks["bf16_tflops"] * TF32_OVER_BF16
             unit_note = "tf32 peak = measured bf16 burst x nominal tf32/bf16 ratio"
         else:
             peak = peaks["bf16_tflops"]
             unit_note = "bf16 burst peak"
         return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": tflops / peak, "traffic": None, "avg_ms": ms / launches, "launches": launches,
+                "frac": tflops / peak, "traffic": traffic_for(name, walkers), "avg_ms": ms / launches,
+                "launches": launches, "products": products,
                 "peak_source": "%s (%s)" % (src, unit_note),
                 "useful_tflops": flops / avg_s / 1e12}
     tflops = flops / avg_s / 1e12
     return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "avg_ms": ms / launches, "launches": launches,
+            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic_for(name, walkers), "avg_ms": ms / launches,
+            "launches": launches,
             "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; FMA probe 1.19 TF/s)"}
 
 
@@ -312,7 +339,10 @@ def run_ours(args, rank, world, device):
     out["clocks"] = clk
     out["kernel_ms"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in (stats or {}).items()}
     peaks, src = load_peaks()
-    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src)
+    rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
+    out["tiles"] = {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)}
+    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r)
+    out["profile_rank"] = rank_r
     msf, _, _ = timed(fwd, args.steps, max(3, args.warmup // 2))
     out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",
                        "ms_per_step": msf / args.steps}
@@ -428,14 +458,16 @@ def main():
         dtype = {"fp64": "f64",
                  "3xtf32": "tf32x3 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum",
                  "tf32x6": "tf32x6 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum",
-                 "bf16x9": "bf16x9 tensor-core contraction (f32 accumulate) + f64 FFT/Gamma/k-sum"}[args.precision]
+                 "bf16x9": "split-bf16 tensor-core contraction (10 products forward, 9 VJP in basis "
+                           "mode; f32 accumulate) + f64 FFT/Gamma/k-sum"}[args.precision]
         line = {"metric": METRIC, "value": out["value"], "unit": "evals/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "walkers_per_gpu": n_walk(w), "precision": args.precision,
                            "l2": "flushed (256 MB write) before every timed step",
-                           "parallelism": "walkers sharded across ranks" if world > 1 else "1 GPU"},
+                           "parallelism": "walkers sharded across ranks" if world > 1 else "1 GPU",
+                           "profile_rank": out.get("profile_rank"), "gemm_tiles": out.get("tiles")},
                 "roofline": out["roofline"], "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "clocks": out["clocks"], "gpu_launches": out["gpu_launches"],
                 "fwd_only": out["fwd_only"], "fp64_gpu_path": out.get("fp64_gpu_path"),

@@ -252,6 +252,14 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
   if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
+  // fixed basis-GEMM tiles "fwd,adj" (tile codes as reported by SWCL_Q_TILE_*) instead of tuning
+  if (const char* v = std::getenv("SWCL_BASIS_TILES")) {
+    int f = 0, a = 0;
+    if (std::sscanf(v, "%d,%d", &f, &a) == 2) {
+      c->bt_fixed_fwd = f;
+      c->bt_fixed_adj = a;
+    }
+  }
   // device status word raised by bounded waits in the tensor-core kernels
   if (swcl::ensure(c, c->ws_status, 16) != SWCL_OK ||
       cudaMemset(c->ws_status.p, 0, 16) != cudaSuccess) {
@@ -278,7 +286,7 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
-                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg};
+                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -586,7 +594,8 @@ static int plan_ell_chunk(swcl_ctx* c, int precision) {
   if (!c->budget || (!fp64 && !basis)) return N_ell;   // knot-stencil tensor-core forms: whole
   const swcl::Stencil sv = swcl::stencil(c);
   const size_t nw = c->n_walk, nrow = nw * c->N_tr, ntr2 = (size_t)c->N_tr * c->N_tr;
-  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float));
+  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float)) +
+                 swcl::quad_scratch_bytes(c->n_walk, c->N_tr, c->N_k, 1);
   if (basis) per_l += swcl::basis_bytes_per_ell(c);
   // workspace that does not scale with the chunk
   size_t fixed = 2 * sizeof(cplx) * nrow * sv.NI * c->n_h              // coefficients, cbar
@@ -599,7 +608,7 @@ static int plan_ell_chunk(swcl_ctx* c, int precision) {
   if (basis) fixed += swcl::basis_fixed_bytes(c);
   const DevBuf* ws[] = {&c->ws_coef, &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar,
                         &c->ws_Cbar, &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_pbpart,
-                        &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
+                        &c->ws_qpart, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
                         &c->bt_himg, &c->bt_dimg};
   size_t ws_now = 0;
   for (const DevBuf* b : ws) ws_now += b->bytes;
@@ -651,6 +660,7 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
   SWCL_TRY(swcl::ensure(c, c->ws_delta, nrow * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
+  SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(nw, N_tr, N_k, n_lc)));
   if (fp64)
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
                                            (const double*)c->d_chipow.p, sv.D, sv.B,
@@ -667,11 +677,14 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                             (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                            N_tr, N_k, N_ell, l_lo, n_l, c->stream), "k-quadrature fp64");
+                                            N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                            c->stream), "k-quadrature fp64");
     else
       SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                            (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                           N_tr, N_k, N_ell, l_lo, n_l, c->stream), "k-quadrature f32");
+                                           N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                           c->stream), "k-quadrature f32");
+    ++c->last_launches;  // the pair-sum reduction
   }
   c->ell_chunk = n_lc;
   const int64_t n_out = out_count(c);

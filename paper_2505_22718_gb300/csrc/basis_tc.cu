@@ -697,6 +697,10 @@ std::vector<int> tile_candidates(int r, bool need_groups) {
 
 int basis_rank(swcl_ctx* c) { return c->lr_true_rank; }
 
+bool valid_tile(int code, const std::vector<int>& cands) {
+  return std::find(cands.begin(), cands.end(), code) != cands.end();
+}
+
 }  // namespace
 
 size_t basis_fixed_bytes(const swcl_ctx* c) {
@@ -745,7 +749,8 @@ int basis_prepare(swcl_ctx* c) {
       c->have_B ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "basis operand tables");
-  c->bt_nt_fwd = c->bt_nt_adj = 0;
+  c->bt_nt_fwd = c->bt_fixed_fwd;
+  c->bt_nt_adj = c->bt_fixed_adj;
   c->bt_ready = true;
   return SWCL_OK;
 }
@@ -837,6 +842,8 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
                                       (const uint8_t*)c->bt_himg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward GEMM");
   };
+  if (c->bt_nt_fwd && !valid_tile(c->bt_nt_fwd, tile_candidates(r, true)))
+    return fail(c, SWCL_ERR_INVALID_ARG, "SWCL_BASIS_TILES: not a forward tile for this rank");
   if (c->bt_nt_fwd == 0) {
     if (c->capturing) c->bt_nt_fwd = 96 % r == 0 ? 96 : 64;
     else if ((st = autotune(c, tile_candidates(r, true), run, c->bt_nt_fwd))) return st;
@@ -870,6 +877,8 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
                                       (const uint8_t*)c->bt_dimg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint GEMM");
   };
+  if (c->bt_nt_adj && !valid_tile(c->bt_nt_adj, tile_candidates(r, false)))
+    return fail(c, SWCL_ERR_INVALID_ARG, "SWCL_BASIS_TILES: not an adjoint tile");
   if (c->bt_nt_adj == 0) {
     if (c->capturing) {
       c->bt_nt_adj = 96;

@@ -5,99 +5,114 @@
 //   Abar_i   = 2 sum_l sum_j S_ij A_j U_ij            (U = C at unit amplitudes),
 // with S = (Cbar + Cbar^T)/2 (zero for multipoles outside a walker's list).
 //
-// The unit-amplitude spectra U are formed per (walker, multipole) by one CTA; each unordered
-// pair (i <= j) is summed once over k and written to both (i,j) and (j,i), so C is symmetric
-// bit for bit.  Delta in FP32 (mixed paths): the products are FP32, the partial sums over 32 k
-// points are compensated FP32 sums (TwoSum; the rounding of each addition is carried in a second
-// float), and the per-pair total over k is FP64.
+// The unit-amplitude spectra U are formed in two passes: partial sums of each unordered pair
+// (i <= j) over chunks of 256 k points (one CTA per multipole and chunk), then the chunks added in
+// a fixed order and written to both (i,j) and (j,i), so C is symmetric bit for bit and the same
+// from run to run.  Delta in FP32 (mixed paths): the products are FP32, the partial sums over 32
+// k points are compensated FP32 sums (TwoSum; the rounding of each addition is carried in a
+// second float), and everything above them is FP64.
+#include <algorithm>
+
 #include "swcl_internal.h"
 
 namespace swcl {
 namespace {
 
 constexpr int QT = 256;    // threads
-constexpr int QC = 128;    // k points staged per step
+constexpr int KC = 256;    // k points per CTA (one partial sum per pair and chunk)
 
+// Partial pair sums over one chunk of KC k points: part[w][l - l_lo][kc][p] for unordered pairs
+// p = (i <= j).  Grid (multipole, k chunk, walker).  Thread t handles pair p = t % npair for the
+// k points t / npair, t / npair + G, ... of the chunk (G = QT / npair groups); groups are combined
+// in shared memory in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(QT)
-k_quad(double* __restrict__ U, const T* __restrict__ delta, const double* __restrict__ P,
-       const double* __restrict__ wk2, int N_tr, int N_k, int N_ell, int l_lo, int n_l) {
+k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double* __restrict__ P,
+            const double* __restrict__ wk2, int N_tr, int N_k, int n_l, int n_kc) {
   extern __shared__ double qsm[];
-  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][QC]
-  __shared__ double us[QC];
-  __shared__ float usf[QC];
+  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][KC]
+  __shared__ double us[KC];
+  __shared__ float usf[KC];
   __shared__ double red[QT];
-  // Delta holds multipoles [l_lo, l_lo + n_l) of each walker; U all N_ell
-  const int l = l_lo + blockIdx.x;
-  const int w = blockIdx.y;
+  const int ll = blockIdx.x, kc = blockIdx.y, w = blockIdx.z;
+  const int q0 = kc * KC;
   const int npair = N_tr * (N_tr + 1) / 2;
-  const T* dl = delta + ((size_t)w * n_l + blockIdx.x) * N_tr * N_k;
-  const double* Pw = P + (size_t)w * N_k;
-  // thread -> (pair slot, k-group)
+  const T* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
+  for (int e = threadIdx.x; e < N_tr * KC; e += QT) {
+    const int t = e / KC, qq = e - t * KC, q = q0 + qq;
+    Ds[e] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
+  }
+  for (int e = threadIdx.x; e < KC; e += QT) {
+    const int q = q0 + e;
+    us[e] = q < N_k ? wk2[q] * P[(size_t)w * N_k + q] : 0.0;
+    usf[e] = (float)us[e];
+  }
+  __syncthreads();
   const int ngroups = max(1, QT / npair);
-  const int group = threadIdx.x / npair;
+  double* out = part + (((size_t)w * n_l + ll) * n_kc + kc) * npair;
   for (int p0 = 0; p0 < npair; p0 += QT) {
-    int p = p0 + (ngroups > 1 ? (threadIdx.x % npair) : threadIdx.x);
-    bool active = (ngroups > 1) ? (group < ngroups) : (p < npair);
-    int pi = 0, pj = 0;
-    if (active && p < npair) {
-      // unordered pair index -> (i <= j)
-      int r = p, ii = 0;
-      while (r >= N_tr - ii) { r -= N_tr - ii; ++ii; }
-      pi = ii; pj = ii + r;
-    }
+    const int p = p0 + (ngroups > 1 ? threadIdx.x % npair : threadIdx.x);
+    const int group = ngroups > 1 ? threadIdx.x / npair : 0;
+    const bool active = p < npair && group < ngroups;
     double acc = 0.0;
-    for (int qb = 0; qb < N_k; qb += QC) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < N_tr * QC; e += QT) {
-        int t = e / QC, qq = e - t * QC;
-        int q = qb + qq;
-        Ds[t * QC + qq] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
-      }
-      for (int e = threadIdx.x; e < QC; e += QT) {
-        int q = qb + e;
-        us[e] = (q < N_k) ? wk2[q] * Pw[q] : 0.0;
-        usf[e] = (float)us[e];
-      }
-      __syncthreads();
-      if (active && p < npair) {
-        const T* di = Ds + pi * QC;
-        const T* dj = Ds + pj * QC;
-        int qs = (ngroups > 1) ? group : 0;
-        int qstep = (ngroups > 1) ? ngroups : 1;
-        if (sizeof(T) == 4) {
-          // FP32 products, compensated FP32 partial sums of 32 points, FP64 total
-          for (int c0 = qs * 32; c0 < QC; c0 += qstep * 32) {
-            float sum = 0.0f, comp = 0.0f;
+    if (active) {
+      int r = p, i = 0;                           // unordered pair index -> (i <= j)
+      while (r >= N_tr - i) { r -= N_tr - i; ++i; }
+      const int j = i + r;
+      const T* di = Ds + i * KC;
+      const T* dj = Ds + j * KC;
+      if (sizeof(T) == 4) {
+        // FP32 products, compensated FP32 sums of 32 points, FP64 across the sums
+        for (int c0 = group * 32; c0 < KC; c0 += ngroups * 32) {
+          float sum = 0.0f, comp = 0.0f;
 #pragma unroll 8
-            for (int qq = c0; qq < c0 + 32; ++qq) {
-              const float t = ((float)di[qq] * usf[qq]) * (float)dj[qq];
-              const float sn = sum + t;
-              const float bp = sn - sum;
-              comp += (sum - (sn - bp)) + (t - bp);
-              sum = sn;
-            }
-            acc += (double)sum + (double)comp;
+          for (int qq = c0; qq < c0 + 32; ++qq) {
+            const float t = ((float)di[qq] * usf[qq]) * (float)dj[qq];
+            const float sn = sum + t;
+            const float bp = sn - sum;
+            comp += (sum - (sn - bp)) + (t - bp);
+            sum = sn;
           }
-        } else {
-          for (int qq = qs; qq < QC; qq += qstep)
-            acc = fma((double)di[qq] * us[qq], (double)dj[qq], acc);
+          acc += (double)sum + (double)comp;
         }
+      } else {
+        for (int qq = group; qq < KC; qq += ngroups)
+          acc = fma((double)di[qq] * us[qq], (double)dj[qq], acc);
       }
     }
-    // combine k-groups
-    __syncthreads();
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (active && p < npair && (ngroups == 1 || group == 0)) {
-      double s = acc;
-      if (ngroups > 1)
-        for (int g = 1; g < ngroups; ++g) s += red[g * npair + (threadIdx.x % npair)];
-      double* out = U + ((size_t)w * N_ell + l) * N_tr * N_tr;
-      out[pi * N_tr + pj] = s;
-      out[pj * N_tr + pi] = s;
+    if (ngroups > 1) {
+      red[threadIdx.x] = acc;
+      __syncthreads();
+      if (active && group == 0) {
+        double s2 = acc;
+        for (int g = 1; g < ngroups; ++g) s2 += red[g * npair + threadIdx.x];
+        out[p] = s2;
+      }
+      __syncthreads();
+    } else if (active) {
+      out[p] = acc;
     }
-    if (ngroups > 1) break;
+  }
+}
+
+// U[w][l][i][j] = U[w][l][j][i] = sum over the k chunks of the pair's partial sums (in order)
+__global__ void k_quad_reduce(double* __restrict__ U, const double* __restrict__ part, int N_tr,
+                              int N_ell, int l_lo, int n_l, int n_kc, int n_walk) {
+  const int npair = N_tr * (N_tr + 1) / 2;
+  const long total = (long)n_walk * n_l * npair;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int p = (int)(e % npair);
+    const long wl = e / npair;                       // w * n_l + ll
+    const int ll = (int)(wl % n_l), w = (int)(wl / n_l);
+    const double* src = part + (size_t)wl * n_kc * npair + p;
+    double s = 0.0;
+    for (int kc = 0; kc < n_kc; ++kc) s += src[(size_t)kc * npair];
+    int r = p, i = 0;
+    while (r >= N_tr - i) { r -= N_tr - i; ++i; }
+    const int j = i + r;
+    double* u = U + ((size_t)w * N_ell + l_lo + ll) * N_tr * N_tr;
+    u[i * N_tr + j] = s;
+    u[j * N_tr + i] = s;
   }
 }
 
@@ -176,7 +191,7 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
   if (threadIdx.x == 0) abar[(size_t)w * N_tr + i] = 2.0 * red[0];
 }
 
-// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, chunk of LC multipoles,
+// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, pair of LC multipoles,
 // walker); one thread per k point.  S_l A_j is staged per multipole chunk in shared memory (in the
 // arithmetic type T: FP32 for the mixed paths, FP64 for the FP64 path), Delta_j(l, q) in a
 // per-thread shared column.  The P_bar partial of each multipole chunk is a compensated sum
@@ -184,7 +199,7 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
 // covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a multipole chunk
 // when Delta is recomputed chunk by chunk); the reduction runs once after the last chunk.
 constexpr int DT = 128;
-constexpr int LC = 8;
+constexpr int LC = 2;
 
 template <typename T>
 __device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {
@@ -250,28 +265,39 @@ __global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restric
 
 template <typename T>
 cudaError_t launch_quad(double* U, const T* delta, const double* P, const double* wk2, int n_walk,
-                        int N_tr, int N_k, int N_ell, int l_lo, int n_l, cudaStream_t s) {
-  size_t smem = (size_t)N_tr * QC * sizeof(T);
+                        int N_tr, int N_k, int N_ell, int l_lo, int n_l, double* scratch,
+                        cudaStream_t s) {
+  size_t smem = (size_t)N_tr * KC * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_quad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_quad_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 g(n_l, n_walk);
-  k_quad<T><<<g, QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell, l_lo, n_l);
+  const int n_kc = (N_k + KC - 1) / KC;
+  dim3 g(n_l, n_kc, n_walk);
+  k_quad_part<T><<<g, QT, smem, s>>>(scratch, delta, P, wk2, N_tr, N_k, n_l, n_kc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long total = (long)n_walk * n_l * N_tr * (N_tr + 1) / 2;
+  const unsigned grid = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+  k_quad_reduce<<<grid, 256, 0, s>>>(U, scratch, N_tr, N_ell, l_lo, n_l, n_kc, n_walk);
   return cudaGetLastError();
+}
+
+size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l) {
+  return sizeof(double) * (size_t)n_walk * n_l * ((N_k + KC - 1) / KC) * (N_tr * (N_tr + 1) / 2);
 }
 
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                             cudaStream_t s) {
-  return launch_quad<double>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
+                             double* scratch, cudaStream_t s) {
+  return launch_quad<double>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, scratch, s);
 }
 
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                            cudaStream_t s) {
-  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
+                            double* scratch, cudaStream_t s) {
+  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, scratch, s);
 }
 
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,

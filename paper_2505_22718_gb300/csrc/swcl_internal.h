@@ -108,6 +108,7 @@ struct swcl_ctx {
   bool bt_disabled = false;    // environment override SWCL_BASIS_GEMM=0
   int bt_f_mt = 0, bt_f_kb = 0, bt_a_mt = 0, bt_a_kb = 0;
   int bt_nt_fwd = 0, bt_nt_adj = 0;   // autotuned column tiles (0 = not tuned yet)
+  int bt_fixed_fwd = 0, bt_fixed_adj = 0;  // tiles fixed by the environment (0 = tune)
   swcl::DevBuf bt_eimg_f, bt_eimg_a;  // phase images: forward A [q][(n,re/im)], adjoint A [(n,re/im)][q]
   swcl::DevBuf bt_gdf, bt_g32;        // Gamma-ratio table as double-float and FP32
   swcl::DevBuf bt_kmu;                // [N_tr][4][N_k] float kpow * mu
@@ -132,6 +133,7 @@ struct swcl_ctx {
   swcl::DevBuf ws_aimg;      // VJP: split Dbar image (tensor-core A operand)
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
+  swcl::DevBuf ws_qpart;     // forward: per-k-chunk partial pair sums of the k-quadrature
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
 
@@ -219,12 +221,14 @@ cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx*
 
 // a4 k-quadrature and VJP reductions (quad.cu).  Delta and Dbar buffers hold the multipoles
 // l_lo .. l_lo + n_l - 1 ([n_walk][n_l][N_tr][N_k]); U and Cbar_full all N_ell.
+// scratch: quad_scratch_bytes(n_walk, N_tr, N_k, n_l) of per-k-chunk pair sums
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                             cudaStream_t s);
+                             double* scratch, cudaStream_t s);
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                            cudaStream_t s);
+                            double* scratch, cudaStream_t s);
+size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l);
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
                               cudaStream_t s);
@@ -233,8 +237,8 @@ cudaError_t launch_unpack_sym(double* Cbar_full, const double* Cbar, const int* 
                               cudaStream_t s);
 cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const double* U,
                            const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s);
-// Dbar for the chunk (l_lo a multiple of 8) and its partial sums of P_bar in scratch (indexed by
-// the global 8-multipole chunk); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
+// Dbar for the chunk (l_lo a multiple of 2) and its partial sums of P_bar in scratch (indexed by
+// the global 2-multipole chunk); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
