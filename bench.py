@@ -111,13 +111,21 @@ def algorithmic_work(w, walkers, rank):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel at the
 # benchmark workload (one walker), from the ncu capture summarised in profiles/, valid only for
 # the kernel source it was taken from (sha256 of the file; otherwise reported as null).
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/basis_gemm_n5k_bf16.md (tiles 96/96, one walker)
+    "basis gemm adj": {"bytes": 29916928 + 0, "walkers": 1,
+                       "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
+                       "sha256": "6e5148653eafb07ff17023ee2d7a8880faac0d7fbf28e5b924940b6637a25ff9"},
+    "basis gemm fwd": {"bytes": 44387840 + 34816, "walkers": 1,
+                       "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
+                       "sha256": "6e5148653eafb07ff17023ee2d7a8880faac0d7fbf28e5b924940b6637a25ff9"},
+}
 
 
 def traffic_for(name, walkers):
     import hashlib
     t = TRAFFIC.get(name)
-    if not t:
+    if not t or t["walkers"] != walkers:
         return None
     try:
         with open(os.path.join(ROOT, t["src"]), "rb") as f:
@@ -125,7 +133,7 @@ def traffic_for(name, walkers):
                 return None
     except OSError:
         return None
-    return t["bytes"] * walkers
+    return t["bytes"]
 
 
 def roofline(stats, w, walkers, precision, peaks, src, rank):
