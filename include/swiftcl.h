@@ -200,6 +200,13 @@ int swcl_fftlog_noalloc(int n_walk, int N_tr, int N_I, int N, double chi_min, do
                         const double* taper_c, const double* W, const double* D, const double* B,
                         double* coef, void* stream);
 
+/* Self-test of the bounded waits of the tensor-core kernels (no counterpart in the paper): one
+ * thread waits on an mbarrier phase that nothing completes.  The wait gives up after the same
+ * poll limit as the kernels' waits and raises the status word, so the call returns
+ * SWCL_ERR_TIMEOUT; *cycles (nullable) receives the clock cycles the wait took.  The context
+ * stays usable (the status word is cleared). */
+int swcl_selftest_wait_timeout(swcl_ctx* ctx, int64_t* cycles);
+
 /* Wait for queued work; returns any deferred device error. */
 int swcl_sync(swcl_ctx* ctx);
 

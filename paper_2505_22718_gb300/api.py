@@ -14,6 +14,8 @@ import numpy as np
 from . import _lib
 
 SWCL_OK = 0
+(SWCL_ERR_INVALID_ARG, SWCL_ERR_UNSUPPORTED, SWCL_ERR_OOM_BUDGET, SWCL_ERR_CUDA, SWCL_ERR_TIMEOUT,
+ SWCL_ERR_NONFINITE, SWCL_ERR_STATE) = -1, -2, -3, -4, -5, -6, -7
 SWCL_DENSITY, SWCL_LENSING = 0, 1
 SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16, SWCL_TF32X6 = 0, 1, 2, 3
 SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES = 1, 2, 3, 4
@@ -177,6 +179,13 @@ def swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, kind, fft_bias, 
     return _lib.load().swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, pk, pb,
                                            *[a[0] for a in args],
                                            ctypes.c_void_p(stream) if stream else None)
+
+
+def swcl_selftest_wait_timeout(ctx):
+    """Runs the bounded-wait self-test; returns (status, cycles) without raising."""
+    v = ctypes.c_int64()
+    st = _lib.load().swcl_selftest_wait_timeout(ctx, ctypes.byref(v))
+    return st, v.value
 
 
 def swcl_sync(ctx):

@@ -978,6 +978,21 @@ int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
   return SWCL_OK;
 }
 
+int swcl_selftest_wait_timeout(swcl_ctx* c, int64_t* cycles) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(swcl::ensure(c, c->d_flag, 16));
+  SWCL_TRY_CUDA(c, swcl::launch_wait_nothing((int*)c->ws_status.p, (long long*)c->d_flag.p, c->stream),
+                "self-test launch");
+  long long h = 0;
+  SWCL_TRY_CUDA(c, cudaMemcpyAsync(&h, c->d_flag.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+                "self-test read");
+  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "self-test sync");
+  if (cycles) *cycles = h;
+  return check_status(c);
+}
+
 int swcl_sync(swcl_ctx* c) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);

@@ -229,6 +229,9 @@ cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, cons
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
                             double* scratch, cudaStream_t s);
 size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l);
+
+// self-test of the bounded waits (selftest.cu)
+cudaError_t launch_wait_nothing(int* status, long long* cycles, cudaStream_t s);
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
                               cudaStream_t s);

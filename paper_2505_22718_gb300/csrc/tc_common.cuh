@@ -11,7 +11,7 @@ namespace tc {
 constexpr int kMTile = 128;            // rows (k points) per CTA = TMEM lanes
 constexpr int kRowBytes = 128;         // bytes of one operand row per K-block and plane
 constexpr int kPlaneA = kMTile * kRowBytes;   // 16 KB
-constexpr long kSpinLimit = 1L << 20;  // bounded mbarrier waits (then the kernel reports a timeout)
+constexpr long kSpinLimit = 1L << 18;  // bounded mbarrier waits (about 1 s), then a timeout
 
 // Arithmetic of the compensated products.  The formed A element is an FP32 value; it is split
 // exactly into planes (A = a0 + a1 [+ a2]).  The B table is FP64 and split into planes of its
