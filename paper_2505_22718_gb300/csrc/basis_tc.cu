@@ -138,41 +138,38 @@ struct GemmShape {
 
 // ------------------------------------------------------------------ epilogues ----
 
+// The epilogues read this thread's accumulator column c at acc[c * stride] (shared memory; see
+// the drain), in loops that are not unrolled: the kernel runs them once per CTA, so a compact
+// body keeps the cold instruction fetch short.
+
 // Forward: Delta[w][l][i][q] = sum_s kmu[i][s][q] Z[q][(w, i, l, s)]
 struct EpiFwd {
   float* delta;
   const float* kmu;     // [N_tr][4][N_k]
   int N_k, N_tr, n_l, r, n_cols;
   // row m, this thread's columns j0 .. j0 + nc - 1 (j0 is a multiple of r)
-  __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
+  __device__ __forceinline__ void operator()(int m, int j0, const float* acc, int stride, int nc) const {
     if (m >= N_k) return;
     // column j = ((w N_tr + i) n_l + l) r + s, walked incrementally
     int s = j0 % r, g = j0 / r;
     int l = g % n_l, wi = g / n_l;
-    int icur = -1;
-    float k0 = 0.f, k1 = 0.f, k2 = 0.f, k3 = 0.f;
+    int i = wi % N_tr, w = wi / N_tr;
+    const float* kr = kmu + (size_t)i * 4 * N_k + m;
     float v = 0.0f;
-#pragma unroll
-    for (int c = 0; c < kHalf; ++c) {
-      if (c < nc && j0 + c < n_cols) {
-        const int i = wi % N_tr;
-        if (i != icur) {
-          icur = i;
-          const float* kr = kmu + (size_t)i * 4 * N_k + m;
-          k0 = __ldg(kr);
-          if (r > 1) k1 = __ldg(kr + N_k);
-          if (r > 2) k2 = __ldg(kr + 2 * N_k);
-          if (r > 3) k3 = __ldg(kr + 3 * N_k);
-        }
-        const float km = s == 0 ? k0 : s == 1 ? k1 : s == 2 ? k2 : k3;
-        v = fmaf(km, acc[c], v);
-        if (s == r - 1) {
-          delta[(((size_t)(wi / N_tr) * n_l + l) * N_tr + i) * N_k + m] = v;
-          v = 0.0f;
-        }
-        if (++s == r) {
-          s = 0;
-          if (++l == n_l) { l = 0; ++wi; }
+    const int ncols = min(nc, n_cols - j0);
+#pragma unroll 1
+    for (int c = 0; c < ncols; ++c) {
+      v = fmaf(__ldg(kr + (size_t)s * N_k), acc[c * stride], v);
+      if (s == r - 1) {
+        delta[(((size_t)w * n_l + l) * N_tr + i) * N_k + m] = v;
+        v = 0.0f;
+      }
+      if (++s == r) {
+        s = 0;
+        if (++l == n_l) {
+          l = 0;
+          if (++i == N_tr) { i = 0; ++w; }
+          kr = kmu + (size_t)i * 4 * N_k + m;
         }
       }
     }
@@ -196,39 +193,56 @@ struct EpiAdj {
       atomicAdd(&dst->y, (double)im);
     }
   }
-  __device__ __forceinline__ void operator()(int m, int j0, const float (&acc)[kHalf], int nc) const {
+  __device__ __forceinline__ void operator()(int m, int j0, const float* acc, int stride, int nc) const {
     const int n = m >> 1, t = m & 1;
     const bool live = n < n_h;
     const int nn = live ? n : 0;
-    float are = 0.0f, aim = 0.0f;
     // column j = ((w N_tr + i) r + s) n_l + l, walked incrementally; the same for every lane,
-    // so the group changes (shuffles) are warp-uniform
+    // so the group changes (shuffles) are warp-uniform.  Gamma values are loaded 8 at a time.
+    const int ncols = min(nc, n_cols - j0);
+    if (ncols <= 0) return;
     int l = j0 % n_l, g = j0 / n_l;
     const float2* grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
-    int gcur = g;
+    float are = 0.0f, aim = 0.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+      // columns c0 .. c0 + 7 belong to at most two groups when n_l >= 8; fetch Gamma rows of the
+      // current group (and of the next one after a change) in one batch
+      float2 G[8];
+      int lb = l, gb = g;
+      const float2* growb = grow;
 #pragma unroll
-    for (int c = 0; c < kHalf; ++c) {
-      if (c < nc && j0 + c < n_cols) {
-        if (g != gcur) {
-          flush(gcur, n, t, are, aim);
-          gcur = g;
-          are = 0.0f;
-          aim = 0.0f;
-          grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
+      for (int u = 0; u < 8; ++u) {
+        G[u] = (c0 + u < ncols) ? __ldg(growb + (size_t)lb * n_h) : make_float2(0.f, 0.f);
+        if (++lb == n_l) {
+          lb = 0;
+          ++gb;
+          growb = g32 + ((size_t)__ldg(cls_of + (gb / r) % N_tr) * N_ell + l_lo) * n_h + nn;
         }
-        const float2 G = __ldg(grow + (size_t)l * n_h);
-        const float y = live ? acc[c] : 0.0f;
-        if (t == 0) {
-          are = fmaf(G.x, y, are);
-          aim = fmaf(-G.y, y, aim);
-        } else {
-          are = fmaf(G.y, y, are);
-          aim = fmaf(G.x, y, aim);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (c0 + u < ncols) {
+          const float y = live ? acc[(c0 + u) * stride] : 0.0f;
+          if (t == 0) {
+            are = fmaf(G[u].x, y, are);
+            aim = fmaf(-G[u].y, y, aim);
+          } else {
+            are = fmaf(G[u].y, y, are);
+            aim = fmaf(G[u].x, y, aim);
+          }
+          if (++l == n_l) {
+            flush(g, n, t, are, aim);
+            are = 0.0f;
+            aim = 0.0f;
+            l = 0;
+            ++g;
+            grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
+          }
         }
-        if (++l == n_l) { l = 0; ++g; }
       }
     }
-    if (nc > 0 && j0 < n_cols) flush(gcur, n, t, are, aim);
+    if (l != 0) flush(g, n, t, are, aim);
   }
 };
 
@@ -282,7 +296,9 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
     if (lane == 0) {
       // ---------------------------------------------------------- copies ----
       // Issues the copies of K-block `next` as soon as its stage is free and forwards landed
-      // K-blocks (ready -> full) in order; both without blocking on either condition.
+      // K-blocks (ready -> full) in order.  Both conditions are polled without suspending
+      // (test_wait): a thread suspended on "stage free" would hold back the forward of a landed
+      // K-block until the tensor core had finished the previous one, a bubble per K-block.
       const uint8_t* asrc = aimg + (size_t)mt * n_kb * L.a_bytes;
       const uint8_t* bsrc = bimg + (size_t)nt * n_kb * L.b_bytes;
       int next = 0, fwd = 0;
@@ -291,7 +307,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
         bool progress = false;
         if (next < n_kb) {
           const int s = next % S, r = next / S;
-          if (r == 0 || mbar_try_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
+          if (r == 0 || mbar_test_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
             uint8_t* st = base + s * L.stage;
             mbar_arrive_tx(smem_u32(&ready[s]), L.stage);
             bulk_g2s(smem_u32(st), asrc + (size_t)next * L.a_bytes, L.a_bytes, smem_u32(&ready[s]));
@@ -301,14 +317,14 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
             progress = true;
           }
         }
-        if (fwd < next && mbar_try_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
+        if (fwd < next && mbar_test_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
           mbar_arrive(smem_u32(&full[fwd % S]));
           ++fwd;
           progress = true;
         }
         if (progress) {
           idle = 0;
-        } else if (++idle > kSpinLimit || *abort_flag) {
+        } else if (++idle > (kSpinLimit << 6) || *abort_flag) {   // non-suspending polls
           *abort_flag = 1;
           break;
         }
@@ -405,7 +421,17 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
     }
     // every lane of a drain warp reaches the epilogue (its shuffles need the full warp)
     const bool all_ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
-    if (all_ok) epi(mt * kM + row, nt * NT + c_begin * 16, acc, my * 16);
+    if (all_ok) {
+      // the stages are idle now (every MMA has completed, every copy has landed): the
+      // accumulators go to shared memory, column-major over the drain threads, and the epilogue
+      // reads them from there in a loop that is not unrolled
+      const int dt = tid - 64;                       // drain thread 0 .. 32 DW - 1
+      float* ep = reinterpret_cast<float*>(base);
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c)
+        if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
+      epi(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+    }
   }
   tc_fence_before();
   __syncthreads();

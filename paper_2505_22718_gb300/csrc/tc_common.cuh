@@ -1,6 +1,6 @@
 // Inline-PTX building blocks for the sm_103a tensor-core kernels: mbarriers, bulk copies,
 // tcgen05 (TMEM allocation, MMA, commit, loads) and the operand splits of the compensated
-// products.  Shared by contract_tc.cu (forward) and contract_tc_adj.cu (VJP).
+// products.  Shared by contract_tc.cu, contract_tc_adj.cu, basis_tc.cu and selftest.cu.
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -98,6 +98,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Non-blocking test of a phase (never suspends the thread, unlike try_wait)
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
   return ok != 0;
