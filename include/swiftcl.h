@@ -64,7 +64,9 @@ typedef struct swcl_ctx swcl_ctx;
 /* arithmetic of the contraction (a3) and of the k-quadrature (a4) */
 #define SWCL_FP64        0  /* FP64 CUDA cores throughout */
 #define SWCL_3XTF32      1  /* tcgen05 kind::tf32, 2-plane splits of both operands, 3 products */
-#define SWCL_SPLIT_BF16  2  /* tcgen05 kind::f16 (bf16), A in 3 planes, B in 4, 9 products */
+#define SWCL_SPLIT_BF16  2  /* tcgen05 kind::f16 (bf16) compensated products, FP32 accumulation:
+                               basis mode (low-rank profiles) 3 + 3 planes, 6 products; knot
+                               stencil A in 3 planes, B in 4, 9 products ("bf16x9") */
 #define SWCL_TF32X6      3  /* tcgen05 kind::tf32, 3-plane splits of both operands, 6 products */
 /* All tensor-core forms accumulate in FP32 (TMEM); the FFTLog (a1), the Gamma table (a2) and the
  * per-pair k-sums of a4 stay FP64, the a4 products are FP32 with compensated partial sums. */

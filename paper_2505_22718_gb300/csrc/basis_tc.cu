@@ -17,10 +17,10 @@
 // its epilogue multiplies by conj(G) and sums over l.
 //
 // Compensated products with FP32 accumulation (the 5th-generation tensor cores take bf16 operands
-// here): the constant operand is split once from FP64 into 4 bf16 planes; the forward B operand
-// H is formed in double-float arithmetic from double-float F and G and split into 4 planes; the
-// adjoint B operand is an FP32 product split exactly into 3 planes.  Products with pa + pb <= 3
-// are issued (10 forward, 9 adjoint).  The tensor core accumulates one 32-deep K-block at a
+// here): the constant operand is split once from FP64 into 3 bf16 planes; the forward B operand
+// H is formed in double-float arithmetic from double-float F and G and split into 3 planes; the
+// adjoint B operand is an FP32 product split exactly into 3 planes.  The 6 products with
+// pa + pb <= 2 are issued.  The tensor core accumulates one 32-deep K-block at a
 // time, the leading product and the corrections in separate TMEM slots (double-buffered); eight
 // drain warps add each K-block's partial sums into FP32 registers with round-to-nearest.
 //
@@ -51,26 +51,16 @@ constexpr int kMaxNT = 128;
 constexpr int kHalf = kMaxNT / 2;       // columns per drain thread at most
 constexpr int kMaxStages = 6;
 
-// A operand 4 planes, B operand 4 planes: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0) (0,3) (1,2) (2,1) (3,0)
-struct A4B4 {
-  static constexpr int kPlanesA = 4, kPlanesB = 4, kProducts = 10;
-  __host__ __device__ static constexpr int pa(int t) {
-    return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : t == 7 ? 1 : t == 8 ? 2 : t == 9 ? 3 : 0;
-  }
-  __host__ __device__ static constexpr int pb(int t) {
-    return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : t == 6 ? 3 : t == 7 ? 2 : t == 8 ? 1 : 0;
-  }
+// Both operands 3 bf16 planes (24 significant bits); the products with pa + pb <= 2:
+// (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0).  The dropped terms are below 2^-24 of each product, the
+// same as the FP32 accumulation in which the sums are formed (measured: the normalised C error of
+// the N5K-shaped and large workloads is the same with 10 products as with these 6).
+struct A3B3 {
+  static constexpr int kPlanesA = 3, kPlanesB = 3, kProducts = 6;
+  __host__ __device__ static constexpr int pa(int t) { return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : 0; }
+  __host__ __device__ static constexpr int pb(int t) { return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : 0; }
 };
-// A operand 4 planes, B operand 3 planes: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0) (1,2) (2,1) (3,0)
-struct A4B3 {
-  static constexpr int kPlanesA = 4, kPlanesB = 3, kProducts = 9;
-  __host__ __device__ static constexpr int pa(int t) {
-    return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : t == 6 ? 1 : t == 7 ? 2 : t == 8 ? 3 : 0;
-  }
-  __host__ __device__ static constexpr int pb(int t) {
-    return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : t == 6 ? 2 : t == 7 ? 1 : 0;
-  }
-};
+constexpr int kPlanes = 3;      // planes of every operand image
 
 // D f32, A/B bf16, K-major A and B, N >> 3 at bit 17, M >> 4 at bit 24
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -154,12 +144,15 @@ struct EpiFwd {
     int s = j0 % r, g = j0 / r;
     int l = g % n_l, wi = g / n_l;
     int i = wi % N_tr, w = wi / N_tr;
-    const float* kr = kmu + (size_t)i * 4 * N_k + m;
+    float kmv[4];                     // kmu[i][s][m] of the current tracer
+#pragma unroll
+    for (int u = 0; u < 4; ++u) kmv[u] = u < r ? __ldg(kmu + ((size_t)i * 4 + u) * N_k + m) : 0.0f;
     float v = 0.0f;
     const int ncols = min(nc, n_cols - j0);
-#pragma unroll 1
+#pragma unroll 4
     for (int c = 0; c < ncols; ++c) {
-      v = fmaf(__ldg(kr + (size_t)s * N_k), acc[c * stride], v);
+      const float km = s == 0 ? kmv[0] : s == 1 ? kmv[1] : s == 2 ? kmv[2] : kmv[3];
+      v = fmaf(km, acc[c * stride], v);
       if (s == r - 1) {
         delta[(((size_t)w * n_l + l) * N_tr + i) * N_k + m] = v;
         v = 0.0f;
@@ -169,7 +162,8 @@ struct EpiFwd {
         if (++l == n_l) {
           l = 0;
           if (++i == N_tr) { i = 0; ++w; }
-          kr = kmu + (size_t)i * 4 * N_k + m;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) kmv[u] = u < r ? __ldg(kmu + ((size_t)i * 4 + u) * N_k + m) : 0.0f;
         }
       }
     }
@@ -198,21 +192,20 @@ struct EpiAdj {
     const bool live = n < n_h;
     const int nn = live ? n : 0;
     // column j = ((w N_tr + i) r + s) n_l + l, walked incrementally; the same for every lane,
-    // so the group changes (shuffles) are warp-uniform.  Gamma values are loaded 8 at a time.
+    // so the group changes (shuffles) are warp-uniform.  Gamma values are loaded 16 at a time.
     const int ncols = min(nc, n_cols - j0);
     if (ncols <= 0) return;
     int l = j0 % n_l, g = j0 / n_l;
     const float2* grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
     float are = 0.0f, aim = 0.0f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < ncols; c0 += 8) {
-      // columns c0 .. c0 + 7 belong to at most two groups when n_l >= 8; fetch Gamma rows of the
-      // current group (and of the next one after a change) in one batch
-      float2 G[8];
+    for (int c0 = 0; c0 < ncols; c0 += 16) {
+      // one batch of loads for columns c0 .. c0 + 15, following the group changes
+      float2 G[16];
       int lb = l, gb = g;
       const float2* growb = grow;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         G[u] = (c0 + u < ncols) ? __ldg(growb + (size_t)lb * n_h) : make_float2(0.f, 0.f);
         if (++lb == n_l) {
           lb = 0;
@@ -221,7 +214,7 @@ struct EpiAdj {
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         if (c0 + u < ncols) {
           const float y = live ? acc[(c0 + u) * stride] : 0.0f;
           if (t == 0) {
@@ -258,7 +251,8 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   const Layout L = layout<P>(NT, S);
   // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
   // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
-  // the TMEM buffer the K-block accumulates into (1 + 32 DW arrivals); mmadone[s] when the
+  // the TMEM buffer the K-block accumulates into (1 + DW arrivals: one per drain warp, since
+  // 32 DW single-thread arrivals would serialise on the barrier word); mmadone[s] when the
   // K-block's MMAs are done (one commit), which frees the stage for the copy warp and the
   // accumulator for the drain warps.  The MMA thread waits once and commits once per K-block:
   // a single thread issues tcgen05.mma only about as fast as the tensor core executes a
@@ -278,7 +272,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&full[s]), 1 + 32 * DW);
+      mbar_init(smem_u32(&full[s]), 1 + DW);     // the copy warp + one arrival per drain warp
       mbar_init(smem_u32(&mmadone[s]), 1);
       mbar_init(smem_u32(&ready[s]), 1);
     }
@@ -379,12 +373,16 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
     for (int t = 0; t < kHalf; ++t) acc[t] = 0.0f;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     // the first two K-blocks find their accumulator buffers empty
-    mbar_arrive(smem_u32(&full[0]));
-    if (n_kb > 1) mbar_arrive(smem_u32(&full[1 % S]));
+    if (lane == 0) {
+      mbar_arrive(smem_u32(&full[0]));
+      if (n_kb > 1) mbar_arrive(smem_u32(&full[1 % S]));
+    }
     bool ok = true;
     for (int kb = 0; kb < n_kb && ok; ++kb) {
       const int b = kb & 1;
-      if (!mbar_wait(smem_u32(&mmadone[kb % S]), (kb / S) & 1, abort_flag)) { ok = false; break; }
+      // warp-uniform exit: every lane leaves the loop together (the loop has warp barriers)
+      const bool got = mbar_wait(smem_u32(&mmadone[kb % S]), (kb / S) & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
       tc_fence_after();
       const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
       const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
@@ -416,8 +414,9 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
         }
       }
       tc_fence_before();
-      // buffer b is free for K-block kb + 2
-      if (kb + 2 < n_kb) mbar_arrive(smem_u32(&full[(kb + 2) % S]));
+      __syncwarp();
+      // buffer b is free for K-block kb + 2: every lane of the warp has finished its loads
+      if (lane == 0 && kb + 2 < n_kb) mbar_arrive(smem_u32(&full[(kb + 2) % S]));
     }
     // every lane of a drain warp reaches the epilogue (its shuffles need the full warp)
     const bool all_ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
@@ -455,15 +454,12 @@ __device__ __forceinline__ void split_f64(double x, __nv_bfloat16 (&p)[NP]) {
     x -= (double)bf(p[k]);
   }
 }
-// double-float (hi + lo) -> 4 bf16 planes
-__device__ __forceinline__ void split_df(float hi, float lo, __nv_bfloat16 (&p)[4]) {
+// double-float (hi + lo) -> 3 bf16 planes (the remainder of each plane rounded into the next)
+__device__ __forceinline__ void split_df(float hi, float lo, __nv_bfloat16 (&p)[3]) {
   p[0] = __float2bfloat16_rn(hi);
   float r = (hi - bf(p[0])) + lo;
   p[1] = __float2bfloat16_rn(r);
-  r -= bf(p[1]);
-  p[2] = __float2bfloat16_rn(r);
-  r -= bf(p[2]);
-  p[3] = __float2bfloat16_rn(r);
+  p[2] = __float2bfloat16_rn(r - bf(p[1]));
 }
 // FP32 -> 3 bf16 planes (exact)
 __device__ __forceinline__ void split_f32(float x, __nv_bfloat16 (&p)[3]) {
@@ -485,7 +481,7 @@ __device__ __forceinline__ void store_planes(uint8_t* dst, uint32_t plane_bytes,
   }
 }
 
-// Forward A image [mt][kb][4 planes][128 rows x 64 B]: (q, 2n + t) = Re/Im E_{q,n}
+// Forward A image [mt][kb][3 planes][128 rows x 64 B]: (q, 2n + t) = Re/Im E_{q,n}
 __global__ void k_eimg_fwd(uint8_t* __restrict__ img, const cplx* __restrict__ phase, int N_k,
                            int n_h, int n_mt, int n_kb) {
   const long total = (long)n_mt * n_kb * kM * 4;
@@ -496,20 +492,21 @@ __global__ void k_eimg_fwd(uint8_t* __restrict__ img, const cplx* __restrict__ p
     const int kb = (int)(t % n_kb); t /= n_kb;
     const int mt = (int)t;
     const int q = mt * kM + row;
-    __nv_bfloat16 v[8][4];
+    __nv_bfloat16 v[8][kPlanes];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int n = (kb * kK + ch * 8) / 2 + u;
       cplx E = {0.0, 0.0};
       if (q < N_k && n < n_h) E = phase[(size_t)q * n_h + n];
-      split_f64<4>(E.x, v[2 * u]);
-      split_f64<4>(E.y, v[2 * u + 1]);
+      split_f64<kPlanes>(E.x, v[2 * u]);
+      split_f64<kPlanes>(E.y, v[2 * u + 1]);
     }
-    store_planes<4>(img + ((size_t)mt * n_kb + kb) * 4 * kPlaneM, kPlaneM, off64(row, ch * 16), v);
+    store_planes<kPlanes>(img + ((size_t)mt * n_kb + kb) * kPlanes * kPlaneM, kPlaneM,
+                          off64(row, ch * 16), v);
   }
 }
 
-// Adjoint A image [mt][kb][4 planes][128 rows x 64 B]: (2n + t, q) = Re E_{q,n}, -Im E_{q,n}
+// Adjoint A image [mt][kb][3 planes][128 rows x 64 B]: (2n + t, q) = Re E_{q,n}, -Im E_{q,n}
 __global__ void k_eimg_adj(uint8_t* __restrict__ img, const cplx* __restrict__ phase, int N_k,
                            int n_h, int n_mt, int n_kb) {
   const long total = (long)n_mt * n_kb * kM * 4;
@@ -521,7 +518,7 @@ __global__ void k_eimg_adj(uint8_t* __restrict__ img, const cplx* __restrict__ p
     const int mt = (int)t;
     const int m = mt * kM + row;
     const int n = m >> 1;
-    __nv_bfloat16 v[8][4];
+    __nv_bfloat16 v[8][kPlanes];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int q = kb * kK + ch * 8 + u;
@@ -530,9 +527,10 @@ __global__ void k_eimg_adj(uint8_t* __restrict__ img, const cplx* __restrict__ p
         const cplx E = phase[(size_t)q * n_h + n];
         x = (m & 1) ? -E.y : E.x;
       }
-      split_f64<4>(x, v[u]);
+      split_f64<kPlanes>(x, v[u]);
     }
-    store_planes<4>(img + ((size_t)mt * n_kb + kb) * 4 * kPlaneM, kPlaneM, off64(row, ch * 16), v);
+    store_planes<kPlanes>(img + ((size_t)mt * n_kb + kb) * kPlanes * kPlaneM, kPlaneM,
+                          off64(row, ch * 16), v);
   }
 }
 
@@ -584,7 +582,7 @@ __device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, 
   lo = l - (hi - s);
 }
 
-// Forward B image [nt][kb][4 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
+// Forward B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
 // (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
 __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
                        const float4* __restrict__ gdf, const int* __restrict__ cls_of, int N_tr,
@@ -598,7 +596,7 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
     const int kb = (int)(t % n_kb); t /= n_kb;
     const int nt = (int)t;
     const int j = nt * NT + row;
-    __nv_bfloat16 v[8][4];
+    __nv_bfloat16 v[8][kPlanes];
     const bool live = j < n_cols;
     int s = 0, l = 0, wi = 0, i = 0;
     if (live) {
@@ -623,8 +621,8 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
       split_df(rh, rl, v[2 * u]);
       split_df(-ih, -il, v[2 * u + 1]);
     }
-    store_planes<4>(img + ((size_t)nt * n_kb + kb) * 4 * NT * kRow, NT * kRow,
-                    off64(row, ch * 16), v);
+    store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
+                          off64(row, ch * 16), v);
   }
 }
 
@@ -660,8 +658,8 @@ __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar
       const float x = (live && q < N_k) ? krow[q] * drow[q] : 0.0f;
       split_f32(x, v[u]);
     }
-    store_planes<3>(img + ((size_t)nt * n_kb + kb) * 3 * NT * kRow, NT * kRow,
-                    off64(row, ch * 16), v);
+    store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
+                          off64(row, ch * 16), v);
   }
 }
 
@@ -733,14 +731,14 @@ size_t basis_fixed_bytes(const swcl_ctx* c) {
   const size_t f_mt = (c->N_k + kM - 1) / kM, f_kb = (2 * c->n_h + kK - 1) / kK;
   const size_t a_mt = (2 * c->n_h + kM - 1) / kM, a_kb = (c->N_k + kK - 1) / kK;
   const size_t ng = (size_t)c->n_cls * c->N_ell * c->n_h;
-  return (f_mt * f_kb + a_mt * a_kb) * 4 * kPlaneM + ng * (sizeof(float4) + sizeof(float2)) +
+  return (f_mt * f_kb + a_mt * a_kb) * kPlanes * kPlaneM + ng * (sizeof(float4) + sizeof(float2)) +
          sizeof(float) * (size_t)c->N_tr * 4 * c->N_k +
-         (size_t)kMaxNT * (f_kb * 4 + a_kb * 3) * kRow;   // column padding of the last tile
+         (size_t)kMaxNT * (f_kb + a_kb) * kPlanes * kRow;   // column padding of the last tile
 }
 
 size_t basis_bytes_per_ell(const swcl_ctx* c) {
   const size_t f_kb = (2 * c->n_h + kK - 1) / kK, a_kb = (c->N_k + kK - 1) / kK;
-  return (size_t)c->n_walk * c->N_tr * std::max(1, c->lr_true_rank) * (f_kb * 4 + a_kb * 3) * kRow;
+  return (size_t)c->n_walk * c->N_tr * std::max(1, c->lr_true_rank) * (f_kb + a_kb) * kPlanes * kRow;
 }
 
 // Constant operands of basis mode: the two phase images, the FP32/double-float Gamma tables and
@@ -754,8 +752,8 @@ int basis_prepare(swcl_ctx* c) {
   c->bt_f_kb = (2 * n_h + kK - 1) / kK;
   c->bt_a_mt = (2 * n_h + kM - 1) / kM;
   c->bt_a_kb = (N_k + kK - 1) / kK;
-  const size_t ef = (size_t)c->bt_f_mt * c->bt_f_kb * 4 * kPlaneM;
-  const size_t ea = (size_t)c->bt_a_mt * c->bt_a_kb * 4 * kPlaneM;
+  const size_t ef = (size_t)c->bt_f_mt * c->bt_f_kb * kPlanes * kPlaneM;
+  const size_t ea = (size_t)c->bt_a_mt * c->bt_a_kb * kPlanes * kPlaneM;
   if ((st = ensure(c, c->bt_eimg_f, ef))) return st;
   if ((st = ensure(c, c->bt_eimg_a, ea))) return st;
   const long ng = (long)c->n_cls * c->N_ell * n_h;
@@ -787,7 +785,7 @@ int build_h(swcl_ctx* c, int NT, int n_nt, int l_lo, int n_l) {
   const Stencil sv = stencil(c);
   const int r = basis_rank(c);
   const int n_cols = c->n_walk * c->N_tr * n_l * r;
-  int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * 4 * NT * kRow);
+  int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * kPlanes * NT * kRow);
   if (st) return st;
   const long tot = (long)n_nt * c->bt_f_kb * NT * 4;
   k_himg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p,
@@ -801,7 +799,7 @@ int build_h(swcl_ctx* c, int NT, int n_nt, int l_lo, int n_l) {
 int build_d(swcl_ctx* c, int NT, int n_nt, int n_l) {
   const int r = basis_rank(c);
   const int n_cols = c->n_walk * c->N_tr * r * n_l;
-  int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * 3 * NT * kRow);
+  int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow);
   if (st) return st;
   const long tot = (long)n_nt * c->bt_a_kb * NT * 4;
   k_dimg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p,
@@ -862,9 +860,9 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
     if (build && (st = build_h(c, NT, n_nt, l_lo, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
-    if ((st = shape_for<A4B4>(c, code, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
+    if ((st = shape_for<A3B3>(c, code, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
     EpiFwd epi{(float*)c->ws_delta.p, (const float*)c->bt_kmu.p, c->N_k, c->N_tr, n_l, r, n_cols};
-    cudaError_t e = launch_gemm<A4B4>(c, code, (const uint8_t*)c->bt_eimg_f.p,
+    cudaError_t e = launch_gemm<A3B3>(c, code, (const uint8_t*)c->bt_eimg_f.p,
                                       (const uint8_t*)c->bt_himg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward GEMM");
   };
@@ -896,10 +894,10 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
     if (build && (st = build_d(c, NT, n_nt, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
-    if ((st = shape_for<A4B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
+    if ((st = shape_for<A3B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
     EpiAdj epi{(cplx*)c->ws_cbar.p, (const float2*)c->bt_g32.p, (const int*)c->d_cls_of.p,
                c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
-    cudaError_t e = launch_gemm<A4B3>(c, code, (const uint8_t*)c->bt_eimg_a.p,
+    cudaError_t e = launch_gemm<A3B3>(c, code, (const uint8_t*)c->bt_eimg_a.p,
                                       (const uint8_t*)c->bt_dimg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint GEMM");
   };
