@@ -249,6 +249,15 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
     }
     c->own_stream = true;
   }
+  // a second stream and two events fork independent kernels of the VJP off the main stream
+  // (the fork and join are recorded into CUDA graphs as branches)
+  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return SWCL_ERR_CUDA;
+  }
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
   if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
@@ -298,6 +307,9 @@ int swcl_destroy(swcl_ctx* c) {
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SWCL_OK;
@@ -746,8 +758,16 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   SWCL_TRY(swcl::ensure(c, c->ws_pbpart, swcl::delta_bar_scratch_bytes(nw, N_k, N_ell)));
   double* Pb = P_bar && swcl::is_device_ptr(P_bar) ? P_bar : (double*)c->ws_outP.p;
   double* Ab = amp_bar && swcl::is_device_ptr(amp_bar) ? amp_bar : (double*)c->ws_outA.p;
+  // amp_bar and the P_bar reduction do not feed the transposed contraction: they run on the
+  // auxiliary stream, beside it (not while profiling, which times kernels one by one)
+  const bool fork = !c->prof;
+  cudaStream_t side = fork ? c->aux : c->stream;
+  if (fork) {
+    SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+    SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "fork");
+  }
   SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
-                                      (const double*)c->d_amp.p, nw, N_tr, N_ell, c->stream),
+                                      (const double*)c->d_amp.p, nw, N_tr, N_ell, side),
               "amp_bar");
   for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
     const int n_l = std::min(n_lc, N_ell - l_lo);
@@ -785,8 +805,13 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
       SWCL_TRY(swcl::contract_adj_tc(c, precision));   // whole multipole range (no chunks)
     }
   }
+  if (fork) {
+    // the reduction waits for the last delta_bar chunk (main stream)
+    SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+    SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "fork");
+  }
   SWCL_LAUNCH(c, swcl::launch_pbar_reduce(Pb, (const double*)c->ws_pbpart.p,
-                                          (const double*)c->d_wk2.p, nw, N_k, N_ell, c->stream),
+                                          (const double*)c->d_wk2.p, nw, N_k, N_ell, side),
               "P_bar reduce");
   if (W_bar) {
     double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
@@ -795,8 +820,13 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                            (const double*)c->d_chipow.p, sv.D, sv.B,
                                            (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                            nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
-    ++c->last_launches;  // the chunk reduction
+    if (!swcl::fftlog_adj_single_launch(nw, N_tr, N_I, N)) ++c->last_launches;  // chunk reduction
     SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
+  }
+  if (fork) {
+    // join: the main stream (and the caller's later work on it) sees the auxiliary kernels
+    SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_join, c->aux), "join");
+    SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
   }
   if (P_bar) SWCL_TRY(swcl::copy_out(c, P_bar, Pb, sizeof(double) * nw * (size_t)N_k));
   if (amp_bar) SWCL_TRY(swcl::copy_out(c, amp_bar, Ab, sizeof(double) * nrow));

@@ -7,7 +7,11 @@
 // memory, and unpacked to X_n = sum_m g_m e^{-2 pi i n m/N}, n = 0..N/2.  The coefficient is
 // c_n = psi_i[n] X_n with psi = T_c chi_min^{-i eta_n}/N.  Twiddles come from a table
 // e^{-2 pi i t/N}, t < N, so the only FP64 arithmetic is the butterflies themselves.
+#include <cooperative_groups.h>
+
 #include "swcl_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace swcl {
 namespace {
@@ -214,14 +218,197 @@ __global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restric
   W_bar[t] = s;
 }
 
+// ---------------------------------------------------------------- cluster form ----
+// With few rows (one walker in basis mode: one row per tracer) one CTA per row leaves most SMs
+// idle, and each row is bound by its SM's FP64 pipe.  A cluster of kCl CTAs then shares a row:
+// four-step DFT of the M = N/2 packed points with n = n1 + kCl t (CTA n1 holds t = 0..L-1,
+// L = M/kCl) and k = k2 + L k1:
+//   X[k2 + L k1] = sum_{n1} w_M^{n1 k2} w_kCl^{n1 k1} Y_{n1}[k2],  Y_{n1} = DFT_L(z[n1 + kCl t]).
+// Step 1 runs in each CTA (Stockham in shared memory), step 2 (the kCl-point DFTs, each CTA a
+// slice of k2) reads the other CTAs' Y through distributed shared memory.
+constexpr int kCl = 8;
+constexpr int kClThreads = 128;
+
+__device__ __forceinline__ cplx tw_mod(const cplx* tw, long x, int N) { return tw[x & (N - 1)]; }
+
+// kCl-point DFTs of step 2 for this CTA's slice of k2: Xo[e kCl + k1] (e = k2 - rank kq)
+__device__ __forceinline__ void step2(cg::cluster_group& cl, cplx* Xo, cplx* Y, int L, int N,
+                                      const cplx* __restrict__ tw) {
+  const int kq = L / kCl;
+  const int c = cl.block_rank();
+  for (int o = threadIdx.x; o < L; o += blockDim.x) {
+    const int e = o / kCl, k1 = o - e * kCl;
+    const int k2 = c * kq + e;
+    cplx s = {0.0, 0.0};
+#pragma unroll
+    for (int n1 = 0; n1 < kCl; ++n1) {
+      const cplx* Yr = cl.map_shared_rank(Y, n1);
+      s = cadd(s, cmul(Yr[k2], tw_mod(tw, (long)((n1 * k1) % kCl) * (N / kCl), N)));
+    }
+    Xo[o] = s;
+  }
+}
+
+template <typename CT>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
+k_fftlog_fwd_cl(CT* __restrict__ coef, const double* __restrict__ W,
+                const double* __restrict__ chipow, const double* __restrict__ D,
+                const double* __restrict__ B, const cplx* __restrict__ psi,
+                const cplx* __restrict__ tw, int N_tr, int N_I, int N) {
+  extern __shared__ cplx smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int M = N / 2, L = M / kCl, kq = L / kCl, n_h = M + 1;
+  cplx* a = smem;
+  cplx* b = smem + L;
+  cplx* Xo = smem + 2 * L;
+  const long row = blockIdx.x / kCl;
+  const int ka = (int)(row % N_I);
+  const long wi = row / N_I;
+  const int i = (int)(wi % N_tr);
+  const double* w = W + wi * N;
+  const double* cp = chipow + (size_t)i * N;
+  const double* d = D + (size_t)ka * N;
+  const double* bb = B ? B + ((size_t)i * N_I + ka) * N : nullptr;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    const int m = 2 * (c + kCl * t);
+    double g0 = w[m] * cp[m] * d[m];
+    double g1 = w[m + 1] * cp[m + 1] * d[m + 1];
+    if (bb) { g0 *= bb[m]; g1 *= bb[m + 1]; }
+    a[t] = {g0, g1};
+  }
+  __syncthreads();
+  cplx* Y = stockham(a, b, L, 1, tw, N);
+  for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x)
+    Y[k2] = cmul(Y[k2], tw_mod(tw, 2L * c * k2, N));            // w_M^{c k2}
+  cl.sync();
+  step2(cl, Xo, Y, L, N, tw);
+  cl.sync();
+  // unpack X_n = E_n + e^{-2 pi i n/N} O_n with Z_{M-n} from the CTA that holds it
+  for (int o = threadIdx.x; o <= L; o += blockDim.x) {
+    int n;
+    cplx zn, zm;
+    if (o < L) {
+      const int e = o / kCl, k1 = o - e * kCl;
+      const int k2 = c * kq + e;
+      n = k2 + L * k1;
+      zn = Xo[o];
+      const int k2p = k2 == 0 ? 0 : L - k2;
+      const int k1p = k2 == 0 ? (kCl - k1) % kCl : kCl - 1 - k1;
+      zm = cl.map_shared_rank(Xo, k2p / kq)[(k2p % kq) * kCl + k1p];
+    } else {
+      if (c != 0) break;
+      n = M;                                                       // Nyquist: Z_M = Z_0
+      zn = Xo[0];
+      zm = Xo[0];
+    }
+    const cplx zc = cconj(zm);
+    const cplx e = {0.5 * (zn.x + zc.x), 0.5 * (zn.y + zc.y)};
+    const cplx dl = {0.5 * (zn.x - zc.x), 0.5 * (zn.y - zc.y)};
+    const cplx od = {dl.y, -dl.x};
+    const cplx x = cadd(e, cmul(tw[n], od));
+    store_coef(coef + row * n_h + n, cmul(psi[(size_t)i * n_h + n], x));
+  }
+  cl.sync();   // the other CTAs may still read this CTA's shared memory until here
+}
+
+// Adjoint in the cluster form for rows (w, i) with all their knots (N_I <= kKnotChunk): the
+// inverse transform of each knot's Hermitian-packed input by the same four-step DFT, the
+// products with chipow D_a B_ia summed over the knots in registers, one chunk of scratch.
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
+k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
+                const double* __restrict__ chipow, const double* __restrict__ D,
+                const double* __restrict__ B, const cplx* __restrict__ psi,
+                const cplx* __restrict__ tw, int N_tr, int N_I, int N) {
+  extern __shared__ cplx smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int M = N / 2, L = M / kCl, kq = L / kCl, n_h = M + 1;
+  cplx* a = smem;
+  cplx* b = smem + L;
+  cplx* Xo = smem + 2 * L;
+  const long wi = blockIdx.x / kCl;
+  const int i = (int)(wi % N_tr);
+  const cplx* ps = psi + (size_t)i * n_h;
+  const double* cp = chipow + (size_t)i * N;
+  constexpr int kOut = 2;                  // outputs per thread (L <= 2 kClThreads)
+  double acc0[kOut], acc1[kOut];
+#pragma unroll
+  for (int u = 0; u < kOut; ++u) acc0[u] = acc1[u] = 0.0;
+  for (int ka = 0; ka < N_I; ++ka) {
+    const cplx* cb = cbar + ((size_t)wi * N_I + ka) * n_h;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+      const int n = c + kCl * t;               // < M
+      cplx y = cmulc(cb[n], ps[n]);
+      cplx h = (n == 0) ? cplx{y.x, 0.0} : cplx{0.5 * y.x, 0.5 * y.y};
+      const int m = M - n;
+      cplx ym = cmulc(cb[m], ps[m]);
+      cplx hm = (m == M) ? cplx{ym.x, 0.0} : cplx{0.5 * ym.x, 0.5 * ym.y};
+      cplx hmc = cconj(hm);
+      cplx e = cadd(h, hmc);
+      cplx dd = csub(h, hmc);
+      cplx od = cmulc(dd, tw[n]);
+      cplx z = {e.x - od.y, e.y + od.x};
+      a[t] = cconj(z);
+    }
+    __syncthreads();
+    cplx* Y = stockham(a, b, L, 1, tw, N);
+    for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x)
+      Y[k2] = cmul(Y[k2], tw_mod(tw, 2L * c * k2, N));
+    cl.sync();
+    step2(cl, Xo, Y, L, N, tw);
+    // x_{2j} + i x_{2j+1} = conj(Z_j), j = k2 + L k1 of this CTA's outputs
+    const double* d = D + (size_t)ka * N;
+    const double* bb = B ? B + ((size_t)i * N_I + ka) * N : nullptr;
+#pragma unroll
+    for (int u = 0; u < kOut; ++u) {
+      const int o = threadIdx.x + u * kClThreads;
+      if (o < L) {
+        const int e = o / kCl, k1 = o - e * kCl;
+        const int j = c * kq + e + L * k1;
+        const cplx v = cconj(Xo[o]);
+        const int m = 2 * j;
+        double f0 = cp[m] * d[m], f1 = cp[m + 1] * d[m + 1];
+        if (bb) { f0 *= bb[m]; f1 *= bb[m + 1]; }
+        acc0[u] = fma(v.x, f0, acc0[u]);
+        acc1[u] = fma(v.y, f1, acc1[u]);
+      }
+    }
+    cl.sync();   // Y and Xo are reused by the next knot; the other CTAs have finished reading
+  }
+  double* out = scratch + (size_t)wi * N;
+#pragma unroll
+  for (int u = 0; u < kOut; ++u) {
+    const int o = threadIdx.x + u * kClThreads;
+    if (o < L) {
+      const int e = o / kCl, k1 = o - e * kCl;
+      const int j = c * kq + e + L * k1;
+      out[2 * j] = acc0[u];
+      out[2 * j + 1] = acc1[u];
+    }
+  }
+}
+
+// The cluster form serves few rows (fewer than a quarter of the SMs' worth) of a length the
+// four-step split supports.
+bool use_cluster(long rows, int N) {
+  return rows * kCl <= 2L * 152 && N >= 256 && N / 2 / kCl <= 2 * kClThreads;
+}
+
 }  // namespace
 
 template <typename CT>
 static cudaError_t fftlog_fwd(CT* coef, const double* W, const double* chipow, const double* D,
                               const double* B, const cplx* psi, const cplx* twiddle, int n_walk,
                               int N_tr, int N_I, int N, cudaStream_t s) {
-  int R = rows_per_cta(N);
   long rows = (long)n_walk * N_tr * N_I;
+  if (use_cluster(rows, N)) {
+    const size_t smem = (size_t)3 * (N / 2 / kCl) * sizeof(cplx);
+    k_fftlog_fwd_cl<CT><<<(unsigned)(rows * kCl), kClThreads, smem, s>>>(coef, W, chipow, D, B, psi,
+                                                                        twiddle, N_tr, N_I, N);
+    return cudaGetLastError();
+  }
+  int R = rows_per_cta(N);
   long grid = (rows + R - 1) / R;
   size_t smem = (size_t)2 * R * (N / 2) * sizeof(cplx);
   if (smem > 48 * 1024) {
@@ -248,6 +435,10 @@ cudaError_t launch_fftlog_fwd_df(float4* coef, const double* W, const double* ch
   return fftlog_fwd(coef, W, chipow, D, B, psi, twiddle, n_walk, N_tr, N_I, N, s);
 }
 
+bool fftlog_adj_single_launch(int n_walk, int N_tr, int N_I, int N) {
+  return (N_I + kKnotChunk - 1) / kKnotChunk == 1 && use_cluster((long)n_walk * N_tr, N);
+}
+
 size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N) {
   int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
   return (size_t)nchunk * n_walk * N_tr * N * sizeof(double);
@@ -258,6 +449,13 @@ cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chi
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
                               double* scratch, cudaStream_t s) {
   int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
+  if (nchunk == 1 && use_cluster((long)n_walk * N_tr, N)) {
+    // one chunk: the cluster kernel writes W_bar directly
+    const size_t csm = (size_t)3 * (N / 2 / kCl) * sizeof(cplx);
+    k_fftlog_adj_cl<<<(unsigned)((long)n_walk * N_tr * kCl), kClThreads, csm, s>>>(
+        W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I, N);
+    return cudaGetLastError();
+  }
   size_t smem = (size_t)(N / 2) * 2 * sizeof(cplx) + (size_t)N * sizeof(double);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fftlog_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -57,6 +57,8 @@ struct swcl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t aux = nullptr;               // second stream for independent VJP kernels
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t budget = 0;      // 0 = unbounded
   size_t held = 0;        // device bytes held
   std::string err;
@@ -206,6 +208,7 @@ cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chi
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
                               double* scratch, cudaStream_t s);
 size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
+bool fftlog_adj_single_launch(int n_walk, int N_tr, int N_I, int N);   // no chunk reduction
 
 // a3 FP64 contraction (contract_fp64.cu)
 cudaError_t launch_contract_fp64(double* delta, const cplx* coef, const cplx* phase,
