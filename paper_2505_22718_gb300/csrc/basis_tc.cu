@@ -241,7 +241,9 @@ struct EpiAdj {
 
 // ------------------------------------------------------------------- GEMM ----
 
-template <class P, class Epi, int DW>
+// CH: 16-column chunks per drain thread at most (3 for tiles up to 96 columns with 8 drain
+// warps, 4 otherwise); it sizes the accumulator registers.
+template <class P, class Epi, int DW, int CH>
 __global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
@@ -368,9 +370,9 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
     const int nch0 = DW == 8 ? (nch + 1) / 2 : nch;
     const int c_begin = half ? nch0 : 0;
     const int my = half ? nch - nch0 : nch0;   // 16-column chunks of this thread (<= 4)
-    float acc[kHalf];
+    float acc[CH * 16];
 #pragma unroll
-    for (int t = 0; t < kHalf; ++t) acc[t] = 0.0f;
+    for (int t = 0; t < CH * 16; ++t) acc[t] = 0.0f;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     // the first two K-blocks find their accumulator buffers empty
     if (lane == 0) {
@@ -386,30 +388,54 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       tc_fence_after();
       const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
       const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
-      // two chunks (main and correction slots) in flight per wait
+      if constexpr (CH <= 3) {
+        // up to three chunks: every load of the K-block in flight behind one wait
+        uint32_t m0[16], r0[16], m1[16], r1[16], m2[16], r2[16];
+        tmem_ld16_async(slot_m, m0);
+        tmem_ld16_async(slot_c, r0);
+        if (my > 1) {
+          tmem_ld16_async(slot_m + 16, m1);
+          tmem_ld16_async(slot_c + 16, r1);
+        }
+        if (my > 2) {
+          tmem_ld16_async(slot_m + 32, m2);
+          tmem_ld16_async(slot_c + 32, r2);
+        }
+        tmem_wait_ld();
+        reg_fence(m0);
+        reg_fence(r0);
 #pragma unroll
-      for (int g = 0; g < kHalf / 16; g += 2) {
-        if (g < my) {
+        for (int t = 0; t < 16; ++t) acc[t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+        if (my > 1) {
+          reg_fence(m1);
+          reg_fence(r1);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+        }
+        if (my > 2) {
+          reg_fence(m2);
+          reg_fence(r2);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[32 + t] += __uint_as_float(m2[t]) + __uint_as_float(r2[t]);
+        }
+      } else {
+        // four chunks: two in flight per wait
+#pragma unroll
+        for (int g = 0; g < CH; g += 2) {
           uint32_t m0[16], r0[16], m1[16], r1[16];
-          const bool two = g + 1 < my;
           tmem_ld16_async(slot_m + g * 16, m0);
           tmem_ld16_async(slot_c + g * 16, r0);
-          if (two) {
-            tmem_ld16_async(slot_m + (g + 1) * 16, m1);
-            tmem_ld16_async(slot_c + (g + 1) * 16, r1);
-          }
+          tmem_ld16_async(slot_m + (g + 1) * 16, m1);
+          tmem_ld16_async(slot_c + (g + 1) * 16, r1);
           tmem_wait_ld();
           reg_fence(m0);
           reg_fence(r0);
+          reg_fence(m1);
+          reg_fence(r1);
 #pragma unroll
-          for (int t = 0; t < 16; ++t)
+          for (int t = 0; t < 16; ++t) {
             acc[g * 16 + t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
-          if (two) {
-            reg_fence(m1);
-            reg_fence(r1);
-#pragma unroll
-            for (int t = 0; t < 16; ++t)
-              acc[(g + 1) * 16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+            acc[(g + 1) * 16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
           }
         }
       }
@@ -427,7 +453,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       const int dt = tid - 64;                       // drain thread 0 .. 32 DW - 1
       float* ep = reinterpret_cast<float*>(base);
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c)
+      for (int c = 0; c < CH * 16; ++c)
         if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
       epi(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
     }
@@ -687,13 +713,13 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   return SWCL_OK;
 }
 
-template <class P, class Epi, int DW>
+template <class P, class Epi, int DW, int CH>
 cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
                            uint32_t smem, int n_nt, const Epi& epi) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW>,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi, DW><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
+  k_gemm_basis<P, Epi, DW, CH><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
       a, b, sh, epi, (int*)c->ws_status.p);
   return cudaGetLastError();
 }
@@ -701,8 +727,12 @@ cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, cons
 template <class P, class Epi>
 cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* b,
                         const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
-  return (code & kPair) ? launch_variant<P, Epi, 4>(c, a, b, sh, smem, n_nt, epi)
-                        : launch_variant<P, Epi, 8>(c, a, b, sh, smem, n_nt, epi);
+  const int nch = sh.NT / 16;
+  if (code & kPair)   // four drain warps: every chunk of a row in one thread
+    return nch <= 3 ? launch_variant<P, Epi, 4, 3>(c, a, b, sh, smem, n_nt, epi)
+                    : launch_variant<P, Epi, 4, 4>(c, a, b, sh, smem, n_nt, epi);
+  return (nch + 1) / 2 <= 3 ? launch_variant<P, Epi, 8, 3>(c, a, b, sh, smem, n_nt, epi)
+                            : launch_variant<P, Epi, 8, 4>(c, a, b, sh, smem, n_nt, epi);
 }
 
 // Candidate tile codes: column tiles that are multiples of 16; in forward tiles each drain
