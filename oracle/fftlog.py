@@ -28,10 +28,18 @@ R6  The k-integral of Eq. (2.1) "over all N_k points" (Sec. 3.2) is the
 R8  The Gamma-ratio table is evaluated from log-Gammas at the smallest ell of each parity and
     carried to larger ell by the exact two-step recurrence of Gamma(z+1) = z Gamma(z)
     (see bessel_power_integral).
+R10 RSD tracers (kernel j_l'', Eq. 2.10) need a larger FFTLog bias than density ones: j_2''
+    tends to a constant at small argument, so the periodic images of the window are damped
+    only through b; b = 0.4 (the strip is -l+1 < b < 1) gives l = 2 to ~6e-7 of brute force.
 R7  Source functions: density Delta = int W D j_ell (Eq. 2.6, the linear bias
     b_1 is the tracer amplitude); lensing Delta = sqrt((l+2)!/(l-2)!) k^-2
-    int W chi^-2 D j_ell (Eq. 2.14).  A per-tracer amplitude A_i multiplies
-    Delta_i; an optional k,z-dependent bias B_i(k, chi) multiplies W D.
+    int W chi^-2 D j_ell (Eq. 2.14; intrinsic alignment, Eq. 2.15, is the same
+    kernel with the window n A_IA); magnification Delta = l(l+1) k^-2
+    int W chi^-2 D j_ell (Eq. 2.9, C_g in the amplitude; CMB lensing, Eq. 2.16, is
+    the same kernel with its own window); RSD Delta = -int W D j_ell'' (Eq. 2.10,
+    f(z) in the window).  A per-tracer amplitude A_i multiplies Delta_i; an
+    optional k,z-dependent bias B_i(k, chi) multiplies W D (primordial
+    non-Gaussianity, Eq. 2.11-2.13, is a density tracer with B = 1/T_alpha).
 """
 from __future__ import annotations
 
@@ -40,6 +48,10 @@ from scipy.special import loggamma
 
 KIND_DENSITY = 0
 KIND_LENSING = 1
+KIND_MAGNIFICATION = 2    # magnification bias (Eq. 2.9) and CMB lensing (Eq. 2.16): l(l+1) k^-2
+KIND_RSD = 3              # redshift-space distortion (Eq. 2.10): -j_l''
+
+_CHI2 = (KIND_LENSING, KIND_MAGNIFICATION)
 
 
 # ---------------------------------------------------------------- grids ----
@@ -57,20 +69,26 @@ def eta_two_sided(N: int, L: float) -> tuple[np.ndarray, np.ndarray]:
 
 
 def chi_power(kind) -> np.ndarray:
-    """Power s of chi multiplying the window: 0 (density, Eq. 2.6), -2 (lensing, Eq. 2.14)."""
-    return np.where(np.asarray(kind) == KIND_LENSING, -2.0, 0.0)
+    """Power s of chi multiplying the window: 0 (density Eq. 2.6, RSD Eq. 2.10), -2 (lensing
+    Eq. 2.14, magnification Eq. 2.9)."""
+    return np.where(np.isin(np.asarray(kind), _CHI2), -2.0, 0.0)
 
 
 def k_power(kind) -> np.ndarray:
-    """Power t of k in front of the chi integral: 0 (density), -2 (lensing, Eq. 2.14)."""
-    return np.where(np.asarray(kind) == KIND_LENSING, -2.0, 0.0)
+    """Power t of k in front of the chi integral: 0 (density, RSD), -2 (lensing, magnification)."""
+    return np.where(np.isin(np.asarray(kind), _CHI2), -2.0, 0.0)
 
 
 def ell_prefactor(ells, kind: int) -> np.ndarray:
-    """c(ell) of Eq. (2.2): 1 for density, sqrt((l+2)!/(l-2)!) for lensing (Eq. 2.14)."""
+    """c(ell) of Eq. (2.2): 1 for density, sqrt((l+2)!/(l-2)!) for lensing (Eq. 2.14), l(l+1) for
+    magnification (Eq. 2.9), -1 for RSD (the sign of Eq. 2.10)."""
     l = np.asarray(ells, dtype=np.float64)
     if kind == KIND_LENSING:
         return np.sqrt((l + 2.0) * (l + 1.0) * l * (l - 1.0))
+    if kind == KIND_MAGNIFICATION:
+        return l * (l + 1.0)
+    if kind == KIND_RSD:
+        return -np.ones_like(l)
     return np.ones_like(l)
 
 
@@ -161,6 +179,25 @@ def bessel_power_integral(ells, p):
 
 # ------------------------------------------------------ k-interpolation ----
 
+def bessel2_power_integral(ells, p):
+    """int_0^inf chi^p j_l''(chi) dchi for the RSD kernel (Eq. 2.10), l >= 2.
+
+    Two steps of the recurrences j_l' = (l j_{l-1} - (l+1) j_{l+1})/(2l+1) give
+        j_l'' = l(l-1)/((2l-1)(2l+1)) j_{l-2} - (2l^2+2l-1)/((2l-1)(2l+3)) j_l
+                + (l+1)(l+2)/((2l+1)(2l+3)) j_{l+2},
+    so the integral is the same combination of the tables of l-2, l and l+2.
+    """
+    ells = np.asarray(ells, dtype=np.int64)
+    if np.any(ells < 2):
+        raise ValueError("the RSD kernel needs ell >= 2")
+    l = ells.astype(np.float64)[:, None]
+    a = l * (l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 1.0))
+    b = (2.0 * l * l + 2.0 * l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 3.0))
+    c = (l + 1.0) * (l + 2.0) / ((2.0 * l + 1.0) * (2.0 * l + 3.0))
+    return (a * bessel_power_integral(ells - 2, p) - b * bessel_power_integral(ells, p)
+            + c * bessel_power_integral(ells + 2, p))
+
+
 def lagrange_matrix(k, knots) -> np.ndarray:
     """Dense interpolation matrix Lam[q, a] (reading R5).
 
@@ -238,12 +275,15 @@ class Grids:
         self.phase = np.exp(-1j * np.outer(np.log(self.k), self.eta))
         self._mtab = {}
 
-    def mtable(self, b: float, ells=None):
-        """I_ell(b + i eta_n) for the requested ells (default: all), [N_ell, N+1]."""
+    def mtable(self, b: float, ells=None, kind: int = KIND_DENSITY):
+        """I_ell(b + i eta_n) of the tracer's kernel (j_l, or j_l'' for RSD) for the requested
+        ells (default: all), [N_ell, N+1]."""
         ells = self.ells if ells is None else np.asarray(ells)
-        key = (float(b), tuple(int(e) for e in ells))
+        rsd = int(kind) == KIND_RSD
+        key = (float(b), rsd, tuple(int(e) for e in ells))
         if key not in self._mtab:
-            self._mtab[key] = bessel_power_integral(ells, b + 1j * self.eta)
+            f = bessel2_power_integral if rsd else bessel_power_integral
+            self._mtab[key] = f(ells, b + 1j * self.eta)
         return self._mtab[key]
 
 
@@ -277,7 +317,7 @@ def delta_from_coefficients(g: Grids, coef, ells=None, tracers=None, q_index=Non
         kind = int(g.kind[i])
         ck = g.lam[q] @ coef[i]                                   # [N_q, N+1] c_n(k_q)
         X = ck * g.phase[q]                                       # c_n(k) e^{-i eta_n ln k}
-        M = g.mtable(b, ells)                                     # [N_ell, N+1]
+        M = g.mtable(b, ells, kind)                               # [N_ell, N+1]
         S = X @ M.T                                               # [N_q, N_ell]
         worst = max(worst, float(np.abs(S.imag).max() / max(np.abs(S.real).max(), 1e-300)))
         kfac = k ** (k_power(kind) - 1.0 - b)
@@ -339,7 +379,7 @@ def vjp(g: Grids, fwd: dict, C_bar, W, D, P, amp, B=None, taper_chi=None, taper_
     for i in range(coef.shape[0]):
         b = g.fft_bias[i]
         kind = int(g.kind[i])
-        M = g.mtable(b, ells)                                     # [N_ell, N+1]
+        M = g.mtable(b, ells, kind)                               # [N_ell, N+1]
         kfac = g.k ** (k_power(kind) - 1.0 - b)
         pre = ell_prefactor(ells, kind)
         # Delta = kfac_q pre_l Re(sum_n X_qn M_ln):  X_bar (d/dRe X + i d/dIm X)
