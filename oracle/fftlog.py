@@ -182,20 +182,20 @@ def bessel_power_integral(ells, p):
 def bessel2_power_integral(ells, p):
     """int_0^inf chi^p j_l''(chi) dchi for the RSD kernel (Eq. 2.10), l >= 2.
 
-    Two steps of the recurrences j_l' = (l j_{l-1} - (l+1) j_{l+1})/(2l+1) give
-        j_l'' = l(l-1)/((2l-1)(2l+1)) j_{l-2} - (2l^2+2l-1)/((2l-1)(2l+3)) j_l
-                + (l+1)(l+2)/((2l+1)(2l+3)) j_{l+2},
-    so the integral is the same combination of the tables of l-2, l and l+2.
+    Integrating by parts twice (the boundary terms vanish inside the strip 1 - l < Re p < 1,
+    where both integrals converge):
+        int chi^p j_l'' dchi = p (p - 1) int chi^{p-2} j_l dchi = p (p - 1) I_l(p - 2).
+    This product form is used rather than the three-term Bessel recurrence
+    j_l'' = a j_{l-2} - b j_l + c j_{l+2}: at large l and small eta the three terms nearly cancel
+    (about seven digits at l ~ 1000) and the result would carry the R8 recurrence error magnified
+    by that amount.  The tests check the two forms against each other where the cancellation is
+    mild, and the j_l'' combination against the Bessel equation.
     """
     ells = np.asarray(ells, dtype=np.int64)
     if np.any(ells < 2):
         raise ValueError("the RSD kernel needs ell >= 2")
-    l = ells.astype(np.float64)[:, None]
-    a = l * (l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 1.0))
-    b = (2.0 * l * l + 2.0 * l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 3.0))
-    c = (l + 1.0) * (l + 2.0) / ((2.0 * l + 1.0) * (2.0 * l + 3.0))
-    return (a * bessel_power_integral(ells - 2, p) - b * bessel_power_integral(ells, p)
-            + c * bessel_power_integral(ells + 2, p))
+    p = np.asarray(p, dtype=np.complex128)
+    return (p * (p - 1.0))[None, :] * bessel_power_integral(ells, p - 2.0)
 
 
 def lagrange_matrix(k, knots) -> np.ndarray:

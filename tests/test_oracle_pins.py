@@ -342,16 +342,26 @@ def test_numpy_fft_matches_direct_sum():
 
 # ------------------------------------------ magnification and RSD kinds ----
 
-def test_rsd_table_equals_integration_by_parts():
-    """The RSD kernel table (Eq. 2.10, three-term recurrence for j_l'') against an independent route:
-    integrating by parts twice, int x^p j_l''(x) dx = p (p - 1) int x^{p-2} j_l(x) dx inside the
-    strip where both converge.  Complex p up to |eta| = 300, l = 2..1500."""
+def test_rsd_table_equals_three_term_recurrence():
+    """The RSD kernel table (Eq. 2.10), formed by integrating by parts twice,
+    int x^p j_l''(x) dx = p (p - 1) I_l(p - 2), against an independent route: the recurrences
+    j_l' = (l j_{l-1} - (l+1) j_{l+1})/(2l+1) applied twice give j_l'' as a combination of
+    j_{l-2}, j_l and j_{l+2}, so the table is the same combination of the l-2, l and l+2 tables.
+    The three terms nearly cancel at large l, so the gate is relative to the sum of their
+    magnitudes.  Complex p up to |eta| = 300, l = 2..1500."""
     ells = np.array([2, 3, 7, 40, 301, 1500])
     rng = np.random.default_rng(4)
     p = rng.uniform(-0.8, 0.9, 12) + 1j * rng.uniform(-300, 300, 12)
-    a = O.bessel2_power_integral(ells, p)
-    b = p[None, :] * (p[None, :] - 1.0) * O.bessel_power_integral(ells, p - 2.0)
-    assert np.max(np.abs(a / b - 1.0)) < 1e-11
+    got = O.bessel2_power_integral(ells, p)
+    l = ells.astype(np.float64)[:, None]
+    t0 = l * (l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 1.0)) * O.bessel_power_integral(ells - 2, p)
+    t1 = ((2.0 * l * l + 2.0 * l - 1.0) / ((2.0 * l - 1.0) * (2.0 * l + 3.0))
+          * O.bessel_power_integral(ells, p))
+    t2 = (l + 1.0) * (l + 2.0) / ((2.0 * l + 1.0) * (2.0 * l + 3.0)) * O.bessel_power_integral(ells + 2, p)
+    scale = np.abs(t0) + np.abs(t1) + np.abs(t2)
+    assert np.all(np.abs(got - (t0 - t1 + t2)) <= 1e-12 * scale)
+    # a dropped p(p-1) factor or a shifted argument is O(1) off
+    assert np.max(np.abs(got / (t0 - t1 + t2) - 1.0)[:4]) < 1e-11
 
 
 def test_rsd_kernel_identity_against_bessel_equation():
