@@ -18,8 +18,18 @@
  *   a5  the vector-Jacobian product of a1-a4 with respect to P(k), the amplitudes A_i and the
  *       window samples W_i(chi_m).
  *
- * Tracer kinds: SWCL_DENSITY (s = 0, t = 0, pi = 1; Eq. 2.6) and SWCL_LENSING
- * (s = -2, t = -2, pi = sqrt((l+2)!/(l-2)!); Eq. 2.14).
+ * Tracer kinds (chi power s in the FFTLog input, k power t in front of the chi integral,
+ * multipole prefactor pi, spherical-Bessel kernel):
+ *   SWCL_DENSITY       s = 0,  t = 0,  pi = 1,                 j_l    (galaxy clustering, Eq. 2.6;
+ *                      primordial non-Gaussianity, Eq. 2.11-2.13, is this kind with its B(k,z));
+ *   SWCL_LENSING       s = -2, t = -2, pi = sqrt((l+2)!/(l-2)!), j_l  (cosmic shear, Eq. 2.14;
+ *                      intrinsic alignments, Eq. 2.15, are this kind with their own window);
+ *   SWCL_MAGNIFICATION s = -2, t = -2, pi = l(l+1),            j_l    (magnification bias,
+ *                      Eq. 2.9; CMB lensing, Eq. 2.16, is this kind with its own window);
+ *   SWCL_RSD           s = 0,  t = 0,  pi = -1,                j_l''  (redshift-space
+ *                      distortions, Eq. 2.10).
+ * A tracer that sums several of these (clustering + RSD + magnification of one bin) is the sum
+ * of its parts: its C_l are block sums of the C_l of the component tracers.
  *
  * Conventions
  *  - Every call returns an int status: SWCL_OK (0) or a negative SWCL_ERR_* code.  No call
@@ -58,8 +68,10 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_ERR_STATE       (-7)  /* call out of order (e.g. compute before set_grids) */
 
 /* tracer kinds */
-#define SWCL_DENSITY 0
-#define SWCL_LENSING 1
+#define SWCL_DENSITY       0
+#define SWCL_LENSING       1
+#define SWCL_MAGNIFICATION 2
+#define SWCL_RSD           3
 
 /* arithmetic of the contraction (a3) and of the k-quadrature (a4) */
 #define SWCL_FP64        0  /* FP64 CUDA cores throughout */
@@ -98,8 +110,9 @@ int swcl_set_grids(swcl_ctx* ctx, double chi_min, double chi_max, int N,
                    const double* k, int N_k, const int* ells, int N_ell,
                    const double* knots, int N_I);
 
-/* Tracers.  kind[N_tr] (SWCL_DENSITY / SWCL_LENSING), fft_bias[N_tr] = b_i with
- * -ell_min - 1 < b_i < 1 (Eq. 3.4 range), taper_chi[N_tr][N] and taper_c[N_tr][N/2+1] optional
+/* Tracers.  kind[N_tr] (SWCL_DENSITY, SWCL_LENSING, SWCL_MAGNIFICATION, SWCL_RSD), fft_bias[N_tr]
+ * = b_i with -ell_min - 1 < b_i < 1 (Eq. 3.4 range; 1 - ell_min < b_i < 1 for SWCL_RSD, whose
+ * j_l'' moment is taken at b_i - 2; lensing and RSD need every ell >= 2), taper_chi[N_tr][N] and taper_c[N_tr][N/2+1] optional
  * smoothing of the tails (Sec. 3.1; NULL = none).  Builds the Gamma-ratio (a2) and phase tables. */
 int swcl_set_tracers(swcl_ctx* ctx, int N_tr, const int* kind, const double* fft_bias,
                      const double* taper_chi, const double* taper_c);

@@ -9,6 +9,7 @@ from .api import (  # noqa: F401
     Context, SwiftClError, PRECISIONS, SWCL_OK, SWCL_ERR_INVALID_ARG, SWCL_ERR_UNSUPPORTED,
     SWCL_ERR_OOM_BUDGET, SWCL_ERR_CUDA, SWCL_ERR_TIMEOUT, SWCL_ERR_NONFINITE, SWCL_ERR_STATE,
     SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16, SWCL_TF32X6, SWCL_DENSITY, SWCL_LENSING,
+    SWCL_MAGNIFICATION, SWCL_RSD,
     SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES,
     SWCL_Q_PROFILE_RANK, SWCL_Q_TILE_FWD, SWCL_Q_TILE_ADJ,
     swcl_create, swcl_destroy, swcl_set_grids, swcl_set_tracers, swcl_set_windows,

@@ -16,7 +16,7 @@ from . import _lib
 SWCL_OK = 0
 (SWCL_ERR_INVALID_ARG, SWCL_ERR_UNSUPPORTED, SWCL_ERR_OOM_BUDGET, SWCL_ERR_CUDA, SWCL_ERR_TIMEOUT,
  SWCL_ERR_NONFINITE, SWCL_ERR_STATE) = -1, -2, -3, -4, -5, -6, -7
-SWCL_DENSITY, SWCL_LENSING = 0, 1
+SWCL_DENSITY, SWCL_LENSING, SWCL_MAGNIFICATION, SWCL_RSD = 0, 1, 2, 3
 SWCL_FP64, SWCL_3XTF32, SWCL_SPLIT_BF16, SWCL_TF32X6 = 0, 1, 2, 3
 SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES = 1, 2, 3, 4
 SWCL_Q_PROFILE_RANK, SWCL_Q_TILE_FWD, SWCL_Q_TILE_ADJ = 5, 6, 7

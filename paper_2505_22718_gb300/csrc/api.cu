@@ -397,12 +397,16 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   int lmin = c->ells_h[0];
   for (int l : c->ells_h) lmin = l < lmin ? l : lmin;
   for (int i = 0; i < N_tr; ++i) {
-    if (kh[i] != SWCL_DENSITY && kh[i] != SWCL_LENSING)
-      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "tracer kind must be SWCL_DENSITY or SWCL_LENSING");
-    if (kh[i] == SWCL_LENSING && lmin < 2)
-      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "lensing tracers need every ell >= 2");
+    if (kh[i] < SWCL_DENSITY || kh[i] > SWCL_RSD)
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG,
+                        "tracer kind must be SWCL_DENSITY, SWCL_LENSING, SWCL_MAGNIFICATION or SWCL_RSD");
+    if ((kh[i] == SWCL_LENSING || kh[i] == SWCL_RSD) && lmin < 2)
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "lensing and RSD tracers need every ell >= 2");
     if (!(bh[i] < 1.0) || !(bh[i] > -(double)lmin - 1.0))
       return swcl::fail(c, SWCL_ERR_INVALID_ARG, "fft_bias must satisfy -ell_min - 1 < b < 1 (Eq. 3.4)");
+    // the j_l'' moment is p (p - 1) M_l(p - 2): p - 2 must stay inside the strip of M_l
+    if (kh[i] == SWCL_RSD && !(bh[i] > 1.0 - (double)lmin))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "RSD tracers need 1 - ell_min < fft_bias < 1 (Eq. 2.10)");
   }
   // classes: distinct (kind, b)
   std::vector<std::pair<int, double>> cls;

@@ -55,7 +55,7 @@ extern "C" int swcl_fftlog_noalloc(int n_walk, int N_tr, int N_I, int N, double 
   if (!(chi_min > 0) || !(chi_max > chi_min) || !kind || !fft_bias || !W || !D || !coef)
     return SWCL_ERR_INVALID_ARG;
   for (int i = 0; i < N_tr; ++i) {
-    if (kind[i] != SWCL_DENSITY && kind[i] != SWCL_LENSING) return SWCL_ERR_INVALID_ARG;
+    if (kind[i] < SWCL_DENSITY || kind[i] > SWCL_RSD) return SWCL_ERR_INVALID_ARG;
     if (!(fft_bias[i] < 1.0)) return SWCL_ERR_INVALID_ARG;
   }
   const int n_h = N / 2 + 1;

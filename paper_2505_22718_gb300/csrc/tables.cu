@@ -153,7 +153,12 @@ __global__ void k_quadw(double* wk2, const double* k, int N_k) {
   wk2[q] = (2.0 / 3.14159265358979323846) * h * kk * kk * kk;
 }
 
-// gtab[l][n] = w_n pi_kind(l) sqrt(pi) 2^{p-1} G((l+1+p)/2) / G((l+2-p)/2), p = b + i eta_n.
+// gtab[l][n] = w_n pi_kind(l) M(l, p), p = b + i eta_n, with the Bessel moment of Eq. 3.4
+//   M(l, p) = sqrt(pi) 2^{p-1} G((l+1+p)/2) / G((l+2-p)/2)            (j_l kernels),
+//   M''(l, p) = p (p-1) M(l, p-2) = M(l, p) p (p-1) / ((l-1+p)(l+2-p))  (RSD, j_l'' of Eq. 2.10),
+// the second form by integrating by parts twice and G(z+1) = z G(z) on both Gammas.
+// pi_kind(l): 1 (density), sqrt((l+2)!/(l-2)!) (lensing, Eq. 2.14), l(l+1) (magnification,
+// Eq. 2.9), -1 (RSD, the sign of Eq. 2.10).
 __global__ void k_gamma(cplx* gtab, const int* ells, int N_ell, int n_h, double L, double b,
                         int kind) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,6 +175,13 @@ __global__ void k_gamma(cplx* gtab, const int* ells, int N_ell, int n_h, double 
   cplx m = cexp(lg);
   double pre = 1.7724538509055160273;  // sqrt(pi)
   if (kind == SWCL_LENSING) pre *= sqrt((l + 2.0) * (l + 1.0) * l * (l - 1.0));
+  if (kind == SWCL_MAGNIFICATION) pre *= l * (l + 1.0);
+  if (kind == SWCL_RSD) {
+    const cplx num = cmul({b, eta}, {b - 1.0, eta});
+    const cplx den = cmul({l - 1.0 + b, eta}, {l + 2.0 - b, -eta});
+    m = cmul(m, cmul(num, cinv(den)));
+    pre = -pre;
+  }
   double wn = (n == 0 || n == n_h - 1) ? 1.0 : 2.0;
   gtab[(size_t)li * n_h + n] = cscale(m, pre * wn);
 }
@@ -179,7 +191,10 @@ __global__ void k_tracer(double* chipow, cplx* psi, double* kpow, const double* 
                          const double* taper_chi, const double* taper_c) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int n_h = N / 2 + 1;
-  double s = (kind == SWCL_LENSING) ? -2.0 : 0.0;
+  // chi^s in the FFTLog input and k^t in front of it: s = t = -2 for the kinds with the lensing
+  // chi^-2 (lensing, magnification), 0 otherwise
+  const bool chi2 = kind == SWCL_LENSING || kind == SWCL_MAGNIFICATION;
+  double s = chi2 ? -2.0 : 0.0;
   if (t < N) {
     double lnchi = log(chi_min) + (double)t * L / (double)N;
     double v = exp((s - b) * lnchi);
@@ -194,7 +209,7 @@ __global__ void k_tracer(double* chipow, cplx* psi, double* kpow, const double* 
     psi[t] = cscale(ph, sc);
   }
   if (t < N_k) {
-    double tk = (kind == SWCL_LENSING) ? -2.0 : 0.0;
+    double tk = chi2 ? -2.0 : 0.0;
     kpow[t] = exp((tk - 1.0 - b) * log(k[t]));
   }
 }

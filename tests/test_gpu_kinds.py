@@ -1,0 +1,181 @@
+"""Every tracer kind on the GPU against the oracle, in one mixed case: galaxy clustering
+(Eq. 2.6), redshift-space distortions (Eq. 2.10, kernel j_l''), magnification bias (Eq. 2.9),
+cosmic shear (Eq. 2.14), intrinsic alignments (Eq. 2.15, the shear kind with its own window),
+a clustering tracer with the scale-dependent bias of primordial non-Gaussianity (Eq. 2.11-2.13,
+the density kind with its B(k, z)) and CMB lensing (Eq. 2.16, the magnification kind with the
+single-source-plane window).
+
+Gates (reading R9) with a conditioning term.  Delta_i(l, k) is a sum of N/2 + 1 complex terms of
+size S_i(l, k) = |pi_i(l)| k^{t_i - 1 - b_i} sum_n |c_n(k)| |M_l(p_n)|.  Where j_l(k chi) is tiny
+over the whole window (l >> k chi_max) the terms cancel to many digits and both sides return
+rounding noise of order eps S, not Delta; the RSD bias b = 0.4 (reading R10) makes S grow as
+k^-1.4 towards small k.  So each entry is gated by
+    |x - x_oracle| <= tol |x_oracle| (C: the normalised floor of R9) + tau E,
+with E the first-order propagation of S into the entry (E = S for Delta;
+E_ij = A_i A_j sum_q u_q (S_i |Delta_j| + |Delta_i| S_j) for C).  tau = 1e-12 in FP64 (table and
+summation rounding of a few parts in 1e14, with margin) and 1e-6 for the FP32-accumulated forms.
+Where the terms do not cancel, E is of the size of the entry and the tau term is far below tol."""
+import numpy as np
+import pytest
+
+from gpu_helpers import lib_context, max_rel, oracle_walker
+from oracle import fftlog as O
+
+pytestmark = pytest.mark.gpu
+
+C_OVER_H0 = 2997.92458
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _mixed_case(seed=21):
+    from workloads.n5k_synth import (CHI_MAX, CHI_MIN, Cosmology, Workload, clustering_window,
+                                     ell_list, lensing_window, power_spectrum, smail_bin_edges)
+    rng = np.random.default_rng(seed)
+    cosmo = Cosmology()
+    N = 1024
+    L = np.log(CHI_MAX / CHI_MIN)
+    chi = CHI_MIN * np.exp(np.arange(N) * L / N)
+    z = cosmo.z_of_chi(chi)
+    k = np.geomspace(1e-4, 5.0, 301)
+    ells = ell_list(2, 1000, 31)
+    knots = np.geomspace(1e-4, 5.0, 23)
+    edges = smail_bin_edges(3)
+    # density, RSD, magnification, shear, IA, fNL density, CMB lensing
+    kind = np.array([O.KIND_DENSITY, O.KIND_RSD, O.KIND_MAGNIFICATION, O.KIND_LENSING,
+                     O.KIND_LENSING, O.KIND_DENSITY, O.KIND_MAGNIFICATION], dtype=np.int32)
+    fft_bias = np.array([-0.3, 0.4, -1.5, -1.5, -1.2, -0.3, -1.5])
+    gal = clustering_window(cosmo, chi, 0.7, 0.1, z)
+    src = lensing_window(cosmo, chi, edges[1], edges[2], 0.0, z)
+    # IA (Eq. 2.15): -A_IA C_1 rho_crit Om / D(z) times the source n(z) dz/dchi of bin 2;
+    # the constants fold into one amplitude of the window, the 1/D into (1 + z)
+    ia = -0.05 * clustering_window(cosmo, chi, 0.9, 0.2, z) * (1.0 + z)
+    # CMB lensing: lens efficiency of one source plane at chi_* = chi(z = 1100), from a distance
+    # table that reaches that far
+    far = Cosmology(z_cap=1100.0)
+    chi_star = float(far.chi(1100.0))
+    zc = far.z_of_chi(np.minimum(chi, chi_star))
+    cmb = np.where(chi < chi_star,
+                   1.5 * far.omega_m / C_OVER_H0 ** 2 * chi * (1.0 + zc) * (1.0 - chi / chi_star), 0.0)
+    W = np.array([gal, gal, 0.4 * src, src, ia, clustering_window(cosmo, chi, 1.1, 0.15, z), cmb])
+    lk = np.log(knots / 0.1)
+    D = (1.0 / (1.0 + z))[None, :] * (1.0 + 0.02 * lk + 0.003 * lk ** 2)[:, None]
+    B = np.ones((len(kind), len(knots), N))
+    B[0] = (1.0 + 0.5 * z)[None, :]
+    # fNL (Eq. 2.12-2.13): b_1 + 3 fNL (b_1 - 1) delta_c Om (H0/c)^2 / (k^2 T(k) D(z)),
+    # fNL = 10, b_1 = 2, a smooth T(k)
+    b1 = 2.0
+    tk = 1.0 / (1.0 + (knots / 0.02) ** 2)
+    dfnl = 3.0 * 10.0 * (b1 - 1.0) * 1.686 * cosmo.omega_m / C_OVER_H0 ** 2
+    B[5] = b1 + dfnl * (1.0 / (knots ** 2 * tk))[:, None] * (1.0 + z)[None, :]
+    P = power_spectrum(k, 3.5e6 * rng.uniform(0.9, 1.1), 0.965)
+    amp = np.array([1.5, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0])
+    w = Workload("kinds", N, CHI_MIN, CHI_MAX, k, ells, knots, kind, fft_bias, W, D, B, P, amp,
+                 None, None, None)
+    return w
+
+
+def _term_scale(w, coef):
+    """S[l][i][q] = |pi_i(l)| k^{t_i - 1 - b_i} sum_n |c_{i,n}(k_q)| |M_l(p_n)| (the size of the
+    terms whose sum is Delta)."""
+    g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
+    S = np.zeros((len(w.ells), w.n_tr, len(w.k)))
+    for i in range(w.n_tr):
+        kind = int(w.kind[i])
+        ck = np.abs(g.lam @ coef[i])                                   # [N_k, N+1]
+        M = np.abs(g.mtable(w.fft_bias[i], w.ells, kind))              # [N_ell, N+1]
+        kf = w.k ** (O.k_power(kind) - 1.0 - w.fft_bias[i])
+        S[:, i, :] = (np.abs(O.ell_prefactor(w.ells, kind))[:, None] * (M @ ck.T) * kf[None, :])
+    return S
+
+
+def _kinds_ref():
+    w = _mixed_case()
+    rng = np.random.default_rng(5)
+    Cb = rng.standard_normal((len(w.ells), w.n_tr, w.n_tr))
+    f, grads = oracle_walker(w, C_bar=Cb)
+    S = _term_scale(w, f["coef"])
+    d = np.abs(f["delta"])
+    u = f["u"]
+    E = (np.einsum("liq,q,ljq->lij", S, u, d) + np.einsum("liq,q,ljq->lij", d, u, S))
+    E = E * w.amp[None, :, None] * w.amp[None, None, :]
+    return w, f, grads, Cb, S, E
+
+
+@pytest.fixture(scope="module")
+def kinds_ref():
+    return _kinds_ref()
+
+
+def _c_excess(C, Co, E, tol, tau):
+    """max over entries of |C - Co| / (tol max(|Co|, 1e-3 sqrt(Co_ii Co_jj)) + tau E); <= 1 passes."""
+    dg = np.abs(np.einsum("lii->li", Co))
+    floor = 1e-3 * np.sqrt(dg[:, :, None] * dg[:, None, :])
+    return float(np.max(np.abs(C - Co) / (tol * np.maximum(np.abs(Co), floor) + tau * E)))
+
+
+@pytest.mark.parametrize("prec,tol,tau,gtol", [("fp64", 1e-10, 1e-12, 1e-9),
+                                               ("bf16x9", 1e-4, 1e-6, 5e-5)])
+def test_mixed_kinds_against_oracle(prec, tol, tau, gtol, kinds_ref):
+    import paper_2505_22718_gb300 as S_
+    w, f, grads, Cb, S, E = kinds_ref
+    ctx = lib_context(w)
+    C = ctx.compute_cl(S_.PRECISIONS[prec])
+    assert np.all(np.isfinite(C))
+    assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
+    delta = S_.swcl_debug_read(ctx.ptr, S_.SWCL_DBG_DELTA).reshape(f["delta"].shape)
+    dx = np.abs(delta - f["delta"]) / (tol * np.abs(f["delta"]).max(axis=2, keepdims=True) + tau * S)
+    cx = _c_excess(C, f["C"], E, tol, tau)
+    g = ctx.vjp(Cb, S_.PRECISIONS[prec])
+    ge = [max_rel(a, b) for a, b in zip(g, grads[:3])]
+    print("kinds %s: Delta excess %.3g  C excess %.3g  Pbar %.2e  Abar %.2e  Wbar %.2e"
+          % (prec, dx.max(), cx, *ge))
+    assert dx.max() <= 1.0
+    assert cx <= 1.0
+    assert all(e < gtol for e in ge)
+
+
+def test_kind_prefactors_exact_on_device(kinds_ref):
+    """The Gamma-ratio tables of the new kinds on the device against the oracle's, entry by
+    entry: magnification l(l+1) M_l(p), RSD -p(p-1) M_l(p-2) (Eq. 2.9, 2.10)."""
+    import paper_2505_22718_gb300 as S_
+    w, f, *_ = kinds_ref
+    ctx = lib_context(w)
+    ctx.compute_cl(S_.SWCL_FP64)
+    gt = S_.swcl_debug_read(ctx.ptr, S_.SWCL_DBG_GTAB)
+    n_h = w.N // 2 + 1
+    gt = (gt[0::2] + 1j * gt[1::2]).reshape(-1, len(w.ells), n_h)
+    g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias)
+    wn = np.full(n_h, 2.0)
+    wn[0] = wn[-1] = 1.0
+    # classes are the distinct (kind, b) in first-appearance order
+    seen = []
+    for i in range(w.n_tr):
+        key = (int(w.kind[i]), float(w.fft_bias[i]))
+        if key in seen:
+            continue
+        seen.append(key)
+        kind, b = key
+        M = g.mtable(b, w.ells, kind)[:, n_h - 1:]                # n = 0..N/2
+        want = O.ell_prefactor(w.ells, kind)[:, None] * M * wn[None, :]
+        got = gt[len(seen) - 1]
+        assert np.max(np.abs(got - want) / np.abs(want)) < 1e-12, key
+
+
+def test_rsd_bias_range_is_checked(kinds_ref):
+    """An RSD tracer needs 1 - l_min < b < 1 (its moment is taken at b - 2); outside it the call
+    fails with SWCL_ERR_INVALID_ARG before any table is built."""
+    import paper_2505_22718_gb300 as S_
+    from paper_2505_22718_gb300 import Context
+    w, *_ = kinds_ref
+    ctx = Context(0, 0)
+    ctx.set_grids(w.chi_min, w.chi_max, w.N, w.k, w.ells, w.knots)
+    with pytest.raises(S_.SwiftClError):
+        ctx.set_tracers(np.array([O.KIND_RSD], np.int32), np.array([-1.2]), None, None)
+    with pytest.raises(S_.SwiftClError):
+        ctx.set_tracers(np.array([7], np.int32), np.array([-0.3]), None, None)
+    ctx.set_tracers(np.array([O.KIND_RSD], np.int32), np.array([0.4]), None, None)

@@ -231,7 +231,7 @@ class Workload:
     k: np.ndarray           # [N_k]
     ells: np.ndarray        # [N_ell] int32 (master list)
     knots: np.ndarray       # [N_I]
-    kind: np.ndarray        # [N_tr] int32 (0 density, 1 lensing)
+    kind: np.ndarray        # [N_tr] int32 (0 density, 1 lensing, 2 magnification, 3 RSD)
     fft_bias: np.ndarray    # [N_tr] FFTLog power-law bias b_i
     W: np.ndarray           # [N_tr][N] or [n_walk][N_tr][N]
     D: np.ndarray           # [N_I][N] growth at the knots on the chi grid
