@@ -8,6 +8,7 @@ library itself never does, and this package imports nothing from the library.
 Modules:
   fftlog   -- the method step by step (FFTLog coefficients, Gamma-ratio table,
               k-interpolation, contraction, k-quadrature, reverse mode).
+  forecast -- forward mode (JVP) and the Gaussian Fisher / chi^2 quadratic form (Sec. 4.3).
   brute    -- independent checks: spherical Bessel functions by recurrence,
               brute-force line-of-sight integrals, the Limber limit.
 """
