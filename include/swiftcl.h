@@ -158,6 +158,33 @@ int swcl_vjp(swcl_ctx* ctx, int precision, const double* C_bar,
 int swcl_compute_batched(swcl_ctx* ctx, int precision, double* C_out, const double* C_bar,
                          double* P_bar, double* amp_bar, double* W_bar);
 
+/* Forward-mode derivative (JVP) of a1-a4 at one parameter point (Sec. 4.3: the Fisher forecasts
+ * differentiate C_l along the parameters).  The context must hold one walker (n_walk = 1).  For
+ * n_dir tangents (1..256) of the inputs
+ *   P_dot[n_dir][N_k], amp_dot[n_dir][N_tr], W_dot[n_dir][N_tr][N]   (each may be NULL = zero),
+ * writes C_dot[n_dir][N_ell][N_tr][N_tr] (every multipole of the master list, full symmetric
+ * matrices): dC_ij = A_i A_j dU_ij + (A'_i A_j + A_i A'_j) U_ij with
+ * dU_ij = sum_q wk2_q [P'_q Delta_i Delta_j + P_q (Delta'_i Delta_j + Delta_i Delta'_j)] (Eq. 2.1
+ * by the product rule); Delta' is the contraction of the tangent windows, since Delta is linear
+ * in W (Eq. 3.1-3.5).  D and B are held fixed.  Host or device arrays; a host C_dot makes the call
+ * synchronous.  Runs the forward kernels over 1 + n_dir walkers, so it replaces the state of the
+ * last swcl_compute_cl: a following swcl_vjp needs a new swcl_compute_cl.  Errors:
+ * SWCL_ERR_UNSUPPORTED (n_walk != 1), SWCL_ERR_INVALID_ARG, SWCL_ERR_OOM_BUDGET. */
+int swcl_jvp(swcl_ctx* ctx, int precision, int n_dir, const double* P_dot, const double* amp_dot,
+             const double* W_dot, double* C_dot);
+
+/* Gaussian Fisher matrix / chi^2 of C_l perturbations (Sec. 4.2-4.3: Gaussian covariance with
+ * cosmic variance and additive noise, scaled by 1/f_sky).  With Ct_l = C_l + diag(noise) from the
+ * last swcl_compute_cl or swcl_jvp (one walker) and nu_l = modes[l] the number of modes behind
+ * C_l (e.g. (2l+1) f_sky times the bin width):
+ *   F[a][b] = sum_l (nu_l / 2) Tr[Ct_l^-1 X_a,l Ct_l^-1 X_b,l],   X[n_x][N_ell][N_tr][N_tr],
+ * which is the Fisher matrix of the Gaussian likelihood of the unique pairs C_l^{ij} when
+ * X_a = dC/dtheta_a (swcl_jvp output) and chi^2 when X = C - C_data.  noise[N_tr] (NULL = 0) and
+ * modes[N_ell] finite and >= 0; n_x in 1..1024; F[n_x][n_x] host or device.  Every Ct_l must be
+ * positive definite, else SWCL_ERR_INVALID_ARG.  Synchronous.  SWCL_ERR_STATE without a forward. */
+int swcl_gaussian_fisher(swcl_ctx* ctx, int n_x, const double* X, const double* noise,
+                         const double* modes, double* F);
+
 /* Per-kernel device timing.  While enabled, every kernel the context launches is bracketed by
  * CUDA events on the context stream (a few microseconds of overhead per launch).
  * swcl_profile_read synchronises the stream and returns, for up to max_entries kernels,

@@ -121,6 +121,28 @@ def swcl_vjp(ctx, precision, C_bar, P_bar=None, amp_bar=None, W_bar=None):
     _check(ctx, _lib.load().swcl_vjp(ctx, precision, pc, *outs))
 
 
+def swcl_jvp(ctx, precision, n_dir, C_dot, P_dot=None, amp_dot=None, W_dot=None):
+    """Forward-mode derivative of C along n_dir tangents (each input may be None = zero)."""
+    pc, keep = _ptr(C_dot, np.float64)
+    if keep is not C_dot:
+        raise TypeError("C_dot must be a contiguous float64 array or tensor (written in place)")
+    pp, _p = _ptr(P_dot, np.float64)
+    pa, _a = _ptr(amp_dot, np.float64)
+    pw, _w = _ptr(W_dot, np.float64)
+    _check(ctx, _lib.load().swcl_jvp(ctx, precision, n_dir, pp, pa, pw, pc))
+
+
+def swcl_gaussian_fisher(ctx, X, modes, F, noise=None):
+    """F[a][b] = sum_l (modes_l/2) Tr[Ct^-1 X_a Ct^-1 X_b] with Ct = C + diag(noise)."""
+    pf, keep = _ptr(F, np.float64)
+    if keep is not F:
+        raise TypeError("F must be a contiguous float64 array or tensor (written in place)")
+    px, a = _ptr(X, np.float64)
+    pm, _m = _ptr(modes, np.float64)
+    pn, _n = _ptr(noise, np.float64)
+    _check(ctx, _lib.load().swcl_gaussian_fisher(ctx, int(F.shape[0]), px, pn, pm, pf))
+
+
 def swcl_compute_batched(ctx, precision, C_out, C_bar=None, P_bar=None, amp_bar=None, W_bar=None):
     """Forward (+ VJP when C_bar is given) for all walkers as one CUDA-graph replay; device
     tensors only."""
@@ -266,6 +288,21 @@ class Context:
         W_bar = np.empty((self.n_walk, self.n_tr, self.N)) if want_W else None
         swcl_vjp(self.ptr, precision, C_bar, P_bar, amp_bar, W_bar)
         return P_bar, amp_bar, W_bar
+
+    def jvp(self, P_dot=None, amp_dot=None, W_dot=None, precision=SWCL_FP64):
+        """dC [n_dir][N_ell][N_tr][N_tr] along tangents P_dot [n_dir][N_k], amp_dot [n_dir][N_tr],
+        W_dot [n_dir][N_tr][N] (None = zero) at the context's single parameter point."""
+        n_dir = next(len(x) for x in (P_dot, amp_dot, W_dot) if x is not None)
+        out = np.empty((n_dir, self.n_ell, self.n_tr, self.n_tr))
+        swcl_jvp(self.ptr, precision, n_dir, out, P_dot, amp_dot, W_dot)
+        return out
+
+    def gaussian_fisher(self, X, modes, noise=None):
+        """Fisher matrix (X = dC/dtheta) or chi^2 (X = C - C_data) with the Gaussian covariance
+        of the last forward pass plus diagonal noise; modes[N_ell] = (2l+1) f_sky (bin width)."""
+        F = np.empty((len(X), len(X)))
+        swcl_gaussian_fisher(self.ptr, X, modes, F, noise)
+        return F
 
     def query(self, key):
         return swcl_query(self.ptr, key)

@@ -295,7 +295,8 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
-                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart};
+                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart,
+                    &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -358,6 +359,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
   c->knots_h = knh;
   c->ells_h = eh;
   c->last_fwd_precision = -1;
+  c->u_valid = false;
   SWCL_TRY(swcl::copy_in(c, c->d_k, kh.data(), sizeof(double) * N_k));
   SWCL_TRY(swcl::copy_in(c, c->d_knots, knh.data(), sizeof(double) * N_I));
   SWCL_TRY(swcl::copy_in(c, c->d_ells, eh.data(), sizeof(int) * N_ell));
@@ -425,6 +427,7 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->bt_ready = false;
   c->last_fwd_precision = -1;
+  c->u_valid = false;
   c->lr_dirty = true;
   c->lr_basis = false;
   c->N_tr = N_tr;
@@ -513,6 +516,7 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
   c->n_walk = n_walk;
   c->have_windows = true;
   c->last_fwd_precision = -1;
+  c->u_valid = false;
   if (c->ragged && (int)c->off_h.size() != n_walk + 1) c->ragged = false;
   return SWCL_OK;
 }
@@ -531,6 +535,7 @@ int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) 
   c->n_walk = n_walk;
   c->have_power = true;
   c->last_fwd_precision = -1;
+  c->u_valid = false;
   return SWCL_OK;
 }
 
@@ -716,6 +721,7 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
                                          N_ell, n_out, c->stream), "scale/pack");
   c->last_fwd_precision = precision;
+  c->u_valid = true;
   if (!dev_out) {
     SWCL_TRY(swcl::copy_out(c, C_out, dst, cbytes));
     SWCL_TRY(check_status(c));
@@ -890,6 +896,177 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
   }
   SWCL_TRY_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
   c->last_launches = c->graph_launches;
+  return SWCL_OK;
+}
+
+namespace {
+
+// c->n_walk is n for the lifetime of the scope: the JVP contracts the base walker and one walker
+// per tangent window with the ordinary forward kernels
+struct WalkScope {
+  swcl_ctx* c;
+  int old;
+  WalkScope(swcl_ctx* c_, int n) : c(c_), old(c_->n_walk) { c->n_walk = n; }
+  ~WalkScope() { c->n_walk = old; }
+};
+
+// bytes from a host or device array to a device address on the context stream; a host source
+// is waited for, so that the caller may reuse it on return
+int copy_to(swcl_ctx* c, void* dst, const void* src, size_t bytes, const char* what) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess && !swcl::is_device_ptr(src)) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? SWCL_OK : swcl::cuda_fail(c, e, what);
+}
+
+}  // namespace
+
+int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const double* amp_dot,
+             const double* W_dot, double* C_dot) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(check_ready(c, precision));
+  if (c->n_walk != 1)
+    return swcl::fail(c, SWCL_ERR_UNSUPPORTED,
+                      "the JVP is taken at one parameter point: set_windows with n_walk = 1");
+  if (n_dir < 1 || n_dir > 256 || !C_dot)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 1 <= n_dir <= 256 and C_dot");
+  if (c->lr_dirty) {
+    SWCL_TRY(swcl::factor_profiles(c));
+    c->lr_dirty = false;
+  }
+  c->last_launches = 0;
+  const swcl::Stencil sv = swcl::stencil(c);
+  const int N_tr = c->N_tr, N_I = sv.NI, n_h = c->n_h, N = c->N, N_k = c->N_k, N_ell = c->N_ell;
+  const bool fp64 = precision == SWCL_FP64;
+  const bool has_w = W_dot != nullptr;
+  const int nw2 = has_w ? 1 + n_dir : 1;
+  const size_t wrow = (size_t)N_tr * N, n2 = (size_t)N_tr * N_tr;
+  SWCL_TRY(swcl::ensure(c, c->ws_jin, sizeof(double) * (nw2 * wrow + (size_t)n_dir * (N_k + N_tr))));
+  double* jW = (double*)c->ws_jin.p;
+  double* jP = jW + nw2 * wrow;
+  double* jA = jP + (size_t)n_dir * N_k;
+  SWCL_TRY(copy_to(c, jW, c->d_W.p, sizeof(double) * wrow, "copy W"));
+  if (has_w) SWCL_TRY(copy_to(c, jW + wrow, W_dot, sizeof(double) * n_dir * wrow, "copy W_dot"));
+  if (P_dot) SWCL_TRY(copy_to(c, jP, P_dot, sizeof(double) * n_dir * N_k, "copy P_dot"));
+  else SWCL_TRY_CUDA(c, cudaMemsetAsync(jP, 0, sizeof(double) * n_dir * N_k, c->stream), "clear P_dot");
+  if (amp_dot) SWCL_TRY(copy_to(c, jA, amp_dot, sizeof(double) * n_dir * N_tr, "copy amp_dot"));
+  else SWCL_TRY_CUDA(c, cudaMemsetAsync(jA, 0, sizeof(double) * n_dir * N_tr, c->stream), "clear amp_dot");
+  SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * N_ell * n2));
+  SWCL_TRY(swcl::ensure(c, c->ws_dU, sizeof(double) * n_dir * N_ell * n2));
+  // the forward kernels see 1 + n_dir walkers: the base, then the tangent windows
+  c->last_fwd_precision = -1;
+  c->u_valid = false;
+  {
+    WalkScope scope(c, nw2);
+    const int n_lc = plan_ell_chunk(c, precision);
+    if (n_lc == 0)
+      return swcl::fail(c, SWCL_ERR_OOM_BUDGET, "memory budget too small for 8 multipoles of Delta");
+    SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nw2 * N_tr * N_I * n_h));
+    SWCL_TRY(swcl::ensure(c, c->ws_delta, (size_t)nw2 * N_tr * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
+    SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(1, N_tr, N_k, n_lc)));
+    if (fp64)
+      SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, jW, (const double*)c->d_chipow.p,
+                                             sv.D, sv.B, (const cplx*)c->d_psi.p,
+                                             (const cplx*)c->d_twiddle.p, nw2, N_tr, N_I, N,
+                                             c->stream), "fftlog");
+    else
+      SWCL_LAUNCH(c, swcl::launch_fftlog_fwd_df((float4*)c->ws_coef.p, jW, (const double*)c->d_chipow.p,
+                                                sv.D, sv.B, (const cplx*)c->d_psi.p,
+                                                (const cplx*)c->d_twiddle.p, nw2, N_tr, N_I, N,
+                                                c->stream), "fftlog");
+    for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
+      const int n_l = std::min(n_lc, N_ell - l_lo);
+      SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
+      // the base walker's U (first block of Delta), then the tangent pair sums
+      if (fp64) {
+        SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
+                                              (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
+                                              N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                              c->stream), "k-quadrature fp64");
+        SWCL_LAUNCH(c, swcl::launch_quad_jvp<double>((double*)c->ws_dU.p, (const double*)c->ws_delta.p,
+                                                     (const double*)c->d_P.p, jP,
+                                                     (const double*)c->d_wk2.p, has_w, n_dir, N_tr,
+                                                     N_k, N_ell, l_lo, n_l, c->stream), "jvp quadrature");
+      } else {
+        SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
+                                             (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
+                                             N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                             c->stream), "k-quadrature f32");
+        SWCL_LAUNCH(c, swcl::launch_quad_jvp<float>((double*)c->ws_dU.p, (const float*)c->ws_delta.p,
+                                                    (const double*)c->d_P.p, jP,
+                                                    (const double*)c->d_wk2.p, has_w, n_dir, N_tr,
+                                                    N_k, N_ell, l_lo, n_l, c->stream), "jvp quadrature");
+      }
+      ++c->last_launches;  // the pair-sum reduction of the base quadrature
+    }
+  }
+  const size_t cbytes = sizeof(double) * n_dir * N_ell * n2;
+  double* dst = C_dot;
+  const bool dev_out = swcl::is_device_ptr(C_dot);
+  if (!dev_out) {
+    SWCL_TRY(swcl::ensure(c, c->ws_jout, cbytes));
+    dst = (double*)c->ws_jout.p;
+  }
+  SWCL_LAUNCH(c, swcl::launch_jvp_combine(dst, (const double*)c->ws_dU.p, (const double*)c->ws_U.p,
+                                          (const double*)c->d_amp.p, jA, n_dir, N_tr, N_ell,
+                                          c->stream), "jvp combine");
+  c->u_valid = true;
+  if (!dev_out) {
+    SWCL_TRY(swcl::copy_out(c, C_dot, dst, cbytes));
+    SWCL_TRY(check_status(c));
+  }
+  return SWCL_OK;
+}
+
+int swcl_gaussian_fisher(swcl_ctx* c, int n_x, const double* X, const double* noise,
+                         const double* modes, double* F) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->u_valid || c->n_walk != 1)
+    return swcl::fail(c, SWCL_ERR_STATE,
+                      "call swcl_compute_cl or swcl_jvp at one parameter point (n_walk = 1) first");
+  if (n_x < 1 || n_x > 1024 || !X || !modes || !F)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need 1 <= n_x <= 1024, X, modes and F");
+  c->last_launches = 0;
+  const int N_tr = c->N_tr, N_ell = c->N_ell;
+  const size_t n2 = (size_t)N_tr * N_tr;
+  std::vector<double> small(N_tr + N_ell, 0.0);
+  if (noise)
+    SWCL_TRY_CUDA(c, cudaMemcpy(small.data(), noise, sizeof(double) * N_tr, cudaMemcpyDefault), "copy noise");
+  SWCL_TRY_CUDA(c, cudaMemcpy(small.data() + N_tr, modes, sizeof(double) * N_ell, cudaMemcpyDefault),
+                "copy modes");
+  for (int i = 0; i < N_tr + N_ell; ++i)
+    if (!(small[i] >= 0.0) || !std::isfinite(small[i]))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "noise and modes must be finite and >= 0");
+  const size_t fbytes = sizeof(double) * n_x * n_x;
+  SWCL_TRY(swcl::ensure(c, c->ws_fsmall, sizeof(double) * (N_tr + N_ell) + fbytes + 16));
+  double* d_noise = (double*)c->ws_fsmall.p;
+  double* d_modes = d_noise + N_tr;
+  double* d_F = d_modes + N_ell;
+  int* d_status = (int*)(d_F + (size_t)n_x * n_x);
+  SWCL_TRY(copy_to(c, d_noise, small.data(), sizeof(double) * (N_tr + N_ell), "copy noise, modes"));
+  const size_t xbytes = sizeof(double) * n_x * N_ell * n2;
+  const double* Xd = X;
+  if (!swcl::is_device_ptr(X)) {
+    SWCL_TRY(swcl::ensure(c, c->ws_jout, xbytes));
+    SWCL_TRY(copy_to(c, c->ws_jout.p, X, xbytes, "copy X"));
+    Xd = (const double*)c->ws_jout.p;
+  }
+  SWCL_TRY(swcl::ensure(c, c->ws_fz, xbytes));
+  SWCL_TRY_CUDA(c, cudaMemsetAsync(d_status, 0, sizeof(int), c->stream), "clear status");
+  SWCL_LAUNCH(c, swcl::launch_fisher(d_F, (double*)c->ws_fz.p, Xd, (const double*)c->ws_U.p,
+                                     (const double*)c->d_amp.p, noise ? d_noise : nullptr, d_modes,
+                                     d_status, n_x, N_tr, N_ell, c->stream), "fisher");
+  ++c->last_launches;  // whitening and Gram kernels
+  int bad = 0;
+  SWCL_TRY_CUDA(c, cudaMemcpyAsync(&bad, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                "read status");
+  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (bad)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C + noise is not positive definite at some multipole");
+  SWCL_TRY(swcl::copy_out(c, F, d_F, fbytes));
   return SWCL_OK;
 }
 

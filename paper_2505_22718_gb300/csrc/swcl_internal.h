@@ -136,6 +136,12 @@ struct swcl_ctx {
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
   swcl::DevBuf ws_qpart;     // forward: per-k-chunk partial pair sums of the k-quadrature
+  swcl::DevBuf ws_jin;       // JVP: windows [1 + n_dir][N_tr][N] (base first), P' [n_dir][N_k], A' [n_dir][N_tr]
+  swcl::DevBuf ws_dU;        // JVP: [n_dir][N_ell][N_tr][N_tr] tangent of U
+  swcl::DevBuf ws_jout;      // JVP output / Fisher input staging for host arrays
+  swcl::DevBuf ws_fz;        // Fisher: whitened perturbations [n_x][N_ell][N_tr][N_tr]
+  swcl::DevBuf ws_fsmall;    // Fisher: noise [N_tr], modes [N_ell], F [n_x][n_x], status
+  bool u_valid = false;      // ws_U holds U of walker 0 at the current inputs (n_walk = 1)
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
 
@@ -252,5 +258,18 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, c
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
                                int n_walk, int N_k, int N_ell, cudaStream_t s);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
+
+// forward mode and Fisher matrix (forecast.cu).  delta holds the base walker and then one
+// walker per tangent ([1 + n_dir][n_l][N_tr][N_k]; only the base when !has_w); Pdot [n_dir][N_k].
+template <typename T>
+cudaError_t launch_quad_jvp(double* dU, const T* delta, const double* P, const double* Pdot,
+                            const double* wk2, bool has_w, int n_dir, int N_tr, int N_k,
+                            int N_ell, int l_lo, int n_l, cudaStream_t s);
+cudaError_t launch_jvp_combine(double* Cdot, const double* dU, const double* U, const double* amp,
+                               const double* Adot, int n_dir, int N_tr, int N_ell, cudaStream_t s);
+// F [n_x][n_x] from X [n_x][N_ell][N_tr][N_tr], Ct = A A U + diag(noise); Z is scratch of X's size
+cudaError_t launch_fisher(double* F, double* Z, const double* X, const double* U,
+                          const double* amp, const double* noise, const double* modes,
+                          int* status, int n_x, int N_tr, int N_ell, cudaStream_t s);
 
 }  // namespace swcl
