@@ -9,6 +9,7 @@ Modules:
   fftlog   -- the method step by step (FFTLog coefficients, Gamma-ratio table,
               k-interpolation, contraction, k-quadrature, reverse mode).
   forecast -- forward mode (JVP) and the Gaussian Fisher / chi^2 quadratic form (Sec. 4.3).
+  limber   -- the Limber branch (Eq. 2.19) on the same grids, its reverse mode, the hybrid C_ell.
   brute    -- independent checks: spherical Bessel functions by recurrence,
               brute-force line-of-sight integrals, the Limber limit.
 """
