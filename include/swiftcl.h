@@ -136,7 +136,19 @@ int swcl_set_power(swcl_ctx* ctx, int n_walk, const double* P, const double* amp
  * every walker".  Outputs of compute/vjp are then packed walker after walker. */
 int swcl_set_ell_lists(swcl_ctx* ctx, const int* offsets, const int* ell_idx);
 
-/* Forward pass a1-a4 for every walker.  C_out[sum_w n_ell(w)][N_tr][N_tr] (full symmetric
+/* Limber branch (Eq. 2.19).  Multipoles l >= ell_switch of the master list (which must then be
+ * ascending) take the Limber form instead of the FFTLog path, in swcl_compute_cl, swcl_vjp and
+ * swcl_jvp (0 = off, the default):
+ *   C_ij(l) = A_i A_j sum_m (L/N) chi_m^-1 Pt(k_m) G_i G_j,   k_m = (l + 1/2)/chi_m,
+ *   G_i = pi_i(l) k_m^{t_i} chi_m^{s_i} W_i(chi_m) sum_a Lam_a(k_m) D_a(chi_m) B_ia(chi_m),
+ * on the FFTLog chi grid (rectangle rule in ln chi), Pt the 4-point Lagrange interpolant in ln k
+ * of P on the k grid (zero outside it), Lam the knot interpolation; tapers do not apply.  FP64
+ * arithmetic in every precision form.  Needs SWCL_FP64 or the basis-mode SWCL_SPLIT_BF16 form
+ * and no SWCL_RSD tracer (else the compute call returns SWCL_ERR_UNSUPPORTED).  The Limber error
+ * is O(1/l) (Eq. 2.19); the switch trades it for the FFTLog work of those multipoles. */
+int swcl_set_limber(swcl_ctx* ctx, int ell_switch);
+
+/* Forward pass a1-a4 for every walker./* Forward pass a1-a4 for every walker.  C_out[sum_w n_ell(w)][N_tr][N_tr] (full symmetric
  * matrices, C^{ij} = C^{ji} bit for bit). */
 int swcl_compute_cl(swcl_ctx* ctx, int precision, double* C_out);
 

@@ -107,6 +107,31 @@ def limber_vjp(g: O.Grids, W, D, P, amp, C_bar, B=None, ells=None):
     return P_bar, A_bar, W_bar
 
 
+def limber_jvp(g: O.Grids, W, D, P, amp, B=None, ells=None, P_dot=None, amp_dot=None, W_dot=None):
+    """Forward mode of limber_cl along one tangent (None = zero), by the product rule:
+    dU = sum_m c_m [Pt' G_i G_j + Pt (G'_i G_j + G_i G'_j)], G' = W' H (G is linear in W),
+    dC = A_i A_j dU + (A'_i A_j + A_i A'_j) U."""
+    ells = g.ells if ells is None else np.asarray(ells)
+    W = np.asarray(W, dtype=np.float64)
+    A = np.asarray(amp, dtype=np.float64)
+    Ad = np.zeros_like(A) if amp_dot is None else np.asarray(amp_dot, dtype=np.float64)
+    c = chi_weights(g)
+    out = np.empty((len(ells), len(A), len(A)))
+    for li, ell in enumerate(ells):
+        H, Rho = limber_parts(g, int(ell), W, D, B)
+        G = W * H
+        pw = c * (Rho @ np.asarray(P, dtype=np.float64))
+        U = (G * pw[None, :]) @ G.T
+        dU = np.zeros_like(U)
+        if P_dot is not None:
+            dU += (G * (c * (Rho @ np.asarray(P_dot, dtype=np.float64)))[None, :]) @ G.T
+        if W_dot is not None:
+            t = ((np.asarray(W_dot) * H) * pw[None, :]) @ G.T
+            dU += t + t.T
+        out[li] = dU * A[:, None] * A[None, :] + U * (Ad[:, None] * A[None, :] + A[:, None] * Ad[None, :])
+    return out
+
+
 def hybrid_forward(g: O.Grids, W, D, P, amp, ell_switch, B=None, taper_chi=None, taper_c=None):
     """C of the FFTLog path for l < ell_switch and of the Limber branch for l >= ell_switch."""
     f = O.forward(g, W, D, P, amp, B, taper_chi, taper_c)
@@ -128,3 +153,15 @@ def hybrid_vjp(g: O.Grids, fwd: dict, C_bar, W, D, P, amp, ell_switch, B=None, t
         Pl, Al, Wl = limber_vjp(g, W, D, P, amp, C_bar[sel], B, np.asarray(g.ells)[sel])
         Pb, Ab, Wb = Pb + Pl, Ab + Al, Wb + Wl
     return Pb, Ab, Wb
+
+
+def hybrid_jvp(g: O.Grids, fwd: dict, D, P, amp, ell_switch, B=None, taper_chi=None, taper_c=None,
+               P_dot=None, amp_dot=None, W_dot=None, W=None):
+    """Forward mode of hybrid_forward: oracle.forecast.jvp on the FFTLog rows, limber_jvp on the
+    Limber rows (W, the base windows, is needed by the latter)."""
+    from . import forecast as F
+    J = F.jvp(g, fwd, D, P, amp, B, taper_chi, taper_c, P_dot=P_dot, amp_dot=amp_dot, W_dot=W_dot)
+    sel = np.asarray(g.ells) >= ell_switch
+    if np.any(sel):
+        J[sel] = limber_jvp(g, W, D, P, amp, B, np.asarray(g.ells)[sel], P_dot, amp_dot, W_dot)
+    return J

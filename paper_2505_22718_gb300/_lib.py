@@ -26,6 +26,7 @@ SIGNATURES = {
     "swcl_set_ell_lists": (c_int, [c_void_p, c_void_p, c_void_p]),
     "swcl_compute_cl": (c_int, [c_void_p, c_int, c_void_p]),
     "swcl_vjp": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "swcl_set_limber": (c_int, [c_void_p, c_int]),
     "swcl_jvp": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "swcl_gaussian_fisher": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "swcl_sync": (c_int, [c_void_p]),

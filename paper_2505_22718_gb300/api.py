@@ -121,6 +121,11 @@ def swcl_vjp(ctx, precision, C_bar, P_bar=None, amp_bar=None, W_bar=None):
     _check(ctx, _lib.load().swcl_vjp(ctx, precision, pc, *outs))
 
 
+def swcl_set_limber(ctx, ell_switch):
+    """Multipoles >= ell_switch take the Limber branch (Eq. 2.19); 0 turns it off."""
+    _check(ctx, _lib.load().swcl_set_limber(ctx, int(ell_switch)))
+
+
 def swcl_jvp(ctx, precision, n_dir, C_dot, P_dot=None, amp_dot=None, W_dot=None):
     """Forward-mode derivative of C along n_dir tangents (each input may be None = zero)."""
     pc, keep = _ptr(C_dot, np.float64)
@@ -288,6 +293,9 @@ class Context:
         W_bar = np.empty((self.n_walk, self.n_tr, self.N)) if want_W else None
         swcl_vjp(self.ptr, precision, C_bar, P_bar, amp_bar, W_bar)
         return P_bar, amp_bar, W_bar
+
+    def set_limber(self, ell_switch):
+        swcl_set_limber(self.ptr, ell_switch)
 
     def jvp(self, P_dot=None, amp_dot=None, W_dot=None, precision=SWCL_FP64):
         """dC [n_dir][N_ell][N_tr][N_tr] along tangents P_dot [n_dir][N_k], amp_dot [n_dir][N_tr],

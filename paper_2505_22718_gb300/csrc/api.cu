@@ -253,7 +253,8 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   // (the fork and join are recorded into CUDA graphs as branches)
   if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_limber, cudaEventDisableTiming) != cudaSuccess) {
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return SWCL_ERR_CUDA;
@@ -296,7 +297,7 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
                     &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart,
-                    &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall};
+                    &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -311,6 +312,7 @@ int swcl_destroy(swcl_ctx* c) {
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_limber) cudaEventDestroy(c->ev_limber);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SWCL_OK;
@@ -658,6 +660,56 @@ static int contract_chunk(swcl_ctx* c, int precision, int l_lo, int n_l) {
   return swcl::compute_delta_tc(c, precision);
 }
 
+// The Limber rows of the master list (multipoles >= the switch, a suffix of the ascending list):
+// fills a and returns SWCL_OK; a.n_lim = 0 when the branch is off or no multipole reaches it.
+static int limber_plan(swcl_ctx* c, int precision, swcl::LimberArgs& a) {
+  a = swcl::LimberArgs();
+  a.l_first = c->N_ell;
+  if (c->limber_switch <= 0) return SWCL_OK;
+  int first = c->N_ell;
+  for (int i = 0; i < c->N_ell; ++i)
+    if (c->ells_h[i] >= c->limber_switch) { first = i; break; }
+  if (first == c->N_ell) return SWCL_OK;
+  for (int i = 1; i < c->N_ell; ++i)
+    if (c->ells_h[i] <= c->ells_h[i - 1])
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG, "the Limber branch needs an ascending multipole list");
+  for (int i = 0; i < c->N_tr; ++i)
+    if (c->kind_h[i] == SWCL_RSD)
+      return swcl::fail(c, SWCL_ERR_UNSUPPORTED, "RSD tracers have no Limber form");
+  if (precision != SWCL_FP64 && !use_basis_gemm(c, precision))
+    return swcl::fail(c, SWCL_ERR_UNSUPPORTED,
+                      "the Limber branch needs SWCL_FP64 or the basis-mode SWCL_SPLIT_BF16 form");
+  a.k = (const double*)c->d_k.p;
+  a.knots = (const double*)c->d_knots.p;
+  a.ells = (const int*)c->d_ells.p;
+  a.D = (const double*)c->d_D.p;
+  a.B = c->have_B ? (const double*)c->d_B.p : nullptr;
+  a.lnchi_min = std::log(c->chi_min);
+  a.L = c->L;
+  a.lnk_lo = std::log(c->k_h.front());
+  a.lnk_hi = std::log(c->k_h.back());
+  a.N = c->N;
+  a.N_k = c->N_k;
+  a.N_I = c->N_I;
+  a.N_tr = c->N_tr;
+  a.N_ell = c->N_ell;
+  a.l_first = first;
+  a.n_lim = c->N_ell - first;
+  for (int i = 0; i < c->N_tr; ++i) a.kind[i] = c->kind_h[i];
+  return SWCL_OK;
+}
+
+int swcl_set_limber(swcl_ctx* c, int ell_switch) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  c->err.clear();
+  if (ell_switch < 0) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell_switch must be >= 0");
+  c->limber_switch = ell_switch;
+  c->last_fwd_precision = -1;
+  c->u_valid = false;
+  ++c->alloc_gen;   // the captured graph of swcl_compute_batched has other kernels now
+  return SWCL_OK;
+}
+
 int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -692,8 +744,11 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                                (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
-  for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
-    const int n_l = std::min(n_lc, N_ell - l_lo);
+  swcl::LimberArgs lim;
+  SWCL_TRY(limber_plan(c, precision, lim));
+  const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
+  for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
+    const int n_l = std::min(n_lc, n_fft - l_lo);
     SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
@@ -707,6 +762,9 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                            c->stream), "k-quadrature f32");
     ++c->last_launches;  // the pair-sum reduction
   }
+  if (lim.n_lim > 0)
+    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, lim, (const double*)c->d_W.p,
+                                            (const double*)c->d_P.p, nw, c->stream), "limber");
   c->ell_chunk = n_lc;
   const int64_t n_out = out_count(c);
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
@@ -746,7 +804,12 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   const size_t nrow = (size_t)nw * N_tr;
   const bool fp64 = precision == SWCL_FP64;
   const int n_lc = c->ell_chunk;
-  const bool recompute = n_lc < N_ell;
+  swcl::LimberArgs lim;
+  SWCL_TRY(limber_plan(c, precision, lim));
+  const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
+  const bool recompute = n_lc < n_fft;
+  if (lim.n_lim > 0)
+    SWCL_TRY(swcl::ensure(c, c->ws_lq, sizeof(double) * (size_t)nw * lim.n_lim * N));
   // cotangent on the device
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
   const double* cb = C_bar;
@@ -779,8 +842,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
                                       (const double*)c->d_amp.p, nw, N_tr, N_ell, side),
               "amp_bar");
-  for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
-    const int n_l = std::min(n_lc, N_ell - l_lo);
+  for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
+    const int n_l = std::min(n_lc, n_fft - l_lo);
     const bool accumulate = l_lo > 0;
     if (recompute) SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
     if (fp64)
@@ -821,18 +884,32 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "fork");
   }
   SWCL_LAUNCH(c, swcl::launch_pbar_reduce(Pb, (const double*)c->ws_pbpart.p,
-                                          (const double*)c->d_wk2.p, nw, N_k, N_ell, side),
+                                          (const double*)c->d_wk2.p, nw, N_k, n_fft, side),
               "P_bar reduce");
+  double* Wb = nullptr;
   if (W_bar) {
-    double* Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
+    Wb = swcl::is_device_ptr(W_bar) ? W_bar : (double*)c->ws_outW.p;
     double* scratch = (double*)((char*)c->ws_outW.p + wbytes);
-    SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
-                                           (const double*)c->d_chipow.p, sv.D, sv.B,
-                                           (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
-                                           nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
-    if (!swcl::fftlog_adj_single_launch(nw, N_tr, N_I, N)) ++c->last_launches;  // chunk reduction
-    SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
+    if (n_fft > 0) {
+      SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
+                                             (const double*)c->d_chipow.p, sv.D, sv.B,
+                                             (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
+                                             nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
+      if (!swcl::fftlog_adj_single_launch(nw, N_tr, N_I, N)) ++c->last_launches;  // chunk reduction
+    } else {
+      SWCL_TRY_CUDA(c, cudaMemsetAsync(Wb, 0, wbytes, c->stream), "clear W_bar");
+    }
   }
+  if (lim.n_lim > 0) {
+    // W_bar (main stream, after the FFTLog adjoint) and P_bar (auxiliary stream, after its
+    // reduction) gain the Limber rows' terms
+    SWCL_LAUNCH(c, swcl::launch_limber_vjp(Wb, Pb, (double*)c->ws_lq.p, lim, (const double*)c->d_W.p,
+                                           (const double*)c->d_P.p, (const double*)c->ws_Cbar.p,
+                                           (const double*)c->d_amp.p, nw, c->stream, side,
+                                           c->ev_limber), "limber vjp");
+    ++c->last_launches;  // the P_bar gather
+  }
+  if (W_bar) SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
   if (fork) {
     // join: the main stream (and the caller's later work on it) sees the auxiliary kernels
     SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_join, c->aux), "join");
@@ -954,6 +1031,9 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
   else SWCL_TRY_CUDA(c, cudaMemsetAsync(jA, 0, sizeof(double) * n_dir * N_tr, c->stream), "clear amp_dot");
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * N_ell * n2));
   SWCL_TRY(swcl::ensure(c, c->ws_dU, sizeof(double) * n_dir * N_ell * n2));
+  swcl::LimberArgs lim;
+  SWCL_TRY(limber_plan(c, precision, lim));
+  const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
   // the forward kernels see 1 + n_dir walkers: the base, then the tangent windows
   c->last_fwd_precision = -1;
   c->u_valid = false;
@@ -975,8 +1055,8 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
                                                 sv.D, sv.B, (const cplx*)c->d_psi.p,
                                                 (const cplx*)c->d_twiddle.p, nw2, N_tr, N_I, N,
                                                 c->stream), "fftlog");
-    for (int l_lo = 0; l_lo < N_ell; l_lo += n_lc) {
-      const int n_l = std::min(n_lc, N_ell - l_lo);
+    for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
+      const int n_l = std::min(n_lc, n_fft - l_lo);
       SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
       // the base walker's U (first block of Delta), then the tangent pair sums
       if (fp64) {
@@ -1000,6 +1080,13 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
       }
       ++c->last_launches;  // the pair-sum reduction of the base quadrature
     }
+  }
+  if (lim.n_lim > 0) {
+    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, lim, jW, (const double*)c->d_P.p, 1,
+                                            c->stream), "limber");
+    SWCL_LAUNCH(c, swcl::launch_limber_jvp((double*)c->ws_dU.p, lim, jW, (const double*)c->d_P.p,
+                                           has_w ? jW + wrow : nullptr, jP, n_dir, c->stream),
+                "limber jvp");
   }
   const size_t cbytes = sizeof(double) * n_dir * N_ell * n2;
   double* dst = C_dot;

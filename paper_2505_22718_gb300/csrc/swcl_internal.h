@@ -51,6 +51,19 @@ struct Stencil {
   const double* B;      // per-tracer factor [N_tr][NI][N] or null
 };
 
+// Grids and tables of the Limber branch (limber.cu): multipoles l_first .. l_first + n_lim - 1 of
+// the master list.  D [N_I][N] and B [N_tr][N_I][N] are the knot profiles as given.
+struct LimberArgs {
+  const double* k = nullptr;
+  const double* knots = nullptr;
+  const int* ells = nullptr;
+  const double* D = nullptr;
+  const double* B = nullptr;
+  double lnchi_min = 0, L = 0, lnk_lo = 0, lnk_hi = 0;
+  int N = 0, N_k = 0, N_I = 0, N_tr = 0, N_ell = 0, l_first = 0, n_lim = 0;
+  int kind[64] = {};
+};
+
 }  // namespace swcl
 
 struct swcl_ctx {
@@ -142,6 +155,9 @@ struct swcl_ctx {
   swcl::DevBuf ws_fz;        // Fisher: whitened perturbations [n_x][N_ell][N_tr][N_tr]
   swcl::DevBuf ws_fsmall;    // Fisher: noise [N_tr], modes [N_ell], F [n_x][n_x], status
   bool u_valid = false;      // ws_U holds U of walker 0 at the current inputs (n_walk = 1)
+  int limber_switch = 0;     // multipoles >= this take the Limber branch (0 = none)
+  swcl::DevBuf ws_lq;        // Limber VJP: per-(walker, multipole, chi) weights of P_bar
+  cudaEvent_t ev_limber = nullptr;
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
 
@@ -258,6 +274,19 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, c
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
                                int n_walk, int N_k, int N_ell, cudaStream_t s);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
+
+// Limber branch (limber.cu): forward rows of U [n_walk][N_ell][N_tr][N_tr]; forward-mode rows of
+// dU [n_dir][N_ell] for the base walker W, P and tangents Wt [n_dir][N_tr][N] (may be null),
+// Pd [n_dir][N_k]; reverse mode adding into Wb (may be null) on s_main and into Pb on s_pbar
+// (after q_ready), with scratch Q [n_walk][n_lim][N].
+cudaError_t launch_limber_rows(double* U, const LimberArgs& a, const double* W, const double* P,
+                               int n_walk, cudaStream_t s);
+cudaError_t launch_limber_jvp(double* dU, const LimberArgs& a, const double* W, const double* P,
+                              const double* Wt, const double* Pd, int n_dir, cudaStream_t s);
+cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* Q, const LimberArgs& a,
+                              const double* W, const double* P, const double* Sfull,
+                              const double* amp, int n_walk, cudaStream_t s_main,
+                              cudaStream_t s_pbar, cudaEvent_t q_ready);
 
 // forward mode and Fisher matrix (forecast.cu).  delta holds the base walker and then one
 // walker per tangent ([1 + n_dir][n_l][N_tr][N_k]; only the base when !has_w); Pdot [n_dir][N_k].

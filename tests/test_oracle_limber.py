@@ -145,3 +145,25 @@ def test_rsd_has_no_limber_form():
     g = O.Grids(256, 1.0, 1e5, np.geomspace(1e-4, 1, 64), [10], [1e-4, 1.0], [O.KIND_RSD], [0.4])
     with pytest.raises(ValueError):
         LB.limber_cl(g, np.ones((1, 256)), np.ones((2, 256)), np.ones(64), [1.0])
+
+
+def test_limber_jvp_against_vjp_and_differences(wl):
+    """Forward mode of the Limber branch: central differences entry by entry, and
+    <C_bar, J v> = <J^T C_bar, v> with the pinned reverse mode."""
+    w, tr, g, Cb = _vjp_case(wl)
+    W, P, amp = w.W[tr], w.P, w.amp[tr]
+    rng = np.random.default_rng(12)
+    dP = rng.standard_normal(len(P)) * P
+    dA = rng.standard_normal(len(amp))
+    dW = rng.standard_normal(W.shape) * W
+    J = LB.limber_jvp(g, W, w.D, P, amp, P_dot=dP, amp_dot=dA, W_dot=dW)
+    h = 1e-5
+    fd = (LB.limber_cl(g, W + h * dW, w.D, P + h * dP, amp + h * dA)[1]
+          - LB.limber_cl(g, W - h * dW, w.D, P - h * dP, amp - h * dA)[1]) / (2 * h)
+    _, C = LB.limber_cl(g, W, w.D, P, amp)
+    dg = np.sqrt(np.abs(np.einsum("lii->li", C)))
+    assert np.max(np.abs(J - fd) / (dg[:, :, None] * dg[:, None, :])) < 1e-7
+    Pb, Ab, Wb = LB.limber_vjp(g, W, w.D, P, amp, Cb)
+    lhs = np.sum(Cb * J)
+    rhs = np.sum(Pb * dP) + np.sum(Ab * dA) + np.sum(Wb * dW)
+    assert abs(lhs - rhs) <= 1e-12 * abs(rhs)
