@@ -61,6 +61,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--sweep", default="none", choices=["none", "nell"],
+                    help="nell: time per evaluation against the number of multipoles (one JSON "
+                         "line per point and a linear fit), instead of the headline line")
+    ap.add_argument("--limber", type=int, default=0,
+                    help="Limber branch for multipoles >= this (0: off, the paper's setting)")
     return ap.parse_args()
 
 
@@ -275,6 +280,8 @@ def run_ours(args, rank, world, device):
     P_d, A_d = t(w.P), t(w.amp)
     ctx.set_windows(W_d, D_d, None if w.B is None else t(w.B))
     ctx.set_power(P_d, A_d)
+    if args.limber:
+        ctx.set_limber(args.limber)
     C_d = torch.empty((nw * len(w.ells), w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
     Cb_d = t(cbar.reshape(C_d.shape))
     Pb_d = torch.empty((nw, len(w.k)), dtype=torch.float64, device=dev)
@@ -411,6 +418,69 @@ def run_ours(args, rank, world, device):
     return out, w, cbar
 
 
+def run_sweep_nell(args, device):
+    """Forward and forward+VJP time per evaluation of the N5K-shaped workload for N_ell
+    log-spaced multipoles in [2, 2000] (the running-time study of Sec. 5 / Appendix A), one
+    CUDA-graph replay per step, L2 flushed before each timed step, CUDA events on the stream."""
+    import torch
+    import paper_2505_22718_gb300 as swcl
+    from workloads import make_workload, ell_list
+    torch.cuda.set_device(device)
+    dev = torch.device("cuda", device)
+    prec = swcl.PRECISIONS[args.precision]
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    steps = max(3, min(args.steps, 200))
+    pts = []
+    for n in (10, 30, 103, 300, 1000, 1999):
+        w = make_workload("n5k")
+        w.ells = ell_list(2, 2000, n)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+        ctx = swcl.Context(device, 0, stream.cuda_stream)
+        ctx.set_grids(w.chi_min, w.chi_max, w.N, w.k, w.ells, w.knots)
+        ctx.set_tracers(w.kind, w.fft_bias)
+        ctx.set_windows(t(w.W), t(w.D), None)
+        ctx.set_power(t(w.P), t(w.amp))
+        if args.limber:
+            ctx.set_limber(args.limber)
+        C = torch.empty((n, w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
+        Cb = torch.randn((n, w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
+        Pb = torch.empty((1, len(w.k)), dtype=torch.float64, device=dev)
+        Ab = torch.empty((1, w.n_tr), dtype=torch.float64, device=dev)
+        Wb = torch.empty((1, w.n_tr, w.N), dtype=torch.float64, device=dev)
+        res = {}
+        for name, fn in (("fwd", lambda: swcl.swcl_compute_batched(ctx.ptr, prec, C)),
+                         ("fwd_vjp", lambda: swcl.swcl_compute_batched(ctx.ptr, prec, C, Cb, Pb, Ab, Wb))):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize(dev)
+            tot = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            res[name] = tot / steps
+        ctx.close()
+        line = {"sweep": "n_ell", "n_ell": n, "ms_fwd": res["fwd"], "ms_fwd_vjp": res["fwd_vjp"],
+                "precision": args.precision, "limber_switch": args.limber, "steps": steps,
+                "workload": WORKLOAD}
+        print(json.dumps(line))
+        pts.append((n, res["fwd"], res["fwd_vjp"]))
+    a = np.array(pts)
+    fit = {}
+    for col, name in ((1, "fwd"), (2, "fwd_vjp")):
+        slope, icpt = np.polyfit(a[:, 0], a[:, col], 1)
+        fit[name] = {"ms_per_ell": slope, "ms_fixed": icpt}
+    print(json.dumps({"sweep": "n_ell", "fit_t_equals_a_nell_plus_b": fit, "precision": args.precision,
+                      "limber_switch": args.limber}))
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -443,6 +513,12 @@ def main():
         return 0
 
     import torch
+    if args.sweep == "nell":
+        if rank != 0:
+            return 0
+        import __graft_entry__
+        __graft_entry__.build()
+        return run_sweep_nell(args, local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
@@ -456,7 +532,7 @@ def main():
         acc = None
         if world == 1 and not args.no_cpu_baseline:
             cpu, f = cpu_baseline(w if n_walk(w) == 1 else w, cbar[:1] if cbar.ndim == 4 else cbar)
-            if n_walk(w) == 1:
+            if n_walk(w) == 1 and not args.limber:
                 Co = f["C"]
                 C0 = out["_C0"]
                 dg = np.abs(np.einsum("lii->li", Co))
@@ -475,7 +551,8 @@ def main():
                 "config": {"workload": WORKLOAD, "walkers_per_gpu": n_walk(w), "precision": args.precision,
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": "walkers sharded across ranks" if world > 1 else "1 GPU",
-                           "profile_rank": out.get("profile_rank"), "gemm_tiles": out.get("tiles")},
+                           "profile_rank": out.get("profile_rank"), "gemm_tiles": out.get("tiles"),
+                           "limber_switch": args.limber or None},
                 "roofline": out["roofline"], "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "clocks": out["clocks"], "gpu_launches": out["gpu_launches"],
                 "fwd_only": out["fwd_only"], "fp64_gpu_path": out.get("fp64_gpu_path"),

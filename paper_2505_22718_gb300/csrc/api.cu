@@ -297,7 +297,8 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
                     &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart,
-                    &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq};
+                    &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq,
+                    &c->ws_ltab};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -382,6 +383,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
                                            c->stream), "quad weights");
   SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "set_grids");
   c->have_grids = true;
+  c->lt_ready = false;
   return SWCL_OK;
 }
 
@@ -699,11 +701,26 @@ static int limber_plan(swcl_ctx* c, int precision, swcl::LimberArgs& a) {
   return SWCL_OK;
 }
 
+// The stencil table of the current grids and switch (built outside graph capture, once) and
+// scratch for n_rows walkers or tangents.
+static int limber_prepare(swcl_ctx* c, const swcl::LimberArgs& a, int n_rows, swcl::LimberTable& t) {
+  if (!c->lt_ready) {
+    if (c->capturing) return swcl::fail(c, SWCL_ERR_STATE, "Limber table built during capture");
+    SWCL_TRY(swcl::ensure(c, c->ws_ltab, swcl::limber_table_bytes(a)));
+    t = swcl::limber_table_view(c->ws_ltab.p, a);
+    SWCL_LAUNCH(c, swcl::launch_limber_table(t, a, c->stream), "limber table");
+    c->lt_ready = true;
+  }
+  t = swcl::limber_table_view(c->ws_ltab.p, a);
+  return swcl::ensure(c, c->ws_lq, swcl::limber_scratch_bytes(a, n_rows));
+}
+
 int swcl_set_limber(swcl_ctx* c, int ell_switch) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   c->err.clear();
   if (ell_switch < 0) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell_switch must be >= 0");
   c->limber_switch = ell_switch;
+  c->lt_ready = false;
   c->last_fwd_precision = -1;
   c->u_valid = false;
   ++c->alloc_gen;   // the captured graph of swcl_compute_batched has other kernels now
@@ -762,9 +779,14 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                            c->stream), "k-quadrature f32");
     ++c->last_launches;  // the pair-sum reduction
   }
-  if (lim.n_lim > 0)
-    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, lim, (const double*)c->d_W.p,
-                                            (const double*)c->d_P.p, nw, c->stream), "limber");
+  if (lim.n_lim > 0) {
+    swcl::LimberTable lt;
+    SWCL_TRY(limber_prepare(c, lim, nw, lt));
+    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt,
+                                            (const double*)c->d_W.p, (const double*)c->d_P.p, nw,
+                                            c->stream), "limber");
+    ++c->last_launches;  // the pair-sum reduction
+  }
   c->ell_chunk = n_lc;
   const int64_t n_out = out_count(c);
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
@@ -808,8 +830,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   SWCL_TRY(limber_plan(c, precision, lim));
   const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
   const bool recompute = n_lc < n_fft;
-  if (lim.n_lim > 0)
-    SWCL_TRY(swcl::ensure(c, c->ws_lq, sizeof(double) * (size_t)nw * lim.n_lim * N));
+  swcl::LimberTable lt;
+  if (lim.n_lim > 0) SWCL_TRY(limber_prepare(c, lim, nw, lt));
   // cotangent on the device
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
   const double* cb = C_bar;
@@ -903,11 +925,11 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   if (lim.n_lim > 0) {
     // W_bar (main stream, after the FFTLog adjoint) and P_bar (auxiliary stream, after its
     // reduction) gain the Limber rows' terms
-    SWCL_LAUNCH(c, swcl::launch_limber_vjp(Wb, Pb, (double*)c->ws_lq.p, lim, (const double*)c->d_W.p,
-                                           (const double*)c->d_P.p, (const double*)c->ws_Cbar.p,
-                                           (const double*)c->d_amp.p, nw, c->stream, side,
-                                           c->ev_limber), "limber vjp");
-    ++c->last_launches;  // the P_bar gather
+    SWCL_LAUNCH(c, swcl::launch_limber_vjp(Wb, Pb, (double*)c->ws_lq.p, lim, lt,
+                                           (const double*)c->d_W.p, (const double*)c->d_P.p,
+                                           (const double*)c->ws_Cbar.p, (const double*)c->d_amp.p,
+                                           nw, c->stream, side, c->ev_limber), "limber vjp");
+    c->last_launches += W_bar ? 3 : 2;  // W_bar reduction, P_bar gather and reduction
   }
   if (W_bar) SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
   if (fork) {
@@ -1082,11 +1104,14 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
     }
   }
   if (lim.n_lim > 0) {
-    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, lim, jW, (const double*)c->d_P.p, 1,
-                                            c->stream), "limber");
-    SWCL_LAUNCH(c, swcl::launch_limber_jvp((double*)c->ws_dU.p, lim, jW, (const double*)c->d_P.p,
-                                           has_w ? jW + wrow : nullptr, jP, n_dir, c->stream),
-                "limber jvp");
+    swcl::LimberTable lt;
+    SWCL_TRY(limber_prepare(c, lim, n_dir, lt));
+    SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt, jW,
+                                            (const double*)c->d_P.p, 1, c->stream), "limber");
+    SWCL_LAUNCH(c, swcl::launch_limber_jvp((double*)c->ws_dU.p, (double*)c->ws_lq.p, lim, lt, jW,
+                                           (const double*)c->d_P.p, has_w ? jW + wrow : nullptr, jP,
+                                           n_dir, c->stream), "limber jvp");
+    c->last_launches += 2;  // the pair-sum reductions
   }
   const size_t cbytes = sizeof(double) * n_dir * N_ell * n2;
   double* dst = C_dot;

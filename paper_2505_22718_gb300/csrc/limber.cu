@@ -4,15 +4,19 @@
 // on the FFTLog chi grid (rectangle rule in ln chi), with Pt the 4-point Lagrange interpolant in
 // ln k of P on the k grid (zero outside it) and Lam the knot weights of the same rule.  Every kind
 // that has a Limber form has s = t (density 0, lensing and magnification -2), so
-// k^t chi^s = nu^t.  All arithmetic is FP64: the branch costs N_lim N N_tr^2 operations, small
-// next to the FFTLog path it replaces.
+// k^t chi^s = nu^t.  All arithmetic is FP64.
 //
-// Kernels: the forward rows (one CTA per Limber multipole and walker, chi in tiles of 32 staged in
-// shared memory, one thread per tracer pair); the forward-mode rows (one CTA per multipole and
-// tangent); the reverse mode, in two steps: per chi tile and walker, W_bar += 2 c Pt H R summed
-// over the multipoles (R_i = sum_j T_ij G_j, T = S A A^T) and the per-(l, chi) weights
-// Q = c sum_i G_i R_i; then P_bar_q += sum_{l,m} rho_q(k_lm) Q_lm, gathered per k point in a fixed
-// order.
+// The stencils depend on the grids only: a table built once per grid (k_limber_table) holds, for
+// every Limber multipole and chi point, the first k point of the P stencil (-1 outside the k
+// range) with its weights times c_m, and the first knot with the knot weights.  Then:
+//  - forward rows: one CTA per (multipole, 256-point chi chunk, walker), chi tiles of 32 staged
+//    in shared memory, one thread per tracer pair (up to 9 pairs); partial pair sums per chunk are
+//    added in a fixed order by the k-quadrature's reduction;
+//  - forward-mode rows: the same kernel with the tangent windows and P';
+//  - reverse mode: one CTA per (chi tile, 8 multipoles, walker) forms R_i = sum_j T_ij G_j with
+//    T = S A A^T, the partial W_bar_i = 2 c Pt H_i R_i of its multipoles and Q = sum_i G_i R_i;
+//    the W_bar partials are added in order into W_bar; P_bar_q gathers sum rho_q c Q over the
+//    (l, m) whose stencil holds q, 32 multipoles per CTA, partials added in order.
 #include <algorithm>
 
 #include "swcl_internal.h"
@@ -21,16 +25,19 @@ namespace swcl {
 namespace {
 
 constexpr int LT = 256;   // threads
-constexpr int MT = 32;    // chi points per tile
+constexpr int MT = 32;    // chi points per staged tile
+constexpr int MC = 256;   // chi points per CTA of the forward rows
+constexpr int LCH = 8;    // multipoles per CTA of the reverse mode
+constexpr int PCH = 32;   // multipoles per CTA of the P_bar gather
 constexpr int MAXR = 9;   // tracer pairs per thread (64 tracers)
 
-// Stencil of R5 on a positive, increasing grid at ln-value x: returns the first row and writes the
-// s = min(4, n) Lagrange weights in ln(grid) (unused entries 0).
-__device__ int stencil_ln(const double* grid, int n, double x, double w[4]) {
+// Stencil of R5 at ln-value x on an increasing grid given by its logarithms: returns the first row
+// and writes the s = min(4, n) Lagrange weights (unused entries 0).
+__device__ int stencil_ln(const double* lng, int n, double x, double w[4]) {
   int lo = 0, hi = n;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (log(grid[mid]) <= x) lo = mid + 1; else hi = mid;
+    if (lng[mid] <= x) lo = mid + 1; else hi = mid;
   }
   const int s = n < 4 ? n : 4;
   int a = lo - 1;
@@ -38,14 +45,12 @@ __device__ int stencil_ln(const double* grid, int n, double x, double w[4]) {
   int start = a - 1;
   if (start > n - s) start = n - s;
   if (start < 0) start = 0;
-  double xs[4];
-  for (int r = 0; r < s; ++r) xs[r] = log(grid[start + r]);
   for (int r = 0; r < 4; ++r) {
     double v = 0.0;
     if (r < s) {
       v = 1.0;
       for (int t = 0; t < s; ++t)
-        if (t != r) v *= (x - xs[t]) / (xs[r] - xs[t]);
+        if (t != r) v *= (x - lng[start + t]) / (lng[start + r] - lng[start + t]);
     }
     w[r] = v;
   }
@@ -58,46 +63,69 @@ __device__ __forceinline__ double ell_pre(int kind, double l) {
   return 1.0;
 }
 
-// Per chi tile: pw[mm] = c_m Pt(k_m) (P of the walker; Pd, if given, the same with the tangent
-// in pwd), the knot stencil (st, lam) and cw[mm] = c_m.
-struct Tile {
-  double pw[MT], pwd[MT], cw[MT], lam[MT][4];
-  int st[MT];
-};
+__global__ void k_limber_lngrid(LimberTable t, LimberArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < a.N_k) t.lnk[e] = log(a.k[e]);
+  else if (e < a.N_k + a.N_I) t.lnknots[e - a.N_k] = log(a.knots[e - a.N_k]);
+  else if (e < a.N_k + a.N_I + a.n_lim)
+    t.lnnu[e - a.N_k - a.N_I] = log((double)a.ells[a.l_first + e - a.N_k - a.N_I] + 0.5);
+}
 
-__device__ void tile_weights(Tile& T, const LimberArgs& a, double lnnu, int m0, const double* P,
-                             const double* Pd) {
-  for (int mm = threadIdx.x; mm < MT; mm += blockDim.x) {
-    const int m = m0 + mm;
-    double pw = 0.0, pwd = 0.0, cw = 0.0, lam[4] = {0.0, 0.0, 0.0, 0.0};
-    int st = 0;
-    if (m < a.N) {
-      const double lnchi = a.lnchi_min + (double)m * a.L / (double)a.N;
-      const double lnk = lnnu - lnchi;
-      cw = (a.L / (double)a.N) * exp(-lnchi);
-      if (lnk >= a.lnk_lo && lnk <= a.lnk_hi) {
-        double w[4];
-        const int s = stencil_ln(a.k, a.N_k, lnk, w);
-        double p = 0.0, pd = 0.0;
-        for (int r = 0; r < 4; ++r) {
-          if (w[r] == 0.0) continue;
-          p += w[r] * P[s + r];
-          if (Pd) pd += w[r] * Pd[s + r];
-        }
-        pw = cw * p;
-        pwd = cw * pd;
-      }
-      st = stencil_ln(a.knots, a.N_I, lnk, lam);
-    }
-    T.pw[mm] = pw;
-    T.pwd[mm] = pwd;
-    T.cw[mm] = cw;
-    T.st[mm] = st;
-    for (int r = 0; r < 4; ++r) T.lam[mm][r] = lam[r];
+// one thread per (Limber multipole li, chi point m)
+__global__ void k_limber_table(LimberTable t, LimberArgs a) {
+  const long total = (long)a.n_lim * a.N;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int li = (int)(e / a.N), m = (int)(e - (long)li * a.N);
+    const double lnchi = a.lnchi_min + (double)m * a.L / (double)a.N;
+    const double lnk = t.lnnu[li] - lnchi;
+    const double c = (a.L / (double)a.N) * exp(-lnchi);
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    int pst = -1;
+    if (lnk >= a.lnk_lo && lnk <= a.lnk_hi) pst = stencil_ln(t.lnk, a.N_k, lnk, w);
+    t.pst[e] = pst;
+    for (int r = 0; r < 4; ++r) t.pw[e * 4 + r] = c * w[r];
+    double lam[4];
+    t.kst[e] = stencil_ln(t.lnknots, a.N_I, lnk, lam);
+    for (int r = 0; r < 4; ++r) t.kw[e * 4 + r] = lam[r];
   }
 }
 
-// H[i][mm] = pi_i(l) nu^{t_i} sum_r lam_r D_{st+r}(m) B_{i,st+r}(m)
+// Per chi tile of one multipole: pw[mm] = c_m Pt(k_m) (and pwd with the tangent P'), the knot
+// stencil (kst, kw).
+struct Tile {
+  double pw[MT], pwd[MT], kw[MT][4];
+  int kst[MT];
+};
+
+__device__ void tile_weights(Tile& T, const LimberArgs& a, const LimberTable& t, int li, int m0,
+                             const double* P, const double* Pd) {
+  for (int mm = threadIdx.x; mm < MT; mm += blockDim.x) {
+    const int m = m0 + mm;
+    double p = 0.0, pd = 0.0;
+    int kst = 0;
+    double kw[4] = {0.0, 0.0, 0.0, 0.0};
+    if (m < a.N) {
+      const size_t e = (size_t)li * a.N + m;
+      const int pst = t.pst[e];
+      if (pst >= 0) {
+        for (int r = 0; r < 4; ++r) {
+          const double wr = t.pw[e * 4 + r];
+          p = fma(wr, P[pst + r], p);
+          if (Pd) pd = fma(wr, Pd[pst + r], pd);
+        }
+      }
+      kst = t.kst[e];
+      for (int r = 0; r < 4; ++r) kw[r] = t.kw[e * 4 + r];
+    }
+    T.pw[mm] = p;
+    T.pwd[mm] = pd;
+    T.kst[mm] = kst;
+    for (int r = 0; r < 4; ++r) T.kw[mm][r] = kw[r];
+  }
+}
+
+// H[i][mm] = pi_i(l) nu^{t_i} sum_r kw_r D_{kst+r}(m) B_{i,kst+r}(m)
 __device__ void tile_h(double* H, const Tile& T, const LimberArgs& a, double l, int m0) {
   const double nu = l + 0.5;
   for (int e = threadIdx.x; e < a.N_tr * MT; e += blockDim.x) {
@@ -108,12 +136,12 @@ __device__ void tile_h(double* H, const Tile& T, const LimberArgs& a, double l, 
       const bool chi2 = kind == SWCL_LENSING || kind == SWCL_MAGNIFICATION;
       double db = 0.0;
       for (int r = 0; r < 4; ++r) {
-        const double lr = T.lam[mm][r];
+        const double lr = T.kw[mm][r];
         if (lr == 0.0) continue;
-        const int row = T.st[mm] + r;
+        const int row = T.kst[mm] + r;
         double v = a.D[(size_t)row * a.N + m];
         if (a.B) v *= a.B[((size_t)i * a.N_I + row) * a.N + m];
-        db += lr * v;
+        db = fma(lr, v, db);
       }
       h = ell_pre(kind, l) * (chi2 ? 1.0 / (nu * nu) : 1.0) * db;
     }
@@ -121,20 +149,20 @@ __device__ void tile_h(double* H, const Tile& T, const LimberArgs& a, double l, 
   }
 }
 
-// Forward (and forward-mode) rows.  Grid (n_lim, n_w): walker w of W (and, for the JVP, tangent
-// w: windows Wt + w, P' Pd + w N_k against the base walker 0).  Writes U[w][l_first + li].
+// Forward (and forward-mode) partial pair sums over one chi chunk.  Grid (n_lim, n_mc, n_w):
+// walker w of W (and, for the JVP, tangent w: windows Wt + w, P' Pd + w N_k against the base
+// walker 0).  part[w][li][mc][pair].
 template <bool JVP>
 __global__ void __launch_bounds__(LT)
-k_limber_rows(double* __restrict__ U, LimberArgs a, const double* __restrict__ W,
+k_limber_part(double* __restrict__ part, LimberArgs a, LimberTable t, const double* __restrict__ W,
               const double* __restrict__ P, const double* __restrict__ Wt,
-              const double* __restrict__ Pd) {
+              const double* __restrict__ Pd, int n_mc) {
   extern __shared__ double lsm[];
   double* G = lsm;                          // [N_tr][MT]
   double* Gt = lsm + a.N_tr * MT;           // [N_tr][MT] (JVP)
   __shared__ Tile T;
-  const int li = blockIdx.x, w = blockIdx.y;
+  const int li = blockIdx.x, mc = blockIdx.y, w = blockIdx.z;
   const double l = (double)a.ells[a.l_first + li];
-  const double lnnu = log(l + 0.5);
   const int n = a.N_tr, npair = n * (n + 1) / 2;
   const double* Ww = JVP ? W : W + (size_t)w * n * a.N;
   const double* Pw = JVP ? P : P + (size_t)w * a.N_k;
@@ -151,8 +179,9 @@ k_limber_rows(double* __restrict__ U, LimberArgs a, const double* __restrict__ W
     pi[r] = i;
     pj[r] = i + p;
   }
-  for (int m0 = 0; m0 < a.N; m0 += MT) {
-    tile_weights(T, a, lnnu, m0, Pw, Pdw);
+  const int m_end = min((mc + 1) * MC, a.N);
+  for (int m0 = mc * MC; m0 < m_end; m0 += MT) {
+    tile_weights(T, a, t, li, m0, Pw, Pdw);
     __syncthreads();
     tile_h(G, T, a, l, m0);
     __syncthreads();
@@ -182,24 +211,20 @@ k_limber_rows(double* __restrict__ U, LimberArgs a, const double* __restrict__ W
     }
     __syncthreads();
   }
-  double* out = U + ((size_t)w * a.N_ell + a.l_first + li) * n * n;
+  double* out = part + (((size_t)w * a.n_lim + li) * n_mc + mc) * npair;
 #pragma unroll
-  for (int r = 0; r < MAXR; ++r) {
-    if (threadIdx.x + r * LT < npair) {
-      out[pi[r] * n + pj[r]] = acc[r];
-      out[pj[r] * n + pi[r]] = acc[r];
-    }
-  }
+  for (int r = 0; r < MAXR; ++r)
+    if (threadIdx.x + r * LT < npair) out[threadIdx.x + r * LT] = acc[r];
 }
 
-// Reverse mode, first step.  Grid (chi tiles, n_walk).  For every Limber multipole:
-// T = S A A^T (S the symmetrised cotangent), R_i = sum_j T_ij G_j, W_bar_i += 2 c Pt H_i R_i
-// (accumulated in registers, added to Wb at the end when Wb is given) and
-// Q[w][li][m] = c_m sum_i G_i R_i.
+// Reverse mode, first step.  Grid (chi tiles, multipole chunks of LCH, n_walk).  For each
+// multipole of the chunk: T = S A A^T (S the symmetrised cotangent), R_i = sum_j T_ij G_j; the
+// chunk's W_bar partial 2 sum_l c Pt H_i R_i goes to Wpart[w][lc][i][m] (when has_wb) and
+// Q[w][li][m] = sum_i G_i R_i.
 __global__ void __launch_bounds__(LT)
-k_limber_vjp(double* __restrict__ Wb, double* __restrict__ Q, LimberArgs a,
+k_limber_vjp(double* __restrict__ Wpart, double* __restrict__ Q, LimberArgs a, LimberTable t,
              const double* __restrict__ W, const double* __restrict__ P,
-             const double* __restrict__ Sfull, const double* __restrict__ amp) {
+             const double* __restrict__ Sfull, const double* __restrict__ amp, int n_lc, int has_wb) {
   extern __shared__ double lsm[];
   const int n = a.N_tr;
   double* H = lsm;                      // [N_tr][MT]
@@ -207,21 +232,22 @@ k_limber_vjp(double* __restrict__ Wb, double* __restrict__ Q, LimberArgs a,
   double* GR = G + n * MT;              // [N_tr][MT]  G_i R_i
   double* Ts = GR + n * MT;             // [N_tr][N_tr]
   __shared__ Tile T;
-  const int m0 = blockIdx.x * MT, w = blockIdx.y;
+  const int m0 = blockIdx.x * MT, lc = blockIdx.y, w = blockIdx.z;
   const double* Ww = W + (size_t)w * n * a.N;
   const double* Aw = amp + (size_t)w * n;
   constexpr int PER = 64 * MT / LT;     // (i, mm) entries per thread
   double wb[PER];
 #pragma unroll
-  for (int t = 0; t < PER; ++t) wb[t] = 0.0;
-  for (int li = 0; li < a.n_lim; ++li) {
+  for (int u = 0; u < PER; ++u) wb[u] = 0.0;
+  const int li_end = min((lc + 1) * LCH, a.n_lim);
+  for (int li = lc * LCH; li < li_end; ++li) {
     const double l = (double)a.ells[a.l_first + li];
     const double* S = Sfull + ((size_t)w * a.N_ell + a.l_first + li) * n * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int i = e / n, j = e - i * n;
       Ts[e] = S[e] * Aw[i] * Aw[j];
     }
-    tile_weights(T, a, log(l + 0.5), m0, P + (size_t)w * a.N_k, nullptr);
+    tile_weights(T, a, t, li, m0, P + (size_t)w * a.N_k, nullptr);
     __syncthreads();
     tile_h(H, T, a, l, m0);
     __syncthreads();
@@ -231,13 +257,13 @@ k_limber_vjp(double* __restrict__ Wb, double* __restrict__ Q, LimberArgs a,
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int e = threadIdx.x + t * LT;
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * LT;
       if (e < n * MT) {
         const int i = e / MT, mm = e - i * MT;
         double r = 0.0;
         for (int j = 0; j < n; ++j) r = fma(Ts[i * n + j], G[j * MT + mm], r);
-        wb[t] = fma(2.0 * T.pw[mm] * H[e], r, wb[t]);
+        wb[u] = fma(2.0 * T.pw[mm] * H[e], r, wb[u]);
         GR[e] = G[e] * r;
       }
     }
@@ -247,92 +273,174 @@ k_limber_vjp(double* __restrict__ Wb, double* __restrict__ Q, LimberArgs a,
       if (m >= a.N) continue;
       double q = 0.0;
       for (int i = 0; i < n; ++i) q += GR[i * MT + mm];
-      Q[((size_t)w * a.n_lim + li) * a.N + m] = T.cw[mm] * q;
+      Q[((size_t)w * a.n_lim + li) * a.N + m] = q;
     }
     __syncthreads();
   }
-  if (!Wb) return;
+  if (!has_wb) return;
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int e = threadIdx.x + t * LT;
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * LT;
     if (e < n * MT) {
       const int i = e / MT, m = m0 + (e - i * MT);
-      if (m < a.N) Wb[((size_t)w * n + i) * a.N + m] += wb[t];
+      if (m < a.N) Wpart[(((size_t)w * n_lc + lc) * n + i) * a.N + m] = wb[u];
     }
   }
 }
 
-// Reverse mode, second step: P_bar[w][q] += sum_l sum_m rho_q(k_lm) Q[w][l][m], where rho_q is q's
-// weight in the stencil of k_lm.  The m whose stencil can hold q have k_lm within
-// [k_{q-3}, k_{q+3}]; each is checked against its exact stencil.  One thread per (q, w).
-__global__ void k_limber_pbar(double* __restrict__ Pb, const double* __restrict__ Q, LimberArgs a,
-                              int n_walk) {
-  const long total = (long)n_walk * a.N_k;
+// Wb[w][i][m] += sum_lc Wpart[w][lc][i][m] in order
+__global__ void k_limber_wreduce(double* __restrict__ Wb, const double* __restrict__ Wpart,
+                                 int n_walk, int N_tr, int N, int n_lc) {
+  const long per = (long)N_tr * N, total = (long)n_walk * per;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % a.N_k), w = (int)(e / a.N_k);
-    const double klo = log(a.k[q >= 3 ? q - 3 : 0]);
-    const double khi = log(a.k[q + 3 < a.N_k ? q + 3 : a.N_k - 1]);
-    const double dm = (double)a.N / a.L;
+    const long w = e / per, r = e - w * per;
+    const double* src = Wpart + (size_t)w * n_lc * per + r;
     double s = 0.0;
-    for (int li = 0; li < a.n_lim; ++li) {
-      const double lnnu = log((double)a.ells[a.l_first + li] + 0.5);
-      // ln k_m = lnnu - lnchi_min - m L/N, decreasing in m
-      int mlo = (int)floor((lnnu - a.lnchi_min - khi) * dm) - 1;
-      int mhi = (int)ceil((lnnu - a.lnchi_min - klo) * dm) + 1;
-      mlo = mlo < 0 ? 0 : mlo;
-      mhi = mhi > a.N - 1 ? a.N - 1 : mhi;
-      const double* Ql = Q + ((size_t)w * a.n_lim + li) * a.N;
-      for (int m = mlo; m <= mhi; ++m) {
-        const double lnk = lnnu - (a.lnchi_min + (double)m * a.L / (double)a.N);
-        if (!(lnk >= a.lnk_lo && lnk <= a.lnk_hi)) continue;
-        double wts[4];
-        const int st = stencil_ln(a.k, a.N_k, lnk, wts);
-        const int r = q - st;
-        if (r >= 0 && r < 4) s = fma(wts[r], Ql[m], s);
-      }
+    for (int c = 0; c < n_lc; ++c) s += src[(size_t)c * per];
+    Wb[e] += s;
+  }
+}
+
+// P_bar gather.  Grid (k blocks, multipole chunks of PCH, n_walk); thread q:
+// Ppart[w][pc][q] = sum over the chunk's l and the m whose P stencil holds q of
+// (c rho_q)(l, m) Q[w][l][m].  Those m have ln k_lm in [ln k_{q-3}, ln k_{q+3}]; each is checked
+// against the table.
+__global__ void k_limber_pbar(double* __restrict__ Ppart, const double* __restrict__ Q,
+                              LimberArgs a, LimberTable t, int n_pc) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, pc = blockIdx.y, w = blockIdx.z;
+  if (q >= a.N_k) return;
+  const double klo = t.lnk[q >= 3 ? q - 3 : 0];
+  const double khi = t.lnk[q + 3 < a.N_k ? q + 3 : a.N_k - 1];
+  const double dm = (double)a.N / a.L;
+  double s = 0.0;
+  const int li_end = min((pc + 1) * PCH, a.n_lim);
+  for (int li = pc * PCH; li < li_end; ++li) {
+    const double x0 = t.lnnu[li] - a.lnchi_min;   // ln k_m = x0 - m L / N
+    int mlo = (int)floor((x0 - khi) * dm) - 1;
+    int mhi = (int)ceil((x0 - klo) * dm) + 1;
+    mlo = mlo < 0 ? 0 : mlo;
+    mhi = mhi > a.N - 1 ? a.N - 1 : mhi;
+    const double* Ql = Q + ((size_t)w * a.n_lim + li) * a.N;
+    for (int m = mlo; m <= mhi; ++m) {
+      const size_t e = (size_t)li * a.N + m;
+      const int st = t.pst[e];
+      const int r = q - st;
+      if (st >= 0 && r >= 0 && r < 4) s = fma(t.pw[e * 4 + r], Ql[m], s);
     }
+  }
+  Ppart[((size_t)w * n_pc + pc) * a.N_k + q] = s;
+}
+
+// Pb[w][q] += sum_pc Ppart[w][pc][q] in order
+__global__ void k_limber_preduce(double* __restrict__ Pb, const double* __restrict__ Ppart,
+                                 int n_walk, int N_k, int n_pc) {
+  const long total = (long)n_walk * N_k;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long w = e / N_k, q = e - w * N_k;
+    double s = 0.0;
+    for (int c = 0; c < n_pc; ++c) s += Ppart[((size_t)w * n_pc + c) * N_k + q];
     Pb[e] += s;
   }
 }
 
+int n_mc(const LimberArgs& a) { return (a.N + MC - 1) / MC; }
+int n_lc(const LimberArgs& a) { return (a.n_lim + LCH - 1) / LCH; }
+int n_pc(const LimberArgs& a) { return (a.n_lim + PCH - 1) / PCH; }
+unsigned grid_of(long total) { return (unsigned)std::min<long>((total + 255) / 256, 152L * 8); }
+
 }  // namespace
 
-cudaError_t launch_limber_rows(double* U, const LimberArgs& a, const double* W, const double* P,
-                               int n_walk, cudaStream_t s) {
+size_t limber_table_bytes(const LimberArgs& a) {
+  const size_t nm = (size_t)a.n_lim * a.N;
+  return nm * (2 * sizeof(int) + 8 * sizeof(double)) + sizeof(double) * (a.N_k + a.N_I + a.n_lim) + 64;
+}
+
+LimberTable limber_table_view(void* base, const LimberArgs& a) {
+  const size_t nm = (size_t)a.n_lim * a.N;
+  LimberTable t;
+  double* d = static_cast<double*>(base);
+  t.pw = d;
+  t.kw = t.pw + nm * 4;
+  t.lnk = t.kw + nm * 4;
+  t.lnknots = t.lnk + a.N_k;
+  t.lnnu = t.lnknots + a.N_I;
+  t.pst = reinterpret_cast<int*>(t.lnnu + a.n_lim);
+  t.kst = t.pst + nm;
+  return t;
+}
+
+size_t limber_scratch_bytes(const LimberArgs& a, int n_rows) {
+  const size_t npair = (size_t)a.N_tr * (a.N_tr + 1) / 2;
+  const size_t part = (size_t)n_rows * a.n_lim * n_mc(a) * npair;
+  const size_t q = (size_t)n_rows * a.n_lim * a.N;
+  const size_t wp = (size_t)n_rows * n_lc(a) * a.N_tr * a.N;
+  const size_t pp = (size_t)n_rows * n_pc(a) * a.N_k;
+  return sizeof(double) * (part + q + wp + pp);
+}
+
+cudaError_t launch_limber_table(const LimberTable& t, const LimberArgs& a, cudaStream_t s) {
+  const int n0 = a.N_k + a.N_I + a.n_lim;
+  k_limber_lngrid<<<(n0 + 255) / 256, 256, 0, s>>>(t, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_limber_table<<<grid_of((long)a.n_lim * a.N), 256, 0, s>>>(t, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_limber_rows(double* U, double* scratch, const LimberArgs& a, const LimberTable& t,
+                               const double* W, const double* P, int n_walk, cudaStream_t s) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
   const size_t smem = sizeof(double) * a.N_tr * MT;
-  k_limber_rows<false><<<dim3(a.n_lim, n_walk), LT, smem, s>>>(U, a, W, P, nullptr, nullptr);
-  return cudaGetLastError();
+  k_limber_part<false><<<dim3(a.n_lim, n_mc(a), n_walk), LT, smem, s>>>(scratch, a, t, W, P, nullptr,
+                                                                         nullptr, n_mc(a));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pair_reduce(U, scratch, n_walk, a.N_tr, a.N_ell, a.l_first, a.n_lim, n_mc(a), s);
 }
 
-cudaError_t launch_limber_jvp(double* dU, const LimberArgs& a, const double* W, const double* P,
-                              const double* Wt, const double* Pd, int n_dir, cudaStream_t s) {
+cudaError_t launch_limber_jvp(double* dU, double* scratch, const LimberArgs& a, const LimberTable& t,
+                              const double* W, const double* P, const double* Wt, const double* Pd,
+                              int n_dir, cudaStream_t s) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
   const size_t smem = 2 * sizeof(double) * a.N_tr * MT;
-  k_limber_rows<true><<<dim3(a.n_lim, n_dir), LT, smem, s>>>(dU, a, W, P, Wt, Pd);
-  return cudaGetLastError();
+  k_limber_part<true><<<dim3(a.n_lim, n_mc(a), n_dir), LT, smem, s>>>(scratch, a, t, W, P, Wt, Pd,
+                                                                       n_mc(a));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pair_reduce(dU, scratch, n_dir, a.N_tr, a.N_ell, a.l_first, a.n_lim, n_mc(a), s);
 }
 
-cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* Q, const LimberArgs& a,
-                              const double* W, const double* P, const double* Sfull,
-                              const double* amp, int n_walk, cudaStream_t s_main,
-                              cudaStream_t s_pbar, cudaEvent_t q_ready) {
+cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const LimberArgs& a,
+                              const LimberTable& t, const double* W, const double* P,
+                              const double* Sfull, const double* amp, int n_walk,
+                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
+  const size_t npair = (size_t)a.N_tr * (a.N_tr + 1) / 2;
+  double* Q = scratch + (size_t)n_walk * a.n_lim * n_mc(a) * npair;   // after the forward partials
+  double* Wpart = Q + (size_t)n_walk * a.n_lim * a.N;
+  double* Ppart = Wpart + (size_t)n_walk * n_lc(a) * a.N_tr * a.N;
   const size_t smem = sizeof(double) * (3 * a.N_tr * MT + a.N_tr * a.N_tr);
   cudaError_t e = cudaFuncSetAttribute(k_limber_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles = (a.N + MT - 1) / MT;
-  k_limber_vjp<<<dim3(tiles, n_walk), LT, smem, s_main>>>(Wb, Q, a, W, P, Sfull, amp);
+  k_limber_vjp<<<dim3(tiles, n_lc(a), n_walk), LT, smem, s_main>>>(Wpart, Q, a, t, W, P, Sfull, amp,
+                                                                   n_lc(a), Wb ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (Wb) {
+    k_limber_wreduce<<<grid_of((long)n_walk * a.N_tr * a.N), 256, 0, s_main>>>(Wb, Wpart, n_walk,
+                                                                              a.N_tr, a.N, n_lc(a));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (s_pbar != s_main) {
     if ((e = cudaEventRecord(q_ready, s_main)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s_pbar, q_ready, 0)) != cudaSuccess) return e;
   }
-  const long total = (long)n_walk * a.N_k;
-  const int blocks = (int)std::min<long>((total + 127) / 128, 152L * 4);
-  k_limber_pbar<<<blocks, 128, 0, s_pbar>>>(Pb, Q, a, n_walk);
+  k_limber_pbar<<<dim3((a.N_k + 127) / 128, n_pc(a), n_walk), 128, 0, s_pbar>>>(Ppart, Q, a, t, n_pc(a));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_limber_preduce<<<grid_of((long)n_walk * a.N_k), 256, 0, s_pbar>>>(Pb, Ppart, n_walk, a.N_k, n_pc(a));
   return cudaGetLastError();
 }
 

@@ -288,6 +288,14 @@ size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l) {
   return sizeof(double) * (size_t)n_walk * n_l * ((N_k + KC - 1) / KC) * (N_tr * (N_tr + 1) / 2);
 }
 
+cudaError_t launch_pair_reduce(double* U, const double* part, int n_walk, int N_tr, int N_ell,
+                               int l_lo, int n_l, int n_chunk, cudaStream_t s) {
+  const long total = (long)n_walk * n_l * (N_tr * (N_tr + 1) / 2);
+  const int grid = (int)std::min<long>((total + 255) / 256, 152L * 8);
+  k_quad_reduce<<<grid, 256, 0, s>>>(U, part, N_tr, N_ell, l_lo, n_l, n_chunk, n_walk);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
                              double* scratch, cudaStream_t s) {

@@ -64,6 +64,19 @@ struct LimberArgs {
   int kind[64] = {};
 };
 
+// Per-(Limber multipole, chi point) stencils (limber.cu), built once per grid: first k point of
+// the P stencil (-1 outside the k range) with weights times (L/N)/chi, first knot with weights;
+// and the logarithms of the k grid, the knots and l + 1/2.
+struct LimberTable {
+  int* pst = nullptr;
+  int* kst = nullptr;
+  double* pw = nullptr;
+  double* kw = nullptr;
+  double* lnk = nullptr;
+  double* lnknots = nullptr;
+  double* lnnu = nullptr;
+};
+
 }  // namespace swcl
 
 struct swcl_ctx {
@@ -156,7 +169,9 @@ struct swcl_ctx {
   swcl::DevBuf ws_fsmall;    // Fisher: noise [N_tr], modes [N_ell], F [n_x][n_x], status
   bool u_valid = false;      // ws_U holds U of walker 0 at the current inputs (n_walk = 1)
   int limber_switch = 0;     // multipoles >= this take the Limber branch (0 = none)
-  swcl::DevBuf ws_lq;        // Limber VJP: per-(walker, multipole, chi) weights of P_bar
+  swcl::DevBuf ws_lq;        // Limber scratch: forward partial pair sums, VJP weights and partials
+  swcl::DevBuf ws_ltab;      // Limber stencil table (LimberTable)
+  bool lt_ready = false;     // ws_ltab matches the grids and the switch
   cudaEvent_t ev_limber = nullptr;
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
@@ -275,18 +290,27 @@ cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const doubl
                                int n_walk, int N_k, int N_ell, cudaStream_t s);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
 
-// Limber branch (limber.cu): forward rows of U [n_walk][N_ell][N_tr][N_tr]; forward-mode rows of
-// dU [n_dir][N_ell] for the base walker W, P and tangents Wt [n_dir][N_tr][N] (may be null),
-// Pd [n_dir][N_k]; reverse mode adding into Wb (may be null) on s_main and into Pb on s_pbar
-// (after q_ready), with scratch Q [n_walk][n_lim][N].
-cudaError_t launch_limber_rows(double* U, const LimberArgs& a, const double* W, const double* P,
-                               int n_walk, cudaStream_t s);
-cudaError_t launch_limber_jvp(double* dU, const LimberArgs& a, const double* W, const double* P,
-                              const double* Wt, const double* Pd, int n_dir, cudaStream_t s);
-cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* Q, const LimberArgs& a,
-                              const double* W, const double* P, const double* Sfull,
-                              const double* amp, int n_walk, cudaStream_t s_main,
-                              cudaStream_t s_pbar, cudaEvent_t q_ready);
+// Limber branch (limber.cu): the stencil table, then forward rows of U [n_walk][N_ell] (or, with
+// the tangents Wt [n_dir][N_tr][N] (may be null) and Pd [n_dir][N_k], forward-mode rows of dU
+// [n_dir][N_ell] for the base walker W, P), and the reverse mode adding into Wb (may be null) on
+// s_main and into Pb on s_pbar (after q_ready).  scratch: limber_scratch_bytes(a, rows).
+size_t limber_table_bytes(const LimberArgs& a);
+LimberTable limber_table_view(void* base, const LimberArgs& a);
+size_t limber_scratch_bytes(const LimberArgs& a, int n_rows);
+cudaError_t launch_limber_table(const LimberTable& t, const LimberArgs& a, cudaStream_t s);
+cudaError_t launch_limber_rows(double* U, double* scratch, const LimberArgs& a, const LimberTable& t,
+                               const double* W, const double* P, int n_walk, cudaStream_t s);
+cudaError_t launch_limber_jvp(double* dU, double* scratch, const LimberArgs& a, const LimberTable& t,
+                              const double* W, const double* P, const double* Wt, const double* Pd,
+                              int n_dir, cudaStream_t s);
+cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const LimberArgs& a,
+                              const LimberTable& t, const double* W, const double* P,
+                              const double* Sfull, const double* amp, int n_walk,
+                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready);
+// U[w][l_lo + ll][i][j] = U[..][j][i] = sum over n_chunk partial pair sums part[w][ll][chunk][pair]
+// (quad.cu)
+cudaError_t launch_pair_reduce(double* U, const double* part, int n_walk, int N_tr, int N_ell,
+                               int l_lo, int n_l, int n_chunk, cudaStream_t s);
 
 // forward mode and Fisher matrix (forecast.cu).  delta holds the base walker and then one
 // walker per tangent ([1 + n_dir][n_l][N_tr][N_k]; only the base when !has_w); Pdot [n_dir][N_k].

@@ -358,3 +358,48 @@ def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256, first_w
 
 
 WORKLOADS = ("tiny2", "n5k", "n5k_vjp", "walkers", "large")
+
+
+# ------------------------------------------------------- convergence study ----
+
+CONV_ELLS = np.array([2, 5, 12, 30, 80, 200, 500, 1200, 2000], dtype=np.int32)
+
+
+def conv_growth(k, z):
+    """Scale-dependent growth of the convergence study: (1+z)^-1 with a smooth 8 % suppression
+    above k ~ 0.1 h/Mpc that grows with 1 - a (a massive-neutrino-like step), so the
+    k-interpolation of Sec. 3.2 has something to resolve.  Broadcasts k against z."""
+    k = np.asarray(k, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    x = (k / 0.1) ** 2
+    return (1.0 - 0.08 * (1.0 - 1.0 / (1.0 + z)) * x / (1.0 + x)) / (1.0 + z)
+
+
+def convergence_case(N: int = 2048, n_interp: int = 150, n_k: int = 2048, knots=None):
+    """A reduced N5K-shaped case for the numerical-parameter study of Appendix A: a narrow and a
+    wide Gaussian clustering bin and one Smail lensing bin, the multipoles CONV_ELLS, k in
+    [1e-4, 10] h/Mpc.  N_FFT = N, N_interp = n_interp log-spaced knots (or the given knots),
+    N_k = n_k; D at the knots from conv_growth.  Returns (Workload, meta) where meta holds the
+    window parameters so a reference can rebuild the windows at any chi."""
+    cosmo = Cosmology(0.3)
+    L = np.log(CHI_MAX / CHI_MIN)
+    chi = CHI_MIN * np.exp(np.arange(N) * L / N)
+    z = cosmo.z_of_chi(chi)
+    k = np.geomspace(1e-4, 10.0, n_k)
+    knots = np.geomspace(1e-4, 10.0, n_interp) if knots is None else np.asarray(knots, dtype=np.float64)
+    gauss = [(0.5, 0.04), (1.0, 0.08)]
+    edges = smail_bin_edges(5)
+    lens_edges = [edges[2], edges[3]]
+    W = _windows(cosmo, chi, gauss, lens_edges)
+    kind = np.array([KIND_DENSITY, KIND_DENSITY, KIND_LENSING], dtype=np.int32)
+    # lensing bias -2.5: the lens efficiency grows like chi at small chi, so its FFTLog input
+    # W chi^{-2-b} is ~ chi^{-1-b}; with b = -1.5 it still holds 2.6 % of its peak at chi_min and
+    # jumps there to the (zero) value at chi_max of the periodic extension; b = -2.5 brings the
+    # jump to ~2e-5 of the peak
+    fft_bias = np.array([B_DENSITY, B_DENSITY, -2.5])
+    D = conv_growth(knots[:, None], z[None, :])
+    P = power_spectrum(k, 3.5e6)
+    amp = np.array([1.3, 1.6, 1.0])
+    meta = dict(omega_m=0.3, chi=chi, gauss=gauss, lens_edges=lens_edges)
+    return Workload("convergence", N, CHI_MIN, CHI_MAX, k, CONV_ELLS.copy(), knots, kind, fft_bias,
+                    W, D, None, P, amp, None, None, meta)
