@@ -21,6 +21,7 @@ namespace {
 
 constexpr int JT = 256;   // threads of the JVP quadrature
 constexpr int KJ = 32;    // k points staged per step
+constexpr int KJS = KJ + 1;  // shared row stride (rows of different tracers in different banks)
 constexpr int MAXR = 9;   // pairs per thread: ceil(64 * 65 / 2 / 256)
 
 // dU[t][l_lo + ll][i][j] for tangent t; delta [1 + n_w][n_l][N_tr][N_k] holds the base walker
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(JT)
 k_quad_jvp(double* __restrict__ dU, const T* __restrict__ delta, const double* __restrict__ P,
            const double* __restrict__ Pdot, const double* __restrict__ wk2, int has_w, int N_tr,
            int N_k, int N_ell, int l_lo, int n_l) {
-  __shared__ double D0[64 * KJ], Dt[64 * KJ], us[KJ], uds[KJ];
+  __shared__ double D0[64 * KJS], Dt[64 * KJS], us[KJ], uds[KJ];
   const int ll = blockIdx.x, t = blockIdx.y;
   const int npair = N_tr * (N_tr + 1) / 2;
   const T* d0 = delta + (size_t)ll * N_tr * N_k;
@@ -51,8 +52,8 @@ k_quad_jvp(double* __restrict__ dU, const T* __restrict__ delta, const double* _
   for (int q0 = 0; q0 < N_k; q0 += KJ) {
     for (int e = threadIdx.x; e < N_tr * KJ; e += JT) {
       const int i = e / KJ, qq = e - i * KJ, q = q0 + qq;
-      D0[e] = q < N_k ? (double)d0[(size_t)i * N_k + q] : 0.0;
-      Dt[e] = (has_w && q < N_k) ? (double)dt[(size_t)i * N_k + q] : 0.0;
+      D0[i * KJS + qq] = q < N_k ? (double)d0[(size_t)i * N_k + q] : 0.0;
+      Dt[i * KJS + qq] = (has_w && q < N_k) ? (double)dt[(size_t)i * N_k + q] : 0.0;
     }
     for (int e = threadIdx.x; e < KJ; e += JT) {
       const int q = q0 + e;
@@ -63,10 +64,10 @@ k_quad_jvp(double* __restrict__ dU, const T* __restrict__ delta, const double* _
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       if (threadIdx.x + r * JT < npair) {
-        const double* ai = D0 + pi[r] * KJ;
-        const double* aj = D0 + pj[r] * KJ;
-        const double* bi = Dt + pi[r] * KJ;
-        const double* bj = Dt + pj[r] * KJ;
+        const double* ai = D0 + pi[r] * KJS;
+        const double* aj = D0 + pj[r] * KJS;
+        const double* bi = Dt + pi[r] * KJS;
+        const double* bj = Dt + pj[r] * KJS;
         double s = acc[r];
         for (int qq = 0; qq < KJ; ++qq)
           s = fma(uds[qq], ai[qq] * aj[qq], fma(us[qq], fma(bi[qq], aj[qq], ai[qq] * bj[qq]), s));

@@ -26,6 +26,8 @@ namespace {
 
 constexpr int LT = 256;   // threads
 constexpr int MT = 32;    // chi points per staged tile
+constexpr int MTS = MT + 1;  // shared row stride of the per-tracer tiles (lanes of different
+                             // tracers at one chi point fall in different banks)
 constexpr int MC = 256;   // chi points per CTA of the forward rows
 constexpr int LCH = 8;    // multipoles per CTA of the reverse mode
 constexpr int PCH = 32;   // multipoles per CTA of the P_bar gather
@@ -145,7 +147,7 @@ __device__ void tile_h(double* H, const Tile& T, const LimberArgs& a, double l, 
       }
       h = ell_pre(kind, l) * (chi2 ? 1.0 / (nu * nu) : 1.0) * db;
     }
-    H[e] = h;
+    H[i * MTS + mm] = h;
   }
 }
 
@@ -158,8 +160,8 @@ k_limber_part(double* __restrict__ part, LimberArgs a, LimberTable t, const doub
               const double* __restrict__ P, const double* __restrict__ Wt,
               const double* __restrict__ Pd, int n_mc) {
   extern __shared__ double lsm[];
-  double* G = lsm;                          // [N_tr][MT]
-  double* Gt = lsm + a.N_tr * MT;           // [N_tr][MT] (JVP)
+  double* G = lsm;                          // [N_tr][MTS]
+  double* Gt = lsm + a.N_tr * MTS;          // [N_tr][MTS] (JVP)
   __shared__ Tile T;
   const int li = blockIdx.x, mc = blockIdx.y, w = blockIdx.z;
   const double l = (double)a.ells[a.l_first + li];
@@ -186,21 +188,21 @@ k_limber_part(double* __restrict__ part, LimberArgs a, LimberTable t, const doub
     tile_h(G, T, a, l, m0);
     __syncthreads();
     for (int e = threadIdx.x; e < n * MT; e += blockDim.x) {
-      const int i = e / MT, m = m0 + (e - i * MT);
-      const double h = G[e];
-      G[e] = m < a.N ? h * Ww[(size_t)i * a.N + m] : 0.0;
-      if (JVP) Gt[e] = Wtw && m < a.N ? h * Wtw[(size_t)i * a.N + m] : 0.0;
+      const int i = e / MT, mm = e - i * MT, m = m0 + mm, x = i * MTS + mm;
+      const double h = G[x];
+      G[x] = m < a.N ? h * Ww[(size_t)i * a.N + m] : 0.0;
+      if (JVP) Gt[x] = Wtw && m < a.N ? h * Wtw[(size_t)i * a.N + m] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       if (threadIdx.x + r * LT < npair) {
-        const double* gi = G + pi[r] * MT;
-        const double* gj = G + pj[r] * MT;
+        const double* gi = G + pi[r] * MTS;
+        const double* gj = G + pj[r] * MTS;
         double s = acc[r];
         if (JVP) {
-          const double* ti = Gt + pi[r] * MT;
-          const double* tj = Gt + pj[r] * MT;
+          const double* ti = Gt + pi[r] * MTS;
+          const double* tj = Gt + pj[r] * MTS;
           for (int mm = 0; mm < MT; ++mm)
             s = fma(T.pwd[mm], gi[mm] * gj[mm], fma(T.pw[mm], fma(ti[mm], gj[mm], gi[mm] * tj[mm]), s));
         } else {
@@ -227,10 +229,10 @@ k_limber_vjp(double* __restrict__ Wpart, double* __restrict__ Q, LimberArgs a, L
              const double* __restrict__ Sfull, const double* __restrict__ amp, int n_lc, int has_wb) {
   extern __shared__ double lsm[];
   const int n = a.N_tr;
-  double* H = lsm;                      // [N_tr][MT]
-  double* G = H + n * MT;               // [N_tr][MT]
-  double* GR = G + n * MT;              // [N_tr][MT]  G_i R_i
-  double* Ts = GR + n * MT;             // [N_tr][N_tr]
+  double* H = lsm;                      // [N_tr][MTS]
+  double* G = H + n * MTS;              // [N_tr][MTS]
+  double* GR = G + n * MTS;             // [N_tr][MTS]  G_i R_i
+  double* Ts = GR + n * MTS;            // [N_tr][N_tr]
   __shared__ Tile T;
   const int m0 = blockIdx.x * MT, lc = blockIdx.y, w = blockIdx.z;
   const double* Ww = W + (size_t)w * n * a.N;
@@ -252,19 +254,19 @@ k_limber_vjp(double* __restrict__ Wpart, double* __restrict__ Q, LimberArgs a, L
     tile_h(H, T, a, l, m0);
     __syncthreads();
     for (int e = threadIdx.x; e < n * MT; e += blockDim.x) {
-      const int i = e / MT, m = m0 + (e - i * MT);
-      G[e] = m < a.N ? H[e] * Ww[(size_t)i * a.N + m] : 0.0;
+      const int i = e / MT, mm = e - i * MT, m = m0 + mm, x = i * MTS + mm;
+      G[x] = m < a.N ? H[x] * Ww[(size_t)i * a.N + m] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = threadIdx.x + u * LT;
       if (e < n * MT) {
-        const int i = e / MT, mm = e - i * MT;
+        const int i = e / MT, mm = e - i * MT, x = i * MTS + mm;
         double r = 0.0;
-        for (int j = 0; j < n; ++j) r = fma(Ts[i * n + j], G[j * MT + mm], r);
-        wb[u] = fma(2.0 * T.pw[mm] * H[e], r, wb[u]);
-        GR[e] = G[e] * r;
+        for (int j = 0; j < n; ++j) r = fma(Ts[i * n + j], G[j * MTS + mm], r);
+        wb[u] = fma(2.0 * T.pw[mm] * H[x], r, wb[u]);
+        GR[x] = G[x] * r;
       }
     }
     __syncthreads();
@@ -272,7 +274,7 @@ k_limber_vjp(double* __restrict__ Wpart, double* __restrict__ Q, LimberArgs a, L
       const int m = m0 + mm;
       if (m >= a.N) continue;
       double q = 0.0;
-      for (int i = 0; i < n; ++i) q += GR[i * MT + mm];
+      for (int i = 0; i < n; ++i) q += GR[i * MTS + mm];
       Q[((size_t)w * a.n_lim + li) * a.N + m] = q;
     }
     __syncthreads();
@@ -392,7 +394,7 @@ cudaError_t launch_limber_table(const LimberTable& t, const LimberArgs& a, cudaS
 cudaError_t launch_limber_rows(double* U, double* scratch, const LimberArgs& a, const LimberTable& t,
                                const double* W, const double* P, int n_walk, cudaStream_t s) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(double) * a.N_tr * MT;
+  const size_t smem = sizeof(double) * a.N_tr * MTS;
   k_limber_part<false><<<dim3(a.n_lim, n_mc(a), n_walk), LT, smem, s>>>(scratch, a, t, W, P, nullptr,
                                                                          nullptr, n_mc(a));
   cudaError_t e = cudaGetLastError();
@@ -404,7 +406,7 @@ cudaError_t launch_limber_jvp(double* dU, double* scratch, const LimberArgs& a, 
                               const double* W, const double* P, const double* Wt, const double* Pd,
                               int n_dir, cudaStream_t s) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
-  const size_t smem = 2 * sizeof(double) * a.N_tr * MT;
+  const size_t smem = 2 * sizeof(double) * a.N_tr * MTS;
   k_limber_part<true><<<dim3(a.n_lim, n_mc(a), n_dir), LT, smem, s>>>(scratch, a, t, W, P, Wt, Pd,
                                                                        n_mc(a));
   cudaError_t e = cudaGetLastError();
@@ -421,7 +423,7 @@ cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const Lim
   double* Q = scratch + (size_t)n_walk * a.n_lim * n_mc(a) * npair;   // after the forward partials
   double* Wpart = Q + (size_t)n_walk * a.n_lim * a.N;
   double* Ppart = Wpart + (size_t)n_walk * n_lc(a) * a.N_tr * a.N;
-  const size_t smem = sizeof(double) * (3 * a.N_tr * MT + a.N_tr * a.N_tr);
+  const size_t smem = sizeof(double) * (3 * a.N_tr * MTS + a.N_tr * a.N_tr);
   cudaError_t e = cudaFuncSetAttribute(k_limber_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

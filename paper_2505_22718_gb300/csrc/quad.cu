@@ -20,6 +20,8 @@ namespace {
 
 constexpr int QT = 256;    // threads
 constexpr int KC = 256;    // k points per CTA (one partial sum per pair and chunk)
+constexpr int KS = KC + 1; // shared row stride: lanes reading rows j at the same k point fall in
+                           // different banks
 
 // Partial pair sums over one chunk of KC k points: part[w][l - l_lo][kc][p] for unordered pairs
 // p = (i <= j).  Grid (multipole, k chunk, walker).  Thread t handles pair p = t % npair for the
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(QT)
 k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double* __restrict__ P,
             const double* __restrict__ wk2, int N_tr, int N_k, int n_l, int n_kc) {
   extern __shared__ double qsm[];
-  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][KC]
+  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][KS]
   __shared__ double us[KC];
   __shared__ float usf[KC];
   __shared__ double red[QT];
@@ -40,7 +42,7 @@ k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double
   const T* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
   for (int e = threadIdx.x; e < N_tr * KC; e += QT) {
     const int t = e / KC, qq = e - t * KC, q = q0 + qq;
-    Ds[e] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
+    Ds[t * KS + qq] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
   }
   for (int e = threadIdx.x; e < KC; e += QT) {
     const int q = q0 + e;
@@ -59,8 +61,8 @@ k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double
       int r = p, i = 0;                           // unordered pair index -> (i <= j)
       while (r >= N_tr - i) { r -= N_tr - i; ++i; }
       const int j = i + r;
-      const T* di = Ds + i * KC;
-      const T* dj = Ds + j * KC;
+      const T* di = Ds + i * KS;
+      const T* dj = Ds + j * KS;
       if (sizeof(T) == 4) {
         // FP32 products, compensated FP32 sums of 32 points, FP64 across the sums
         for (int c0 = group * 32; c0 < KC; c0 += ngroups * 32) {
@@ -218,6 +220,7 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   T* S = reinterpret_cast<T*>(dsm_raw);            // [LC][N_tr][N_tr]  S_ij A_j
   T* Dl = S + LC * N_tr * N_tr;                    // [N_tr][DT]
+  T* As = Dl + N_tr * DT;                          // [N_tr] A_i
   const int w = blockIdx.z;
   // Delta and Dbar hold multipoles [l_lo, l_lo + n_l) (l_lo a multiple of LC); Cf all N_ell
   const int lc = l_lo / LC + blockIdx.y;
@@ -229,11 +232,13 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
     const int ll = e / (N_tr * N_tr), r = e - ll * N_tr * N_tr;
     S[e] = (T)(Cf[((size_t)w * N_ell + l0 + ll) * N_tr * N_tr + r] * A[r % N_tr]);
   }
+  for (int e = threadIdx.x; e < N_tr; e += DT) As[e] = (T)A[e];
   const T two_u = (q < N_k) ? (T)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : T(0);
   T ps = 0, pc = 0;
   for (int ll = 0; ll < nl; ++ll) {
     __syncthreads();
     const T* dl = delta + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
+#pragma unroll 8
     for (int t = 0; t < N_tr; ++t)
       Dl[t * DT + threadIdx.x] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
     __syncthreads();
@@ -243,7 +248,7 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
       for (int ii = 0; ii < N_tr; ++ii) {
         T t = 0;
         for (int j = 0; j < N_tr; ++j) t = fma(Sl[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
-        const T ai = (T)A[ii];
+        const T ai = As[ii];
         two_sum_acc(ps, pc, ai * Dl[ii * DT + threadIdx.x] * t);
         db[(size_t)ii * N_k + q] = two_u * ai * t;
       }
@@ -267,7 +272,7 @@ template <typename T>
 cudaError_t launch_quad(double* U, const T* delta, const double* P, const double* wk2, int n_walk,
                         int N_tr, int N_k, int N_ell, int l_lo, int n_l, double* scratch,
                         cudaStream_t s) {
-  size_t smem = (size_t)N_tr * KC * sizeof(T);
+  size_t smem = (size_t)N_tr * KS * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_quad_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -335,7 +340,7 @@ template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s) {
-  const size_t smem = (size_t)(LC * N_tr * N_tr + N_tr * DT) * sizeof(T);
+  const size_t smem = (size_t)(LC * N_tr * N_tr + N_tr * DT + N_tr) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
