@@ -8,9 +8,9 @@
 // The unit-amplitude spectra U are formed in two passes: partial sums of each unordered pair
 // (i <= j) over chunks of 256 k points (one CTA per multipole and chunk), then the chunks added in
 // a fixed order and written to both (i,j) and (j,i), so C is symmetric bit for bit and the same
-// from run to run.  Delta in FP32 (mixed paths): the products are FP32, the partial sums over 32
-// k points are compensated FP32 sums (TwoSum; the rounding of each addition is carried in a
-// second float), and everything above them is FP64.
+// from run to run.  Delta in FP32 (mixed paths): the products are FP32, each thread's share of a
+// chunk is one compensated FP32 sum (TwoSum; the rounding of each addition is carried in a
+// second float), and everything above it is FP64.
 #include <algorithm>
 
 #include "swcl_internal.h"
@@ -64,9 +64,11 @@ k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double
       const T* di = Ds + i * KS;
       const T* dj = Ds + j * KS;
       if (sizeof(T) == 4) {
-        // FP32 products, compensated FP32 sums of 32 points, FP64 across the sums
+        // FP32 products in one compensated FP32 sum (the rounding error of each addition,
+        // from TwoSum, carried in a second float), widened to FP64 once: GB300 runs FP64 at a
+        // small fraction of its FP32 rate
+        float sum = 0.0f, comp = 0.0f;
         for (int c0 = group * 32; c0 < KC; c0 += ngroups * 32) {
-          float sum = 0.0f, comp = 0.0f;
 #pragma unroll 8
           for (int qq = c0; qq < c0 + 32; ++qq) {
             const float t = ((float)di[qq] * usf[qq]) * (float)dj[qq];
@@ -75,8 +77,8 @@ k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double
             comp += (sum - (sn - bp)) + (t - bp);
             sum = sn;
           }
-          acc += (double)sum + (double)comp;
         }
+        acc = (double)sum + (double)comp;
       } else {
         for (int qq = group; qq < KC; qq += ngroups)
           acc = fma((double)di[qq] * us[qq], (double)dj[qq], acc);
@@ -193,7 +195,7 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
   if (threadIdx.x == 0) abar[(size_t)w * N_tr + i] = 2.0 * red[0];
 }
 
-// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, pair of LC multipoles,
+// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, LC multipoles,
 // walker); one thread per k point.  S_l A_j is staged per multipole chunk in shared memory (in the
 // arithmetic type T: FP32 for the mixed paths, FP64 for the FP64 path), Delta_j(l, q) in a
 // per-thread shared column.  The P_bar partial of each multipole chunk is a compensated sum
@@ -201,7 +203,7 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
 // covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a multipole chunk
 // when Delta is recomputed chunk by chunk); the reduction runs once after the last chunk.
 constexpr int DT = 128;
-constexpr int LC = 2;
+constexpr int LC = 1;   // multipoles per CTA: one, for enough CTAs to hide the load latency
 
 template <typename T>
 __device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {

@@ -280,8 +280,8 @@ cudaError_t launch_unpack_sym(double* Cbar_full, const double* Cbar, const int* 
                               cudaStream_t s);
 cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const double* U,
                            const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s);
-// Dbar for the chunk (l_lo a multiple of 2) and its partial sums of P_bar in scratch (indexed by
-// the global 2-multipole chunk); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
+// Dbar for the chunk and its partial sums of P_bar in scratch (indexed by
+// the global multipole); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
