@@ -123,3 +123,37 @@ def test_rank_two_profiles():
     assert norm_err(C, f["C"]) < GATE_C
     assert max_rel(Pb[0], Pbo) < GATE_G
     assert max_rel(Wb[0], Wbo) < GATE_G
+
+
+@pytest.mark.parametrize("code", [96, 128, 48, 64 | 256, 32 | 256])
+def test_every_tile_variant_against_oracle(code):
+    """Each GEMM variant, fixed through SWCL_BASIS_TILES: one CTA per SM (48, 96, 128 columns)
+    and two CTAs per SM (| 256); three walkers, a ragged k tail (333 points), 17 K-blocks in the
+    forward GEMM, against the oracle."""
+    import paper_2505_22718_gb300 as S
+    w, tapers = make_ragged_case(n_walk=3, seed=51)
+    old = os.environ.get("SWCL_BASIS_TILES")
+    os.environ["SWCL_BASIS_TILES"] = "%d,%d" % (code, code)
+    try:
+        ctx = _context(w, tapers)
+    finally:
+        if old is None:
+            del os.environ["SWCL_BASIS_TILES"]
+        else:
+            os.environ["SWCL_BASIS_TILES"] = old
+    ctx.set_ell_lists(None)
+    rng = np.random.default_rng(2)
+    Cb = rng.standard_normal((3 * len(w.ells), w.n_tr, w.n_tr))
+    try:
+        C, (Pb, Ab, Wb) = _fwd_vjp(ctx, Cb)
+    except S.SwiftClError as e:
+        # a forward tile must hold whole groups of r basis columns
+        assert "not a forward tile" in str(e)
+        pytest.skip("tile %d does not hold whole basis groups at this rank" % code)
+    assert ctx.query(S.SWCL_Q_TILE_FWD) == code and ctx.query(S.SWCL_Q_TILE_ADJ) == code
+    C = C.reshape(3, len(w.ells), w.n_tr, w.n_tr)
+    Cb = Cb.reshape(3, len(w.ells), w.n_tr, w.n_tr)
+    for wk in range(3):
+        f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, tapers, C_bar=Cb[wk])
+        assert norm_err(C[wk], f["C"]) < GATE_C
+        assert max(max_rel(Pb[wk], Pbo), max_rel(Ab[wk], Abo), max_rel(Wb[wk], Wbo)) < GATE_G
