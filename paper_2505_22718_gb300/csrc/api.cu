@@ -81,6 +81,17 @@ int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes) {
   return SWCL_OK;
 }
 
+// Queues a copy without waiting; *host_src becomes true when src is host memory, and the caller
+// then synchronises the stream once before returning (it may reuse its arrays on return).
+int copy_in_queued(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes, bool* host_src) {
+  int st = ensure(c, dst, bytes);
+  if (st) return st;
+  cudaError_t e = cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync (input)");
+  if (!is_device_ptr(src)) *host_src = true;
+  return SWCL_OK;
+}
+
 int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes) {
   if (dst == src || bytes == 0) return SWCL_OK;
   cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
@@ -472,6 +483,18 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
   return SWCL_OK;
 }
 
+namespace {
+// On an early error return, waits for copies already queued from host arrays, which the caller
+// may free once the call returns.
+struct QueuedHostCopies {
+  swcl_ctx* c;
+  bool pending = false;
+  ~QueuedHostCopies() {
+    if (pending) cudaStreamSynchronize(c->stream);
+  }
+};
+}  // namespace
+
 int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, const double* B) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -481,7 +504,10 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
   if (c->have_power && c->n_walk != n_walk)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_power");
   const int N = c->N;
-  SWCL_TRY(swcl::copy_in(c, c->d_W, W, sizeof(double) * (size_t)n_walk * c->N_tr * N));
+  // host sources are waited for once, at the end of the call
+  QueuedHostCopies q{c};
+  bool& host_src = q.pending;
+  SWCL_TRY(swcl::copy_in_queued(c, c->d_W, W, sizeof(double) * (size_t)n_walk * c->N_tr * N, &host_src));
   // D and B: the knot profiles are re-factorised (low-rank mode) only when their values change
   const size_t dn = (size_t)c->N_I * N, bn = B ? (size_t)c->N_tr * c->N_I * N : 0;
   const bool had_prev = c->have_windows && c->have_B == (B != nullptr) && c->d_D.p &&
@@ -493,14 +519,14 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
     if (e != cudaSuccess) return swcl::cuda_fail(c, e, "keep previous D");
   }
   if (D) {
-    SWCL_TRY(swcl::copy_in(c, c->d_D, D, sizeof(double) * dn));
+    SWCL_TRY(swcl::copy_in_queued(c, c->d_D, D, sizeof(double) * dn, &host_src));
   } else {
     std::vector<double> ones(dn, 1.0);
     SWCL_TRY(swcl::copy_in(c, c->d_D, ones.data(), sizeof(double) * ones.size()));
   }
   if (c->have_B != (B != nullptr) || c->n_walk != n_walk) ++c->alloc_gen;  // new graph needed
   c->have_B = B != nullptr;
-  if (B) SWCL_TRY(swcl::copy_in(c, c->d_B, B, sizeof(double) * bn));
+  if (B) SWCL_TRY(swcl::copy_in_queued(c, c->d_B, B, sizeof(double) * bn, &host_src));
   if (had_prev && !c->lr_dirty) {
     SWCL_TRY(swcl::ensure(c, c->d_flag, sizeof(int)));
     int flag = 0;
@@ -512,9 +538,14 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
                                              (const double*)c->d_prev.p + dn, (long)bn);
     SWCL_TRY_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag read");
     SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "flag sync");
+    host_src = false;   // the flag read waited for the copies too
     if (flag) c->lr_dirty = true;
   } else {
     c->lr_dirty = true;
+  }
+  if (host_src) {
+    host_src = false;
+    SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   }
   SWCL_TRY(swcl::ensure(c, c->d_prev, sizeof(double) * (dn + bn)));
   c->n_walk = n_walk;
@@ -534,8 +565,13 @@ int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) 
   if (c->have_windows && c->n_walk != n_walk)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_windows");
   if (c->n_walk != n_walk) ++c->alloc_gen;
-  SWCL_TRY(swcl::copy_in(c, c->d_P, P, sizeof(double) * (size_t)n_walk * c->N_k));
-  SWCL_TRY(swcl::copy_in(c, c->d_amp, amp, sizeof(double) * (size_t)n_walk * c->N_tr));
+  QueuedHostCopies q{c};
+  SWCL_TRY(swcl::copy_in_queued(c, c->d_P, P, sizeof(double) * (size_t)n_walk * c->N_k, &q.pending));
+  SWCL_TRY(swcl::copy_in_queued(c, c->d_amp, amp, sizeof(double) * (size_t)n_walk * c->N_tr, &q.pending));
+  if (q.pending) {
+    q.pending = false;
+    SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  }
   c->n_walk = n_walk;
   c->have_power = true;
   c->last_fwd_precision = -1;

@@ -206,6 +206,7 @@ int ensure(swcl_ctx* c, DevBuf& b, size_t bytes);
 void release(swcl_ctx* c, DevBuf& b);
 bool is_device_ptr(const void* p);
 int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes);
+int copy_in_queued(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes, bool* host_src);
 int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes);
 Stencil stencil(const swcl_ctx* c);
 int factor_profiles(swcl_ctx* c);
