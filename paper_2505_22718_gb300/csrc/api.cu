@@ -81,12 +81,32 @@ int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes) {
   return SWCL_OK;
 }
 
-// Queues a copy without waiting; *host_src becomes true when src is host memory, and the caller
-// then synchronises the stream once before returning (it may reuse its arrays on return).
+constexpr size_t kStageBytes = 256 * 1024;   // pinned staging per context
+constexpr size_t kStageMax = 64 * 1024;      // host inputs up to this size go through it
+
+// Queues a copy without waiting.  A small host array is first copied on the host into the
+// context's pinned staging buffer (the caller may reuse it at once); a larger host array sets
+// *host_src, and the caller then synchronises the stream once before returning.
 int copy_in_queued(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes, bool* host_src) {
   int st = ensure(c, dst, bytes);
   if (st) return st;
-  cudaError_t e = cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, c->stream);
+  cudaError_t e;
+  if (!is_device_ptr(src) && bytes <= kStageMax && c->stage) {
+    if (c->stage_off + bytes > kStageBytes) {
+      // every earlier copy out of the staging buffer has finished before it is overwritten
+      e = cudaEventSynchronize(c->ev_stage);
+      if (e != cudaSuccess) return cuda_fail(c, e, "staging wait");
+      c->stage_off = 0;
+    }
+    unsigned char* p = c->stage + c->stage_off;
+    std::memcpy(p, src, bytes);
+    e = cudaMemcpyAsync(dst.p, p, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_stage, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync (staged input)");
+    c->stage_off += (bytes + 255) & ~size_t(255);
+    return SWCL_OK;
+  }
+  e = cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync (input)");
   if (!is_device_ptr(src)) *host_src = true;
   return SWCL_OK;
@@ -265,7 +285,9 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_limber, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_limber, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc((void**)&c->stage, swcl::kStageBytes, cudaHostAllocDefault) != cudaSuccess) {
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return SWCL_ERR_CUDA;
@@ -325,6 +347,8 @@ int swcl_destroy(swcl_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_limber) cudaEventDestroy(c->ev_limber);
+  if (c->ev_stage) cudaEventDestroy(c->ev_stage);
+  if (c->stage) cudaFreeHost(c->stage);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SWCL_OK;

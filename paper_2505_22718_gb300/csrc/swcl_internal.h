@@ -173,6 +173,10 @@ struct swcl_ctx {
   swcl::DevBuf ws_ltab;      // Limber stencil table (LimberTable)
   bool lt_ready = false;     // ws_ltab matches the grids and the switch
   cudaEvent_t ev_limber = nullptr;
+  // pinned staging for small host inputs: copied on the host, then sent without a wait
+  unsigned char* stage = nullptr;
+  size_t stage_off = 0;
+  cudaEvent_t ev_stage = nullptr;   // after the last copy out of `stage`
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
 
