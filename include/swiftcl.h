@@ -211,7 +211,9 @@ int swcl_profile_reset(swcl_ctx* ctx);
 /* Stage read-back for element-wise testing of each step.  Copies an internal array of the last
  * compute into out (host or device), as FP64 values (complex arrays as interleaved re, im):
  *   SWCL_DBG_COEF   a1 c[n_walk][N_tr][N_I][N/2+1] complex
- *   SWCL_DBG_DELTA  a3 Delta[n_walk][N_ell][N_tr][N_k] (mixed paths: FP32 values widened)
+ *   SWCL_DBG_DELTA  a3 Delta[n_walk][N_ell][N_tr][N_k] (mixed paths: FP32 values widened); only
+ *                   when the last forward pass held Delta for every multipole at once (no
+ *                   memory-budget chunks, no Limber rows), else SWCL_ERR_STATE
  *   SWCL_DBG_GTAB   a2 w_n pi(l) M_{l,n} per tracer class [n_cls][N_ell][N/2+1] complex
  *   SWCL_DBG_PHASE  e^{-i eta_n ln k_q} [N_k][N/2+1] complex
  *   SWCL_DBG_UNIT   a4 unit-amplitude C [n_walk][N_ell][N_tr][N_tr]

@@ -672,11 +672,14 @@ static int check_ready(swcl_ctx* c, int precision) {
 // Dbar (and, in basis mode, the per-call GEMM operands) for every multipole at once.  Then the
 // forward pass contracts and integrates chunk by chunk, and the VJP recomputes each chunk's
 // Delta before its reverse mode.  Returns 0 when not even 8 multipoles fit.
-static int plan_ell_chunk(swcl_ctx* c, int precision) {
+static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
+  // n_need: the multipoles that take the FFTLog path (all but the Limber rows)
+  if (n_need <= 0) return c->N_ell;
   const int N_ell = c->N_ell;
   const bool fp64 = precision == SWCL_FP64;
   const bool basis = use_basis_gemm(c, precision);
-  if (!c->budget || (!fp64 && !basis)) return N_ell;   // knot-stencil tensor-core forms: whole
+  if (!fp64 && !basis) return N_ell;   // knot-stencil tensor-core forms: every multipole at once
+  if (!c->budget) return n_need;
   const swcl::Stencil sv = swcl::stencil(c);
   const size_t nw = c->n_walk, nrow = nw * c->N_tr, ntr2 = (size_t)c->N_tr * c->N_tr;
   size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float)) +
@@ -698,10 +701,10 @@ static int plan_ell_chunk(swcl_ctx* c, int precision) {
   size_t ws_now = 0;
   for (const DevBuf* b : ws) ws_now += b->bytes;
   const size_t other = c->held - ws_now;     // tables, inputs
-  if (other + fixed + per_l * N_ell <= c->budget) return N_ell;
+  if (other + fixed + per_l * n_need <= c->budget) return n_need;
   if (other + fixed + per_l * 8 > c->budget) return 0;
   const size_t n = (c->budget - other - fixed) / per_l;
-  return (int)std::min<size_t>(N_ell, std::max<size_t>(8, n / 8 * 8));
+  return (int)std::min<size_t>(n_need, std::max<size_t>(8, n / 8 * 8));
 }
 
 // Delta for multipoles [l_lo, l_lo + n_l) into ws_delta ([n_walk][n_l][N_tr][N_k])
@@ -804,7 +807,13 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   const int N_k = c->N_k, N_ell = c->N_ell;
   const size_t nrow = (size_t)nw * N_tr;
   const bool fp64 = precision == SWCL_FP64;
-  const int n_lc = plan_ell_chunk(c, precision);
+  swcl::LimberArgs lim;
+  SWCL_TRY(limber_plan(c, precision, lim));
+  const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
+  // the Limber table and scratch first, so that the multipole chunks are planned around them
+  swcl::LimberTable lt;
+  if (lim.n_lim > 0) SWCL_TRY(limber_prepare(c, lim, nw, lt));
+  const int n_lc = plan_ell_chunk(c, precision, n_fft);
   if (n_lc == 0)
     return swcl::fail(c, SWCL_ERR_OOM_BUDGET, "memory budget too small for 8 multipoles of Delta");
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
@@ -821,9 +830,6 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                                (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
-  swcl::LimberArgs lim;
-  SWCL_TRY(limber_plan(c, precision, lim));
-  const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
   for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
     const int n_l = std::min(n_lc, n_fft - l_lo);
     SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
@@ -840,14 +846,13 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
     ++c->last_launches;  // the pair-sum reduction
   }
   if (lim.n_lim > 0) {
-    swcl::LimberTable lt;
-    SWCL_TRY(limber_prepare(c, lim, nw, lt));
     SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt,
                                             (const double*)c->d_W.p, (const double*)c->d_P.p, nw,
                                             c->stream), "limber");
     ++c->last_launches;  // the pair-sum reduction
   }
   c->ell_chunk = n_lc;
+  c->ell_fft = n_fft;
   const int64_t n_out = out_count(c);
   const size_t cbytes = sizeof(double) * (size_t)n_out * N_tr * N_tr;
   double* dst = C_out;
@@ -1116,14 +1121,18 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
   swcl::LimberArgs lim;
   SWCL_TRY(limber_plan(c, precision, lim));
   const int n_fft = lim.l_first;   // FFTLog multipoles [0, n_fft), Limber [n_fft, N_ell)
+  swcl::LimberTable lt;
+  if (lim.n_lim > 0) SWCL_TRY(limber_prepare(c, lim, n_dir, lt));
   // the forward kernels see 1 + n_dir walkers: the base, then the tangent windows
   c->last_fwd_precision = -1;
   c->u_valid = false;
   {
     WalkScope scope(c, nw2);
-    const int n_lc = plan_ell_chunk(c, precision);
+    const int n_lc = plan_ell_chunk(c, precision, n_fft);
     if (n_lc == 0)
       return swcl::fail(c, SWCL_ERR_OOM_BUDGET, "memory budget too small for 8 multipoles of Delta");
+    c->ell_chunk = n_lc;
+    c->ell_fft = n_fft;
     SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nw2 * N_tr * N_I * n_h));
     SWCL_TRY(swcl::ensure(c, c->ws_delta, (size_t)nw2 * N_tr * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
     SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(1, N_tr, N_k, n_lc)));
@@ -1164,8 +1173,6 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
     }
   }
   if (lim.n_lim > 0) {
-    swcl::LimberTable lt;
-    SWCL_TRY(limber_prepare(c, lim, n_dir, lt));
     SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt, jW,
                                             (const double*)c->d_P.p, 1, c->stream), "limber");
     SWCL_LAUNCH(c, swcl::launch_limber_jvp((double*)c->ws_dU.p, (double*)c->ws_lq.p, lim, lt, jW,
@@ -1337,6 +1344,11 @@ int swcl_debug_read(swcl_ctx* c, int what, double* out, int64_t* count) {
   if (!src) return swcl::fail(c, SWCL_ERR_STATE, "array not computed yet");
   if (what == SWCL_DBG_DELTA && c->last_fwd_precision < 0)
     return swcl::fail(c, SWCL_ERR_STATE, "no forward pass yet");
+  if (what == SWCL_DBG_DELTA &&
+      (c->ell_chunk != c->N_ell || c->ell_fft != c->N_ell ||
+       c->ws_delta.bytes < (size_t)n * (c->last_fwd_precision == SWCL_FP64 ? sizeof(double) : sizeof(float))))
+    return swcl::fail(c, SWCL_ERR_STATE,
+                      "Delta is held in multipole chunks (memory budget or Limber rows): not readable");
   if (dfpair) {
     // double-float pairs (re_hi, im_hi, re_lo, im_lo) -> (re, im)
     DevBuf tmp;
@@ -1388,7 +1400,7 @@ int swcl_query(swcl_ctx* c, int key, int64_t* value) {
   if (!c || !value) return SWCL_ERR_INVALID_ARG;
   switch (key) {
     case SWCL_Q_WORKSPACE_BYTES: *value = (int64_t)c->held; return SWCL_OK;
-    case SWCL_Q_RECOMPUTE: *value = c->ell_chunk > 0 && c->ell_chunk < c->N_ell ? 1 : 0; return SWCL_OK;
+    case SWCL_Q_RECOMPUTE: *value = c->ell_chunk > 0 && c->ell_chunk < c->ell_fft ? 1 : 0; return SWCL_OK;
     case SWCL_Q_N_HALF: *value = c->n_h; return SWCL_OK;
     case SWCL_Q_KERNEL_LAUNCHES: *value = c->last_launches; return SWCL_OK;
     case SWCL_Q_PROFILE_RANK: *value = c->lr_basis ? c->lr_true_rank : 0; return SWCL_OK;

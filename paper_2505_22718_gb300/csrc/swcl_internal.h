@@ -179,6 +179,7 @@ struct swcl_ctx {
   cudaEvent_t ev_stage = nullptr;   // after the last copy out of `stage`
   int last_fwd_precision = -1;
   int ell_chunk = 0;         // multipoles per Delta chunk of the last forward pass (N_ell = whole)
+  int ell_fft = 0;           // multipoles on the FFTLog path in the last forward pass (Limber after)
 
   // CUDA graph of the batched call (swcl_compute_batched)
   cudaGraphExec_t graph_exec = nullptr;

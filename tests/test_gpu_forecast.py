@@ -161,3 +161,24 @@ def test_forecast_argument_and_state_errors(ref):
     ctx2 = lib_context(w2, tapers)
     with pytest.raises(S.SwiftClError):
         ctx2.jvp(Pd, None, None, S.SWCL_FP64)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x9"])
+def test_jvp_under_a_memory_budget(prec, wl):
+    """The JVP's Delta (base walker and one walker per tangent) in multipole chunks under a
+    memory budget gives the same C_dot as without a budget."""
+    import paper_2505_22718_gb300 as S
+    w0 = wl("n5k_vjp")
+    w = copy.copy(w0)
+    rng = np.random.default_rng(4)
+    Pd = rng.standard_normal((2, len(w.k))) * w.P
+    Wd = rng.standard_normal((2, w.n_tr, w.N)) * w.W
+    p = S.PRECISIONS[prec]
+    ctx = lib_context(w)
+    J1 = ctx.jvp(Pd, None, Wd, p)
+    held = ctx.query(S.SWCL_Q_WORKSPACE_BYTES)
+    es = 8 if prec == "fp64" else 4
+    ctx2 = lib_context(w, budget=held - w.n_tr * len(w.ells) * len(w.k) * es // 2)
+    J2 = ctx2.jvp(Pd, None, Wd, p)
+    assert ctx2.query(S.SWCL_Q_RECOMPUTE) == 1
+    assert np.array_equal(J1, J2)

@@ -97,3 +97,33 @@ def test_large_configuration_sampled_against_oracle(prec):
         assert np.array_equal(C, C2)
         assert max_rel(Pb2, Pb) < 1e-12
         assert max_rel(Wb2[0][tr], Wb[0][tr]) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x9"])
+def test_chunked_recompute_with_limber_rows(prec, wl):
+    """Limber rows for l >= 500 and a budget that splits the FFTLog multipoles into chunks: the
+    results equal the unchunked run's, only the FFTLog multipoles are held as Delta, and Delta is
+    then not readable through the debug call."""
+    import paper_2505_22718_gb300 as S
+    w = wl("n5k_vjp")
+
+    def run(budget):
+        ctx = lib_context(w, budget=budget)
+        ctx.set_limber(500)
+        C = ctx.compute_cl(S.PRECISIONS[prec])
+        g = ctx.vjp(w.C_bar, S.PRECISIONS[prec])
+        return ctx, C, g
+
+    full, C1, (P1, A1, W1) = run(0)
+    assert full.query(S.SWCL_Q_RECOMPUTE) == 0
+    with pytest.raises(S.SwiftClError):
+        S.swcl_debug_read(full.ptr, S.SWCL_DBG_DELTA)
+    n_fft = int(np.sum(w.ells < 500))
+    es = 8 if prec == "fp64" else 4
+    held = full.query(S.SWCL_Q_WORKSPACE_BYTES)
+    ctx, C2, (P2, A2, W2) = run(held - w.n_tr * n_fft * len(w.k) * es // 2)
+    assert ctx.query(S.SWCL_Q_RECOMPUTE) == 1
+    assert np.array_equal(C1, C2)
+    assert np.array_equal(A1, A2)
+    assert np.array_equal(P1, P2)
+    assert max_rel(W2, W1) < (1e-12 if prec == "fp64" else 1e-5)
