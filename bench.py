@@ -119,13 +119,13 @@ def algorithmic_work(w, walkers, rank):
 # benchmark workload (one walker), from the ncu capture summarised in profiles/, valid only for
 # the kernel source it was taken from (sha256 of the file; otherwise reported as null).
 TRAFFIC = {
-    # profiles/basis_gemm_n5k_bf16.md (tiles 96/96, one walker)
-    "basis gemm adj": {"bytes": 25414656 + 0, "walkers": 1,
+    # profiles/basis_gemm_n5k_bf16.md (tiles 1120/1120: 96 columns, two K-blocks per stage; one walker)
+    "basis gemm adj": {"bytes": 25438720 + 0, "walkers": 1,
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "23207160f2114c26d2a36992b6b831c9904d6a4d727b4da5ab252c9042270a60"},
-    "basis gemm fwd": {"bytes": 33246464 + 0, "walkers": 1,
+                       "sha256": "f99a681600c9cafb91d4b8ead17c1935b547e3c7882d1aeb41f4e2679094da9b"},
+    "basis gemm fwd": {"bytes": 33252096 + 0, "walkers": 1,
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "23207160f2114c26d2a36992b6b831c9904d6a4d727b4da5ab252c9042270a60"},
+                       "sha256": "f99a681600c9cafb91d4b8ead17c1935b547e3c7882d1aeb41f4e2679094da9b"},
 }
 
 

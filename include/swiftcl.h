@@ -91,7 +91,7 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_Q_PROFILE_RANK    5  /* rank r of the knot profiles D*B used (0 = one FFT per knot) */
 #define SWCL_Q_TILE_FWD        6  /* autotuned tile of the basis-mode forward GEMM (0 = none yet):
                                      column tile in bits 0-7, bit 8 set for the variant that runs
-                                     two CTAs per SM */
+                                     two CTAs per SM, bit 10 for two K-blocks per stage */
 #define SWCL_Q_TILE_ADJ        7  /* the same for the basis-mode adjoint GEMM */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the device memory the

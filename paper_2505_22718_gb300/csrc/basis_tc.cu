@@ -105,16 +105,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
+// A stage holds KS consecutive K-blocks (contiguous in both images): KS A-blocks of a1 bytes,
+// then KS B-blocks of b1 bytes.
 struct Layout {
-  uint32_t a_bytes, b_bytes, stage, bar_off, total;
+  uint32_t a1, b1, a_bytes, b_bytes, stage, bar_off, total;
   int stages;
 };
 template <class P>
-__host__ __device__ inline Layout layout(int NT, int stages) {
+__host__ __device__ inline Layout layout(int NT, int stages, int KS) {
   Layout L;
   L.stages = stages;
-  L.a_bytes = P::kPlanesA * kPlaneM;
-  L.b_bytes = P::kPlanesB * NT * kRow;
+  L.a1 = P::kPlanesA * kPlaneM;
+  L.b1 = P::kPlanesB * NT * kRow;
+  L.a_bytes = KS * L.a1;
+  L.b_bytes = KS * L.b1;
   L.stage = L.a_bytes + L.b_bytes;
   L.bar_off = stages * L.stage;
   L.total = L.bar_off + 8 * (3 * stages + 1) + 16 + 1024;
@@ -243,14 +247,15 @@ struct EpiAdj {
 
 // CH: 16-column chunks per drain thread at most (3 for tiles up to 96 columns with 8 drain
 // warps, 4 otherwise); it sizes the accumulator registers.
-template <class P, class Epi, int DW, int CH>
+template <class P, class Epi, int DW, int CH, int KS>
 __global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int NT = sh.NT, S = sh.stages, n_kb = sh.n_kb;
-  const Layout L = layout<P>(NT, S);
+  // n_kb counts the stages' worth of K (KS K-blocks each, the last one possibly short)
+  const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
+  const Layout L = layout<P>(NT, S, KS);
   // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
   // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
   // the TMEM buffer the K-block accumulates into (1 + DW arrivals: one per drain warp, since
@@ -295,8 +300,8 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       // K-blocks (ready -> full) in order.  Both conditions are polled without suspending
       // (test_wait): a thread suspended on "stage free" would hold back the forward of a landed
       // K-block until the tensor core had finished the previous one, a bubble per K-block.
-      const uint8_t* asrc = aimg + (size_t)mt * n_kb * L.a_bytes;
-      const uint8_t* bsrc = bimg + (size_t)nt * n_kb * L.b_bytes;
+      const uint8_t* asrc = aimg + (size_t)mt * n_kb1 * L.a1;
+      const uint8_t* bsrc = bimg + (size_t)nt * n_kb1 * L.b1;
       int next = 0, fwd = 0;
       long idle = 0;
       while (fwd < n_kb) {
@@ -305,9 +310,10 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
           const int s = next % S, r = next / S;
           if (r == 0 || mbar_test_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
             uint8_t* st = base + s * L.stage;
-            mbar_arrive_tx(smem_u32(&ready[s]), L.stage);
-            bulk_g2s(smem_u32(st), asrc + (size_t)next * L.a_bytes, L.a_bytes, smem_u32(&ready[s]));
-            bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)next * L.b_bytes, L.b_bytes,
+            const int nk = min(KS, n_kb1 - next * KS);      // K-blocks in this stage
+            mbar_arrive_tx(smem_u32(&ready[s]), nk * (L.a1 + L.b1));
+            bulk_g2s(smem_u32(st), asrc + (size_t)next * KS * L.a1, nk * L.a1, smem_u32(&ready[s]));
+            bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)next * KS * L.b1, nk * L.b1,
                      smem_u32(&ready[s]));
             ++next;
             progress = true;
@@ -339,19 +345,24 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
         if (!mbar_wait(smem_u32(&full[s]), r & 1, abort_flag)) break;
         tc_fence_after();
         const uint32_t a0 = smem_u32(base + s * L.stage);
-        const uint64_t da = desc64(a0), db = desc64(a0 + L.a_bytes);
         const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
         const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+        const int nk = min(KS, n_kb1 - kb * KS);
 #pragma unroll
-        for (int j = 0; j < kK / 16; ++j) {
+        for (int h = 0; h < KS; ++h) {
+          if (h >= nk) break;
+          const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
 #pragma unroll
-          for (int t = 0; t < P::kProducts; ++t) {
-            // descriptor start addresses advance in 16-byte units
-            const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
-            const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
-            const bool lead = (t == 0);
-            const bool first = (j == 0) && (t <= 1);
-            mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+          for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+            for (int t = 0; t < P::kProducts; ++t) {
+              // descriptor start addresses advance in 16-byte units
+              const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+              const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+              const bool lead = (t == 0);
+              const bool first = (h == 0) && (j == 0) && (t <= 1);
+              mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+            }
           }
         }
         mma_commit(smem_u32(&mmadone[s]));
@@ -695,15 +706,18 @@ unsigned grid_for(long total) {
 
 // Tile configuration code: column tile NT in bits 0-7, bit 8 = the two-CTAs-per-SM variant.
 constexpr int kPair = 256;
+// bit 10 = two K-blocks per pipeline stage: one barrier round trip, commit and drain per 64 of K
+constexpr int kDeep = 1024;
 
 template <class P>
 int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
   const int NT = code & 255;
   const bool pair = code & kPair;
+  const int KS = (code & kDeep) ? 2 : 1;
   const uint32_t cap = pair ? 113 * 1024 : 227 * 1024;
   int stages = kMaxStages;
-  Layout L = layout<P>(NT, stages);
-  while (stages > 2 && L.total > cap) L = layout<P>(NT, --stages);
+  Layout L = layout<P>(NT, stages, KS);
+  while (stages > 2 && L.total > cap) L = layout<P>(NT, --stages, KS);
   if (L.total > cap) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
@@ -713,13 +727,13 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   return SWCL_OK;
 }
 
-template <class P, class Epi, int DW, int CH>
+template <class P, class Epi, int DW, int CH, int KS>
 cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
                            uint32_t smem, int n_nt, const Epi& epi) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH>,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi, DW, CH><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
+  k_gemm_basis<P, Epi, DW, CH, KS><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
       a, b, sh, epi, (int*)c->ws_status.p);
   return cudaGetLastError();
 }
@@ -729,10 +743,13 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
                         const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
   const int nch = sh.NT / 16;
   if (code & kPair)   // four drain warps: every chunk of a row in one thread
-    return nch <= 3 ? launch_variant<P, Epi, 4, 3>(c, a, b, sh, smem, n_nt, epi)
-                    : launch_variant<P, Epi, 4, 4>(c, a, b, sh, smem, n_nt, epi);
-  return (nch + 1) / 2 <= 3 ? launch_variant<P, Epi, 8, 3>(c, a, b, sh, smem, n_nt, epi)
-                            : launch_variant<P, Epi, 8, 4>(c, a, b, sh, smem, n_nt, epi);
+    return nch <= 3 ? launch_variant<P, Epi, 4, 3, 1>(c, a, b, sh, smem, n_nt, epi)
+                    : launch_variant<P, Epi, 4, 4, 1>(c, a, b, sh, smem, n_nt, epi);
+  if (code & kDeep)
+    return (nch + 1) / 2 <= 3 ? launch_variant<P, Epi, 8, 3, 2>(c, a, b, sh, smem, n_nt, epi)
+                              : launch_variant<P, Epi, 8, 4, 2>(c, a, b, sh, smem, n_nt, epi);
+  return (nch + 1) / 2 <= 3 ? launch_variant<P, Epi, 8, 3, 1>(c, a, b, sh, smem, n_nt, epi)
+                            : launch_variant<P, Epi, 8, 4, 1>(c, a, b, sh, smem, n_nt, epi);
 }
 
 // Candidate tile codes: column tiles that are multiples of 16; in forward tiles each drain
@@ -746,6 +763,10 @@ std::vector<int> tile_candidates(int r, bool need_groups) {
   }
   for (int nt = 32; nt <= 64; nt += 16)
     if (!need_groups || nt % r == 0) v.push_back(nt | kPair);
+  for (int nt = 64; nt <= kMaxNT; nt += 32) {
+    const int half0 = 16 * ((nt / 16 + 1) / 2);
+    if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt | kDeep);
+  }
   return v;
 }
 
