@@ -122,10 +122,10 @@ TRAFFIC = {
     # profiles/basis_gemm_n5k_bf16.md (tiles 1120/1120: 96 columns, two K-blocks per stage; one walker)
     "basis gemm adj": {"bytes": 25438720 + 0, "walkers": 1,
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "f99a681600c9cafb91d4b8ead17c1935b547e3c7882d1aeb41f4e2679094da9b"},
+                       "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
     "basis gemm fwd": {"bytes": 33252096 + 0, "walkers": 1,
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "f99a681600c9cafb91d4b8ead17c1935b547e3c7882d1aeb41f4e2679094da9b"},
+                       "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
 }
 
 

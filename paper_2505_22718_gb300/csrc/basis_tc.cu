@@ -20,9 +20,10 @@
 // here): the constant operand is split once from FP64 into 3 bf16 planes; the forward B operand
 // H is formed in double-float arithmetic from double-float F and G and split into 3 planes; the
 // adjoint B operand is an FP32 product split exactly into 3 planes.  The 6 products with
-// pa + pb <= 2 are issued.  The tensor core accumulates one 32-deep K-block at a
-// time, the leading product and the corrections in separate TMEM slots (double-buffered); eight
-// drain warps add each K-block's partial sums into FP32 registers with round-to-nearest.
+// pa + pb <= 2 are issued.  The tensor core accumulates one pipeline stage at a time (KS = 1 or 2
+// consecutive 32-deep K-blocks), the leading product and the corrections in separate TMEM slots
+// (double-buffered); the drain warps add each stage's partial sums into FP32 registers with
+// round-to-nearest.
 //
 // Warp roles: warp 0 streams both operand images into a shared-memory ring with cp.async.bulk;
 // warp 1 owns TMEM and issues tcgen05.mma; the remaining 4 or 8 warps drain TMEM (with 8, two
@@ -258,12 +259,13 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   const Layout L = layout<P>(NT, S, KS);
   // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
   // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
-  // the TMEM buffer the K-block accumulates into (1 + DW arrivals: one per drain warp, since
+  // the TMEM buffer the stage accumulates into (1 + DW arrivals: one per drain warp, since
   // 32 DW single-thread arrivals would serialise on the barrier word); mmadone[s] when the
-  // K-block's MMAs are done (one commit), which frees the stage for the copy warp and the
-  // accumulator for the drain warps.  The MMA thread waits once and commits once per K-block:
+  // stage's MMAs are done (one commit), which frees the stage for the copy warp and the
+  // accumulator for the drain warps.  The MMA thread waits once and commits once per stage:
   // a single thread issues tcgen05.mma only about as fast as the tensor core executes a
-  // 128 x 96 x 16 product, so its own time between MMAs is the critical resource.
+  // 128 x 96 x 16 product, so its own time between MMAs is the critical resource, and two
+  // K-blocks per stage halve the round trips.
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
   uint64_t* full = bars;
   uint64_t* mmadone = bars + S;
