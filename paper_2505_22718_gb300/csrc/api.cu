@@ -287,6 +287,9 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_limber, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_pre, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_unpack, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_pack, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc((void**)&c->stage, swcl::kStageBytes, cudaHostAllocDefault) != cudaSuccess) {
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -348,6 +351,9 @@ int swcl_destroy(swcl_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_limber) cudaEventDestroy(c->ev_limber);
   if (c->ev_stage) cudaEventDestroy(c->ev_stage);
+  if (c->ev_pre) cudaEventDestroy(c->ev_pre);
+  if (c->ev_unpack) cudaEventDestroy(c->ev_unpack);
+  if (c->ev_pack) cudaEventDestroy(c->ev_pack);
   if (c->stage) cudaFreeHost(c->stage);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -861,10 +867,18 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
     SWCL_TRY(swcl::ensure(c, c->ws_C, cbytes));
     dst = (double*)c->ws_C.p;
   }
+  // in a batched forward + VJP the packing runs on the auxiliary stream beside the VJP, which
+  // joins it at its end
+  cudaStream_t pack_stream = c->stream;
+  if (c->overlap && dev_out) {
+    SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_pack, c->stream), "fork pack");
+    SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_pack, 0), "fork pack");
+    pack_stream = c->aux;
+  }
   SWCL_LAUNCH(c, swcl::launch_scale_pack(dst, (const double*)c->ws_U.p, (const double*)c->d_amp.p,
                                          c->ragged ? (const int*)c->d_off.p : nullptr,
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
-                                         N_ell, n_out, c->stream), "scale/pack");
+                                         N_ell, n_out, pack_stream), "scale/pack");
   c->last_fwd_precision = precision;
   c->u_valid = true;
   if (!dev_out) {
@@ -911,10 +925,15 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   SWCL_TRY(swcl::ensure(c, c->ws_outA, sizeof(double) * nrow));
   const size_t wbytes = sizeof(double) * nrow * N;
   SWCL_TRY(swcl::ensure(c, c->ws_outW, wbytes + swcl::fftlog_adj_scratch_bytes(nw, N_tr, N_I, N)));
-  SWCL_LAUNCH(c, swcl::launch_unpack_sym((double*)c->ws_Cbar.p, cb,
-                                         c->ragged ? (const int*)c->d_off.p : nullptr,
-                                         c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
-                                         N_ell, n_out, c->stream), "unpack cotangent");
+  if (c->overlap) {
+    // unpacked on the auxiliary stream during the forward pass (swcl_compute_batched)
+    SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_unpack, 0), "join unpack");
+  } else {
+    SWCL_LAUNCH(c, swcl::launch_unpack_sym((double*)c->ws_Cbar.p, cb,
+                                           c->ragged ? (const int*)c->d_off.p : nullptr,
+                                           c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
+                                           N_ell, n_out, c->stream), "unpack cotangent");
+  }
   SWCL_TRY(swcl::ensure(c, c->ws_pbpart, swcl::delta_bar_scratch_bytes(nw, N_k, N_ell)));
   double* Pb = P_bar && swcl::is_device_ptr(P_bar) ? P_bar : (double*)c->ws_outP.p;
   double* Ab = amp_bar && swcl::is_device_ptr(amp_bar) ? amp_bar : (double*)c->ws_outA.p;
@@ -1019,8 +1038,31 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
       return swcl::fail(c, SWCL_ERR_INVALID_ARG, "swcl_compute_batched takes device pointers only");
   if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
   auto run = [&]() -> int {
+    // the cotangent's unpacking depends on C_bar alone: on the auxiliary stream, beside the
+    // forward pass (not while profiling, which times kernels one by one)
+    const bool overlap = C_bar && !c->prof;
+    if (overlap) {
+      const size_t n = (size_t)c->n_walk * c->N_ell * c->N_tr * c->N_tr;
+      int st0 = swcl::ensure(c, c->ws_Cbar, sizeof(double) * n);
+      if (st0) return st0;
+      cudaError_t e = cudaEventRecord(c->ev_pre, c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_pre, 0);
+      if (e == cudaSuccess)
+        e = swcl::launch_unpack_sym((double*)c->ws_Cbar.p, C_bar,
+                                    c->ragged ? (const int*)c->d_off.p : nullptr,
+                                    c->ragged ? (const int*)c->d_idx.p : nullptr, c->n_walk,
+                                    c->N_tr, c->N_ell, out_count(c), c->aux);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_unpack, c->aux);
+      if (e != cudaSuccess) return swcl::cuda_fail(c, e, "unpack cotangent");
+    }
+    c->overlap = overlap;
     int st = swcl_compute_cl(c, precision, C_out);
-    if (st == SWCL_OK && C_bar) st = swcl_vjp(c, precision, C_bar, P_bar, amp_bar, W_bar);
+    const int64_t n_fwd = c->last_launches;
+    if (st == SWCL_OK && C_bar) {
+      st = swcl_vjp(c, precision, C_bar, P_bar, amp_bar, W_bar);
+      c->last_launches += n_fwd + (overlap ? 1 : 0);   // forward and unpack kernels too
+    }
+    c->overlap = false;
     return st;
   };
   bool same = c->graph_exec && c->graph_key.precision == precision &&

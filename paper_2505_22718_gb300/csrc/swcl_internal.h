@@ -173,6 +173,10 @@ struct swcl_ctx {
   swcl::DevBuf ws_ltab;      // Limber stencil table (LimberTable)
   bool lt_ready = false;     // ws_ltab matches the grids and the switch
   cudaEvent_t ev_limber = nullptr;
+  // swcl_compute_batched with a cotangent: the cotangent is unpacked on the auxiliary stream beside
+  // the forward pass, and C is packed there beside the VJP (joined at the end of the VJP)
+  bool overlap = false;
+  cudaEvent_t ev_pre = nullptr, ev_unpack = nullptr, ev_pack = nullptr;
   // pinned staging for small host inputs: copied on the host, then sent without a wait
   unsigned char* stage = nullptr;
   size_t stage_off = 0;
