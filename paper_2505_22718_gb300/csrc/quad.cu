@@ -22,6 +22,7 @@ constexpr int QT = 256;    // threads
 constexpr int KC = 256;    // k points per CTA (one partial sum per pair and chunk)
 constexpr int KS = KC + 1; // shared row stride: lanes reading rows j at the same k point fall in
                            // different banks
+static_assert(QT == KC, "k_quad_part stages one k point per thread");
 
 // Partial pair sums over one chunk of KC k points: part[w][l - l_lo][kc][p] for unordered pairs
 // p = (i <= j).  Grid (multipole, k chunk, walker).  Thread t handles pair p = t % npair for the
@@ -40,9 +41,12 @@ k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double
   const int q0 = kc * KC;
   const int npair = N_tr * (N_tr + 1) / 2;
   const T* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
-  for (int e = threadIdx.x; e < N_tr * KC; e += QT) {
-    const int t = e / KC, qq = e - t * KC, q = q0 + qq;
-    Ds[t * KS + qq] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
+  {
+    // one k point per thread (QT == KC); the rows' loads are unrolled so that several are in
+    // flight at once
+    const int qq = threadIdx.x, q = q0 + qq;
+#pragma unroll 8
+    for (int t = 0; t < N_tr; ++t) Ds[t * KS + qq] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
   }
   for (int e = threadIdx.x; e < KC; e += QT) {
     const int q = q0 + e;
@@ -196,14 +200,30 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
 }
 
 // Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, LC multipoles,
-// walker); one thread per k point.  S_l A_j is staged per multipole chunk in shared memory (in the
-// arithmetic type T: FP32 for the mixed paths, FP64 for the FP64 path), Delta_j(l, q) in a
-// per-thread shared column.  The P_bar partial of each multipole chunk is a compensated sum
-// (TwoSum) written as FP64 to pbar_part[chunk][w][q]; k_pbar_reduce adds the chunks.  A launch
-// covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a multipole chunk
-// when Delta is recomputed chunk by chunk); the reduction runs once after the last chunk.
+// walker); one thread per k point.  S_ij A_j is staged per multipole chunk in shared memory,
+// transposed (St[j][i], rows padded to a multiple of DG with zeros) so that DG consecutive rows i
+// load as one vector, in the arithmetic type T (FP32 for the mixed paths, FP64 for the FP64 path);
+// Delta_j(l, q) sits in a per-thread shared column.  Each thread forms T_i for DG rows i at a time,
+// DG independent FMA chains over j in ascending order.  The P_bar partial of each multipole chunk
+// is a compensated sum (TwoSum) written as FP64 to pbar_part[chunk][w][q]; k_pbar_reduce adds the
+// chunks.  A launch covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a
+// multipole chunk when Delta is recomputed chunk by chunk); the reduction runs once after the last
+// chunk.
 constexpr int DT = 128;
 constexpr int LC = 1;   // multipoles per CTA: one, for enough CTAs to hide the load latency
+constexpr int DG = 4;   // rows i per pass
+
+__host__ __device__ inline int delta_bar_pitch(int N_tr) { return (N_tr + DG - 1) / DG * DG; }
+
+__device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
+  const double2 x = reinterpret_cast<const double2*>(p)[0];
+  const double2 y = reinterpret_cast<const double2*>(p)[1];
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
 
 template <typename T>
 __device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {
@@ -220,8 +240,9 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
             int N_ell, int n_walk, int l_lo, int n_l) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  T* S = reinterpret_cast<T*>(dsm_raw);            // [LC][N_tr][N_tr]  S_ij A_j
-  T* Dl = S + LC * N_tr * N_tr;                    // [N_tr][DT]
+  const int NP = delta_bar_pitch(N_tr);
+  T* St = reinterpret_cast<T*>(dsm_raw);           // [LC][N_tr][NP]  St[j][i] = S_ij A_j
+  T* Dl = St + LC * N_tr * NP;                     // [N_tr][DT]
   T* As = Dl + N_tr * DT;                          // [N_tr] A_i
   const int w = blockIdx.z;
   // Delta and Dbar hold multipoles [l_lo, l_lo + n_l) (l_lo a multiple of LC); Cf all N_ell
@@ -230,12 +251,14 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
   const int l0 = lc * LC;
   const int nl = min(LC, l_lo + n_l - l0);
   const double* A = amp + (size_t)w * N_tr;
-  for (int e = threadIdx.x; e < nl * N_tr * N_tr; e += DT) {
-    const int ll = e / (N_tr * N_tr), r = e - ll * N_tr * N_tr;
-    S[e] = (T)(Cf[((size_t)w * N_ell + l0 + ll) * N_tr * N_tr + r] * A[r % N_tr]);
+  for (int e = threadIdx.x; e < nl * N_tr * NP; e += DT) {
+    const int ll = e / (N_tr * NP), r = e - ll * N_tr * NP, j = r / NP, i = r - j * NP;
+    St[e] = i < N_tr ? (T)(Cf[((size_t)w * N_ell + l0 + ll) * N_tr * N_tr + i * N_tr + j] * A[j])
+                     : T(0);
   }
   for (int e = threadIdx.x; e < N_tr; e += DT) As[e] = (T)A[e];
   const T two_u = (q < N_k) ? (T)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : T(0);
+  const T* dq = Dl + threadIdx.x;
   T ps = 0, pc = 0;
   for (int ll = 0; ll < nl; ++ll) {
     __syncthreads();
@@ -245,14 +268,29 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
       Dl[t * DT + threadIdx.x] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
     __syncthreads();
     if (q < N_k) {
-      const T* Sl = S + ll * N_tr * N_tr;
+      const T* Sl = St + ll * N_tr * NP;
       T* db = dbar + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
-      for (int ii = 0; ii < N_tr; ++ii) {
-        T t = 0;
-        for (int j = 0; j < N_tr; ++j) t = fma(Sl[ii * N_tr + j], Dl[j * DT + threadIdx.x], t);
-        const T ai = As[ii];
-        two_sum_acc(ps, pc, ai * Dl[ii * DT + threadIdx.x] * t);
-        db[(size_t)ii * N_k + q] = two_u * ai * t;
+      for (int i0 = 0; i0 < N_tr; i0 += DG) {
+        T t[DG];
+#pragma unroll
+        for (int g = 0; g < DG; ++g) t[g] = 0;
+#pragma unroll 4
+        for (int j = 0; j < N_tr; ++j) {
+          T sv[DG];
+          lds4(Sl + j * NP + i0, sv);
+          const T d = dq[j * DT];
+#pragma unroll
+          for (int g = 0; g < DG; ++g) t[g] = fma(sv[g], d, t[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < DG; ++g) {
+          const int ii = i0 + g;
+          if (ii < N_tr) {
+            const T ai = As[ii];
+            two_sum_acc(ps, pc, ai * dq[ii * DT] * t[g]);
+            db[(size_t)ii * N_k + q] = two_u * ai * t[g];
+          }
+        }
       }
     }
   }
@@ -342,7 +380,7 @@ template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s) {
-  const size_t smem = (size_t)(LC * N_tr * N_tr + N_tr * DT + N_tr) * sizeof(T);
+  const size_t smem = (size_t)(LC * N_tr * delta_bar_pitch(N_tr) + N_tr * DT + N_tr) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
