@@ -97,7 +97,8 @@ def n_walk(w):
 
 def algorithmic_work(w, walkers, rank):
     """Algorithmic FLOPs per launch of each kernel and, for tensor-core kernels, the number of
-    compensated products each useful multiply-add costs ('Measurement')."""
+    compensated bf16 products each useful multiply-add costs (6 in basis mode: both operands in 3
+    planes, the products with plane indices summing to at most 2)."""
     n_h = w.N // 2 + 1
     ntr, nk, nl, ni, N = w.n_tr, len(w.k), len(w.ells), len(w.knots), w.N
     contraction = 4.0 * n_h * ntr * nk * nl * walkers          # Re sum_n of complex products
