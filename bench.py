@@ -10,7 +10,7 @@ before every timed step.  Under torchrun every rank evaluates its own parameter 
 scaling, no collective on the data path) and the slowest rank's time counts.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x9|tf32x6|3xtf32|fp64]
-                    [--walkers B] [--impl ours|reference]
+                    [--walkers B] [--impl ours|reference] [--sweep none|nell|cpu] [--limber L]
 
 --impl reference times the FP64 oracle (NumPy/SciPy on the host cores) on the same workload, one
 tracer's forward + VJP per step (15 steps = one evaluation), so that the default step count ends in
@@ -63,9 +63,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--sweep", default="none", choices=["none", "nell"],
+    ap.add_argument("--sweep", default="none", choices=["none", "nell", "cpu", "cpu-child"],
                     help="nell: time per evaluation against the number of multipoles (one JSON "
-                         "line per point and a linear fit), instead of the headline line")
+                         "line per point and a linear fit), instead of the headline line; cpu: the "
+                         "oracle on the host cores for each workload size, with the BLAS thread "
+                         "count pinned to one and to all cores")
     ap.add_argument("--limber", type=int, default=0,
                     help="Limber branch for multipoles >= this (0: off, the paper's setting)")
     return ap.parse_args()
@@ -294,6 +296,57 @@ class TracerSample:
         B = None if w.B is None else w.B[i:i + 1]
         f = O.forward(g, W, w.D, P, A, B)
         O.vjp(g, f, self.cb[:, i:i + 1, i:i + 1], W, w.D, P, A, B)
+
+
+def cpu_baseline_sweep_child(threads):
+    """The CPU-baseline leg at every workload size, one JSON line per workload: the oracle as it
+    stands, timed on the host cores with the BLAS thread count the parent pinned.  tiny2 and n5k
+    forward, n5k_vjp forward + VJP, and (all cores only) one forward pass of the large workload;
+    the Gamma-ratio tables are built before the timed region, as the paper excludes them."""
+    from oracle import fftlog as O
+    from workloads import make_workload
+    cases = [("tiny2", False, 3.0), ("n5k", False, 3.0), ("n5k_vjp", True, 3.0)]
+    if threads > 1:
+        cases.append(("large", False, 0.0))
+    for name, vjp, budget in cases:
+        w = make_workload(name)
+        g = oracle_grids(w)
+        for b in np.unique(w.fft_bias):
+            g.mtable(b)
+        W = w.W if w.W.ndim == 2 else w.W[0]
+        cb = None
+        if vjp:
+            cb = w.C_bar if w.C_bar.ndim == 3 else w.C_bar[0]
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            f = O.forward(g, W, w.D, w.P, w.amp, w.B)
+            if vjp:
+                O.vjp(g, f, cb, W, w.D, w.P, w.amp, w.B)
+            n += 1
+            if time.perf_counter() - t0 >= budget:
+                break
+        dt = time.perf_counter() - t0
+        print(json.dumps({"sweep": "cpu", "workload": name, "pass": "fwd+vjp" if vjp else "fwd",
+                          "blas_threads": threads, "cores": os.cpu_count(), "evals": n,
+                          "s_per_eval": dt / n, "evals_per_s": n / dt,
+                          "shape": {"n_tr": w.n_tr, "N": w.N, "n_k": len(w.k), "n_ell": len(w.ells),
+                                    "n_knots": len(w.knots)}}), flush=True)
+    return 0
+
+
+def cpu_baseline_sweep():
+    """The oracle's CPU cost per workload size with BLAS pinned to one thread and to all cores;
+    each setting runs in a child process, since BLAS fixes its thread count when it loads."""
+    for threads in (1, os.cpu_count() or 1):
+        env = dict(os.environ)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[var] = str(threads)
+        env["SWCL_CPU_SWEEP_THREADS"] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--sweep", "cpu-child"], env=env)
+        if r.returncode != 0:
+            return r.returncode
+    return 0
 
 
 # ----------------------------------------------------------------- our arm ----
@@ -526,6 +579,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.sweep == "cpu":
+        return cpu_baseline_sweep() if rank == 0 else 0
+    if args.sweep == "cpu-child":
+        return cpu_baseline_sweep_child(int(os.environ.get("SWCL_CPU_SWEEP_THREADS", os.cpu_count() or 1)))
     if args.impl == "reference":
         if rank != 0:
             return 0
