@@ -229,14 +229,34 @@ def swcl_last_error(ctx) -> str:
     return _lib.load().swcl_last_error(ctx).decode()
 
 
+def _need(a, n, what):
+    """ValueError unless array or tensor `a` (None allowed) holds exactly n elements: the C ABI
+    takes plain pointers, so the sizes are checked here, where the context's shapes are known."""
+    if a is None or n is None:
+        return
+    size = a.numel() if hasattr(a, "numel") else np.asarray(a).size
+    if size != n:
+        raise ValueError("%s has %d elements, expected %d" % (what, size, n))
+
+
 class Context:
-    """Owning wrapper: one swcl_ctx on one device."""
+    """Owning wrapper: one swcl_ctx on one device.  Its methods check every array's element count
+    against the shapes set so far before calling the library (the functions above do not)."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None):
         self.ptr = swcl_create(device, mem_budget_bytes, stream)
-        self.n_tr = self.n_ell = self.n_k = self.N = 0
+        self.n_tr = self.n_ell = self.n_k = self.N = self.n_knots = 0
         self.n_walk = 1
         self.n_out = 0
+
+    def _shape(self, *dims):
+        """Product of dims, or None (no check) while a dimension is still unset."""
+        n = 1
+        for d in dims:
+            if not d:
+                return None
+            n *= d
+        return n
 
     def close(self):
         if self.ptr:
@@ -251,7 +271,7 @@ class Context:
 
     def set_grids(self, chi_min, chi_max, N, k, ells, knots):
         swcl_set_grids(self.ptr, chi_min, chi_max, N, k, ells, knots)
-        self.N, self.n_k, self.n_ell = N, len(k), len(ells)
+        self.N, self.n_k, self.n_ell, self.n_knots = N, len(k), len(ells), len(knots)
         self.n_out = self.n_walk * self.n_ell
 
     def set_tracers(self, kind, fft_bias, taper_chi=None, taper_c=None):
@@ -260,12 +280,17 @@ class Context:
 
     def set_windows(self, W, D=None, B=None):
         n_walk = 1 if W.ndim == 2 else W.shape[0]
+        _need(W, self._shape(n_walk, self.n_tr, self.N), "W [n_walk][N_tr][N]")
+        _need(D, self._shape(self.n_knots, self.N), "D [N_knots][N]")
+        _need(B, self._shape(self.n_tr, self.n_knots, self.N), "B [N_tr][N_knots][N]")
         swcl_set_windows(self.ptr, n_walk, W, D, B)
         self.n_walk = n_walk
         self.n_out = n_walk * self.n_ell
 
     def set_power(self, P, amp):
         n_walk = 1 if P.ndim == 1 else P.shape[0]
+        _need(P, self._shape(n_walk, self.n_k), "P [n_walk][N_k]")
+        _need(amp, self._shape(n_walk, self.n_tr), "amp [n_walk][N_tr]")
         swcl_set_power(self.ptr, n_walk, P, amp)
         self.n_walk = n_walk
         self.n_out = n_walk * self.n_ell
@@ -284,10 +309,12 @@ class Context:
     def compute_cl(self, precision=SWCL_FP64, out=None):
         if out is None:
             out = np.empty((self.n_out, self.n_tr, self.n_tr))
+        _need(out, self._shape(self.n_out, self.n_tr, self.n_tr), "C_out [outputs][N_tr][N_tr]")
         swcl_compute_cl(self.ptr, precision, out)
         return out
 
     def vjp(self, C_bar, precision=SWCL_FP64, want_W=True):
+        _need(C_bar, self._shape(self.n_out, self.n_tr, self.n_tr), "C_bar [outputs][N_tr][N_tr]")
         P_bar = np.empty((self.n_walk, self.n_k))
         amp_bar = np.empty((self.n_walk, self.n_tr))
         W_bar = np.empty((self.n_walk, self.n_tr, self.N)) if want_W else None
@@ -301,6 +328,9 @@ class Context:
         """dC [n_dir][N_ell][N_tr][N_tr] along tangents P_dot [n_dir][N_k], amp_dot [n_dir][N_tr],
         W_dot [n_dir][N_tr][N] (None = zero) at the context's single parameter point."""
         n_dir = next(len(x) for x in (P_dot, amp_dot, W_dot) if x is not None)
+        _need(P_dot, self._shape(n_dir, self.n_k), "P_dot [n_dir][N_k]")
+        _need(amp_dot, self._shape(n_dir, self.n_tr), "amp_dot [n_dir][N_tr]")
+        _need(W_dot, self._shape(n_dir, self.n_tr, self.N), "W_dot [n_dir][N_tr][N]")
         out = np.empty((n_dir, self.n_ell, self.n_tr, self.n_tr))
         swcl_jvp(self.ptr, precision, n_dir, out, P_dot, amp_dot, W_dot)
         return out
@@ -309,6 +339,9 @@ class Context:
         """Fisher matrix (X = dC/dtheta) or chi^2 (X = C - C_data) with the Gaussian covariance
         of the last forward pass plus diagonal noise; modes[N_ell] = (2l+1) f_sky (bin width)."""
         F = np.empty((len(X), len(X)))
+        _need(X, self._shape(len(X), self.n_ell, self.n_tr, self.n_tr), "X [n_x][N_ell][N_tr][N_tr]")
+        _need(modes, self._shape(self.n_ell), "modes [N_ell]")
+        _need(noise, self._shape(self.n_tr), "noise [N_tr]")
         swcl_gaussian_fisher(self.ptr, X, modes, F, noise)
         return F
 
