@@ -37,6 +37,9 @@ METRIC = "C_ell evals/s (120 spectra×103 ℓ), fwd & fwd+grad, vs FP64 GPU path
 WORKLOAD = ("N5K-shaped: 15 tracers (10 Gaussian clustering + 5 Smail lensing bins), 120 spectra, "
             "103 log-spaced ell in [2,2000], N_FFT=2048, N_k=1024 in [1e-4,10] h/Mpc, N_I=150 k-knots, "
             "D(k,z)=(1+z)^-1(1+0.01 ln(k/0.1)); one evaluation = forward + VJP")
+WORKLOAD_LARGE = ("large: 30 tracers (20 Gaussian clustering bins, sigma_z=0.03 + 10 Smail lensing bins), "
+                  "465 spectra, every ell in [2,3000], N_FFT=4096, N_k=4096 in [1e-5,20] h/Mpc, N_I=200 "
+                  "k-knots, bias b(k,z)=b0(1+z)^0.5(1+0.1k^2) in B_i; one evaluation = forward + VJP")
 
 # measured peaks (MEASURED_PEAKS.json written by the pool driver); FP64 derived below
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM (FMA-loop probe: 1.19 TF/s at 2070 MHz)
@@ -70,16 +73,28 @@ def parse():
                          "count pinned to one and to all cores")
     ap.add_argument("--limber", type=int, default=0,
                     help="Limber branch for multipoles >= this (0: off, the paper's setting)")
+    ap.add_argument("--workload", default="n5k", choices=["n5k", "large"],
+                    help="large: one evaluation of the 30-tracer, 2999-multipole configuration "
+                         "(one GPU, one walker; no CPU baseline)")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="the context's memory budget in GiB (0: unlimited); a budget below the "
+                         "whole-Delta workspace makes the VJP recompute Delta chunk by chunk")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ inputs ----
 
-def make_inputs(walkers: int, rank: int, world: int):
+def make_inputs(walkers: int, rank: int, world: int, workload: str = "n5k"):
     """This rank's parameter points: walkers per GPU x world in all (weak scaling), the rank's
-    contiguous block from paper_2505_22718_gb300.sharding.shard."""
+    contiguous block from paper_2505_22718_gb300.sharding.shard.  The large workload is one
+    evaluation on one GPU, with a seeded N(0,1) cotangent."""
     from workloads import make_workload
     from paper_2505_22718_gb300.sharding import shard
+    if workload == "large":
+        if walkers != 1 or world != 1:
+            raise SystemExit("--workload large runs one evaluation on one GPU")
+        w = make_workload("large")
+        return w, np.random.default_rng(31).standard_normal((1, len(w.ells), w.n_tr, w.n_tr))
     if walkers <= 1 and world == 1:
         w = make_workload("n5k_vjp")
         return w, w.C_bar[None] if w.C_bar.ndim == 3 else w.C_bar
@@ -123,19 +138,19 @@ def algorithmic_work(w, walkers, rank):
 # the kernel source it was taken from (sha256 of the file; otherwise reported as null).
 TRAFFIC = {
     # profiles/basis_gemm_n5k_bf16.md (tiles 1120/1120: 96 columns, two K-blocks per stage; one walker)
-    "basis gemm adj": {"bytes": 25438720 + 0, "walkers": 1,
+    "basis gemm adj": {"bytes": 25438720 + 0, "walkers": 1, "workload": "n5k",
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
                        "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
-    "basis gemm fwd": {"bytes": 33252096 + 0, "walkers": 1,
+    "basis gemm fwd": {"bytes": 33252096 + 0, "walkers": 1, "workload": "n5k",
                        "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
                        "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
 }
 
 
-def traffic_for(name, walkers):
+def traffic_for(name, walkers, workload="n5k"):
     import hashlib
     t = TRAFFIC.get(name)
-    if not t or t["walkers"] != walkers:
+    if not t or t["walkers"] != walkers or t["workload"] != workload:
         return None
     try:
         with open(os.path.join(ROOT, t["src"]), "rb") as f:
@@ -146,7 +161,7 @@ def traffic_for(name, walkers):
     return t["bytes"]
 
 
-def roofline(stats, w, walkers, precision, peaks, src, rank):
+def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k"):
     if not stats:
         return None
     name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
@@ -166,13 +181,13 @@ def roofline(stats, w, walkers, precision, peaks, src, rank):
             peak = peaks["bf16_tflops"]
             unit_note = "bf16 burst peak"
         return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": tflops / peak, "traffic": traffic_for(name, walkers), "avg_ms": ms / launches,
+                "frac": tflops / peak, "traffic": traffic_for(name, walkers, workload), "avg_ms": ms / launches,
                 "launches": launches, "products": products,
                 "peak_source": "%s (%s)" % (src, unit_note),
                 "useful_tflops": flops / avg_s / 1e12}
     tflops = flops / avg_s / 1e12
     return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic_for(name, walkers), "avg_ms": ms / launches,
+            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic_for(name, walkers, workload), "avg_ms": ms / launches,
             "launches": launches,
             "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; FMA probe 1.19 TF/s)"}
 
@@ -359,13 +374,13 @@ def run_ours(args, rank, world, device):
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
     prec = swcl.PRECISIONS[args.precision]
-    w, cbar = make_inputs(args.walkers, rank, world)
+    w, cbar = make_inputs(args.walkers, rank, world, args.workload)
     nw = n_walk(w)
     # one dedicated stream: the library's kernels, the L2 flush and the timing events are
     # all ordered on it
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    ctx = swcl.Context(device, 0, stream.cuda_stream)
+    ctx = swcl.Context(device, int(args.budget_gb * (1 << 30)), stream.cuda_stream)
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     # the per-grid tables (Gamma ratios, phases, tracer powers) are built once, outside the step,
     # as the paper excludes them from its timings; their cost is reported beside the step
@@ -461,7 +476,8 @@ def run_ours(args, rank, world, device):
     peaks, src = load_peaks()
     rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
     out["tiles"] = {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)}
-    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r)
+    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r, args.workload)
+    out["recompute"] = ctx.query(swcl.SWCL_Q_RECOMPUTE)
     out["profile_rank"] = rank_r
     msf, _, _ = timed(fwd, args.steps, max(3, args.warmup // 2))
     out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",
@@ -639,7 +655,7 @@ def main():
     if rank == 0:
         cpu = None
         acc = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "n5k":
             cpu, f = cpu_baseline(w if n_walk(w) == 1 else w, cbar[:1] if cbar.ndim == 4 else cbar)
             if n_walk(w) == 1 and not args.limber:
                 Co = f["C"]
@@ -657,7 +673,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "walkers_per_gpu": n_walk(w), "precision": args.precision,
+                "config": {"workload": WORKLOAD if args.workload == "n5k" else WORKLOAD_LARGE,
+                           "walkers_per_gpu": n_walk(w), "precision": args.precision,
+                           "budget_gb": args.budget_gb or None, "delta_recomputed": bool(out["recompute"]),
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": "walkers sharded across ranks" if world > 1 else "1 GPU",
                            "profile_rank": out.get("profile_rank"), "gemm_tiles": out.get("tiles"),
