@@ -161,7 +161,12 @@ def traffic_for(name, walkers, workload="n5k"):
     return t["bytes"]
 
 
-def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k"):
+def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", steps=None,
+             recompute=False):
+    """Roofline of the longest kernel of the profiled steps.  The algorithmic work is per step:
+    when the multipoles run in chunks (a memory budget), a launch covers one chunk, so the work per
+    launch is the step's work over the step's launches of that kernel; with Delta recomputed in
+    the VJP, the forward contraction runs twice per step."""
     if not stats:
         return None
     name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
@@ -170,6 +175,9 @@ def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k"):
     avg_s = ms / launches / 1e3
     if flops is None:
         return {"kernel": name, "bound": None, "avg_ms": ms / launches, "note": "no algorithmic count"}
+    per_step = launches / steps if steps else 1.0
+    reps = 2 if recompute and name in ("basis gemm fwd", "contract fp64") else 1
+    flops = flops * reps / per_step
     if bound == "tensor":
         if products is None:
             products = {"3xtf32": 3, "tf32x6": 6, "bf16x9": 9}[precision]
@@ -476,8 +484,9 @@ def run_ours(args, rank, world, device):
     peaks, src = load_peaks()
     rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
     out["tiles"] = {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)}
-    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r, args.workload)
     out["recompute"] = ctx.query(swcl.SWCL_Q_RECOMPUTE)
+    out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r, args.workload,
+                               k_prof, bool(out["recompute"]))
     out["profile_rank"] = rank_r
     msf, _, _ = timed(fwd, args.steps, max(3, args.warmup // 2))
     out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",
