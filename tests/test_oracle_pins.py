@@ -191,7 +191,15 @@ def test_interpolation_exact_for_growth_linear_in_lnk(wl):
 # ---------------------------------------------------- k-quadrature (a4) ----
 
 def test_lnk_trapezoid_second_order():
-    """Reading R6: the rule integrates int k^2 e^-k dk over [1e-4, 30] with O(h^2) error."""
+    """Reading R6: the rule integrates int k^2 e^-k dk over [1e-4, 30] with O(h^2) error, and is
+    exact for integrands linear in ln k in the measure dln k = dk/k (which fixes the half
+    intervals at the two ends), on an uneven grid."""
+    k = np.sort(np.random.default_rng(3).uniform(1e-4, 30.0, 57))
+    w = O.lnk_trapezoid_weights(k)
+    lk = np.log(k)
+    for a, b in ((1.0, 0.0), (0.3, -1.7)):
+        exact = a * (lk[-1] - lk[0]) + 0.5 * b * (lk[-1] ** 2 - lk[0] ** 2)
+        assert abs(np.sum(w * (a + b * lk) / k) - exact) <= 1e-13 * max(abs(exact), 1.0)
     errs = []
     for n in (200, 400, 800):
         k = np.geomspace(1e-4, 30.0, n)
