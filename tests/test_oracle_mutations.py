@@ -1,14 +1,19 @@
 """Planted mistakes: each case replaces one function of the oracle, on the CPU, by a plausible
 wrong version of it (a dropped term, a wrong sign, index or weight) and checks that one of the
-oracle's pins in test_oracle_pins.py then fails.  This is the evidence that the pins constrain
-the oracle, rather than restate it.  Nothing here runs on the GPU or touches the CUDA path."""
+oracle's pins (test_oracle_pins.py, test_oracle_limber.py, test_oracle_forecast.py) then fails.
+This is the evidence that the pins constrain the oracle, rather than restate it.  Nothing here
+runs on the GPU or touches the CUDA path."""
 import numpy as np
 import pytest
 from scipy.special import loggamma
 
+import test_oracle_forecast as fpins
+import test_oracle_limber as lpins
 import test_oracle_pins as pins
 from conftest import cached_workload
 from oracle import fftlog as O
+from oracle import forecast as F
+from oracle import limber as LB
 
 
 def _printed_gamma_denominator(orig):
@@ -24,9 +29,9 @@ def _printed_gamma_denominator(orig):
 def _dft_sign_flipped(orig):
     # e^{+2 pi i n m / N}: for real samples, the conjugate of the right sum (the chi_min phase
     # and the Nyquist halving then act on the wrong coefficients)
-    def f(F, chi_min, chi_max, b, *a, **kw):
-        c = orig(F, chi_min, chi_max, b, *a, **kw)
-        n, eta = O.eta_two_sided(c.shape[-1] - 1, np.log(chi_max / chi_min))
+    def f(samples, chi_min, chi_max, b, *a, **kw):
+        c = orig(samples, chi_min, chi_max, b, *a, **kw)
+        _, eta = O.eta_two_sided(c.shape[-1] - 1, np.log(chi_max / chi_min))
         ph = np.exp(-1j * eta * np.log(chi_min))
         return np.conj(c / ph) * ph
     return f
@@ -42,8 +47,8 @@ def _nyquist_not_halved(orig):
 
 
 def _chi_min_phase_dropped(orig):
-    def f(F, chi_min, chi_max, b, *a, **kw):
-        c = orig(F, chi_min, chi_max, b, *a, **kw)
+    def f(samples, chi_min, chi_max, b, *a, **kw):
+        c = orig(samples, chi_min, chi_max, b, *a, **kw)
         _, eta = O.eta_two_sided(c.shape[-1] - 1, np.log(chi_max / chi_min))
         return c * np.exp(1j * eta * np.log(chi_min))
     return f
@@ -103,6 +108,33 @@ def _p_bar_without_measure(orig):
     return f
 
 
+def _limber_measure_without_inverse_chi(orig):
+    def f(g):
+        return orig(g) * g.chi
+    return f
+
+
+def _limber_p_bar_half(orig):
+    def f(*a, **kw):
+        Pb, Ab, Wb = orig(*a, **kw)
+        return 0.5 * Pb, Ab, Wb
+    return f
+
+
+def _fisher_full_modes(orig):
+    # nu_l in place of nu_l / 2
+    def f(C, X, noise, modes):
+        return 2.0 * orig(C, X, noise, modes)
+    return f
+
+
+def _jvp_without_amplitude_term(orig):
+    def f(*a, **kw):
+        kw["amp_dot"] = None
+        return orig(*a, **kw)
+    return f
+
+
 CASES = [
     ("printed Gamma denominator", "bessel_power_integral", _printed_gamma_denominator,
      lambda: pins.test_gamma_ratio_matches_mellin_integral()),
@@ -127,16 +159,26 @@ CASES = [
     ("2/pi in P_bar", "vjp", _p_bar_without_measure,
      lambda: pins.test_vjp_homogeneity_identities(cached_workload)),
 ]
+CASES = [(name, O, attr, mutate, pin) for name, attr, mutate, pin in CASES] + [
+    ("Limber measure dchi/chi^2", LB, "chi_weights", _limber_measure_without_inverse_chi,
+     lambda: lpins.test_closed_form_gaussian_windows()),
+    ("Limber P_bar", LB, "limber_vjp", _limber_p_bar_half,
+     lambda: lpins.test_limber_vjp_identities_and_differences(cached_workload)),
+    ("Fisher mode count", F, "gaussian_quad", _fisher_full_modes,
+     lambda: fpins.test_single_tracer_closed_form()),
+    ("JVP amplitude term", F, "jvp", _jvp_without_amplitude_term,
+     lambda: fpins.test_jvp_against_central_differences(cached_workload)),
+]
 
 
-@pytest.mark.parametrize("name,attr,mutate,pin", CASES, ids=[c[0] for c in CASES])
-def test_planted_mistake_fails_a_pin(name, attr, mutate, pin, monkeypatch):
-    monkeypatch.setattr(O, attr, mutate(getattr(O, attr)))
+@pytest.mark.parametrize("name,module,attr,mutate,pin", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_a_pin(name, module, attr, mutate, pin, monkeypatch):
+    monkeypatch.setattr(module, attr, mutate(getattr(module, attr)))
     with pytest.raises(AssertionError):
         pin()
 
 
 def test_unmutated_pins_pass():
     """The same pin calls pass against the oracle as it stands."""
-    for _, _, _, pin in CASES:
-        pin()
+    for case in CASES:
+        case[-1]()
