@@ -108,6 +108,23 @@ def _p_bar_without_measure(orig):
     return f
 
 
+def _rsd_moment_sign(orig):
+    # p (p + 1) I(p - 2) in place of p (p - 1) I(p - 2)
+    def f(ells, p):
+        p = np.asarray(p, dtype=np.complex128)
+        return orig(ells, p) * ((p + 1.0) / (p - 1.0))[None, :]
+    return f
+
+
+def _magnification_prefactor_sqrt(orig):
+    # the lensing prefactor sqrt((l+2)!/(l-2)!) in place of l(l+1)
+    def f(ells, kind):
+        if kind == O.KIND_MAGNIFICATION:
+            return orig(ells, O.KIND_LENSING)
+        return orig(ells, kind)
+    return f
+
+
 def _limber_measure_without_inverse_chi(orig):
     def f(g):
         return orig(g) * g.chi
@@ -158,6 +175,10 @@ CASES = [
      lambda: pins.test_vjp_homogeneity_identities(cached_workload)),
     ("2/pi in P_bar", "vjp", _p_bar_without_measure,
      lambda: pins.test_vjp_homogeneity_identities(cached_workload)),
+    ("RSD moment p(p-1)", "bessel2_power_integral", _rsd_moment_sign,
+     lambda: pins.test_rsd_delta_matches_brute_force()),
+    ("magnification prefactor", "ell_prefactor", _magnification_prefactor_sqrt,
+     lambda: pins.test_magnification_delta_matches_brute_force(cached_workload)),
 ]
 CASES = [(name, O, attr, mutate, pin) for name, attr, mutate, pin in CASES] + [
     ("Limber measure dchi/chi^2", LB, "chi_weights", _limber_measure_without_inverse_chi,
