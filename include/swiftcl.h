@@ -64,7 +64,9 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_ERR_OOM_BUDGET  (-3)  /* the request does not fit the context's memory budget */
 #define SWCL_ERR_CUDA        (-4)  /* a CUDA runtime call failed (message has the CUDA error) */
 #define SWCL_ERR_TIMEOUT     (-5)  /* a bounded device wait gave up */
-#define SWCL_ERR_NONFINITE   (-6)  /* an input or output contains NaN or Inf */
+#define SWCL_ERR_NONFINITE   (-6)  /* reserved for NaN/Inf checks; no call returns it yet: the
+                                      library does not scan its inputs, and a NaN or Inf input
+                                      propagates to the outputs it reaches */
 #define SWCL_ERR_STATE       (-7)  /* call out of order (e.g. compute before set_grids) */
 
 /* tracer kinds */
