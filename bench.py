@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the sub-records (general profile, 256-walker batch) and the TF32/FP64 "
+                         "peak measurement")
     ap.add_argument("--sweep", default="none", choices=["none", "nell", "cpu", "cpu-child"],
                     help="nell: time per evaluation against the number of multipoles (one JSON "
                          "line per point and a linear fit), instead of the headline line; cpu: the "
@@ -112,13 +115,17 @@ def n_walk(w):
 
 # ---------------------------------------------------------------- roofline ----
 
-def algorithmic_work(w, walkers, rank):
+def algorithmic_work(w, walkers, rank, n_ell_useful=None):
     """Algorithmic FLOPs per launch of each kernel and, for tensor-core kernels, the number of
-    compensated bf16 products each useful multiply-add costs (6 in basis mode: both operands in 3
-    planes, the products with plane indices summing to at most 2)."""
+    compensated products each useful multiply-add costs (6 in basis mode: both operands in 3 bf16
+    planes, the products with plane indices summing to at most 2; 9 for the knot-stencil bf16x9
+    form; 3 or 6 for the TF32 forms).  The useful work of the contraction is
+    4 n_h N_tr N_k N_ell per parameter point (the real form of the complex sum over n); with
+    ragged multipole lists only the listed multipoles count (n_ell_useful = sum over walkers)."""
     n_h = w.N // 2 + 1
     ntr, nk, nl, ni, N = w.n_tr, len(w.k), len(w.ells), len(w.knots), w.N
-    contraction = 4.0 * n_h * ntr * nk * nl * walkers          # Re sum_n of complex products
+    ell_units = n_ell_useful if n_ell_useful is not None else nl * walkers
+    contraction = 4.0 * n_h * ntr * nk * ell_units
     rows = rank if rank else ni                                 # FFT rows per tracer
     fft = 2.5 * N * np.log2(N) * ntr * rows * walkers           # real FFT of length N per row
     return {
@@ -161,16 +168,60 @@ def traffic_for(name, walkers, workload="n5k"):
     return t["bytes"]
 
 
+def measure_matmul_peaks(dev):
+    """TF32 and FP64 dense rates of this GPU, measured here the way the bf16 peaks of
+    MEASURED_PEAKS.json were: cuBLAS through torch.matmul, best of 5 after warm-up, CUDA events
+    (TF32: 8192^3 with TF32 tensor cores allowed; FP64: 4096^3).  Used only as roofline
+    denominators: the library itself calls no cuBLAS."""
+    import torch
+    out = {}
+    cases = (("tf32_tflops", torch.float32, 8192), ("fp64_tflops", torch.float64, 4096))
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = True
+        for key, dt, n in cases:
+            a = torch.randn(n, n, device=dev, dtype=dt)
+            b = torch.randn(n, n, device=dev, dtype=dt)
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[key] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    out["how"] = ("torch.matmul (cuBLAS), best of 5: TF32 8192^3 with allow_tf32, FP64 4096^3; "
+                  "2 n^3 flops / CUDA-event time")
+    return out
+
+
 def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", steps=None,
-             recompute=False):
-    """Roofline of the longest kernel of the profiled steps.  The algorithmic work is per step:
-    when the multipoles run in chunks (a memory budget), a launch covers one chunk, so the work per
-    launch is the step's work over the step's launches of that kernel; with Delta recomputed in
-    the VJP, the forward contraction runs twice per step."""
+             recompute=False, kernel=None, n_ell_useful=None):
+    """Roofline of one kernel of the profiled steps (default: the longest).  `achieved` is the
+    method's useful work (algorithmic_work) per launch over the kernel's average CUDA-event time,
+    and `frac` is that over the measured peak of the kernel's arithmetic (bf16 burst from
+    MEASURED_PEAKS.json for the split-bf16 GEMMs; TF32 and FP64 matmul rates measured in this run).
+    `pipe_occupancy` counts every compensated product the kernel executes (useful x products):
+    how busy the tensor pipe is, not how fast the method runs.  When the multipoles run in chunks
+    (a memory budget) a launch covers one chunk, so the work per launch is the step's work over
+    the step's launches of that kernel; with Delta recomputed in the VJP, the forward contraction
+    runs twice per step."""
     if not stats:
         return None
-    name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
-    work = algorithmic_work(w, walkers, rank)
+    if kernel is None:
+        name, (launches, ms) = max(stats.items(), key=lambda kv: kv[1][1])
+    else:
+        if kernel not in stats:
+            return None
+        name, (launches, ms) = kernel, stats[kernel]
+    work = algorithmic_work(w, walkers, rank, n_ell_useful)
     bound, flops, products = work.get(name, ("alu", None, 1))
     avg_s = ms / launches / 1e3
     if flops is None:
@@ -178,26 +229,33 @@ def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", ste
     per_step = launches / steps if steps else 1.0
     reps = 2 if recompute and name in ("basis gemm fwd", "contract fp64") else 1
     flops = flops * reps / per_step
+    useful = flops / avg_s / 1e12
     if bound == "tensor":
         if products is None:
             products = {"3xtf32": 3, "tf32x6": 6, "bf16x9": 9}[precision]
-        tflops = flops * products / avg_s / 1e12
         if precision in ("3xtf32", "tf32x6") and not name.startswith("basis"):
-            peak = peaks["bf16_tflops"] * TF32_OVER_BF16
-            unit_note = "tf32 peak = measured bf16 burst x nominal tf32/bf16 ratio"
+            if peaks.get("tf32_tflops"):
+                peak, note = peaks["tf32_tflops"], "tf32 dense rate measured in this run (cuBLAS)"
+            else:
+                peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+                note = "tf32 peak = measured bf16 burst x nominal tf32/bf16 ratio"
         else:
-            peak = peaks["bf16_tflops"]
-            unit_note = "bf16 burst peak"
-        return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": tflops / peak, "traffic": traffic_for(name, walkers, workload), "avg_ms": ms / launches,
-                "launches": launches, "products": products,
-                "peak_source": "%s (%s)" % (src, unit_note),
-                "useful_tflops": flops / avg_s / 1e12}
-    tflops = flops / avg_s / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic_for(name, walkers, workload), "avg_ms": ms / launches,
-            "launches": launches,
-            "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; FMA probe 1.19 TF/s)"}
+            peak, note = peaks["bf16_tflops"], "bf16 burst peak (%s)" % src
+        return {"kernel": name, "bound": "tensor", "achieved": useful, "peak": peak, "unit": "TFLOP/s",
+                "frac": useful / peak, "pipe_occupancy": useful * products / peak,
+                "products": products, "traffic": traffic_for(name, walkers, workload),
+                "avg_ms": ms / launches, "launches": launches, "peak_source": note,
+                "work": "4 n_h N_tr N_k N_ell useful flops per evaluation (%.3g per launch)" % flops}
+    if peaks.get("fp64_tflops"):
+        peak = peaks["fp64_tflops"]
+        note = "FP64 dense rate measured in this run (cuBLAS DGEMM); derived DFMA pipe %.2f TF/s" % FP64_PEAK_TFLOPS
+    else:
+        peak = FP64_PEAK_TFLOPS
+        note = "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"
+    return {"kernel": name, "bound": "alu", "achieved": useful, "peak": peak, "unit": "TFLOP/s",
+            "frac": useful / peak, "traffic": traffic_for(name, walkers, workload),
+            "avg_ms": ms / launches, "launches": launches, "peak_source": note,
+            "work": "%.3g useful flops per launch" % flops}
 
 
 # ------------------------------------------------------------------ clocks ----
@@ -374,6 +432,54 @@ def cpu_baseline_sweep():
 
 # ----------------------------------------------------------------- our arm ----
 
+class Step:
+    """The library calls of one timed step on device buffers: forward + VJP (or forward only) of
+    every walker as one CUDA-graph replay, and the same kernels launched one by one for per-kernel
+    CUDA-event timing."""
+
+    def __init__(self, swcl, ctx, C, Cb, Pb, Ab, Wb):
+        self.swcl, self.ctx = swcl, ctx
+        self.C, self.Cb, self.Pb, self.Ab, self.Wb = C, Cb, Pb, Ab, Wb
+
+    def full(self, p):
+        self.swcl.swcl_compute_batched(self.ctx.ptr, p, self.C, self.Cb, self.Pb, self.Ab, self.Wb)
+        return self.ctx.query(self.swcl.SWCL_Q_KERNEL_LAUNCHES)
+
+    def fwd(self, p):
+        self.swcl.swcl_compute_batched(self.ctx.ptr, p, self.C)
+        return self.ctx.query(self.swcl.SWCL_Q_KERNEL_LAUNCHES)
+
+    def profiled(self, p):
+        # per-kernel event timing needs the kernels launched one by one (not from a graph)
+        self.swcl.swcl_compute_cl(self.ctx.ptr, p, self.C)
+        n1 = self.ctx.query(self.swcl.SWCL_Q_KERNEL_LAUNCHES)
+        self.swcl.swcl_vjp(self.ctx.ptr, p, self.Cb, self.Pb, self.Ab, self.Wb)
+        return n1 + self.ctx.query(self.swcl.SWCL_Q_KERNEL_LAUNCHES)
+
+
+def device_inputs(swcl, ctx, w, cbar, dev, with_grids=True):
+    """Sets the workload on the context from device tensors and returns the Step buffers."""
+    import torch
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    if with_grids:
+        ctx.set_grids(w.chi_min, w.chi_max, w.N, w.k, w.ells, w.knots)
+        ctx.set_tracers(w.kind, w.fft_bias)
+    ctx.set_windows(t(w.W), t(w.D), None if w.B is None else t(w.B))
+    ctx.set_power(t(w.P), t(w.amp))
+    nw = n_walk(w)
+    if w.ell_lists is not None:
+        ctx.set_ell_lists(w.ell_lists)
+        n_out = sum(len(x) for x in w.ell_lists)
+    else:
+        n_out = nw * len(w.ells)
+    C = torch.empty((n_out, w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
+    Cb = t(np.asarray(cbar).reshape(C.shape))
+    Pb = torch.empty((nw, len(w.k)), dtype=torch.float64, device=dev)
+    Ab = torch.empty((nw, w.n_tr), dtype=torch.float64, device=dev)
+    Wb = torch.empty((nw, w.n_tr, w.N), dtype=torch.float64, device=dev)
+    return Step(swcl, ctx, C, Cb, Pb, Ab, Wb)
+
+
 def run_ours(args, rank, world, device):
     import torch
     import paper_2505_22718_gb300 as swcl
@@ -389,7 +495,6 @@ def run_ours(args, rank, world, device):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = swcl.Context(device, int(args.budget_gb * (1 << 30)), stream.cuda_stream)
-    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     # the per-grid tables (Gamma ratios, phases, tracer powers) are built once, outside the step,
     # as the paper excludes them from its timings; their cost is reported beside the step
     torch.cuda.synchronize(dev)
@@ -398,47 +503,22 @@ def run_ours(args, rank, world, device):
     ctx.set_tracers(w.kind, w.fft_bias)
     torch.cuda.synchronize(dev)
     tables_ms = (time.perf_counter() - t_tab) * 1e3
-    W_d, D_d = t(w.W), t(w.D)
-    P_d, A_d = t(w.P), t(w.amp)
-    ctx.set_windows(W_d, D_d, None if w.B is None else t(w.B))
-    ctx.set_power(P_d, A_d)
+    st = device_inputs(swcl, ctx, w, cbar, dev, with_grids=False)
     if args.limber:
         ctx.set_limber(args.limber)
-    C_d = torch.empty((nw * len(w.ells), w.n_tr, w.n_tr), dtype=torch.float64, device=dev)
-    Cb_d = t(cbar.reshape(C_d.shape))
-    Pb_d = torch.empty((nw, len(w.k)), dtype=torch.float64, device=dev)
-    Ab_d = torch.empty((nw, w.n_tr), dtype=torch.float64, device=dev)
-    Wb_d = torch.empty((nw, w.n_tr, w.N), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    # a step is one CUDA-graph replay of the forward + VJP kernels of all walkers of this GPU
-    def step(p=prec):
-        swcl.swcl_compute_batched(ctx.ptr, p, C_d, Cb_d, Pb_d, Ab_d, Wb_d)
-        return ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
-
-    def fwd(p=prec):
-        swcl.swcl_compute_batched(ctx.ptr, p, C_d)
-        return ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
-
-    def step_profiled(p=prec):
-        # per-kernel event timing needs the kernels launched one by one (not from a graph)
-        swcl.swcl_compute_cl(ctx.ptr, p, C_d)
-        n1 = ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
-        swcl.swcl_vjp(ctx.ptr, p, Cb_d, Pb_d, Ab_d, Wb_d)
-        return n1 + ctx.query(swcl.SWCL_Q_KERNEL_LAUNCHES)
-
     last = {}
 
-    def timed(fn, steps, warmup, profile=False):
+    def timed(fn, steps, warmup, profile_ctx=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
-        if profile:
-            swcl.swcl_profile_reset(ctx.ptr)
-            swcl.swcl_profile_enable(ctx.ptr, True)
+        if profile_ctx is not None:
+            swcl.swcl_profile_reset(profile_ctx.ptr)
+            swcl.swcl_profile_enable(profile_ctx.ptr, True)
         evs = []
         launches = 0
         for _ in range(steps):
@@ -451,9 +531,9 @@ def run_ours(args, rank, world, device):
             evs.append((e0, e1))
         torch.cuda.synchronize(dev)
         stats = None
-        if profile:
-            stats = swcl.swcl_profile_read(ctx.ptr)
-            swcl.swcl_profile_enable(ctx.ptr, False)
+        if profile_ctx is not None:
+            stats = swcl.swcl_profile_read(profile_ctx.ptr)
+            swcl.swcl_profile_enable(profile_ctx.ptr, False)
         per = [a.elapsed_time(b) for a, b in evs]
         last["median_ms"] = statistics.median(per)
         ms = sum(per)
@@ -466,68 +546,76 @@ def run_ours(args, rank, world, device):
     clocks = ClockSampler(device) if rank == 0 else None
     if clocks:
         clocks.start()
-    ms, launches, _ = timed(step, args.steps, args.warmup)
+    ms, launches, _ = timed(lambda: st.full(prec), args.steps, args.warmup)
     clk = clocks.stop() if clocks else None
     ms_step = ms / args.steps
     out["ms_per_step_median"] = last["median_ms"]
     out["tables_ms"] = tables_ms
+    peaks, src = load_peaks()
+    if rank == 0 and not args.no_extra:
+        peaks = dict(peaks)
+        peaks.update(measure_matmul_peaks(dev))
+        out["peaks_measured_here"] = {k: peaks[k] for k in ("tf32_tflops", "fp64_tflops", "how")}
     # per-kernel device times for the roofline: the same step launched kernel by kernel with
     # CUDA events around each kernel on the library's stream
     k_prof = max(3, min(args.steps, 200))
-    _, _, stats = timed(step_profiled, k_prof, 2, profile=True)
+    _, _, stats = timed(lambda: st.profiled(prec), k_prof, 2, profile_ctx=ctx)
     value = nw * world / (ms_step / 1e3)
     out["value"] = value
     out["ms_per_step"] = ms_step
     out["gpu_launches"] = launches    # kernels of the graph replays in the timed region
+    out["kernels_per_step"] = launches // max(args.steps, 1)
     out["clocks"] = clk
     out["kernel_ms"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in (stats or {}).items()}
-    peaks, src = load_peaks()
     rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
     out["tiles"] = {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)}
     out["recompute"] = ctx.query(swcl.SWCL_Q_RECOMPUTE)
     out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r, args.workload,
                                k_prof, bool(out["recompute"]))
     out["profile_rank"] = rank_r
-    msf, _, _ = timed(fwd, args.steps, max(3, args.warmup // 2))
+    msf, _, _ = timed(lambda: st.fwd(prec), args.steps, max(3, args.warmup // 2))
     out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",
                        "ms_per_step": msf / args.steps}
     if not args.no_fp64_compare and args.precision != "fp64":
         k64 = max(3, args.steps // 20)
-        ms64, _, _ = timed(lambda: step(swcl.SWCL_FP64), k64, 2)
+        ms64, _, _ = timed(lambda: st.full(swcl.SWCL_FP64), k64, 2)
+        _, _, st64 = timed(lambda: st.profiled(swcl.SWCL_FP64), 3, 1, profile_ctx=ctx)
         out["fp64_gpu_path"] = {"value": nw * world / (ms64 / k64 / 1e3), "unit": "evals/s",
-                                "ms_per_step": ms64 / k64}
+                                "ms_per_step": ms64 / k64,
+                                "roofline": roofline(st64, w, nw, "fp64", peaks, src, rank_r,
+                                                     args.workload, 3, bool(out["recompute"]))}
     # result of this precision (rank 0, walker 0) for the accuracy check against the oracle
-    step()
+    st.full(prec)
     torch.cuda.synchronize(dev)
-    out["_C0"] = C_d[:len(w.ells)].cpu().numpy()
+    out["_C0"] = st.C[:len(w.ells)].cpu().numpy()
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: the per-step inputs of a
+    # sampler (window samples, P(k), amplitudes, cotangent) go host -> device, the graph replays,
+    # and every result comes back; D (growth at the knots) was set once with the windows
     if not args.no_e2e:
         def pinned(a):
             h = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
             h.numpy()[...] = a
             return h
-        W_h, D_h, P_h, A_h = pinned(w.W), pinned(w.D), pinned(w.P), pinned(w.amp)
-        B_h = None if w.B is None else pinned(w.B)
-        Cb_h = pinned(cbar.reshape(C_d.shape))
-        C_h = torch.empty(C_d.shape, dtype=torch.float64, pin_memory=True)
-        Pb_h = torch.empty(Pb_d.shape, dtype=torch.float64, pin_memory=True)
-        Ab_h = torch.empty(Ab_d.shape, dtype=torch.float64, pin_memory=True)
-        Wb_h = torch.empty(Wb_d.shape, dtype=torch.float64, pin_memory=True)
+        W_h, P_h, A_h = pinned(w.W), pinned(w.P), pinned(w.amp)
+        Cb_h = pinned(np.asarray(cbar).reshape(st.C.shape))
+        C_h = torch.empty(st.C.shape, dtype=torch.float64, pin_memory=True)
+        Pb_h = torch.empty(st.Pb.shape, dtype=torch.float64, pin_memory=True)
+        Ab_h = torch.empty(st.Ab.shape, dtype=torch.float64, pin_memory=True)
+        Wb_h = torch.empty(st.Wb.shape, dtype=torch.float64, pin_memory=True)
 
         def e2e_step():
-            # host -> device inputs through the public API, the graph replay, device -> host results
-            swcl.swcl_set_windows(ctx.ptr, nw, W_h, D_h, B_h)
+            swcl.swcl_set_window_samples(ctx.ptr, nw, W_h)
             swcl.swcl_set_power(ctx.ptr, nw, P_h, A_h)
-            Cb_d.copy_(Cb_h, non_blocking=True)
-            swcl.swcl_compute_batched(ctx.ptr, prec, C_d, Cb_d, Pb_d, Ab_d, Wb_d)
-            C_h.copy_(C_d, non_blocking=True)
-            Pb_h.copy_(Pb_d, non_blocking=True)
-            Ab_h.copy_(Ab_d, non_blocking=True)
-            Wb_h.copy_(Wb_d, non_blocking=True)
+            st.Cb.copy_(Cb_h, non_blocking=True)
+            swcl.swcl_compute_batched(ctx.ptr, prec, st.C, st.Cb, st.Pb, st.Ab, st.Wb)
+            C_h.copy_(st.C, non_blocking=True)
+            Pb_h.copy_(st.Pb, non_blocking=True)
+            Ab_h.copy_(st.Ab, non_blocking=True)
+            Wb_h.copy_(st.Wb, non_blocking=True)
             torch.cuda.current_stream(dev).synchronize()
 
-        for _ in range(max(2, args.warmup // 2)):
+        for _ in range(max(3, args.warmup // 2)):
             e2e_step()
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -539,13 +627,97 @@ def run_ours(args, rank, world, device):
         el = time.perf_counter() - t0
         if world > 1:
             el = max_over_ranks(el, dev)
-        h2d = sum(x.numel() * 8 for x in (W_h, D_h, P_h, A_h, Cb_h) if x is not None)
-        h2d += 0 if B_h is None else B_h.numel() * 8
+        h2d = sum(x.numel() * 8 for x in (W_h, P_h, A_h, Cb_h))
         d2h = sum(x.numel() * 8 for x in (C_h, Pb_h, Ab_h, Wb_h))
         out["e2e"] = {"value": nw * world * args.steps / el, "unit": "evals/s", "h2d_bytes_per_step": h2d,
-                      "d2h_bytes_per_step": d2h}
+                      "d2h_bytes_per_step": d2h,
+                      "calls": "swcl_set_window_samples + swcl_set_power + cotangent copy + "
+                               "swcl_compute_batched + result copies, one stream sync per step"}
     ctx.close()
+    del st
+    if rank == 0 and world == 1 and args.workload == "n5k" and not args.no_extra:
+        out["general_profile"] = run_general_profile(args, dev, stream, flush, timed, peaks, src)
+        out["batched"] = run_batched(args, dev, stream, timed, peaks, src)
     return out, w, cbar
+
+
+def run_general_profile(args, dev, stream, flush, timed, peaks, src):
+    """Sub-record for a growth that is not of low rank (n5k_general): one FFTLog per k-knot and
+    the knot-stencil tcgen05 kernels (Sec. 3.2's interpolation along k in their producers).
+    Forward + VJP and forward-only evals/s, the FP64 GPU path on the same inputs, the roofline
+    of both contraction kernels, and the normalised C error against the oracle."""
+    import torch
+    import paper_2505_22718_gb300 as swcl
+    from workloads import make_workload
+    w = make_workload("n5k_general")
+    prec = swcl.PRECISIONS[args.precision]
+    ctx = swcl.Context(dev.index, 0, stream.cuda_stream)
+    st = device_inputs(swcl, ctx, w, w.C_bar[None], dev)
+    steps = max(3, min(args.steps, 200))
+    ms, launches, _ = timed(lambda: st.full(prec), steps, 3)
+    msf, _, _ = timed(lambda: st.fwd(prec), steps, 3)
+    _, _, stats = timed(lambda: st.profiled(prec), 10, 2, profile_ctx=ctx)
+    rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
+    rec = {"workload": "N5K shape with D(k,z) = (1+z)^-1 exp(0.02 ln(k/0.1) g(z)) (profiles of high "
+                       "rank: one FFTLog per knot, 150 knots per tracer)",
+           "profile_rank": rank_r, "value": 1e3 * steps / ms, "unit": "evals/s", "ms_per_step": ms / steps,
+           "fwd_only": {"value": 1e3 * steps / msf, "ms_per_step": msf / steps},
+           "kernels_per_step": launches // steps,
+           "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in stats.items()},
+           "roofline": roofline(stats, w, 1, args.precision, peaks, src, rank_r, "n5k_general", 10),
+           "roofline_fwd_contraction": roofline(stats, w, 1, args.precision, peaks, src, rank_r,
+                                                "n5k_general", 10, kernel="contract tc"),
+           "roofline_adj_contraction": roofline(stats, w, 1, args.precision, peaks, src, rank_r,
+                                                "n5k_general", 10, kernel="contract adj tc")}
+    if not args.no_fp64_compare:
+        ms64, _, _ = timed(lambda: st.full(swcl.SWCL_FP64), 3, 1)
+        rec["fp64_gpu_path"] = {"value": 3e3 / ms64, "unit": "evals/s", "ms_per_step": ms64 / 3}
+    st.full(prec)
+    torch.cuda.synchronize(dev)
+    C = st.C.cpu().numpy()
+    ctx.close()
+    if not args.no_cpu_baseline:
+        from oracle import fftlog as O
+        g = oracle_grids(w)
+        Co = O.forward(g, w.W, w.D, w.P, w.amp, w.B)["C"]
+        dg = np.abs(np.einsum("lii->li", Co))
+        floor = 1e-3 * np.sqrt(dg[:, :, None] * dg[:, None, :])
+        rec["accuracy"] = {"max_norm_err_vs_oracle": float(np.max(np.abs(C - Co) / np.maximum(np.abs(Co), floor))),
+                           "gate": 1e-4}
+    return rec
+
+
+def run_batched(args, dev, stream, timed, peaks, src, n_walkers=256):
+    """Sub-record for the batched configuration: 256 parameter points with their own P(k)
+    amplitude and tilt, clustering amplitudes and window shifts, and ragged multipole lists
+    (50-103 of the 103), forward + VJP and forward-only as one CUDA-graph replay per step.
+    evals/s counts parameter points; the roofline counts only the listed multipoles as useful."""
+    import paper_2505_22718_gb300 as swcl
+    from workloads import make_workload
+    w = make_workload("walkers", n_walkers=n_walkers)
+    n_out = sum(len(x) for x in w.ell_lists)
+    cbar = np.random.default_rng(99).standard_normal((n_out, w.n_tr, w.n_tr))
+    prec = swcl.PRECISIONS[args.precision]
+    ctx = swcl.Context(dev.index, 0, stream.cuda_stream)
+    st = device_inputs(swcl, ctx, w, cbar, dev)
+    steps = max(3, min(args.steps // 40, 50))
+    ms, launches, _ = timed(lambda: st.full(prec), steps, 3)
+    msf, _, _ = timed(lambda: st.fwd(prec), steps, 3)
+    _, _, stats = timed(lambda: st.profiled(prec), 3, 1, profile_ctx=ctx)
+    rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
+    rec = {"walkers": n_walkers, "listed_multipoles": n_out,
+           "value": n_walkers * 1e3 * steps / ms, "unit": "evals/s", "ms_per_step": ms / steps,
+           "fwd_only": {"value": n_walkers * 1e3 * steps / msf, "ms_per_step": msf / steps},
+           "kernels_per_step": launches // steps, "tiles": {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD),
+                                                            "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)},
+           "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in stats.items()},
+           "roofline": roofline(stats, w, n_walkers, args.precision, peaks, src, rank_r, "walkers", 3,
+                                n_ell_useful=n_out)}
+    if not args.no_fp64_compare:
+        ms64, _, _ = timed(lambda: st.full(swcl.SWCL_FP64), 2, 1)
+        rec["fp64_gpu_path"] = {"value": n_walkers * 2e3 / ms64, "unit": "evals/s", "ms_per_step": ms64 / 2}
+    ctx.close()
+    return rec
 
 
 def run_sweep_nell(args, device):
@@ -693,7 +865,10 @@ def main():
                 "clocks": out["clocks"], "gpu_launches": out["gpu_launches"],
                 "ms_per_step_median": out["ms_per_step_median"], "tables_ms": out["tables_ms"],
                 "fwd_only": out["fwd_only"], "fp64_gpu_path": out.get("fp64_gpu_path"),
-                "accuracy": acc, "kernel_ms": out["kernel_ms"]}
+                "accuracy": acc, "kernel_ms": out["kernel_ms"],
+                "kernels_per_step": out["kernels_per_step"],
+                "peaks_measured_here": out.get("peaks_measured_here"),
+                "general_profile": out.get("general_profile"), "batched": out.get("batched")}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -64,9 +64,12 @@ typedef struct swcl_ctx swcl_ctx;
 #define SWCL_ERR_OOM_BUDGET  (-3)  /* the request does not fit the context's memory budget */
 #define SWCL_ERR_CUDA        (-4)  /* a CUDA runtime call failed (message has the CUDA error) */
 #define SWCL_ERR_TIMEOUT     (-5)  /* a bounded device wait gave up */
-#define SWCL_ERR_NONFINITE   (-6)  /* reserved for NaN/Inf checks; no call returns it yet: the
-                                      library does not scan its inputs, and a NaN or Inf input
-                                      propagates to the outputs it reaches */
+#define SWCL_ERR_NONFINITE   (-6)  /* an output holds a NaN or Inf: the kernels that write C,
+                                      P_bar, amp_bar, W_bar and dC test every value they store
+                                      and raise the context's status word, which the next
+                                      synchronising call (swcl_sync, or a call with host outputs)
+                                      reports and clears.  Inputs are not scanned: a NaN or Inf
+                                      input shows up in the outputs it reaches */
 #define SWCL_ERR_STATE       (-7)  /* call out of order (e.g. compute before set_grids) */
 
 /* tracer kinds */
@@ -129,6 +132,15 @@ int swcl_set_tracers(swcl_ctx* ctx, int N_tr, const int* kind, const double* fft
  * knots (NULL = 1).  Window samples may differ per walker; D and B are shared. */
 int swcl_set_windows(swcl_ctx* ctx, int n_walk, const double* W, const double* D, const double* B);
 
+/* New window samples W[n_walk][N_tr][N] for the same parameter points, keeping D, B and the
+ * profile factorisation of the last swcl_set_windows (no comparison of D and B, hence no host
+ * wait: a host W up to 1 MiB goes through the context's pinned staging ring and the call returns
+ * at once; a larger host W is waited for).  n_walk must equal that of the last swcl_set_windows.
+ * This is the per-step input of a sampler whose windows move (mean shifts, Sec. 4.3) while the
+ * growth and bias tables stay fixed.  Errors: SWCL_ERR_STATE before swcl_set_windows,
+ * SWCL_ERR_INVALID_ARG. */
+int swcl_set_window_samples(swcl_ctx* ctx, int n_walk, const double* W);
+
 /* Power spectrum and amplitudes: P[n_walk][N_k] = P(k_q, z_fid) (Eq. 2.3), amp[n_walk][N_tr] = A_i
  * (linear bias for density, amplitude for lensing). */
 int swcl_set_power(swcl_ctx* ctx, int n_walk, const double* P, const double* amp);
@@ -150,8 +162,9 @@ int swcl_set_ell_lists(swcl_ctx* ctx, const int* offsets, const int* ell_idx);
  * is O(1/l) (Eq. 2.19); the switch trades it for the FFTLog work of those multipoles. */
 int swcl_set_limber(swcl_ctx* ctx, int ell_switch);
 
-/* Forward pass a1-a4 for every walker./* Forward pass a1-a4 for every walker.  C_out[sum_w n_ell(w)][N_tr][N_tr] (full symmetric
- * matrices, C^{ij} = C^{ji} bit for bit). */
+/* Forward pass a1-a4 for every walker.  C_out[sum_w n_ell(w)][N_tr][N_tr] (full symmetric
+ * matrices, C^{ij} = C^{ji} bit for bit).  A host C_out makes the call synchronous and reports
+ * SWCL_ERR_NONFINITE or SWCL_ERR_TIMEOUT from the device status word. */
 int swcl_compute_cl(swcl_ctx* ctx, int precision, double* C_out);
 
 /* Vector-Jacobian product (a5) of the last swcl_compute_cl for the same precision.

@@ -13,7 +13,7 @@ from .api import (  # noqa: F401
     SWCL_Q_WORKSPACE_BYTES, SWCL_Q_RECOMPUTE, SWCL_Q_N_HALF, SWCL_Q_KERNEL_LAUNCHES,
     SWCL_Q_PROFILE_RANK, SWCL_Q_TILE_FWD, SWCL_Q_TILE_ADJ,
     swcl_create, swcl_destroy, swcl_set_grids, swcl_set_tracers, swcl_set_windows,
-    swcl_set_power, swcl_set_ell_lists, swcl_compute_cl, swcl_vjp, swcl_sync, swcl_query,
+    swcl_set_power, swcl_set_window_samples, swcl_set_ell_lists, swcl_compute_cl, swcl_vjp, swcl_sync, swcl_query,
     swcl_selftest_wait_timeout, swcl_jvp, swcl_gaussian_fisher, swcl_set_limber,
     swcl_profile_enable, swcl_profile_read, swcl_profile_reset, swcl_debug_read,
     SWCL_DBG_COEF, SWCL_DBG_DELTA, SWCL_DBG_GTAB, SWCL_DBG_PHASE, SWCL_DBG_UNIT,

@@ -22,6 +22,7 @@ SIGNATURES = {
                                c_void_p, c_int]),
     "swcl_set_tracers": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "swcl_set_windows": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "swcl_set_window_samples": (c_int, [c_void_p, c_int, c_void_p]),
     "swcl_set_power": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "swcl_set_ell_lists": (c_int, [c_void_p, c_void_p, c_void_p]),
     "swcl_compute_cl": (c_int, [c_void_p, c_int, c_void_p]),

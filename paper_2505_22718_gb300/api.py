@@ -91,6 +91,11 @@ def swcl_set_windows(ctx, n_walk, W, D=None, B=None):
     _check(ctx, _lib.load().swcl_set_windows(ctx, n_walk, pw, pd, pb))
 
 
+def swcl_set_window_samples(ctx, n_walk, W):
+    pw, _w = _ptr(W, np.float64)
+    _check(ctx, _lib.load().swcl_set_window_samples(ctx, n_walk, pw))
+
+
 def swcl_set_power(ctx, n_walk, P, amp):
     pp, _p = _ptr(P, np.float64)
     pa, _a = _ptr(amp, np.float64)
@@ -197,11 +202,34 @@ def swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, kind, fft_bias, 
                         W, D, B, coef, stream=None):
     """FFTLog coefficients without a context or any device allocation (see include/swiftcl.h).
 
-    kind, fft_bias: host arrays; taper_chi, taper_c, W, D, B, coef: CUDA tensors of the current
-    device (taper_*, B may be None).  Returns the status code (0 = ok) instead of raising, so a
-    caller can test the size limit."""
-    pk, _k = _ptr(np.asarray(kind, dtype=np.int32), np.int32)
-    pb, _b = _ptr(np.asarray(fft_bias, dtype=np.float64), np.float64)
+    kind, fft_bias: host arrays of N_tr entries; taper_chi [N_tr][N], taper_c [N_tr][N/2+1],
+    W [n_walk][N_tr][N], D [N_I][N], B [N_tr][N_I][N], coef [n_walk][N_tr][N_I][N/2+1][2]:
+    contiguous float64 CUDA tensors of the current device (taper_*, B may be None).  The C call
+    takes plain pointers and cannot tell a host array, a tensor of another device or a short
+    buffer from a good one, so each of these is checked here and a TypeError or ValueError is
+    raised before the library is called.  Returns the status code (0 = ok) instead of raising, so
+    a caller can test the size limit."""
+    import torch
+    n_h = N // 2 + 1
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    fft_bias = np.ascontiguousarray(fft_bias, dtype=np.float64)
+    _need(kind, N_tr, "kind [N_tr]")
+    _need(fft_bias, N_tr, "fft_bias [N_tr]")
+    dev = torch.cuda.current_device()
+    sizes = {"taper_chi": (taper_chi, N_tr * N), "taper_c": (taper_c, N_tr * n_h),
+             "W": (W, n_walk * N_tr * N), "D": (D, N_I * N), "B": (B, N_tr * N_I * N),
+             "coef": (coef, n_walk * N_tr * N_I * n_h * 2)}
+    for name, (x, n) in sizes.items():
+        if x is None:
+            if name in ("W", "D", "coef"):
+                raise ValueError("%s is required" % name)
+            continue
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.device.index == dev
+                and x.dtype == torch.float64 and x.is_contiguous()):
+            raise TypeError("%s must be a contiguous float64 CUDA tensor on device %d" % (name, dev))
+        _need(x, n, name)
+    pk, _k = _ptr(kind, np.int32)
+    pb, _b = _ptr(fft_bias, np.float64)
     args = [_ptr(x, np.float64) for x in (taper_chi, taper_c, W, D, B, coef)]
     return _lib.load().swcl_fftlog_noalloc(n_walk, N_tr, N_I, N, chi_min, chi_max, pk, pb,
                                            *[a[0] for a in args],
@@ -286,6 +314,11 @@ class Context:
         swcl_set_windows(self.ptr, n_walk, W, D, B)
         self.n_walk = n_walk
         self.n_out = n_walk * self.n_ell
+
+    def set_window_samples(self, W):
+        """New window samples for the same walkers, keeping D and B (no host wait)."""
+        _need(W, self._shape(self.n_walk, self.n_tr, self.N), "W [n_walk][N_tr][N]")
+        swcl_set_window_samples(self.ptr, self.n_walk, W)
 
     def set_power(self, P, amp):
         n_walk = 1 if P.ndim == 1 else P.shape[0]

@@ -81,8 +81,8 @@ int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes) {
   return SWCL_OK;
 }
 
-constexpr size_t kStageBytes = 256 * 1024;   // pinned staging per context
-constexpr size_t kStageMax = 64 * 1024;      // host inputs up to this size go through it
+constexpr size_t kStageBytes = 4 << 20;      // pinned staging ring per context
+constexpr size_t kStageMax = 1 << 20;        // host inputs up to this size go through it
 
 // Queues a copy without waiting.  A small host array is first copied on the host into the
 // context's pinned staging buffer (the caller may reuse it at once); a larger host array sets
@@ -586,6 +586,26 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
   return SWCL_OK;
 }
 
+int swcl_set_window_samples(swcl_ctx* c, int n_walk, const double* W) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  if (!c->have_windows)
+    return swcl::fail(c, SWCL_ERR_STATE, "swcl_set_windows first (it sets D, B and n_walk)");
+  if (!W || n_walk != c->n_walk)
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need W and the n_walk of the last swcl_set_windows");
+  QueuedHostCopies q{c};
+  SWCL_TRY(swcl::copy_in_queued(c, c->d_W, W, sizeof(double) * (size_t)n_walk * c->N_tr * c->N,
+                                &q.pending));
+  if (q.pending) {
+    q.pending = false;
+    SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  }
+  c->last_fwd_precision = -1;
+  c->u_valid = false;
+  return SWCL_OK;
+}
+
 int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) {
   if (!c) return SWCL_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -646,7 +666,9 @@ int swcl_set_ell_lists(swcl_ctx* c, const int* offsets, const int* ell_idx) {
   return SWCL_OK;
 }
 
-// Reads (and clears) the device status word the tensor-core kernels raise on a wait timeout.
+// Reads (and clears) the device status word: raised by the tensor-core kernels on a wait
+// timeout, and by the kernels that write C, P_bar, amp_bar, W_bar or dC when a value they store
+// is NaN or Inf.  A timeout is reported first.
 static int check_status(swcl_ctx* c) {
   if (!c->ws_status.p) return SWCL_OK;
   int h = 0;
@@ -654,7 +676,10 @@ static int check_status(swcl_ctx* c) {
   if (e != cudaSuccess) return swcl::cuda_fail(c, e, "status read");
   if (h) {
     cudaMemset(c->ws_status.p, 0, sizeof(int));
-    return swcl::fail(c, SWCL_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on an mbarrier");
+    if (h & swcl::kStatusTimeout)
+      return swcl::fail(c, SWCL_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on an mbarrier");
+    return swcl::fail(c, SWCL_ERR_NONFINITE,
+                      "an output (C, P_bar, amp_bar, W_bar or dC) holds a NaN or Inf");
   }
   return SWCL_OK;
 }
@@ -878,7 +903,8 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   SWCL_LAUNCH(c, swcl::launch_scale_pack(dst, (const double*)c->ws_U.p, (const double*)c->d_amp.p,
                                          c->ragged ? (const int*)c->d_off.p : nullptr,
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
-                                         N_ell, n_out, pack_stream), "scale/pack");
+                                         N_ell, n_out, pack_stream, (int*)c->ws_status.p),
+              "scale/pack");
   c->last_fwd_precision = precision;
   c->u_valid = true;
   if (!dev_out) {
@@ -946,7 +972,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "fork");
   }
   SWCL_LAUNCH(c, swcl::launch_amp_bar(Ab, (const double*)c->ws_Cbar.p, (const double*)c->ws_U.p,
-                                      (const double*)c->d_amp.p, nw, N_tr, N_ell, side),
+                                      (const double*)c->d_amp.p, nw, N_tr, N_ell, side,
+                                      (int*)c->ws_status.p),
               "amp_bar");
   for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
     const int n_l = std::min(n_lc, n_fft - l_lo);
@@ -990,7 +1017,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "fork");
   }
   SWCL_LAUNCH(c, swcl::launch_pbar_reduce(Pb, (const double*)c->ws_pbpart.p,
-                                          (const double*)c->d_wk2.p, nw, N_k, n_fft, side),
+                                          (const double*)c->d_wk2.p, nw, N_k, n_fft, side,
+                                          (int*)c->ws_status.p),
               "P_bar reduce");
   double* Wb = nullptr;
   if (W_bar) {
@@ -1000,7 +1028,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
       SWCL_LAUNCH(c, swcl::launch_fftlog_adj(Wb, (const cplx*)c->ws_cbar.p,
                                              (const double*)c->d_chipow.p, sv.D, sv.B,
                                              (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
-                                             nw, N_tr, N_I, N, scratch, c->stream), "fftlog adj");
+                                             nw, N_tr, N_I, N, scratch, c->stream,
+                                             (int*)c->ws_status.p), "fftlog adj");
       if (!swcl::fftlog_adj_single_launch(nw, N_tr, N_I, N)) ++c->last_launches;  // chunk reduction
     } else {
       SWCL_TRY_CUDA(c, cudaMemsetAsync(Wb, 0, wbytes, c->stream), "clear W_bar");
@@ -1012,7 +1041,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     SWCL_LAUNCH(c, swcl::launch_limber_vjp(Wb, Pb, (double*)c->ws_lq.p, lim, lt,
                                            (const double*)c->d_W.p, (const double*)c->d_P.p,
                                            (const double*)c->ws_Cbar.p, (const double*)c->d_amp.p,
-                                           nw, c->stream, side, c->ev_limber), "limber vjp");
+                                           nw, c->stream, side, c->ev_limber,
+                                           (int*)c->ws_status.p), "limber vjp");
     c->last_launches += W_bar ? 3 : 2;  // W_bar reduction, P_bar gather and reduction
   }
   if (W_bar) SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
@@ -1023,6 +1053,9 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   }
   if (P_bar) SWCL_TRY(swcl::copy_out(c, P_bar, Pb, sizeof(double) * nw * (size_t)N_k));
   if (amp_bar) SWCL_TRY(swcl::copy_out(c, amp_bar, Ab, sizeof(double) * nrow));
+  // host outputs made the call synchronous: report a deferred device status now
+  if ((P_bar && P_bar != Pb) || (amp_bar && amp_bar != Ab) || (W_bar && W_bar != Wb))
+    SWCL_TRY(check_status(c));
   return SWCL_OK;
 }
 
@@ -1231,7 +1264,7 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
   }
   SWCL_LAUNCH(c, swcl::launch_jvp_combine(dst, (const double*)c->ws_dU.p, (const double*)c->ws_U.p,
                                           (const double*)c->d_amp.p, jA, n_dir, N_tr, N_ell,
-                                          c->stream), "jvp combine");
+                                          c->stream, (int*)c->ws_status.p), "jvp combine");
   c->u_valid = true;
   if (!dev_out) {
     SWCL_TRY(swcl::copy_out(c, C_dot, dst, cbytes));

@@ -210,11 +210,12 @@ k_fftlog_adj(double* __restrict__ scratch, const cplx* __restrict__ cbar,
 }
 
 __global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restrict__ scratch,
-                             long per_chunk, int nchunk) {
+                             long per_chunk, int nchunk, int* __restrict__ status) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per_chunk) return;
   double s = 0.0;
   for (int c = 0; c < nchunk; ++c) s += scratch[(size_t)c * per_chunk + t];
+  flag_nonfinite(status, s);
   W_bar[t] = s;
 }
 
@@ -319,7 +320,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClThreads)
 k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
                 const double* __restrict__ chipow, const double* __restrict__ D,
                 const double* __restrict__ B, const cplx* __restrict__ psi,
-                const cplx* __restrict__ tw, int N_tr, int N_I, int N) {
+                const cplx* __restrict__ tw, int N_tr, int N_I, int N, int* __restrict__ status) {
   extern __shared__ cplx smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
@@ -383,6 +384,7 @@ k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
     if (o < L) {
       const int e = o / kCl, k1 = o - e * kCl;
       const int j = c * kq + e + L * k1;
+      flag_nonfinite(status, acc0[u] + acc1[u]);
       out[2 * j] = acc0[u];
       out[2 * j + 1] = acc1[u];
     }
@@ -447,13 +449,13 @@ size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N) {
 cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
-                              double* scratch, cudaStream_t s) {
+                              double* scratch, cudaStream_t s, int* status) {
   int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
   if (nchunk == 1 && use_cluster((long)n_walk * N_tr, N)) {
     // one chunk: the cluster kernel writes W_bar directly
     const size_t csm = (size_t)3 * (N / 2 / kCl) * sizeof(cplx);
     k_fftlog_adj_cl<<<(unsigned)((long)n_walk * N_tr * kCl), kClThreads, csm, s>>>(
-        W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I, N);
+        W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I, N, status);
     return cudaGetLastError();
   }
   size_t smem = (size_t)(N / 2) * 2 * sizeof(cplx) + (size_t)N * sizeof(double);
@@ -468,7 +470,7 @@ cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chi
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   long per = (long)n_walk * N_tr * N;
-  k_sum_chunks<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(W_bar, scratch, per, nchunk);
+  k_sum_chunks<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(W_bar, scratch, per, nchunk, status);
   return cudaGetLastError();
 }
 

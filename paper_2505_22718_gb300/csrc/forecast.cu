@@ -89,7 +89,8 @@ k_quad_jvp(double* __restrict__ dU, const T* __restrict__ delta, const double* _
 // Cdot[t][l][i][j] = A_i A_j dU + (A'_i A_j + A_i A'_j) U
 __global__ void k_jvp_combine(double* __restrict__ Cdot, const double* __restrict__ dU,
                               const double* __restrict__ U, const double* __restrict__ amp,
-                              const double* __restrict__ Adot, int n_dir, int N_tr, int N_ell) {
+                              const double* __restrict__ Adot, int n_dir, int N_tr, int N_ell,
+                              int* __restrict__ status) {
   const long n2 = (long)N_tr * N_tr, per = (long)N_ell * n2, total = per * n_dir;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -101,7 +102,9 @@ __global__ void k_jvp_combine(double* __restrict__ Cdot, const double* __restric
     // every operation symmetric in (i, j), no contraction into FMAs: dC is symmetric bit for bit
     const double aa = __dmul_rn(amp[i], amp[j]);
     const double cross = __dadd_rn(__dmul_rn(ad[i], amp[j]), __dmul_rn(amp[i], ad[j]));
-    Cdot[e] = __dadd_rn(__dmul_rn(aa, dU[e]), __dmul_rn(cross, U[r]));
+    const double v = __dadd_rn(__dmul_rn(aa, dU[e]), __dmul_rn(cross, U[r]));
+    flag_nonfinite(status, v);
+    Cdot[e] = v;
   }
 }
 
@@ -223,10 +226,11 @@ template cudaError_t launch_quad_jvp<float>(double*, const float*, const double*
                                             cudaStream_t);
 
 cudaError_t launch_jvp_combine(double* Cdot, const double* dU, const double* U, const double* amp,
-                               const double* Adot, int n_dir, int N_tr, int N_ell, cudaStream_t s) {
+                               const double* Adot, int n_dir, int N_tr, int N_ell, cudaStream_t s,
+                               int* status) {
   const long total = (long)n_dir * N_ell * N_tr * N_tr;
   const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 8);
-  k_jvp_combine<<<blocks, 256, 0, s>>>(Cdot, dU, U, amp, Adot, n_dir, N_tr, N_ell);
+  k_jvp_combine<<<blocks, 256, 0, s>>>(Cdot, dU, U, amp, Adot, n_dir, N_tr, N_ell, status);
   return cudaGetLastError();
 }
 

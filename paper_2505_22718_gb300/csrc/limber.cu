@@ -292,7 +292,7 @@ k_limber_vjp(double* __restrict__ Wpart, double* __restrict__ Q, LimberArgs a, L
 
 // Wb[w][i][m] += sum_lc Wpart[w][lc][i][m] in order
 __global__ void k_limber_wreduce(double* __restrict__ Wb, const double* __restrict__ Wpart,
-                                 int n_walk, int N_tr, int N, int n_lc) {
+                                 int n_walk, int N_tr, int N, int n_lc, int* __restrict__ status) {
   const long per = (long)N_tr * N, total = (long)n_walk * per;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -300,7 +300,9 @@ __global__ void k_limber_wreduce(double* __restrict__ Wb, const double* __restri
     const double* src = Wpart + (size_t)w * n_lc * per + r;
     double s = 0.0;
     for (int c = 0; c < n_lc; ++c) s += src[(size_t)c * per];
-    Wb[e] += s;
+    const double v = Wb[e] + s;
+    flag_nonfinite(status, v);
+    Wb[e] = v;
   }
 }
 
@@ -336,14 +338,16 @@ __global__ void k_limber_pbar(double* __restrict__ Ppart, const double* __restri
 
 // Pb[w][q] += sum_pc Ppart[w][pc][q] in order
 __global__ void k_limber_preduce(double* __restrict__ Pb, const double* __restrict__ Ppart,
-                                 int n_walk, int N_k, int n_pc) {
+                                 int n_walk, int N_k, int n_pc, int* __restrict__ status) {
   const long total = (long)n_walk * N_k;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     const long w = e / N_k, q = e - w * N_k;
     double s = 0.0;
     for (int c = 0; c < n_pc; ++c) s += Ppart[((size_t)w * n_pc + c) * N_k + q];
-    Pb[e] += s;
+    const double v = Pb[e] + s;
+    flag_nonfinite(status, v);
+    Pb[e] = v;
   }
 }
 
@@ -417,7 +421,8 @@ cudaError_t launch_limber_jvp(double* dU, double* scratch, const LimberArgs& a, 
 cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const LimberArgs& a,
                               const LimberTable& t, const double* W, const double* P,
                               const double* Sfull, const double* amp, int n_walk,
-                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready) {
+                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready,
+                              int* status) {
   if (a.N_tr > 64 || a.n_lim < 1) return cudaErrorInvalidValue;
   const size_t npair = (size_t)a.N_tr * (a.N_tr + 1) / 2;
   double* Q = scratch + (size_t)n_walk * a.n_lim * n_mc(a) * npair;   // after the forward partials
@@ -433,7 +438,8 @@ cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const Lim
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (Wb) {
     k_limber_wreduce<<<grid_of((long)n_walk * a.N_tr * a.N), 256, 0, s_main>>>(Wb, Wpart, n_walk,
-                                                                              a.N_tr, a.N, n_lc(a));
+                                                                              a.N_tr, a.N, n_lc(a),
+                                                                              status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (s_pbar != s_main) {
@@ -442,7 +448,8 @@ cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const Lim
   }
   k_limber_pbar<<<dim3((a.N_k + 127) / 128, n_pc(a), n_walk), 128, 0, s_pbar>>>(Ppart, Q, a, t, n_pc(a));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_limber_preduce<<<grid_of((long)n_walk * a.N_k), 256, 0, s_pbar>>>(Pb, Ppart, n_walk, a.N_k, n_pc(a));
+  k_limber_preduce<<<grid_of((long)n_walk * a.N_k), 256, 0, s_pbar>>>(Pb, Ppart, n_walk, a.N_k, n_pc(a),
+                                                                      status);
   return cudaGetLastError();
 }
 

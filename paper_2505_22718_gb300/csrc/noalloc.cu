@@ -26,10 +26,23 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device.  A cached
+// address is checked against the runtime's view of it first: after a cudaDeviceReset (or any
+// reload of the module on that device) the old address no longer belongs to device memory, and
+// it is then looked up again instead of being written through.
+bool still_device_memory(void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return SWCL_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_scratch_addr[dev] && !still_device_memory(g_scratch_addr[dev])) g_scratch_addr[dev] = nullptr;
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -52,7 +65,8 @@ extern "C" int swcl_fftlog_noalloc(int n_walk, int N_tr, int N_I, int N, double 
                                    double* coef, void* stream) {
   if (n_walk < 1 || N_tr < 1 || N_I < 1 || N < 16 || N > 8192 || (N & (N - 1)))
     return SWCL_ERR_INVALID_ARG;
-  if (!(chi_min > 0) || !(chi_max > chi_min) || !kind || !fft_bias || !W || !D || !coef)
+  if (!(chi_min > 0) || !(chi_max > chi_min) || !std::isfinite(chi_max) || !kind || !fft_bias ||
+      !W || !D || !coef)
     return SWCL_ERR_INVALID_ARG;
   for (int i = 0; i < N_tr; ++i) {
     if (kind[i] < SWCL_DENSITY || kind[i] > SWCL_RSD) return SWCL_ERR_INVALID_ARG;

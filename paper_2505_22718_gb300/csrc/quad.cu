@@ -128,7 +128,7 @@ __global__ void k_quad_reduce(double* __restrict__ U, const double* __restrict__
 __global__ void k_scale_pack(double* __restrict__ C, const double* __restrict__ U,
                              const double* __restrict__ amp, const int* __restrict__ off,
                              const int* __restrict__ idx, int n_walk, int N_tr, int N_ell,
-                             long n_out) {
+                             long n_out, int* __restrict__ status) {
   long o = blockIdx.x;
   if (o >= n_out) return;
   int w, l;
@@ -148,7 +148,9 @@ __global__ void k_scale_pack(double* __restrict__ C, const double* __restrict__ 
     int i = e / N_tr, j = e - i * N_tr;
     double ai = A[i], aj = A[j];
     double s = (i <= j) ? ai * aj : aj * ai;
-    C[o * N_tr * N_tr + e] = s * u[e];
+    const double v = s * u[e];
+    flag_nonfinite(status, v);
+    C[o * N_tr * N_tr + e] = v;
   }
 }
 
@@ -179,7 +181,7 @@ __global__ void k_unpack_sym(double* __restrict__ Cf, const double* __restrict__
 // amp_bar[w][i] = 2 sum_l sum_j S_ij A_j U_ij
 __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ Cf,
                           const double* __restrict__ U, const double* __restrict__ amp,
-                          int N_tr, int N_ell) {
+                          int N_tr, int N_ell, int* __restrict__ status) {
   const int w = blockIdx.y;
   const int i = blockIdx.x;
   __shared__ double red[256];
@@ -196,7 +198,10 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
     if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) abar[(size_t)w * N_tr + i] = 2.0 * red[0];
+  if (threadIdx.x == 0) {
+    flag_nonfinite(status, red[0]);
+    abar[(size_t)w * N_tr + i] = 2.0 * red[0];
+  }
 }
 
 // Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, LC multipoles,
@@ -298,12 +303,15 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
 }
 
 __global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restrict__ part,
-                              const double* __restrict__ wk2, int n_chunk, int n_walk, int N_k) {
+                              const double* __restrict__ wk2, int n_chunk, int n_walk, int N_k,
+                              int* __restrict__ status) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)n_walk * N_k) return;
   double s = 0.0;
   for (int c = 0; c < n_chunk; ++c) s += part[(size_t)c * n_walk * N_k + t];
-  Pbar[t] = wk2[t % N_k] * s;
+  const double v = wk2[t % N_k] * s;
+  flag_nonfinite(status, v);
+  Pbar[t] = v;
 }
 
 }  // namespace
@@ -355,9 +363,10 @@ cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, cons
 
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
-                              cudaStream_t s) {
+                              cudaStream_t s, int* status) {
   if (n_out == 0) return cudaSuccess;
-  k_scale_pack<<<(unsigned)n_out, 128, 0, s>>>(C, U, amp, off, idx, n_walk, N_tr, N_ell, n_out);
+  k_scale_pack<<<(unsigned)n_out, 128, 0, s>>>(C, U, amp, off, idx, n_walk, N_tr, N_ell, n_out,
+                                               status);
   return cudaGetLastError();
 }
 
@@ -370,9 +379,9 @@ cudaError_t launch_unpack_sym(double* Cf, const double* Cb, const int* off, cons
 }
 
 cudaError_t launch_amp_bar(double* amp_bar, const double* Cf, const double* U, const double* amp,
-                           int n_walk, int N_tr, int N_ell, cudaStream_t s) {
+                           int n_walk, int N_tr, int N_ell, cudaStream_t s, int* status) {
   dim3 g(N_tr, n_walk);
-  k_amp_bar<<<g, 256, 0, s>>>(amp_bar, Cf, U, amp, N_tr, N_ell);
+  k_amp_bar<<<g, 256, 0, s>>>(amp_bar, Cf, U, amp, N_tr, N_ell, status);
   return cudaGetLastError();
 }
 
@@ -393,10 +402,11 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const do
 }
 
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
-                               int n_walk, int N_k, int N_ell, cudaStream_t s) {
+                               int n_walk, int N_k, int N_ell, cudaStream_t s, int* status) {
   const int n_chunk = (N_ell + LC - 1) / LC;
   const long n = (long)n_walk * N_k;
-  k_pbar_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P_bar, scratch, wk2, n_chunk, n_walk, N_k);
+  k_pbar_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P_bar, scratch, wk2, n_chunk, n_walk, N_k,
+                                                           status);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,16 @@ namespace swcl {
 
 struct cplx { double x, y; };
 
+// Bits of the context's device status word (ws_status): a tensor-core kernel gave up a bounded
+// wait, or a kernel that writes an output (C, P_bar, amp_bar, W_bar, dC) stored a NaN or Inf.
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusNonfinite = 2;
+
+// Raises kStatusNonfinite in *status when v is NaN or Inf (status may be null).
+__device__ __forceinline__ void flag_nonfinite(int* status, double v) {
+  if (status && !isfinite(v)) atomicOr(status, kStatusNonfinite);
+}
+
 // Device buffer with a byte count, owned by the context.
 struct DevBuf {
   void* p = nullptr;
@@ -253,7 +263,7 @@ cudaError_t launch_fftlog_fwd_df(float4* coef, const double* W, const double* ch
 cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
-                              double* scratch, cudaStream_t s);
+                              double* scratch, cudaStream_t s, int* status = nullptr);
 size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
 bool fftlog_adj_single_launch(int n_walk, int N_tr, int N_I, int N);   // no chunk reduction
 
@@ -284,12 +294,13 @@ size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l);
 cudaError_t launch_wait_nothing(int* status, long long* cycles, cudaStream_t s);
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
-                              cudaStream_t s);
+                              cudaStream_t s, int* status = nullptr);
 cudaError_t launch_unpack_sym(double* Cbar_full, const double* Cbar, const int* off,
                               const int* idx, int n_walk, int N_tr, int N_ell, int64_t n_out,
                               cudaStream_t s);
 cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const double* U,
-                           const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s);
+                           const double* amp, int n_walk, int N_tr, int N_ell, cudaStream_t s,
+                           int* status = nullptr);
 // Dbar for the chunk and its partial sums of P_bar in scratch (indexed by
 // the global multipole); launch_pbar_reduce adds all chunks into P_bar [n_walk][N_k]
 template <typename T>
@@ -297,7 +308,8 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, c
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s);
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
-                               int n_walk, int N_k, int N_ell, cudaStream_t s);
+                               int n_walk, int N_k, int N_ell, cudaStream_t s,
+                               int* status = nullptr);
 size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell);
 
 // Limber branch (limber.cu): the stencil table, then forward rows of U [n_walk][N_ell] (or, with
@@ -316,7 +328,8 @@ cudaError_t launch_limber_jvp(double* dU, double* scratch, const LimberArgs& a, 
 cudaError_t launch_limber_vjp(double* Wb, double* Pb, double* scratch, const LimberArgs& a,
                               const LimberTable& t, const double* W, const double* P,
                               const double* Sfull, const double* amp, int n_walk,
-                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready);
+                              cudaStream_t s_main, cudaStream_t s_pbar, cudaEvent_t q_ready,
+                              int* status = nullptr);
 // U[w][l_lo + ll][i][j] = U[..][j][i] = sum over n_chunk partial pair sums part[w][ll][chunk][pair]
 // (quad.cu)
 cudaError_t launch_pair_reduce(double* U, const double* part, int n_walk, int N_tr, int N_ell,
@@ -329,7 +342,8 @@ cudaError_t launch_quad_jvp(double* dU, const T* delta, const double* P, const d
                             const double* wk2, bool has_w, int n_dir, int N_tr, int N_k,
                             int N_ell, int l_lo, int n_l, cudaStream_t s);
 cudaError_t launch_jvp_combine(double* Cdot, const double* dU, const double* U, const double* amp,
-                               const double* Adot, int n_dir, int N_tr, int N_ell, cudaStream_t s);
+                               const double* Adot, int n_dir, int N_tr, int N_ell, cudaStream_t s,
+                               int* status = nullptr);
 // F [n_x][n_x] from X [n_x][N_ell][N_tr][N_tr], Ct = A A U + diag(noise); Z is scratch of X's size
 cudaError_t launch_fisher(double* F, double* Z, const double* X, const double* U,
                           const double* amp, const double* noise, const double* modes,

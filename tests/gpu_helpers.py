@@ -18,6 +18,19 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.abs(b).max(), 1e-300))
 
 
+def grad_err(g, go, floor=1e-3):
+    """Per-element error of a gradient: max |g - go| / max(|go|, floor * max |go| of its row),
+    rows along the last axis (P_bar: one row of N_k per walker; W_bar: one row of N per walker
+    and tracer; amp_bar: one row of N_tr).  The floor keeps entries that are zero or
+    sign-changing from being gated at an impossible relative tolerance, while every entry of a
+    row's upper three decades is gated on its own."""
+    g = np.asarray(g, dtype=np.float64)
+    go = np.asarray(go, dtype=np.float64).reshape(g.shape)
+    rmax = np.abs(go).max(axis=-1, keepdims=True)
+    den = np.maximum(np.abs(go), np.maximum(floor * rmax, 1e-300))
+    return float(np.max(np.abs(g - go) / den))
+
+
 def lib_context(w, tapers=None, budget=0):
     from paper_2505_22718_gb300 import Context
     ctx = Context(0, budget)

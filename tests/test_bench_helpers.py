@@ -35,9 +35,11 @@ def test_roofline_of_a_whole_delta_step(n5k):
     stats = {"basis gemm adj": (200, 200 * 0.0744), "basis gemm fwd": (200, 200 * 0.057)}
     r = bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "measured", 1, "n5k", 200, False)
     assert r["kernel"] == "basis gemm adj"
-    assert r["achieved"] == pytest.approx(flops * 6 / 0.0744e-3 / 1e12)
+    # achieved and frac count the method's useful flops; the executed compensated products
+    # (6 per useful multiply-add in basis mode) only enter the pipe occupancy
+    assert r["achieved"] == pytest.approx(flops / 0.0744e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / 1890.6)
-    assert r["useful_tflops"] == pytest.approx(flops / 0.0744e-3 / 1e12)
+    assert r["pipe_occupancy"] == pytest.approx(6 * r["frac"])
 
 
 def test_roofline_follows_chunks_and_recompute(n5k):
@@ -46,7 +48,7 @@ def test_roofline_follows_chunks_and_recompute(n5k):
     stats = {"basis gemm fwd": (30, 30 * 0.02), "basis gemm adj": (15, 15 * 0.025)}
     r = bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "measured", 1, "n5k", 5, True)
     assert r["kernel"] == "basis gemm fwd"
-    assert r["achieved"] == pytest.approx(flops * 2 / 6 * 6 / 0.02e-3 / 1e12)
+    assert r["achieved"] == pytest.approx(flops * 2 / 6 / 0.02e-3 / 1e12)
     # without recompute the same launches would be six chunks of one pass
     r2 = bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "measured", 1, "n5k", 5, False)
     assert r2["achieved"] == pytest.approx(r["achieved"] / 2)
@@ -54,12 +56,33 @@ def test_roofline_follows_chunks_and_recompute(n5k):
 
 def test_tf32_and_fp64_peaks(n5k):
     stats = {"contract tc": (10, 10 * 0.1)}
+    # without a TF32 rate measured in the run: the bf16 peak times the nominal ratio
     r = bench.roofline(stats, n5k, 1, "tf32x6", PEAKS, "measured", 0, "n5k", 10)
     assert r["peak"] == pytest.approx(1890.6 * 1.1 / 2.25)
     assert r["products"] == 6
+    measured = dict(PEAKS, tf32_tflops=950.0, fp64_tflops=1.1)
+    r = bench.roofline(stats, n5k, 1, "tf32x6", measured, "measured", 0, "n5k", 10)
+    assert r["peak"] == 950.0
     stats = {"contract fp64": (10, 10 * 5.0)}
     r = bench.roofline(stats, n5k, 1, "fp64", PEAKS, "measured", 0, "n5k", 10)
     assert r["bound"] == "alu" and r["peak"] == pytest.approx(bench.FP64_PEAK_TFLOPS)
+    r = bench.roofline(stats, n5k, 1, "fp64", measured, "measured", 0, "n5k", 10)
+    assert r["peak"] == 1.1 and r["frac"] == pytest.approx(r["achieved"] / 1.1)
+
+
+def test_ragged_lists_count_only_listed_multipoles(n5k):
+    stats = {"basis gemm adj": (1, 1.0)}
+    full = bench.roofline(stats, n5k, 2, "bf16x9", PEAKS, "measured", 1, "walkers", 1)
+    part = bench.roofline(stats, n5k, 2, "bf16x9", PEAKS, "measured", 1, "walkers", 1,
+                          n_ell_useful=103)
+    assert part["achieved"] == pytest.approx(full["achieved"] / 2)
+
+
+def test_named_kernel_roofline(n5k):
+    stats = {"contract tc": (10, 1.0), "contract adj tc": (10, 2.0)}
+    r = bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "measured", 0, "n5k", 10, kernel="contract tc")
+    assert r["kernel"] == "contract tc" and r["products"] == 9
+    assert bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "m", 0, "n5k", 10, kernel="nope") is None
 
 
 def test_stored_traffic_applies_only_to_its_workload_and_source():

@@ -4,7 +4,7 @@ window mean shifts."""
 import numpy as np
 import pytest
 
-from gpu_helpers import max_rel, norm_err, oracle_walker
+from gpu_helpers import grad_err, max_rel, norm_err, oracle_walker
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +35,9 @@ def test_autograd_matches_oracle_gradient(precision, gate, wl):
     (C * Cb).sum().backward()
     f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=w.C_bar)
     assert norm_err(C.detach().cpu().numpy(), f["C"]) < (1e-10 if precision == "fp64" else 1e-4)
-    assert max_rel(P.grad.cpu().numpy(), Pbo) < gate
-    assert max_rel(A.grad.cpu().numpy(), Abo) < gate
-    assert max_rel(W.grad.cpu().numpy(), Wbo) < gate
+    assert grad_err(P.grad.cpu().numpy(), Pbo) < gate
+    assert grad_err(A.grad.cpu().numpy(), Abo) < gate
+    assert grad_err(W.grad.cpu().numpy(), Wbo) < gate
 
 
 def test_autograd_central_differences_fp64(wl):
@@ -112,5 +112,5 @@ def test_backward_after_a_second_forward(wl):
     Cb = rng.standard_normal(C1.shape)
     C1.backward(torch.tensor(Cb, device=dev))
     f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=Cb)
-    assert max_rel(P.grad.cpu().numpy()[0] if P.grad.dim() > 1 else P.grad.cpu().numpy(), Pbo) < 1e-10
-    assert max_rel(W.grad.cpu().numpy(), Wbo) < 1e-9
+    assert grad_err(P.grad.cpu().numpy()[0] if P.grad.dim() > 1 else P.grad.cpu().numpy(), Pbo) < 1e-10
+    assert grad_err(W.grad.cpu().numpy(), Wbo) < 1e-9

@@ -3,7 +3,7 @@ lists, per-walker P(k), amplitudes and window shifts; replay after a parameter u
 import numpy as np
 import pytest
 
-from gpu_helpers import lib_context, max_rel, norm_err, oracle_walker
+from gpu_helpers import grad_err, lib_context, max_rel, norm_err, oracle_walker
 
 pytestmark = pytest.mark.gpu
 
@@ -48,9 +48,9 @@ def test_batched_graph_against_oracle(prec, walkers8):
         Cbw[lst] = Cb[o:o + n]
         f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, C_bar=Cbw)
         assert norm_err(C[o:o + n].cpu().numpy(), f["C"][lst]) < gate_c, wk
-        assert max_rel(Pb[wk].cpu().numpy(), Pbo) < gate_g
-        assert max_rel(Ab[wk].cpu().numpy(), Abo) < gate_g
-        assert max_rel(Wb[wk].cpu().numpy(), Wbo) < gate_g
+        assert grad_err(Pb[wk].cpu().numpy(), Pbo) < gate_g
+        assert grad_err(Ab[wk].cpu().numpy(), Abo) < gate_g
+        assert grad_err(Wb[wk].cpu().numpy(), Wbo) < gate_g
         o += n
 
 

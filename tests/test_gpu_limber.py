@@ -10,7 +10,7 @@ import copy
 import numpy as np
 import pytest
 
-from gpu_helpers import lib_context, make_ragged_case, max_rel, norm_err
+from gpu_helpers import grad_err, lib_context, make_ragged_case, max_rel, norm_err
 from oracle import fftlog as O
 from oracle import limber as LB
 
@@ -59,7 +59,7 @@ def test_hybrid_forward_and_vjp(prec, sw, case):
     C = ctx.compute_cl(p)
     e = norm_err(C, Co)
     Pb, Ab, Wb = ctx.vjp(np.concatenate(Cb), p)
-    ge = [max(max_rel(x[wk], go[wk][t]) for wk in range(len(go))) for t, x in enumerate((Pb, Ab, Wb))]
+    ge = [max(grad_err(x[wk], go[wk][t]) for wk in range(len(go))) for t, x in enumerate((Pb, Ab, Wb))]
     print("limber %s switch %d: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e" % (prec, sw, e, *ge))
     assert e < tol
     assert ge[0] < gtol and ge[1] < gtol and ge[2] < wtol

@@ -6,7 +6,7 @@ Gamma-ratio operand; its error is checked against a looser documented bound."""
 import numpy as np
 import pytest
 
-from gpu_helpers import lib_context, make_ragged_case, norm_err, oracle_walker
+from gpu_helpers import grad_err, lib_context, make_ragged_case, norm_err, oracle_walker
 
 pytestmark = pytest.mark.gpu
 
@@ -100,13 +100,13 @@ VJP_GATE = 5e-5   # max |g - g_oracle| / max |g_oracle| for P_bar, amp_bar, W_ba
 def test_n5k_vjp(prec, wl):
     """Reverse mode through the tensor-core transposed contraction against the oracle's gradient."""
     import paper_2505_22718_gb300 as S
-    from gpu_helpers import max_rel
+    from gpu_helpers import grad_err, max_rel
     w = wl("n5k_vjp")
     f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=w.C_bar)
     ctx = lib_context(w)
     ctx.compute_cl(S.PRECISIONS[prec])
     Pb, Ab, Wb = ctx.vjp(w.C_bar, S.PRECISIONS[prec])
-    errs = (max_rel(Pb[0], Pbo), max_rel(Ab[0], Abo), max_rel(Wb[0], Wbo))
+    errs = (grad_err(Pb[0], Pbo), grad_err(Ab[0], Abo), grad_err(Wb[0], Wbo))
     print("n5k %s VJP errors P_bar %.2e amp_bar %.2e W_bar %.2e" % ((prec,) + errs))
     assert max(errs) < VJP_GATE
 
@@ -114,7 +114,7 @@ def test_n5k_vjp(prec, wl):
 @pytest.mark.parametrize("prec", ["bf16x9", "tf32x6"])
 def test_ragged_vjp(prec):
     import paper_2505_22718_gb300 as S
-    from gpu_helpers import max_rel
+    from gpu_helpers import grad_err, max_rel
     w, tapers = make_ragged_case()
     ctx = lib_context(w, tapers)
     C = ctx.compute_cl(S.PRECISIONS[prec])
@@ -127,7 +127,7 @@ def test_ragged_vjp(prec):
         Cbw = np.zeros((len(w.ells), 7, 7))
         Cbw[lst] = Cb[o:o + n]
         f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, tapers, C_bar=Cbw)
-        assert max_rel(Pb[wk], Pbo) < VJP_GATE
-        assert max_rel(Ab[wk], Abo) < VJP_GATE
-        assert max_rel(Wb[wk], Wbo) < VJP_GATE
+        assert grad_err(Pb[wk], Pbo) < VJP_GATE
+        assert grad_err(Ab[wk], Abo) < VJP_GATE
+        assert grad_err(Wb[wk], Wbo) < VJP_GATE
         o += n

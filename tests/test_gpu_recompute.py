@@ -11,7 +11,7 @@ import copy
 import numpy as np
 import pytest
 
-from gpu_helpers import lib_context, max_rel, norm_err
+from gpu_helpers import grad_err, lib_context, max_rel, norm_err
 from oracle import fftlog as O
 
 pytestmark = pytest.mark.gpu
@@ -61,13 +61,13 @@ def _sub_workload(w, tr, li):
 def test_large_configuration_sampled_against_oracle(prec):
     """Full-size forward + VJP of the large configuration under the 40 GB budget (and, for the
     mixed form, again under a budget that forces multipole chunks), compared with the FP64 oracle
-    on 4 tracers x 4 multipoles; the cotangent is nonzero only there, so every gradient of the
-    other tracers is exactly zero."""
+    on every tracer at 16 multipoles spread logarithmically over [2, 3000]; the cotangent is
+    nonzero only there."""
     import paper_2505_22718_gb300 as S
     from workloads import make_workload
     w = make_workload("large")
-    tr = np.array([0, 13, 22, 29])
-    li = np.array([0, 98, 998, len(w.ells) - 1])          # ell = 2, 100, 1000, 3000
+    tr = np.arange(w.n_tr)
+    li = np.unique(np.round(np.geomspace(2, 3000, 16)).astype(int)) - 2   # ell = 2 ... 3000
     rng = np.random.default_rng(31)
     Cb = np.zeros((len(w.ells), w.n_tr, w.n_tr))
     Cb[np.ix_(li, tr, tr)] = rng.standard_normal((len(li), len(tr), len(tr)))
@@ -80,13 +80,11 @@ def test_large_configuration_sampled_against_oracle(prec):
     gate_c, gate_g = (1e-10, 1e-9) if prec == "fp64" else (1e-4, 5e-5)
     e_c = norm_err(C[np.ix_(li, tr, tr)], f["C"])
     print("large %s: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e" % (
-        prec, e_c, max_rel(Pb[0], Pbo), max_rel(Ab[0][tr], Abo), max_rel(Wb[0][tr], Wbo)))
+        prec, e_c, grad_err(Pb[0], Pbo), grad_err(Ab[0][tr], Abo), grad_err(Wb[0][tr], Wbo)))
     assert e_c < gate_c
-    assert max_rel(Pb[0], Pbo) < gate_g
-    assert max_rel(Ab[0][tr], Abo) < gate_g
-    assert max_rel(Wb[0][tr], Wbo) < gate_g
-    rest = np.setdiff1d(np.arange(w.n_tr), tr)
-    assert not np.any(Ab[0][rest]) and not np.any(Wb[0][rest])
+    assert grad_err(Pb[0], Pbo) < gate_g
+    assert grad_err(Ab[0][tr], Abo) < gate_g
+    assert grad_err(Wb[0][tr], Wbo) < gate_g
     # symmetry and per-ell PSD of the full output
     assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
     if prec == "bf16x9":

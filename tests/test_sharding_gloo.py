@@ -32,6 +32,13 @@ def _free_port():
     return port
 
 
+def _oracle_cl(w, i):
+    """The oracle's C_ell of walker i of a walkers workload (numpy.fft form of Eq. 3.2)."""
+    from oracle import fftlog as O
+    g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, w.ells, w.knots, w.kind, w.fft_bias, fft="numpy")
+    return O.forward(g, w.W[i], w.D, w.P[i], w.amp[i], w.B)["C"]
+
+
 def _worker(rank, world, port, n_total, out):
     import torch
     import torch.distributed as dist
@@ -40,9 +47,10 @@ def _worker(rank, world, port, n_total, out):
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
                             world_size=world)
     first, count = shard(n_total, world, rank)
-    # a rank builds only its own walkers; a per-walker summary stands in for its C_ell
+    # a rank builds only its own walkers and evaluates their C_ell (the oracle stands in for the
+    # GPU compute of each rank)
     w = make_workload("walkers", n_walkers=count, first_walker=first)
-    block = torch.tensor(np.stack([w.P[i][:4] * w.amp[i][0] for i in range(count)]))
+    block = torch.tensor(np.stack([_oracle_cl(w, i) for i in range(count)]))
     full = gather_blocks(block, n_total)
     t = max_over_ranks(10.0 + rank)
     dist.barrier()
@@ -54,7 +62,7 @@ def _worker(rank, world, port, n_total, out):
 def test_two_gloo_ranks_match_one_process():
     import torch.multiprocessing as mp
     from workloads import make_workload
-    n_total, world = 5, 2
+    n_total, world = 3, 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -66,28 +74,36 @@ def test_two_gloo_ranks_match_one_process():
         p.join(timeout=120)
         assert p.exitcode == 0
     w = make_workload("walkers", n_walkers=n_total)
-    ref = np.stack([w.P[i][:4] * w.amp[i][0] for i in range(n_total)])
+    ref = np.stack([_oracle_cl(w, i) for i in range(n_total)])
     assert np.array_equal(full, ref)
     assert t == 11.0
 
 
-def _ell_worker(rank, world, port, out):
-    import torch
-    import torch.distributed as dist
+def _oracle_block(su, Cb, precision):
+    """A rank's compute in the multipole split, with the oracle standing in for the library."""
     from oracle import fftlog as O
-    from paper_2505_22718_gb300.sharding import ell_block, gather_blocks, reduce_gradients
+    g = O.Grids(su["N"], su["chi_min"], su["chi_max"], su["k"], su["ells"], su["knots"], su["kind"],
+                su["fft_bias"])
+    f = O.forward(g, su["W"], su["D"], su["P"], su["amp"], su.get("B"))
+    Pb, Ab, Wb, _ = O.vjp(g, f, Cb, su["W"], su["D"], su["P"], su["amp"], su.get("B"))
+    return f["C"], Pb, Ab, Wb
+
+
+def _setup(w):
+    return dict(chi_min=w.chi_min, chi_max=w.chi_max, N=w.N, k=w.k, ells=w.ells, knots=w.knots,
+                kind=w.kind, fft_bias=w.fft_bias, W=w.W, D=w.D, B=w.B, P=w.P, amp=w.amp)
+
+
+def _ell_worker(rank, world, port, out):
+    import torch.distributed as dist
+    from paper_2505_22718_gb300.sharding import evaluate_ell_split
     from workloads import make_workload
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
                             world_size=world)
     w = make_workload("tiny2")
-    first, count = ell_block(len(w.ells), world, rank)
-    ells = w.ells[first:first + count]
-    Cb = np.random.default_rng(5).standard_normal((len(w.ells), w.n_tr, w.n_tr))[first:first + count]
-    g = O.Grids(w.N, w.chi_min, w.chi_max, w.k, ells, w.knots, w.kind, w.fft_bias)
-    f = O.forward(g, w.W, w.D, w.P, w.amp, w.B)
-    Pb, Ab, Wb, _ = O.vjp(g, f, Cb, w.W, w.D, w.P, w.amp, w.B)
-    C = gather_blocks(torch.tensor(f["C"]), len(w.ells))
-    Pb, Ab, Wb = reduce_gradients(torch.tensor(Pb), torch.tensor(Ab), torch.tensor(Wb))
+    Cb = np.random.default_rng(5).standard_normal((len(w.ells), w.n_tr, w.n_tr))
+    # the end-to-end entry point: ell_block, the rank's block, gather_blocks, reduce_gradients
+    C, Pb, Ab, Wb = evaluate_ell_split(_setup(w), Cb, block=_oracle_block)
     dist.barrier()
     if rank == 0:
         out.put((C.numpy(), Pb.numpy(), Ab.numpy(), Wb.numpy()))

@@ -74,6 +74,36 @@ def test_noalloc_rejects_tables_beyond_its_static_array(wl):
     st = S.swcl_fftlog_noalloc(1, big_tr, 1, N, w.chi_min, w.chi_max, np.zeros(big_tr, np.int32),
                                np.full(big_tr, -0.3), None, None, W, D, None, coef)
     assert st == -3  # SWCL_ERR_OOM_BUDGET, reported before any launch
-    st = S.swcl_fftlog_noalloc(1, 1, 1, 300, w.chi_min, w.chi_max, np.zeros(1, np.int32),
-                               np.full(1, -0.3), None, None, W, D, None, coef)
+    n = 300   # not a power of two
+    W3 = torch.zeros((1, n), dtype=torch.float64, device=dev)
+    D3 = torch.ones((1, n), dtype=torch.float64, device=dev)
+    c3 = torch.zeros((n // 2 + 1) * 2, dtype=torch.float64, device=dev)
+    st = S.swcl_fftlog_noalloc(1, 1, 1, n, w.chi_min, w.chi_max, np.zeros(1, np.int32),
+                               np.full(1, -0.3), None, None, W3, D3, None, c3)
     assert st == -1
+    # an infinite chi_max is rejected like in swcl_set_grids
+    W4 = torch.zeros((1, 256), dtype=torch.float64, device=dev)
+    D4 = torch.ones((1, 256), dtype=torch.float64, device=dev)
+    c4 = torch.zeros(129 * 2, dtype=torch.float64, device=dev)
+    st = S.swcl_fftlog_noalloc(1, 1, 1, 256, w.chi_min, float("inf"), np.zeros(1, np.int32),
+                               np.full(1, -0.3), None, None, W4, D4, None, c4)
+    assert st == -1
+
+
+def test_noalloc_binding_rejects_host_and_short_buffers(wl):
+    """The entry point takes plain device pointers: the binding refuses a host array and a short
+    output buffer before the library sees them."""
+    import torch
+    import paper_2505_22718_gb300 as S
+    w = wl("tiny2")
+    dev = torch.device("cuda:0")
+    n_h = w.N // 2 + 1
+    W = torch.as_tensor(w.W, dtype=torch.float64, device=dev)
+    D = torch.as_tensor(w.D, dtype=torch.float64, device=dev)
+    coef = torch.zeros(w.n_tr * n_h * 2, dtype=torch.float64, device=dev)
+    args = (1, w.n_tr, 1, w.N, w.chi_min, w.chi_max, w.kind, w.fft_bias, None, None)
+    with pytest.raises(TypeError):
+        S.swcl_fftlog_noalloc(*args, np.ascontiguousarray(w.W), D, None, coef)
+    with pytest.raises(ValueError):
+        S.swcl_fftlog_noalloc(*args, W, D, None, coef[:-2])
+    assert S.swcl_fftlog_noalloc(*args, W, D, None, coef) == 0

@@ -2,7 +2,7 @@
 
 Units: chi in Mpc/h, k in h/Mpc, P in (Mpc/h)^3.  c/H0 = 2997.92458 Mpc/h.
 
-Five workload shapes:
+Six workload shapes:
 
 * ``tiny2``    2 Gaussian clustering windows (z = 0.5, 1.0, sigma_z = 0.05),
                3 spectra, 20 ell in [2, 200], N = 256, 256 k in [1e-4, 10],
@@ -15,6 +15,10 @@ Five workload shapes:
                1024 k in [1e-4, 10], D(k, z) = (1+z)^-1 (1 + 0.01 ln(k/0.1))
                sampled at 150 log-spaced k-knots.
 * ``n5k_vjp``  ``n5k`` plus a seeded N(0, 1) cotangent on every C_ell entry.
+* ``n5k_general``  ``n5k`` with a growth that is not of low rank in (k, z):
+               D(k, z) = (1+z)^-1 exp(0.02 ln(k/0.1) g(z)) with g a mix of three
+               redshift profiles (general_growth_factor), plus the cotangent of
+               ``n5k_vjp``.
 * ``walkers``  256 parameter points of the ``n5k`` shape, each with its own
                P(k) amplitude (+-10 %), tilt in [0.94, 0.99], clustering
                amplitudes in [1, 2.5], window mean shifts in [-0.02, 0.02]
@@ -285,7 +289,7 @@ def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256, first_w
         gauss = [(0.5, 0.05), (1.0, 0.05)]
         lens_edges = []
         n_i = 1
-    elif name in ("n5k", "n5k_vjp", "walkers"):
+    elif name in ("n5k", "n5k_vjp", "walkers", "n5k_general"):
         N, nk, kmin, kmax = 2048, 1024, 1e-4, 10.0
         ells = ell_list(2, 2000, 103)
         gauss = list(zip(np.linspace(0.25, 1.25, 10), np.linspace(0.04, 0.08, 10)))
@@ -310,6 +314,8 @@ def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256, first_w
     growth = 1.0 / (1.0 + z)
     if name == "tiny2":
         D = growth[None, :].copy()
+    elif name == "n5k_general":
+        D = growth[None, :] * general_growth_factor(knots[:, None], z[None, :])
     else:
         D = growth[None, :] * (1.0 + 0.01 * np.log(knots / 0.1))[:, None]
     B = None
@@ -350,14 +356,26 @@ def make_workload(name: str, seed: int = 20250528, n_walkers: int = 256, first_w
     else:
         amp = np.concatenate([1.0 + 0.15 * np.arange(ng), np.ones(nl)])
     C_bar = None
-    if name == "n5k_vjp":
+    if name in ("n5k_vjp", "n5k_general"):
         C_bar = rng.standard_normal((len(ells), ng + nl, ng + nl))
     meta.update(A=A)
     return Workload(name, N, CHI_MIN, CHI_MAX, k, ells, knots, kind, fft_bias, W, D, B, P, amp,
                     C_bar, None, meta)
 
 
-WORKLOADS = ("tiny2", "n5k", "n5k_vjp", "walkers", "large")
+WORKLOADS = ("tiny2", "n5k", "n5k_vjp", "n5k_general", "walkers", "large")
+
+
+def general_growth_factor(k, z):
+    """Scale-dependent growth factor of the n5k_general workload, exp(0.02 ln(k/0.1) g(z)), with
+    g(z) a mix of three independent redshift profiles.  Its power series in ln k carries a new
+    function of z at every order, so the knot profiles D(k_a, z) are of high numerical rank (about
+    ten at a 1e-14 tolerance) and the k-interpolation of Sec. 3.2 cannot be folded into a few basis
+    profiles: the library then transforms every knot.  Broadcasts k against z."""
+    k = np.asarray(k, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    g = 0.5 + 0.8 * z / (1.0 + z) + 0.3 * np.sin(2.3 * z) * np.exp(-0.5 * z)
+    return np.exp(0.02 * np.log(k / 0.1) * g)
 
 
 # ------------------------------------------------------- convergence study ----
