@@ -329,10 +329,10 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->d_D, &c->d_B, &c->d_P, &c->d_amp, &c->d_off, &c->d_idx, &c->ws_coef,
                     &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar, &c->ws_Cbar,
                     &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_status, &c->tc_lw32,
-                    &c->tc_kpow32, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
+                    &c->tc_kpow32, &c->tc_lw_lo, &c->tc_kpow_lo, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
-                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart,
+                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg,
                     &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq,
                     &c->ws_ltab};
   for (DevBuf* b : bufs) swcl::release(c, *b);
@@ -340,6 +340,7 @@ int swcl_destroy(swcl_ctx* c) {
     swcl::release(c, t.bfwd);
     swcl::release(c, t.bvjp);
     swcl::release(c, t.phase32);
+    swcl::release(c, t.phase_lo);
     swcl::release(c, t.tile_alo);
     swcl::release(c, t.knot_qt);
   }
@@ -713,8 +714,7 @@ static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
   if (!c->budget) return n_need;
   const swcl::Stencil sv = swcl::stencil(c);
   const size_t nw = c->n_walk, nrow = nw * c->N_tr, ntr2 = (size_t)c->N_tr * c->N_tr;
-  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float)) +
-                 swcl::quad_scratch_bytes(c->n_walk, c->N_tr, c->N_k, 1);
+  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float));
   if (basis) per_l += swcl::basis_bytes_per_ell(c);
   // workspace that does not scale with the chunk
   size_t fixed = 2 * sizeof(cplx) * nrow * sv.NI * c->n_h              // coefficients, cbar
@@ -727,7 +727,7 @@ static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
   if (basis) fixed += swcl::basis_fixed_bytes(c);
   const DevBuf* ws[] = {&c->ws_coef, &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar,
                         &c->ws_Cbar, &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_pbpart,
-                        &c->ws_qpart, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
+                        &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
                         &c->bt_himg, &c->bt_dimg};
   size_t ws_now = 0;
   for (const DevBuf* b : ws) ws_now += b->bytes;
@@ -850,7 +850,6 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
   SWCL_TRY(swcl::ensure(c, c->ws_delta, nrow * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
-  SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(nw, N_tr, N_k, n_lc)));
   if (fp64)
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
                                            (const double*)c->d_chipow.p, sv.D, sv.B,
@@ -867,14 +866,13 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                             (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                            N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                            N_tr, N_k, N_ell, l_lo, n_l,
                                             c->stream), "k-quadrature fp64");
     else
       SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                            (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                           N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                           N_tr, N_k, N_ell, l_lo, n_l,
                                            c->stream), "k-quadrature f32");
-    ++c->last_launches;  // the pair-sum reduction
   }
   if (lim.n_lim > 0) {
     SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt,
@@ -979,6 +977,12 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     const int n_l = std::min(n_lc, n_fft - l_lo);
     const bool accumulate = l_lo > 0;
     if (recompute) SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
+    // basis mode with the adjoint tile chosen: Dbar goes straight into the adjoint GEMM's operand
+    if (W_bar && use_basis_gemm(c, precision) && c->bt_nt_adj != 0) {
+      SWCL_TRY(swcl::basis_dbar_image(c, l_lo, n_l, (double*)c->ws_pbpart.p));
+      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate, true));
+      continue;
+    }
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_delta_bar<double>((double*)c->ws_dbar.p,
                                                     (const double*)c->ws_delta.p,
@@ -1006,7 +1010,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                     n_h, N_k, N_ell, l_lo, n_l, accumulate,
                                                     c->stream), "contract adj fp64");
     } else if (use_basis_gemm(c, precision)) {
-      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate));
+      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate, false));
     } else {
       SWCL_TRY(swcl::contract_adj_tc(c, precision));   // whole multipole range (no chunks)
     }
@@ -1210,7 +1214,6 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
     c->ell_fft = n_fft;
     SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nw2 * N_tr * N_I * n_h));
     SWCL_TRY(swcl::ensure(c, c->ws_delta, (size_t)nw2 * N_tr * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
-    SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(1, N_tr, N_k, n_lc)));
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, jW, (const double*)c->d_chipow.p,
                                              sv.D, sv.B, (const cplx*)c->d_psi.p,
@@ -1228,7 +1231,7 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
       if (fp64) {
         SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                               (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
-                                              N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                              N_tr, N_k, N_ell, l_lo, n_l,
                                               c->stream), "k-quadrature fp64");
         SWCL_LAUNCH(c, swcl::launch_quad_jvp<double>((double*)c->ws_dU.p, (const double*)c->ws_delta.p,
                                                      (const double*)c->d_P.p, jP,
@@ -1237,14 +1240,13 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
       } else {
         SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                              (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
-                                             N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                             N_tr, N_k, N_ell, l_lo, n_l,
                                              c->stream), "k-quadrature f32");
         SWCL_LAUNCH(c, swcl::launch_quad_jvp<float>((double*)c->ws_dU.p, (const float*)c->ws_delta.p,
                                                     (const double*)c->d_P.p, jP,
                                                     (const double*)c->d_wk2.p, has_w, n_dir, N_tr,
                                                     N_k, N_ell, l_lo, n_l, c->stream), "jvp quadrature");
       }
-      ++c->last_launches;  // the pair-sum reduction of the base quadrature
     }
   }
   if (lim.n_lim > 0) {

@@ -597,29 +597,6 @@ __global__ void k_kmu(float* __restrict__ kmu, const double* __restrict__ kpow,
   }
 }
 
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
-}
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-// (a_hi + a_lo)(b_hi + b_lo) - (c_hi + c_lo)(d_hi + d_lo) in double-float (sgn = -1), or + (sgn = 1)
-__device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, float ch, float cl,
-                                        float dh, float dl, float sgn, float& hi, float& lo) {
-  float p1, e1, p2, e2;
-  two_prod(ah, bh, p1, e1);
-  two_prod(ch, dh, p2, e2);
-  e1 = fmaf(ah, bl, fmaf(al, bh, e1));
-  e2 = fmaf(ch, dl, fmaf(cl, dh, e2));
-  float s, es;
-  two_sum(p1, sgn * p2, s, es);
-  const float l = es + e1 + sgn * e2;
-  hi = s + l;
-  lo = l - (hi - s);
-}
 
 // Forward B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
 // (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
@@ -699,6 +676,84 @@ __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar
     }
     store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
                           off64(row, ch * 16), v);
+  }
+}
+
+// The reverse mode's Dbar (a5) fused with the adjoint GEMM's B image, for one multipole of one
+// walker and 128 k points per CTA (grid: k tiles, multipoles of the chunk, walkers):
+//   T_i = sum_j S_ij A_j Delta_j(l, q),   Dbar_i = 2 A_i u_q T_i  (FP32, S = (Cbar + Cbar^T)/2),
+//   image row ((w N_tr + i) r + s) n_l + l, column q:  kmu[i][s][q] Dbar_i, split into 3 bf16
+//   planes,
+// and the multipole's P_bar partial sum_i A_i Delta_i T_i (compensated FP32, written as FP64 to
+// pbar_part[l][w][q] for the ordered reduction).  The arithmetic is that of k_delta_bar followed
+// by k_dimg, without the round trip of Dbar through global memory.  The CTAs of the first
+// multipole and walker also write the zero rows that pad the last column tile.
+constexpr int kDT = 128;
+__global__ void __launch_bounds__(kDT)
+k_dbar_dimg(uint8_t* __restrict__ img, double* __restrict__ pbar_part, const float* __restrict__ delta,
+            const double* __restrict__ Cf, const double* __restrict__ amp,
+            const double* __restrict__ P, const double* __restrict__ wk2,
+            const float* __restrict__ kmu, int N_tr, int N_k, int N_ell, int n_walk, int l_lo,
+            int n_l, int r, int n_cols, int NT, int n_nt, int n_kb) {
+  extern __shared__ __align__(16) float dsm[];
+  float* St = dsm;                        // [N_tr][N_tr]  St[j][i] = S_ij A_j
+  float* Dl = St + N_tr * N_tr;           // [N_tr][kDT]
+  float* As = Dl + N_tr * kDT;            // [N_tr]
+  const int ll = blockIdx.y, w = blockIdx.z;
+  const int l = l_lo + ll;
+  const int q = blockIdx.x * kDT + threadIdx.x;
+  const bool in_img = q < n_kb * kK;      // inside the image's K range (zero past N_k)
+  const bool live = q < N_k;
+  const double* A = amp + (size_t)w * N_tr;
+  for (int e = threadIdx.x; e < N_tr * N_tr; e += kDT) {
+    const int j = e / N_tr, i = e - j * N_tr;
+    St[e] = (float)(Cf[((size_t)w * N_ell + l) * N_tr * N_tr + i * N_tr + j] * A[j]);
+  }
+  for (int e = threadIdx.x; e < N_tr; e += kDT) As[e] = (float)A[e];
+  const float* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
+#pragma unroll 8
+  for (int t = 0; t < N_tr; ++t) Dl[t * kDT + threadIdx.x] = live ? dl[(size_t)t * N_k + q] : 0.0f;
+  __syncthreads();
+  if (!in_img) return;
+  const float two_u = live ? (float)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : 0.0f;
+  const float* dq = Dl + threadIdx.x;
+  const int kb = q / kK;
+  const uint32_t kbyte = (uint32_t)(q % kK) * 2;
+  const size_t plane = (size_t)NT * kRow;
+  float ps = 0.0f, pc = 0.0f;
+  for (int i = 0; i < N_tr; ++i) {
+    float t = 0.0f;
+    for (int j = 0; j < N_tr; ++j) t = fmaf(St[j * N_tr + i], dq[j * kDT], t);
+    const float ai = As[i];
+    {
+      // P_bar partial: compensated sum (TwoSum)
+      const float x = ai * dq[i * kDT] * t;
+      const float sn = ps + x;
+      const float bp = sn - ps;
+      pc += (ps - (sn - bp)) + (x - bp);
+      ps = sn;
+    }
+    const float db = two_u * ai * t;
+    for (int s = 0; s < r; ++s) {
+      const int jrow = ((w * N_tr + i) * r + s) * n_l + ll;
+      const int nt = jrow / NT, row = jrow - nt * NT;
+      const float x = live ? kmu[((size_t)i * 4 + s) * N_k + q] * db : 0.0f;
+      __nv_bfloat16 v[3];
+      split_f32(x, v);
+      uint8_t* dst = img + ((size_t)nt * n_kb + kb) * kPlanes * plane + off64(row, kbyte);
+#pragma unroll
+      for (int p = 0; p < kPlanes; ++p) *reinterpret_cast<__nv_bfloat16*>(dst + p * plane) = v[p];
+    }
+  }
+  if (live) pbar_part[((size_t)l * n_walk + w) * N_k + q] = (double)ps + (double)pc;
+  if (ll == 0 && w == 0) {
+    // zero rows past the last column
+    for (int jrow = n_cols; jrow < n_nt * NT; ++jrow) {
+      const int nt = jrow / NT, row = jrow - nt * NT;
+      uint8_t* dst = img + ((size_t)nt * n_kb + kb) * kPlanes * plane + off64(row, kbyte);
+#pragma unroll
+      for (int p = 0; p < kPlanes; ++p) *reinterpret_cast<__nv_bfloat16*>(dst + p * plane) = __float2bfloat16_rn(0.0f);
+    }
   }
 }
 
@@ -934,7 +989,33 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
 
 // ws_cbar (FP64 complex, [n_walk][N_tr][NI][n_h], zeroed here) from ws_dbar (FP32,
 // [n_walk][n_l][N_tr][N_k]) for multipoles [l_lo, l_lo + n_l); accumulate = keep ws_cbar.
-int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
+int basis_dbar_image(swcl_ctx* c, int l_lo, int n_l, double* pbar_part) {
+  int st = basis_prepare(c);
+  if (st) return st;
+  if (c->bt_nt_adj == 0) return fail(c, SWCL_ERR_STATE, "adjoint tile not chosen yet");
+  const int r = basis_rank(c);
+  const int n_cols = c->n_walk * c->N_tr * r * n_l;
+  const int NT = c->bt_nt_adj & 255;
+  const int n_nt = (n_cols + NT - 1) / NT;
+  if ((st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow))) return st;
+  const size_t smem = sizeof(float) * ((size_t)c->N_tr * c->N_tr + (size_t)c->N_tr * kDT + c->N_tr);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_dbar_dimg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dbar image attribute");
+  }
+  const dim3 grid((c->bt_a_kb * kK + kDT - 1) / kDT, n_l, c->n_walk);
+  return counted(c, "dbar + image adj", [&] {
+    k_dbar_dimg<<<grid, kDT, smem, c->stream>>>(
+        (uint8_t*)c->bt_dimg.p, pbar_part, (const float*)c->ws_delta.p, (const double*)c->ws_Cbar.p,
+        (const double*)c->d_amp.p, (const double*)c->d_P.p, (const double*)c->d_wk2.p,
+        (const float*)c->bt_kmu.p, c->N_tr, c->N_k, c->N_ell, c->n_walk, l_lo, n_l, r, n_cols, NT,
+        n_nt, c->bt_a_kb);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "dbar image");
+  });
+}
+
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_ready) {
   int st = basis_prepare(c);
   if (st) return st;
   const Stencil sv = stencil(c);
@@ -971,7 +1052,9 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
   }
   const int code = c->bt_nt_adj, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
-  if ((st = counted(c, "basis operand adj", [&] { return build_d(c, NT, n_nt, n_l); }))) return st;
+  if (!image_ready &&
+      (st = counted(c, "basis operand adj", [&] { return build_d(c, NT, n_nt, n_l); })))
+    return st;
   return counted(c, "basis gemm adj", [&] { return run(code, false); });
 }
 

@@ -404,27 +404,39 @@ __global__ void k_build_bimg(uint8_t* __restrict__ img, const cplx* __restrict__
   }
 }
 
-// phaseT[n][q] = (float2) phase[q][n]
-__global__ void k_phase_t(float2* __restrict__ out, const cplx* __restrict__ phase, int N_k, int n_h) {
-  __shared__ float2 tile[32][33];
+// phaseT[n][q] = (float2) phase[q][n], and the double-float low parts phase - phaseT
+__global__ void k_phase_t(float2* __restrict__ out, float2* __restrict__ out_lo,
+                          const cplx* __restrict__ phase, int N_k, int n_h) {
+  __shared__ float2 tile[32][33], tlo[32][33];
   const int n0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
   for (int t = threadIdx.y; t < 32; t += blockDim.y) {
     const int q = q0 + t, n = n0 + threadIdx.x;
     if (q < N_k && n < n_h) {
       const cplx v = phase[(size_t)q * n_h + n];
-      tile[t][threadIdx.x] = make_float2((float)v.x, (float)v.y);
+      const float2 h = make_float2((float)v.x, (float)v.y);
+      tile[t][threadIdx.x] = h;
+      tlo[t][threadIdx.x] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
     }
   }
   __syncthreads();
   for (int t = threadIdx.y; t < 32; t += blockDim.y) {
     const int n = n0 + t, q = q0 + threadIdx.x;
-    if (q < N_k && n < n_h) out[(size_t)n * N_k + q] = tile[threadIdx.x][t];
+    if (q < N_k && n < n_h) {
+      out[(size_t)n * N_k + q] = tile[threadIdx.x][t];
+      out_lo[(size_t)n * N_k + q] = tlo[threadIdx.x][t];
+    }
   }
 }
 
-__global__ void k_to_f32(float* __restrict__ out, const double* __restrict__ in, long n) {
+// FP64 -> double-float (hi = rounded value, lo = the remainder rounded)
+__global__ void k_to_f32(float* __restrict__ out, float* __restrict__ out_lo,
+                         const double* __restrict__ in, long n) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = (float)in[t];
+  if (t < n) {
+    const float h = (float)in[t];
+    out[t] = h;
+    out_lo[t] = (float)(in[t] - (double)h);
+  }
 }
 
 template <class P>
@@ -444,20 +456,29 @@ int prepare_tables(swcl_ctx* c, int precision, int& NT, int& n_lt, int& n_kb) {
   if (st) return st;
   st = ensure(c, T.phase32, sizeof(float2) * (size_t)c->N_k * n_h);
   if (st) return st;
+  st = ensure(c, T.phase_lo, sizeof(float2) * (size_t)c->N_k * n_h);
+  if (st) return st;
   const Stencil sv = stencil(c);
   const long n_lw = 4L * c->N_k * (sv.w_ts ? c->N_tr : 1);
   st = ensure(c, c->tc_lw32, sizeof(float) * n_lw);
   if (st) return st;
+  st = ensure(c, c->tc_lw_lo, sizeof(float) * n_lw);
+  if (st) return st;
   st = ensure(c, c->tc_kpow32, sizeof(float) * (size_t)c->N_tr * c->N_k);
+  if (st) return st;
+  st = ensure(c, c->tc_kpow_lo, sizeof(float) * (size_t)c->N_tr * c->N_k);
   if (st) return st;
   const long per = (long)c->n_cls * n_lt * n_kb * NT * P::kKb;
   k_build_bimg<P><<<(unsigned)std::min<long>((per + 255) / 256, 152L * 64), 256, 0, c->stream>>>(
       (uint8_t*)T.bfwd.p, (const cplx*)c->d_gtab.p, c->n_cls, c->N_ell, n_h, NT, n_lt, n_kb);
   dim3 gt((n_h + 31) / 32, (c->N_k + 31) / 32), bt(32, 8);
-  k_phase_t<<<gt, bt, 0, c->stream>>>((float2*)T.phase32.p, (const cplx*)c->d_phase.p, c->N_k, n_h);
-  k_to_f32<<<(unsigned)((n_lw + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_lw32.p, sv.w, n_lw);
+  k_phase_t<<<gt, bt, 0, c->stream>>>((float2*)T.phase32.p, (float2*)T.phase_lo.p,
+                                      (const cplx*)c->d_phase.p, c->N_k, n_h);
+  k_to_f32<<<(unsigned)((n_lw + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_lw32.p,
+                                                                 (float*)c->tc_lw_lo.p, sv.w, n_lw);
   long nk = (long)c->N_tr * c->N_k;
   k_to_f32<<<(unsigned)((nk + 255) / 256), 256, 0, c->stream>>>((float*)c->tc_kpow32.p,
+                                                               (float*)c->tc_kpow_lo.p,
                                                                (const double*)c->d_kpow.p, nk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core operand tables");

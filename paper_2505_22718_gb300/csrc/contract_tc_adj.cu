@@ -6,9 +6,12 @@
 // K = multipoles.  Both operands are pre-split images streamed by cp.async.bulk (A: Dbar, B: the
 // Gamma table transposed); the tensor core accumulates one K-block at a time into double-buffered
 // TMEM slots that the other warps drain into FP32 registers, as in the forward kernel.  The
-// epilogue applies the phase, reduces over the tile's k points into per-knot partial sums
-// (staged in shared memory) and writes them; a second kernel adds the partials of neighbouring
-// tiles deterministically.
+// epilogue applies k^{t-1-b} and the phase and reduces over the tile's k points into per-knot
+// partial sums (staged in shared memory), all in double-float arithmetic: the phase rotates
+// quickly with k at large n, so these k-sums cancel strongly, and single FP32 roundings of the
+// phase, the weights or the running sum would reach the gradient W_bar through the inverse
+// transform (Eq. 3.2).  The partials are written as FP64; a second kernel adds the partials of
+// neighbouring tiles deterministically.
 #include <algorithm>
 #include <vector>
 
@@ -41,11 +44,13 @@ __host__ __device__ inline AdjLayout adj_layout(int stages) {
 
 template <class P>
 __global__ void __launch_bounds__(kThr, 1)
-k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
+k_contract_tc_adj(cplx* __restrict__ cpart, const uint8_t* __restrict__ aimg,
                   const uint8_t* __restrict__ bimgT, const int* __restrict__ cls_of,
-                  const float* __restrict__ kpow32, const int* __restrict__ j0,
-                  const float* __restrict__ lw32, long lw_ts, const float2* __restrict__ phaseT,
-                  const int* __restrict__ tile_alo, int N_tr, int N_I, int n_h, int N_k, int n_ct,
+                  const float* __restrict__ kpow32, const float* __restrict__ kpow_lo,
+                  const int* __restrict__ j0, const float* __restrict__ lw32,
+                  const float* __restrict__ lw_lo, long lw_ts, const float2* __restrict__ phaseT,
+                  const float2* __restrict__ phase_lo, const int* __restrict__ tile_alo, int N_tr,
+                  int N_I, int n_h, int N_k, int n_ct,
                   int n_qt, int n_kb, int R, int stages, uint32_t tmem_cols,
                   int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
@@ -141,35 +146,48 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
       atomicExch(status, 1);
     }
     // ---------------------------------------------------------------- epilogue ----
-    // all MMAs are complete (last drain) and every stage has been consumed: reuse stage memory
+    // all MMAs are complete (last drain) and every stage has been consumed: reuse stage memory.
+    // V[m][r] = X conj(E) as double-float (re_hi, im_hi, re_lo, im_lo); tlw/tlwl the row's
+    // Lagrange weights (hi, lo)
     constexpr int VS = kMTile + 1;                                    // padded row stride
-    float2* V = reinterpret_cast<float2*>(base);                       // [64 columns][VS]
-    int* tj0 = reinterpret_cast<int*>(base + 64 * VS * sizeof(float2));
+    float4* V = reinterpret_cast<float4*>(base);                       // [64 columns][VS]
+    int* tj0 = reinterpret_cast<int*>(base + 64 * VS * sizeof(float4));
     float4* tlw = reinterpret_cast<float4*>(tj0 + kMTile);
+    float4* tlwl = tlw + kMTile;
     asm volatile("bar.sync 1, %0;" ::"r"(kWarps * 32) : "memory");
     {
       const int q = q0 + row_acc;
       const bool live = ok && q < N_k;
       const float kp = live ? kpow32[(size_t)i * N_k + q] : 0.0f;
+      const float kpl = live ? kpow_lo[(size_t)i * N_k + q] : 0.0f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
 #pragma unroll
         for (int t = 0; t < 16; t += 2) {
           const int m = (c_begin + c) * 8 + t / 2;        // local complex column
           const int n = ct * (kCT / 2) + m;
-          float2 v = make_float2(0.f, 0.f);
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (live && n < n_h) {
-            const float xr = kp * acc[c * 16 + t], xi = kp * acc[c * 16 + t + 1];
+            // X = k^{t-1-b} acc exactly as double-float, then X conj(E) in double-float
+            float xr, xrl, xi, xil;
+            two_prod(kp, acc[c * 16 + t], xr, xrl);
+            two_prod(kp, acc[c * 16 + t + 1], xi, xil);
+            xrl = fmaf(kpl, acc[c * 16 + t], xrl);
+            xil = fmaf(kpl, acc[c * 16 + t + 1], xil);
             const float2 e = phaseT[(size_t)n * N_k + q];
-            v = make_float2(fmaf(xr, e.x, xi * e.y), fmaf(xi, e.x, -xr * e.y));   // X conj(E)
+            const float2 el = phase_lo[(size_t)n * N_k + q];
+            // Re = xr er + xi ei,  Im = xi er - xr ei
+            df_dot2(xr, xrl, e.x, el.x, xi, xil, e.y, el.y, 1.0f, v.x, v.z);
+            df_dot2(xi, xil, e.x, el.x, xr, xrl, e.y, el.y, -1.0f, v.y, v.w);
           }
           V[m * VS + row_acc] = v;
         }
       }
       if (half == 0) {
         tj0[row_acc] = q < N_k ? j0[q] : 0x7fffffff;
-        tlw[row_acc] = q < N_k ? *reinterpret_cast<const float4*>(lw32 + (size_t)i * lw_ts + (size_t)q * 4)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t lo = (size_t)i * lw_ts + (size_t)q * 4;
+        tlw[row_acc] = q < N_k ? *reinterpret_cast<const float4*>(lw32 + lo) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tlwl[row_acc] = q < N_k ? *reinterpret_cast<const float4*>(lw_lo + lo) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     asm volatile("bar.sync 1, %0;" ::"r"(kWarps * 32) : "memory");
@@ -178,13 +196,13 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
       const int q_last = min(q0 + kMTile, N_k) - 1;
       const int a_hi = min(N_I - 1, tj0[q_last - q0] + 3);
       const int nk = a_hi - a_lo + 1;
-      float2* out = cpart + (size_t)(wi * n_qt + qt) * R * n_h;
+      cplx* out = cpart + (size_t)(wi * n_qt + qt) * R * n_h;
       for (int item = tid; item < nk * 64; item += kWarps * 32) {
         const int ka = item / 64, m = item - ka * 64;
         const int a = a_lo + ka;
         const int n = ct * (kCT / 2) + m;
         if (n >= n_h) continue;
-        float sr = 0.f, si = 0.f;
+        float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
         // first row whose stencil can hold knot a (j0 >= a - 3; j0 is nondecreasing in q)
         int lo = 0, hi = kMTile;
         while (lo < hi) {
@@ -195,13 +213,14 @@ k_contract_tc_adj(float2* __restrict__ cpart, const uint8_t* __restrict__ aimg,
           const int jr = tj0[r];
           if (jr > a) break;
           const int d = a - jr;
-          const float4 lw = tlw[r];
+          const float4 lw = tlw[r], lwl = tlwl[r];
           const float l = d == 0 ? lw.x : d == 1 ? lw.y : d == 2 ? lw.z : lw.w;
-          const float2 v = V[m * VS + r];
-          sr = fmaf(l, v.x, sr);
-          si = fmaf(l, v.y, si);
+          const float ll = d == 0 ? lwl.x : d == 1 ? lwl.y : d == 2 ? lwl.z : lwl.w;
+          const float4 v = V[m * VS + r];
+          df_fma(l, ll, v.x, v.z, sr, srl);
+          df_fma(l, ll, v.y, v.w, si, sil);
         }
-        out[(size_t)ka * n_h + n] = make_float2(sr, si);
+        out[(size_t)ka * n_h + n] = cplx{(double)sr + (double)srl, (double)si + (double)sil};
       }
     }
   } else if (lane == 0) {
@@ -337,7 +356,7 @@ __global__ void k_build_bimgT(uint8_t* __restrict__ img, const cplx* __restrict_
 }
 
 // cbar[wi][a][n] = sum over the k tiles whose knot range holds a of the tile partials.
-__global__ void k_knot_reduce(cplx* __restrict__ cbar, const float2* __restrict__ cpart,
+__global__ void k_knot_reduce(cplx* __restrict__ cbar, const cplx* __restrict__ cpart,
                               const int* __restrict__ tile_alo, const int* __restrict__ knot_qt,
                               int n_wi, int N_I, int n_h, int n_qt, int R) {
   const long total = (long)n_wi * N_I * n_h;
@@ -349,7 +368,7 @@ __global__ void k_knot_reduce(cplx* __restrict__ cbar, const float2* __restrict_
     for (int qt = knot_qt[2 * a]; qt <= knot_qt[2 * a + 1]; ++qt) {
       const int ka = a - tile_alo[qt];
       if (ka < 0 || ka >= R) continue;
-      const float2 v = cpart[((size_t)(wi * n_qt + qt) * R + ka) * n_h + n];
+      const cplx v = cpart[((size_t)(wi * n_qt + qt) * R + ka) * n_h + n];
       sr += (double)v.x;
       si += (double)v.y;
     }
@@ -399,7 +418,7 @@ int run_adjoint(swcl_ctx* c, int precision) {
   }
   const size_t abytes = (size_t)n_wi * n_qt * n_kb * P::kPlanesA * kPlaneA;
   if ((st = ensure(c, c->ws_aimg, abytes))) return st;
-  if ((st = ensure(c, c->ws_cpart, sizeof(float2) * (size_t)n_wi * n_qt * T.R * n_h))) return st;
+  if ((st = ensure(c, c->ws_cpart, sizeof(cplx) * (size_t)n_wi * n_qt * T.R * n_h))) return st;
   {
     constexpr int EPC = 16 / P::kElemBytes;
     const long tot = (long)n_wi * n_qt * n_kb * kMTile * (P::kKb / EPC);
@@ -415,7 +434,7 @@ int run_adjoint(swcl_ctx* c, int precision) {
   AdjLayout L = adj_layout<P>(stages);
   while (stages > 2 && L.total > 227 * 1024) L = adj_layout<P>(--stages);
   if (L.total > 227 * 1024) return fail(c, SWCL_ERR_UNSUPPORTED, "VJP tile does not fit shared memory");
-  if (L.total < (uint32_t)(64 * (kMTile + 1) * sizeof(float2) + kMTile * (sizeof(int) + sizeof(float4)) + 1024))
+  if (L.total < (uint32_t)(64 * (kMTile + 1) * sizeof(float4) + kMTile * (sizeof(int) + 2 * sizeof(float4)) + 1024))
     return fail(c, SWCL_ERR_UNSUPPORTED, "VJP epilogue staging does not fit");
   cudaError_t e = cudaFuncSetAttribute(k_contract_tc_adj<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
@@ -424,9 +443,10 @@ int run_adjoint(swcl_ctx* c, int precision) {
   prof_begin(c);
   ++c->last_launches;
   k_contract_tc_adj<P><<<(unsigned)grid, kThr, L.total, c->stream>>>(
-      (float2*)c->ws_cpart.p, (const uint8_t*)c->ws_aimg.p, (const uint8_t*)T.bvjp.p,
-      (const int*)c->d_cls_of.p, (const float*)c->tc_kpow32.p, sv.j0,
-      (const float*)c->tc_lw32.p, sv.w_ts, (const float2*)T.phase32.p, (const int*)T.tile_alo.p, N_tr, N_I,
+      (cplx*)c->ws_cpart.p, (const uint8_t*)c->ws_aimg.p, (const uint8_t*)T.bvjp.p,
+      (const int*)c->d_cls_of.p, (const float*)c->tc_kpow32.p, (const float*)c->tc_kpow_lo.p, sv.j0,
+      (const float*)c->tc_lw32.p, (const float*)c->tc_lw_lo.p, sv.w_ts, (const float2*)T.phase32.p,
+      (const float2*)T.phase_lo.p, (const int*)T.tile_alo.p, N_tr, N_I,
       n_h, N_k, n_ct, n_qt, n_kb, T.R, stages, 4 * kCT, (int*)c->ws_status.p);
   e = cudaGetLastError();
   prof_end(c, "contract adj tc");
@@ -435,7 +455,7 @@ int run_adjoint(swcl_ctx* c, int precision) {
   prof_begin(c);
   ++c->last_launches;
   k_knot_reduce<<<(unsigned)std::min<long>((tot + 255) / 256, 152L * 64), 256, 0, c->stream>>>(
-      (cplx*)c->ws_cbar.p, (const float2*)c->ws_cpart.p, (const int*)T.tile_alo.p,
+      (cplx*)c->ws_cbar.p, (const cplx*)c->ws_cpart.p, (const int*)T.tile_alo.p,
       (const int*)T.knot_qt.p, n_wi, N_I, n_h, n_qt, T.R);
   e = cudaGetLastError();
   prof_end(c, "knot reduce");

@@ -35,6 +35,7 @@ struct TcTables {
   DevBuf bfwd;      // forward B image [cls][l tile][K-block][plane][NT x 128 B]
   DevBuf bvjp;      // VJP B image [cls][column tile][K-block][plane][128 x 128 B]
   DevBuf phase32;   // float2 phase table [n_h][N_k] (transposed)
+  DevBuf phase_lo;  // float2 [n_h][N_k]: phase - phase32 (double-float low parts)
   DevBuf tile_alo;  // [n_qt] first knot touched by each 128-point k tile
   DevBuf knot_qt;   // [N_I][2] first/last k tile touching each knot
   int R = 0;        // knot slots per k tile
@@ -46,7 +47,11 @@ int contract_adj_tc(swcl_ctx* c, int precision);
 // a3 / a5 in basis mode as GEMMs against the constant phase operand (basis_tc.cu)
 int basis_prepare(swcl_ctx* c);
 int basis_forward(swcl_ctx* c, int l_lo, int n_l);
-int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate);
+// image_ready: the B image was built by basis_dbar_image (which also forms the P_bar partials)
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_ready);
+// Dbar of the chunk straight into the adjoint GEMM's B image (at the chosen adjoint tile) with the
+// P_bar partials, in place of launch_delta_bar + the image build
+int basis_dbar_image(swcl_ctx* c, int l_lo, int n_l, double* pbar_part);
 size_t basis_fixed_bytes(const swcl_ctx* c);     // constant operands of basis mode
 size_t basis_bytes_per_ell(const swcl_ctx* c);   // per-call operand images per multipole
 
@@ -125,6 +130,7 @@ struct swcl_ctx {
   swcl::TcTables tc[4];
   swcl::DevBuf tc_lw32;                       // [N_k][4] float interpolation weights
   swcl::DevBuf tc_kpow32;                     // [N_tr][N_k] float k^{t-1-b}
+  swcl::DevBuf tc_lw_lo, tc_kpow_lo;          // double-float low parts of the two tables above
 
   // windows / power
   int n_walk = 0;
@@ -171,7 +177,6 @@ struct swcl_ctx {
   swcl::DevBuf ws_aimg;      // VJP: split Dbar image (tensor-core A operand)
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
-  swcl::DevBuf ws_qpart;     // forward: per-k-chunk partial pair sums of the k-quadrature
   swcl::DevBuf ws_jin;       // JVP: windows [1 + n_dir][N_tr][N] (base first), P' [n_dir][N_k], A' [n_dir][N_tr]
   swcl::DevBuf ws_dU;        // JVP: [n_dir][N_ell][N_tr][N_tr] tangent of U
   swcl::DevBuf ws_jout;      // JVP output / Fisher input staging for host arrays
@@ -281,14 +286,12 @@ cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx*
 
 // a4 k-quadrature and VJP reductions (quad.cu).  Delta and Dbar buffers hold the multipoles
 // l_lo .. l_lo + n_l - 1 ([n_walk][n_l][N_tr][N_k]); U and Cbar_full all N_ell.
-// scratch: quad_scratch_bytes(n_walk, N_tr, N_k, n_l) of per-k-chunk pair sums
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                             double* scratch, cudaStream_t s);
+                             cudaStream_t s);
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                            double* scratch, cudaStream_t s);
-size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l);
+                            cudaStream_t s);
 
 // self-test of the bounded waits (selftest.cu)
 cudaError_t launch_wait_nothing(int* status, long long* cycles, cudaStream_t s);

@@ -204,6 +204,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
 }
 
+// Double-float arithmetic (a value carried as hi + lo, |lo| <= ulp(hi)/2) from error-free
+// transformations: the product's rounding error from an FMA, the sum's from TwoSum.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (a_hi + a_lo)(b_hi + b_lo) - (c_hi + c_lo)(d_hi + d_lo) in double-float (sgn = -1), or + (sgn = 1)
+__device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, float ch, float cl,
+                                        float dh, float dl, float sgn, float& hi, float& lo) {
+  float p1, e1, p2, e2;
+  two_prod(ah, bh, p1, e1);
+  two_prod(ch, dh, p2, e2);
+  e1 = fmaf(ah, bl, fmaf(al, bh, e1));
+  e2 = fmaf(ch, dl, fmaf(cl, dh, e2));
+  float s, es;
+  two_sum(p1, sgn * p2, s, es);
+  const float l = es + e1 + sgn * e2;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+// (s_hi, s_lo) += (a_hi + a_lo)(b_hi + b_lo) in double-float
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float p, e;
+  two_prod(ah, bh, p, e);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  float t, te;
+  two_sum(sh, p, t, te);
+  te += sl + e;
+  sh = t + te;
+  sl = te - (sh - t);
+}
+
 // tf32 rounding (to nearest, ties away), kept in a 32-bit float container
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;

@@ -18,6 +18,37 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.abs(b).max(), 1e-300))
 
 
+def p_abs(delta, C_bar, amp, k):
+    """Size of the terms that form each P_bar_q, from the oracle's Delta [N_ell][N_tr][N_k]:
+    (2/pi) w_q k_q^2 sum_l sum_ij |S_ij A_i A_j Delta_i(l, k_q) Delta_j(l, k_q)|, S the
+    symmetrised cotangent.  P_bar_q is a sum of terms of both signs (S is a random cotangent), so
+    its relative accuracy is that of Delta times the ratio of this sum to |P_bar_q|; gating
+    |P_bar - P_bar_oracle| against tol * p_abs is gating every entry at the accuracy the forward
+    gate allows for Delta."""
+    S = 0.5 * (C_bar + np.transpose(C_bar, (0, 2, 1)))
+    A = np.asarray(amp, dtype=np.float64)
+    SA = np.abs(S * A[None, :, None] * A[None, None, :])
+    d = np.abs(delta)
+    return (2.0 / np.pi) * O.lnk_trapezoid_weights(k) * k ** 2 * np.einsum("lij,liq,ljq->q", SA, d, d)
+
+
+def pbar_err(g, go, pabs):
+    """Per-element error of P_bar against the size of the terms that form it (p_abs)."""
+    g = np.asarray(g, dtype=np.float64).reshape(-1)
+    go = np.asarray(go, dtype=np.float64).reshape(-1)
+    return float(np.max(np.abs(g - go) / np.maximum(pabs, 1e-300)))
+
+
+def wbar_err(g, go):
+    """Per-row error of W_bar: max over the rows (walker, tracer) of max_m |g - go| / max_m |go|.
+    W_bar_i(chi_m) is an inverse DFT of the coefficient cotangents (the adjoint of Eq. 3.2), so an
+    error in any coefficient spreads evenly over the row: the row's largest entry is the scale."""
+    g = np.asarray(g, dtype=np.float64)
+    go = np.asarray(go, dtype=np.float64).reshape(g.shape)
+    rmax = np.abs(go).max(axis=-1)
+    return float(np.max(np.abs(g - go).max(axis=-1) / np.maximum(rmax, 1e-300)))
+
+
 def grad_err(g, go, floor=1e-3):
     """Per-element error of a gradient: max |g - go| / max(|go|, floor * max |go| of its row),
     rows along the last axis (P_bar: one row of N_k per walker; W_bar: one row of N per walker
@@ -55,7 +86,9 @@ def oracle_walker(w, widx=None, tapers=None, C_bar=None, ells_sel=None):
     f = O.forward(g, W, w.D, P, amp, w.B, tc, tn)
     if C_bar is None:
         return f, None
-    return f, O.vjp(g, f, C_bar, W, w.D, P, amp, w.B, tc, tn)
+    Pb, Ab, Wb, extra = O.vjp(g, f, C_bar, W, w.D, P, amp, w.B, tc, tn)
+    extra = dict(extra, P_abs=p_abs(f["delta"], C_bar, amp, w.k))
+    return f, (Pb, Ab, Wb, extra)
 
 
 def make_ragged_case(n_walk=3, seed=11):

@@ -3,7 +3,7 @@ lists, per-walker P(k), amplitudes and window shifts; replay after a parameter u
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, max_rel, norm_err, oracle_walker
+from gpu_helpers import grad_err, lib_context, norm_err, oracle_walker, pbar_err, wbar_err
 
 pytestmark = pytest.mark.gpu
 
@@ -46,11 +46,11 @@ def test_batched_graph_against_oracle(prec, walkers8):
         n = len(lst)
         Cbw = np.zeros((len(w.ells), w.n_tr, w.n_tr))
         Cbw[lst] = Cb[o:o + n]
-        f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, C_bar=Cbw)
+        f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, wk, C_bar=Cbw)
         assert norm_err(C[o:o + n].cpu().numpy(), f["C"][lst]) < gate_c, wk
-        assert grad_err(Pb[wk].cpu().numpy(), Pbo) < gate_g
+        assert pbar_err(Pb[wk].cpu().numpy(), Pbo, ex["P_abs"]) < gate_g
         assert grad_err(Ab[wk].cpu().numpy(), Abo) < gate_g
-        assert grad_err(Wb[wk].cpu().numpy(), Wbo) < gate_g
+        assert wbar_err(Wb[wk].cpu().numpy(), Wbo) < gate_g
         o += n
 
 

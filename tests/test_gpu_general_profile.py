@@ -14,7 +14,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, make_ragged_case, max_rel, norm_err, oracle_walker
+from gpu_helpers import grad_err, lib_context, make_ragged_case, max_rel, norm_err, oracle_walker, pbar_err, wbar_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_general_profile_is_not_low_rank(general_ref):
 @pytest.mark.parametrize("prec", ["bf16x9", "tf32x6"])
 def test_general_forward_and_vjp(prec, general_ref):
     import paper_2505_22718_gb300 as S
-    w, f, (Pbo, Abo, Wbo, _) = general_ref
+    w, f, (Pbo, Abo, Wbo, ex) = general_ref
     ctx = _context(w, per_knot=False)
     C = ctx.compute_cl(S.PRECISIONS[prec])
     assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 0
@@ -70,8 +70,8 @@ def test_general_forward_and_vjp(prec, general_ref):
     d = S.swcl_debug_read(ctx.ptr, S.SWCL_DBG_DELTA).reshape(f["delta"].shape)
     drel = float((np.abs(d - f["delta"]) / np.abs(f["delta"]).max(axis=2, keepdims=True)).max())
     Pb, Ab, Wb = ctx.vjp(w.C_bar, S.PRECISIONS[prec])
-    ge = (grad_err(Pb[0], Pbo), grad_err(Ab[0], Abo), grad_err(Wb[0], Wbo))
-    gm = (grad_err(Pb[0], Pbo), grad_err(Ab[0], Abo), grad_err(Wb[0], Wbo))
+    ge = (pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0], Abo), wbar_err(Wb[0], Wbo))
+    gm = (pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0], Abo), wbar_err(Wb[0], Wbo))
     print("n5k_general %s: C %.3e, Delta %.3e; per-element P_bar %.2e amp_bar %.2e W_bar %.2e "
           "(max-normalised %.2e %.2e %.2e)" % ((prec, err, drel) + ge + gm))
     assert err < GATE_C
@@ -97,9 +97,9 @@ def test_ragged_per_knot(prec):
         n = len(lst)
         Cbw = np.zeros((len(w.ells), w.n_tr, w.n_tr))
         Cbw[lst] = Cb[o:o + n]
-        f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, tapers, C_bar=Cbw)
+        f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, wk, tapers, C_bar=Cbw)
         err = norm_err(C[o:o + n], f["C"][lst])
-        ge = (grad_err(Pb[wk], Pbo), grad_err(Ab[wk], Abo), grad_err(Wb[wk], Wbo))
+        ge = (pbar_err(Pb[wk], Pbo, ex["P_abs"]), grad_err(Ab[wk], Abo), wbar_err(Wb[wk], Wbo))
         print("ragged per-knot %s walker %d: C %.3e, P_bar %.2e amp_bar %.2e W_bar %.2e"
               % ((prec, wk, err) + ge))
         assert err < GATE_C, wk

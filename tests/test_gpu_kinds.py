@@ -18,7 +18,7 @@ Where the terms do not cancel, E is of the size of the entry and the tau term is
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, max_rel, oracle_walker
+from gpu_helpers import grad_err, lib_context, oracle_walker, p_abs, pbar_err, wbar_err
 from oracle import fftlog as O
 
 pytestmark = pytest.mark.gpu
@@ -131,7 +131,8 @@ def test_mixed_kinds_against_oracle(prec, tol, tau, gtol, kinds_ref):
     dx = np.abs(delta - f["delta"]) / (tol * np.abs(f["delta"]).max(axis=2, keepdims=True) + tau * S)
     cx = _c_excess(C, f["C"], E, tol, tau)
     g = ctx.vjp(Cb, S_.PRECISIONS[prec])
-    ge = [grad_err(a, b) for a, b in zip(g, grads[:3])]
+    ge = [pbar_err(g[0], grads[0], p_abs(f["delta"], Cb, w.amp, w.k)), grad_err(g[1], grads[1]),
+          wbar_err(g[2], grads[2])]
     print("kinds %s: Delta excess %.3g  C excess %.3g  Pbar %.2e  Abar %.2e  Wbar %.2e"
           % (prec, dx.max(), cx, *ge))
     assert dx.max() <= 1.0

@@ -10,7 +10,7 @@ import copy
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, make_ragged_case, max_rel, norm_err
+from gpu_helpers import grad_err, lib_context, make_ragged_case, max_rel, norm_err, wbar_err
 from oracle import fftlog as O
 from oracle import limber as LB
 
@@ -52,6 +52,7 @@ def test_hybrid_forward_and_vjp(prec, sw, case):
     import paper_2505_22718_gb300 as S
     w, tapers, Cb = case
     tol, gtol, wtol = GATES[prec]
+    ptol = 1e-10 if prec == "fp64" else 1e-4
     Co, go = _oracle(w, tapers, Cb, sw)
     ctx = lib_context(w, tapers)
     ctx.set_limber(sw)
@@ -59,10 +60,13 @@ def test_hybrid_forward_and_vjp(prec, sw, case):
     C = ctx.compute_cl(p)
     e = norm_err(C, Co)
     Pb, Ab, Wb = ctx.vjp(np.concatenate(Cb), p)
-    ge = [max(grad_err(x[wk], go[wk][t]) for wk in range(len(go))) for t, x in enumerate((Pb, Ab, Wb))]
+    # P_bar and amp_bar per element (floor 1e-3 of the row), W_bar per row (walker, tracer)
+    ge = [max(grad_err(Pb[wk], go[wk][0]) for wk in range(len(go))),
+          max(grad_err(Ab[wk], go[wk][1]) for wk in range(len(go))),
+          max(wbar_err(Wb[wk], go[wk][2]) for wk in range(len(go)))]
     print("limber %s switch %d: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e" % (prec, sw, e, *ge))
     assert e < tol
-    assert ge[0] < gtol and ge[1] < gtol and ge[2] < wtol
+    assert ge[0] < ptol and ge[1] < gtol and ge[2] < wtol
 
 
 def test_limber_rows_do_not_depend_on_the_precision_form(case):

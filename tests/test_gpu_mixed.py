@@ -1,12 +1,14 @@
 """Parity of the tensor-core (tcgen05) forms with the FP64 oracle.
 
 Gate (reading R9): |C - C_oracle| <= 1e-4 max(|C_ij|, 1e-3 sqrt(C_ii C_jj)) on every entry for
-the split-BF16 (bf16x9) and TF32x6 forms.  The classic 3xTF32 form keeps only 22 bits of the
-Gamma-ratio operand; its error is checked against a looser documented bound."""
+the split-BF16 (bf16x9) and TF32x6 forms.  The classic 3xTF32 form keeps only 22 bits of each
+operand and does NOT meet the 1e-4 gate on the N5K-shaped workload (measured about 1.6e-4): its
+tests report the error and hold it to a regression bound ten times the gate, which is not a pass
+of the gate."""
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, make_ragged_case, norm_err, oracle_walker
+from gpu_helpers import grad_err, lib_context, make_ragged_case, norm_err, oracle_walker, pbar_err, wbar_err
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +55,9 @@ def test_n5k_forward(prec, n5k_ref):
     assert rel.max() < 1e-4
 
 
-def test_n5k_3xtf32_bound(n5k_ref):
-    """3xTF32 (2-plane splits) is reported, not gated at 1e-4: its 22-bit Gamma-ratio operand gives
-    ~1.5e-4 normalised error on this workload."""
+def test_n5k_3xtf32_misses_gate_and_is_reported(n5k_ref):
+    """3xTF32 (2-plane splits, 22 bits per operand) fails the 1e-4 gate on this workload (about
+    1.6e-4).  The error is printed and held to a regression bound of 1e-3."""
     import paper_2505_22718_gb300 as S
     w, f = n5k_ref
     ctx = lib_context(w)
@@ -93,28 +95,28 @@ def test_mixed_then_fp64_on_one_context(wl):
     assert norm_err(C, f["C"]) < 1e-10
 
 
-VJP_GATE = 5e-5   # max |g - g_oracle| / max |g_oracle| for P_bar, amp_bar, W_bar
+VJP_GATE = 5e-5   # P_bar per entry against the size of its terms, amp_bar per entry, W_bar per row
 
 
 @pytest.mark.parametrize("prec", ["bf16x9", "tf32x6", "3xtf32"])
 def test_n5k_vjp(prec, wl):
+    """Gradients of the tensor-core forms; 3xTF32, which misses the forward gate, is held to a
+    regression bound of twice the gradient gate instead (reported, not a pass of the gate)."""
     """Reverse mode through the tensor-core transposed contraction against the oracle's gradient."""
     import paper_2505_22718_gb300 as S
-    from gpu_helpers import grad_err, max_rel
     w = wl("n5k_vjp")
-    f, (Pbo, Abo, Wbo, _) = oracle_walker(w, C_bar=w.C_bar)
+    f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, C_bar=w.C_bar)
     ctx = lib_context(w)
     ctx.compute_cl(S.PRECISIONS[prec])
     Pb, Ab, Wb = ctx.vjp(w.C_bar, S.PRECISIONS[prec])
-    errs = (grad_err(Pb[0], Pbo), grad_err(Ab[0], Abo), grad_err(Wb[0], Wbo))
+    errs = (pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0], Abo), wbar_err(Wb[0], Wbo))
     print("n5k %s VJP errors P_bar %.2e amp_bar %.2e W_bar %.2e" % ((prec,) + errs))
-    assert max(errs) < VJP_GATE
+    assert max(errs) < (2 * VJP_GATE if prec == "3xtf32" else VJP_GATE)
 
 
 @pytest.mark.parametrize("prec", ["bf16x9", "tf32x6"])
 def test_ragged_vjp(prec):
     import paper_2505_22718_gb300 as S
-    from gpu_helpers import grad_err, max_rel
     w, tapers = make_ragged_case()
     ctx = lib_context(w, tapers)
     C = ctx.compute_cl(S.PRECISIONS[prec])
@@ -126,8 +128,8 @@ def test_ragged_vjp(prec):
         n = len(lst)
         Cbw = np.zeros((len(w.ells), 7, 7))
         Cbw[lst] = Cb[o:o + n]
-        f, (Pbo, Abo, Wbo, _) = oracle_walker(w, wk, tapers, C_bar=Cbw)
-        assert grad_err(Pb[wk], Pbo) < VJP_GATE
+        f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, wk, tapers, C_bar=Cbw)
+        assert pbar_err(Pb[wk], Pbo, ex["P_abs"]) < VJP_GATE
         assert grad_err(Ab[wk], Abo) < VJP_GATE
-        assert grad_err(Wb[wk], Wbo) < VJP_GATE
+        assert wbar_err(Wb[wk], Wbo) < VJP_GATE
         o += n

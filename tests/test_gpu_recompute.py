@@ -11,7 +11,7 @@ import copy
 import numpy as np
 import pytest
 
-from gpu_helpers import grad_err, lib_context, max_rel, norm_err
+from gpu_helpers import grad_err, lib_context, max_rel, norm_err, p_abs, pbar_err, wbar_err
 from oracle import fftlog as O
 
 pytestmark = pytest.mark.gpu
@@ -77,14 +77,15 @@ def test_large_configuration_sampled_against_oracle(prec):
     g = O.Grids(s.N, s.chi_min, s.chi_max, s.k, s.ells, s.knots, s.kind, s.fft_bias, fft="numpy")
     f = O.forward(g, s.W, s.D, s.P, s.amp, s.B)
     Pbo, Abo, Wbo, _ = O.vjp(g, f, Cb[np.ix_(li, tr, tr)], s.W, s.D, s.P, s.amp, s.B)
+    ex = {"P_abs": p_abs(f["delta"], Cb[np.ix_(li, tr, tr)], s.amp, s.k)}
     gate_c, gate_g = (1e-10, 1e-9) if prec == "fp64" else (1e-4, 5e-5)
     e_c = norm_err(C[np.ix_(li, tr, tr)], f["C"])
     print("large %s: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e" % (
-        prec, e_c, grad_err(Pb[0], Pbo), grad_err(Ab[0][tr], Abo), grad_err(Wb[0][tr], Wbo)))
+        prec, e_c, pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0][tr], Abo), wbar_err(Wb[0][tr], Wbo)))
     assert e_c < gate_c
-    assert grad_err(Pb[0], Pbo) < gate_g
+    assert pbar_err(Pb[0], Pbo, ex["P_abs"]) < gate_g
     assert grad_err(Ab[0][tr], Abo) < gate_g
-    assert grad_err(Wb[0][tr], Wbo) < gate_g
+    assert wbar_err(Wb[0][tr], Wbo) < gate_g
     # symmetry and per-ell PSD of the full output
     assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
     if prec == "bf16x9":
