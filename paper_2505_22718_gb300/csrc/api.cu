@@ -270,6 +270,11 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   DeviceGuard g(device);
   swcl_ctx* c = new swcl_ctx();
   c->device = device;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      c->num_sms < 1) {
+    cudaGetLastError();
+    c->num_sms = 148;
+  }
   c->budget = mem_budget_bytes;
   if (stream) {
     c->stream = (cudaStream_t)stream;
@@ -298,6 +303,13 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
   if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
+  // a subset of the six compensated products of the basis GEMMs, for accuracy studies (bit t =
+  // product t in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0); the leading product and at least
+  // one correction are kept)
+  if (const char* v = std::getenv("SWCL_BASIS_PRODUCTS")) {
+    const unsigned m = (unsigned)std::strtoul(v, nullptr, 0) & 0x3Fu;
+    if ((m & 1u) && (m & 0x3Eu)) c->bt_pmask = m;
+  }
   // fixed basis-GEMM tiles "fwd,adj" (tile codes as reported by SWCL_Q_TILE_*) instead of tuning
   if (const char* v = std::getenv("SWCL_BASIS_TILES")) {
     int f = 0, a = 0;
@@ -332,7 +344,8 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->tc_kpow32, &c->tc_lw_lo, &c->tc_kpow_lo, &c->ws_aimg, &c->ws_cpart, &c->ws_pbpart, &c->d_prev,
                     &c->d_flag, &c->lr_res, &c->lr_norms, &c->lr_Q, &c->lr_coef, &c->lr_w,
                     &c->lr_j0, &c->lr_ones, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf,
-                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg,
+                    &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart, &c->bt_cmap_f,
+                    &c->bt_cmap_a, &c->bt_lpos, &c->bt_wbase,
                     &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq,
                     &c->ws_ltab};
   for (DevBuf* b : bufs) swcl::release(c, *b);
@@ -387,6 +400,7 @@ int swcl_set_grids(swcl_ctx* c, double chi_min, double chi_max, int N, const dou
   for (int l = 0; l < N_ell; ++l)
     if (eh[l] < 0 || eh[l] > 100000) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "ell out of range");
   c->have_grids = c->have_tracers = c->have_windows = c->have_power = false;
+  ++c->lists_gen;
   c->lr_dirty = true;
   c->lr_basis = false;
   c->ragged = false;
@@ -470,6 +484,7 @@ int swcl_set_tracers(swcl_ctx* c, int N_tr, const int* kind, const double* fft_b
     cls_of[i] = found;
   }
   c->have_tracers = false;
+  ++c->lists_gen;
   for (auto& t : c->tc) t.ready = t.adj_ready = false;
   c->bt_ready = false;
   c->last_fwd_precision = -1;
@@ -556,6 +571,7 @@ int swcl_set_windows(swcl_ctx* c, int n_walk, const double* W, const double* D, 
     SWCL_TRY(swcl::copy_in(c, c->d_D, ones.data(), sizeof(double) * ones.size()));
   }
   if (c->have_B != (B != nullptr) || c->n_walk != n_walk) ++c->alloc_gen;  // new graph needed
+  if (c->n_walk != n_walk) ++c->lists_gen;
   c->have_B = B != nullptr;
   if (B) SWCL_TRY(swcl::copy_in_queued(c, c->d_B, B, sizeof(double) * bn, &host_src));
   if (had_prev && !c->lr_dirty) {
@@ -615,7 +631,10 @@ int swcl_set_power(swcl_ctx* c, int n_walk, const double* P, const double* amp) 
   if (n_walk < 1 || !P || !amp) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "need n_walk >= 1, P, amp");
   if (c->have_windows && c->n_walk != n_walk)
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "n_walk differs from set_windows");
-  if (c->n_walk != n_walk) ++c->alloc_gen;
+  if (c->n_walk != n_walk) {
+    ++c->alloc_gen;
+    ++c->lists_gen;
+  }
   QueuedHostCopies q{c};
   SWCL_TRY(swcl::copy_in_queued(c, c->d_P, P, sizeof(double) * (size_t)n_walk * c->N_k, &q.pending));
   SWCL_TRY(swcl::copy_in_queued(c, c->d_amp, amp, sizeof(double) * (size_t)n_walk * c->N_tr, &q.pending));
@@ -635,6 +654,7 @@ int swcl_set_ell_lists(swcl_ctx* c, const int* offsets, const int* ell_idx) {
   DeviceGuard g(c->device);
   c->err.clear();
   ++c->alloc_gen;
+  ++c->lists_gen;
   if (!c->have_windows && !c->have_power)
     return swcl::fail(c, SWCL_ERR_STATE, "set_windows or set_power first (they fix n_walk)");
   if (!offsets) {
@@ -714,7 +734,8 @@ static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
   if (!c->budget) return n_need;
   const swcl::Stencil sv = swcl::stencil(c);
   const size_t nw = c->n_walk, nrow = nw * c->N_tr, ntr2 = (size_t)c->N_tr * c->N_tr;
-  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float));
+  size_t per_l = 2 * nrow * c->N_k * (fp64 ? sizeof(double) : sizeof(float)) +
+                 swcl::quad_scratch_bytes(c->n_walk, c->N_tr, c->N_k, 1);
   if (basis) per_l += swcl::basis_bytes_per_ell(c);
   // workspace that does not scale with the chunk
   size_t fixed = 2 * sizeof(cplx) * nrow * sv.NI * c->n_h              // coefficients, cbar
@@ -727,7 +748,7 @@ static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
   if (basis) fixed += swcl::basis_fixed_bytes(c);
   const DevBuf* ws[] = {&c->ws_coef, &c->ws_delta, &c->ws_U, &c->ws_C, &c->ws_cbar, &c->ws_dbar,
                         &c->ws_Cbar, &c->ws_outP, &c->ws_outA, &c->ws_outW, &c->ws_pbpart,
-                        &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
+                        &c->ws_qpart, &c->bt_eimg_f, &c->bt_eimg_a, &c->bt_gdf, &c->bt_g32, &c->bt_kmu,
                         &c->bt_himg, &c->bt_dimg};
   size_t ws_now = 0;
   for (const DevBuf* b : ws) ws_now += b->bytes;
@@ -741,6 +762,7 @@ static int plan_ell_chunk(swcl_ctx* c, int precision, int n_need) {
 // Delta for multipoles [l_lo, l_lo + n_l) into ws_delta ([n_walk][n_l][N_tr][N_k])
 static int contract_chunk(swcl_ctx* c, int precision, int l_lo, int n_l) {
   const swcl::Stencil sv = swcl::stencil(c);
+  if (!use_basis_gemm(c, precision)) c->bt_delta_clean = false;   // every row rewritten
   if (precision == SWCL_FP64) {
     SWCL_LAUNCH(c, swcl::launch_contract_fp64((double*)c->ws_delta.p, (const cplx*)c->ws_coef.p,
                                               (const cplx*)c->d_phase.p, (const cplx*)c->d_gtab.p,
@@ -850,6 +872,7 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
   SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nrow * N_I * n_h));
   SWCL_TRY(swcl::ensure(c, c->ws_delta, nrow * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
   SWCL_TRY(swcl::ensure(c, c->ws_U, sizeof(double) * nw * (size_t)N_ell * N_tr * N_tr));
+  SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(nw, N_tr, N_k, n_lc)));
   if (fp64)
     SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, (const double*)c->d_W.p,
                                            (const double*)c->d_chipow.p, sv.D, sv.B,
@@ -866,13 +889,17 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                             (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                            N_tr, N_k, N_ell, l_lo, n_l,
+                                            N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
                                             c->stream), "k-quadrature fp64");
     else
       SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                            (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
-                                           N_tr, N_k, N_ell, l_lo, n_l,
-                                           c->stream), "k-quadrature f32");
+                                           N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
+                                           c->stream,
+                                           use_basis_gemm(c, precision) && c->bt_compact
+                                               ? (const int*)c->bt_lpos.p : nullptr),
+                  "k-quadrature f32");
+    ++c->last_launches;  // the pair-sum reduction
   }
   if (lim.n_lim > 0) {
     SWCL_LAUNCH(c, swcl::launch_limber_rows((double*)c->ws_U.p, (double*)c->ws_lq.p, lim, lt,
@@ -977,12 +1004,6 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     const int n_l = std::min(n_lc, n_fft - l_lo);
     const bool accumulate = l_lo > 0;
     if (recompute) SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
-    // basis mode with the adjoint tile chosen: Dbar goes straight into the adjoint GEMM's operand
-    if (W_bar && use_basis_gemm(c, precision) && c->bt_nt_adj != 0) {
-      SWCL_TRY(swcl::basis_dbar_image(c, l_lo, n_l, (double*)c->ws_pbpart.p));
-      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate, true));
-      continue;
-    }
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_delta_bar<double>((double*)c->ws_dbar.p,
                                                     (const double*)c->ws_delta.p,
@@ -997,7 +1018,9 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                    (const double*)c->ws_Cbar.p,
                                                    (const double*)c->d_amp.p, (const double*)c->d_P.p,
                                                    (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
-                                                   l_lo, n_l, (double*)c->ws_pbpart.p, c->stream),
+                                                   l_lo, n_l, (double*)c->ws_pbpart.p, c->stream,
+                                                   use_basis_gemm(c, precision) && c->bt_compact
+                                                       ? (const int*)c->bt_lpos.p : nullptr),
                   "delta_bar f32");
     if (!W_bar) continue;
     if (fp64) {
@@ -1010,7 +1033,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                     n_h, N_k, N_ell, l_lo, n_l, accumulate,
                                                     c->stream), "contract adj fp64");
     } else if (use_basis_gemm(c, precision)) {
-      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate, false));
+      SWCL_TRY(swcl::basis_adjoint(c, l_lo, n_l, accumulate));
     } else {
       SWCL_TRY(swcl::contract_adj_tc(c, precision));   // whole multipole range (no chunks)
     }
@@ -1119,9 +1142,16 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
     const int64_t launches_before = c->last_launches;
     int st = run();
     c->capturing = false;
+    if (st != SWCL_OK) {
+      // a failed capture: join the auxiliary stream so that the capture can end, then drop the
+      // partial graph and the capture error it leaves behind
+      cudaEventRecord(c->ev_join, c->aux);
+      cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    }
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (st != SWCL_OK) {
       if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
       return st;
     }
     if (e != cudaSuccess) return swcl::cuda_fail(c, e, "end capture");
@@ -1214,6 +1244,7 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
     c->ell_fft = n_fft;
     SWCL_TRY(swcl::ensure(c, c->ws_coef, sizeof(cplx) * nw2 * N_tr * N_I * n_h));
     SWCL_TRY(swcl::ensure(c, c->ws_delta, (size_t)nw2 * N_tr * n_lc * N_k * (fp64 ? sizeof(double) : sizeof(float))));
+    SWCL_TRY(swcl::ensure(c, c->ws_qpart, swcl::quad_scratch_bytes(1, N_tr, N_k, n_lc)));
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_fftlog_fwd((cplx*)c->ws_coef.p, jW, (const double*)c->d_chipow.p,
                                              sv.D, sv.B, (const cplx*)c->d_psi.p,
@@ -1231,7 +1262,7 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
       if (fp64) {
         SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                               (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
-                                              N_tr, N_k, N_ell, l_lo, n_l,
+                                              N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
                                               c->stream), "k-quadrature fp64");
         SWCL_LAUNCH(c, swcl::launch_quad_jvp<double>((double*)c->ws_dU.p, (const double*)c->ws_delta.p,
                                                      (const double*)c->d_P.p, jP,
@@ -1240,13 +1271,14 @@ int swcl_jvp(swcl_ctx* c, int precision, int n_dir, const double* P_dot, const d
       } else {
         SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                              (const double*)c->d_P.p, (const double*)c->d_wk2.p, 1,
-                                             N_tr, N_k, N_ell, l_lo, n_l,
+                                             N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
                                              c->stream), "k-quadrature f32");
         SWCL_LAUNCH(c, swcl::launch_quad_jvp<float>((double*)c->ws_dU.p, (const float*)c->ws_delta.p,
                                                     (const double*)c->d_P.p, jP,
                                                     (const double*)c->d_wk2.p, has_w, n_dir, N_tr,
                                                     N_k, N_ell, l_lo, n_l, c->stream), "jvp quadrature");
       }
+      ++c->last_launches;  // the pair-sum reduction of the base quadrature
     }
   }
   if (lim.n_lim > 0) {

@@ -129,6 +129,10 @@ __host__ __device__ inline Layout layout(int NT, int stages, int KS) {
 struct GemmShape {
   int n_mt, n_kb, NT, stages;
   uint32_t tmem_cols;
+  // products issued (bit t = product t of A3B3; bit 0, the leading product, always set) and the
+  // first correction issued, whose MMA overwrites the correction slot of each stage
+  uint32_t pmask;
+  int first_corr;
 };
 
 // ------------------------------------------------------------------ epilogues ----
@@ -141,10 +145,15 @@ struct GemmShape {
 struct EpiFwd {
   float* delta;
   const float* kmu;     // [N_tr][4][N_k]
+  const int2* cmap;     // ragged lists: column group -> {w N_tr + i, l}; null: every multipole
   int N_k, N_tr, n_l, r, n_cols;
   // row m, this thread's columns j0 .. j0 + nc - 1 (j0 is a multiple of r)
   __device__ __forceinline__ void operator()(int m, int j0, const float* acc, int stride, int nc) const {
     if (m >= N_k) return;
+    if (cmap) {
+      ragged(m, j0, acc, stride, nc);
+      return;
+    }
     // column j = ((w N_tr + i) n_l + l) r + s, walked incrementally
     int s = j0 % r, g = j0 / r;
     int l = g % n_l, wi = g / n_l;
@@ -173,6 +182,37 @@ struct EpiFwd {
       }
     }
   }
+  // Ragged lists: each group of r columns is one (w, i, l) of the column map.  Kept out of line so
+  // that the kernels of the common case keep their register allocation.
+  __device__ __noinline__ void ragged(int m, int j0, const float* acc, int stride, int nc) const {
+    const int ncols = min(nc, n_cols - j0);
+    int s = j0 % r, g = j0 / r;
+    int i = -1;
+    float kmv[4] = {0.f, 0.f, 0.f, 0.f};
+    float v = 0.0f;
+    for (int c = 0; c < ncols; ++c) {
+      if (s == 0 || c == 0) {
+        const int2 cm = __ldg(cmap + g);
+        const int ni = cm.x % N_tr;
+        if (ni != i) {
+          i = ni;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) kmv[u] = u < r ? __ldg(kmu + ((size_t)i * 4 + u) * N_k + m) : 0.0f;
+        }
+      }
+      const float km = s == 0 ? kmv[0] : s == 1 ? kmv[1] : s == 2 ? kmv[2] : kmv[3];
+      v = fmaf(km, acc[c * stride], v);
+      if (s == r - 1) {
+        const int2 cm = __ldg(cmap + g);
+        delta[(((size_t)(cm.x / N_tr) * n_l + cm.y) * N_tr + i) * N_k + m] = v;
+        v = 0.0f;
+      }
+      if (++s == r) {
+        s = 0;
+        ++g;
+      }
+    }
+  }
 };
 
 // Adjoint: Fbar[(w, i, s)][n] += sum_l conj(G[l][n]) Y[(n, re/im)][(w, i, s, l)]; the lanes of
@@ -181,6 +221,7 @@ struct EpiAdj {
   cplx* cbar;           // [n_walk][N_tr][NI][n_h]
   const float2* g32;    // [n_cls][N_ell][n_h]
   const int* cls_of;
+  const int2* cmap;     // ragged lists: column -> {(w N_tr + i) r + s, l}; null: every multipole
   int n_h, N_tr, N_ell, l_lo, n_l, r, NI, n_cols;
   __device__ __forceinline__ void flush(int g, int n, int t, float are, float aim) const {
     const float re = are + __shfl_xor_sync(0xffffffffu, are, 1);
@@ -200,6 +241,10 @@ struct EpiAdj {
     // so the group changes (shuffles) are warp-uniform.  Gamma values are loaded 16 at a time.
     const int ncols = min(nc, n_cols - j0);
     if (ncols <= 0) return;
+    if (cmap) {
+      ragged(n, t, live, nn, j0, acc, stride, ncols);
+      return;
+    }
     int l = j0 % n_l, g = j0 / n_l;
     const float2* grow = g32 + ((size_t)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo) * n_h + nn;
     float are = 0.0f, aim = 0.0f;
@@ -241,6 +286,48 @@ struct EpiAdj {
       }
     }
     if (l != 0) flush(g, n, t, are, aim);
+  }
+  // The same with the column map: a group (w, i, s) is a run of columns with equal map.x, which
+  // is the same for every lane (the group changes and their shuffles stay warp-uniform).
+  __device__ __noinline__ void ragged(int n, int t, bool live, int nn, int j0, const float* acc,
+                                      int stride, int ncols) const {
+    int g = __ldg(&cmap[j0].x);
+    float are = 0.0f, aim = 0.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < ncols; c0 += 16) {
+      float2 G[16];
+      int gg[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        gg[u] = -1;
+        G[u] = make_float2(0.f, 0.f);
+        if (c0 + u < ncols) {
+          const int2 cm = __ldg(cmap + j0 + c0 + u);
+          gg[u] = cm.x;
+          G[u] = __ldg(g32 + ((size_t)__ldg(cls_of + (cm.x / r) % N_tr) * N_ell + l_lo + cm.y) * n_h + nn);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        if (c0 + u < ncols) {
+          if (gg[u] != g) {
+            flush(g, n, t, are, aim);
+            are = 0.0f;
+            aim = 0.0f;
+            g = gg[u];
+          }
+          const float y = live ? acc[(c0 + u) * stride] : 0.0f;
+          if (t == 0) {
+            are = fmaf(G[u].x, y, are);
+            aim = fmaf(-G[u].y, y, aim);
+          } else {
+            are = fmaf(G[u].y, y, are);
+            aim = fmaf(G[u].x, y, aim);
+          }
+        }
+      }
+    }
+    flush(g, n, t, are, aim);
   }
 };
 
@@ -358,11 +445,12 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
           for (int j = 0; j < kK / 16; ++j) {
 #pragma unroll
             for (int t = 0; t < P::kProducts; ++t) {
+              if (!((sh.pmask >> t) & 1u)) continue;
               // descriptor start addresses advance in 16-byte units
               const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
               const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
               const bool lead = (t == 0);
-              const bool first = (h == 0) && (j == 0) && (t <= 1);
+              const bool first = (h == 0) && (j == 0) && (lead || t == sh.first_corr);
               mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
             }
           }
@@ -465,6 +553,215 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       // reads them from there in a loop that is not unrolled
       const int dt = tid - 64;                       // drain thread 0 .. 32 DW - 1
       float* ep = reinterpret_cast<float*>(base);
+#pragma unroll
+      for (int c = 0; c < CH * 16; ++c)
+        if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
+      epi(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(status, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, sh.tmem_cols);
+  }
+}
+
+// Persistent form of the two-K-block GEMM (tile code bit 12): one CTA per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The barriers, the TMEM allocation and the stage ring
+// stay live across tiles: the stage counter g runs over all of the CTA's stages, so the copy warp
+// fetches the next tile's first stages while the drain warps run the epilogue of the previous
+// tile, and the MMA thread starts the next tile as soon as two accumulator buffers are free.  The
+// epilogue stages its accumulators in a region of its own (not in the stage ring, which is being
+// refilled).  Arithmetic per tile as in k_gemm_basis<..., KS = 2>.
+template <class P>
+__host__ __device__ inline Layout layout_persist(int NT, int stages, int CH) {
+  Layout L = layout<P>(NT, stages, 2);
+  const uint32_t ep_bytes = (uint32_t)CH * 16 * 256 * sizeof(float);
+  L.bar_off = stages * L.stage + ep_bytes;
+  L.total = L.bar_off + 8 * (3 * stages + 1) + 16 + 1024;
+  return L;
+}
+
+template <class P, class Epi, int CH>
+__global__ void __launch_bounds__(threads_for(8), 1)
+k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
+               int n_tiles, Epi epi, int* __restrict__ status) {
+  constexpr int DW = 8, KS = 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
+  const Layout L = layout_persist<P>(NT, S, CH);
+  // barriers as in k_gemm_basis: full[s] (copies landed and the TMEM buffer drained: the copy
+  // warp + one arrival per drain warp), mmadone[s] (one commit), ready[s] (transaction count)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
+  uint64_t* full = bars;
+  uint64_t* mmadone = bars + S;
+  uint64_t* ready = bars + 2 * S;
+  uint64_t* done = bars + 3 * S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ep = reinterpret_cast<float*>(base + S * L.stage);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_my = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int T = n_my * n_kb;             // this CTA's stages over all its tiles
+  const int stride = (NT + 31) & ~31;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1 + DW);
+      mbar_init(smem_u32(&mmadone[s]), 1);
+      mbar_init(smem_u32(&ready[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), sh.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- copies ----
+      int next = 0, fwd = 0;
+      long idle = 0;
+      while (fwd < T) {
+        bool progress = false;
+        if (next < T) {
+          const int s = next % S, r = next / S;
+          if (r == 0 || mbar_test_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
+            const int tile = blockIdx.x + (next / n_kb) * gridDim.x, kb = next % n_kb;
+            const int mt = tile % sh.n_mt, nt = tile / sh.n_mt;
+            uint8_t* st = base + s * L.stage;
+            const int nk = min(KS, n_kb1 - kb * KS);
+            mbar_arrive_tx(smem_u32(&ready[s]), nk * (L.a1 + L.b1));
+            bulk_g2s(smem_u32(st), aimg + ((size_t)mt * n_kb1 + kb * KS) * L.a1, nk * L.a1,
+                     smem_u32(&ready[s]));
+            bulk_g2s(smem_u32(st + L.a_bytes), bimg + ((size_t)nt * n_kb1 + kb * KS) * L.b1,
+                     nk * L.b1, smem_u32(&ready[s]));
+            ++next;
+            progress = true;
+          }
+        }
+        if (fwd < next && mbar_test_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
+          mbar_arrive(smem_u32(&full[fwd % S]));
+          ++fwd;
+          progress = true;
+        }
+        if (progress) {
+          idle = 0;
+        } else if (++idle > (kSpinLimit << 6) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      for (int g = fwd; g < next; ++g) mbar_wait_drain(smem_u32(&ready[g % S]), (g / S) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA ----
+      const uint32_t idesc = idesc_bf16(kM, NT);
+      const uint32_t b_plane = NT * kRow;
+      for (int g = 0; g < T; ++g) {
+        const int s = g % S, r = g / S, b = g & 1, kb = g % n_kb;
+        if (!mbar_wait(smem_u32(&full[s]), r & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(base + s * L.stage);
+        const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
+        const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+        const int nk = min(KS, n_kb1 - kb * KS);
+#pragma unroll
+        for (int h = 0; h < KS; ++h) {
+          if (h >= nk) break;
+          const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
+#pragma unroll
+          for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+            for (int t = 0; t < P::kProducts; ++t) {
+              if (!((sh.pmask >> t) & 1u)) continue;
+              const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+              const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+              const bool lead = (t == 0);
+              const bool first = (h == 0) && (j == 0) && (lead || t == sh.first_corr);
+              mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(smem_u32(&mmadone[s]));
+      }
+      mma_commit(smem_u32(done));
+      mbar_wait_drain(smem_u32(done), 0);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ drain ----
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+    const int nch = NT / 16;
+    const int nch0 = (nch + 1) / 2;
+    const int c_begin = half ? nch0 : 0;
+    const int my = half ? nch - nch0 : nch0;
+    const int dt = tid - 64;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    if (lane == 0) {
+      mbar_arrive(smem_u32(&full[0]));
+      if (T > 1) mbar_arrive(smem_u32(&full[1 % S]));
+    }
+    bool ok = true;
+    for (int it = 0; it < n_my && ok; ++it) {
+      const int tile = blockIdx.x + it * gridDim.x;
+      const int mt = tile % sh.n_mt, nt = tile / sh.n_mt;
+      float acc[CH * 16];
+#pragma unroll
+      for (int t = 0; t < CH * 16; ++t) acc[t] = 0.0f;
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int g = it * n_kb + kb, b = g & 1;
+        const bool got = mbar_wait(smem_u32(&mmadone[g % S]), (g / S) & 1, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
+        const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
+        uint32_t m0[16], r0[16], m1[16], r1[16], m2[16], r2[16];
+        tmem_ld16_async(slot_m, m0);
+        tmem_ld16_async(slot_c, r0);
+        if (my > 1) {
+          tmem_ld16_async(slot_m + 16, m1);
+          tmem_ld16_async(slot_c + 16, r1);
+        }
+        if (my > 2) {
+          tmem_ld16_async(slot_m + 32, m2);
+          tmem_ld16_async(slot_c + 32, r2);
+        }
+        tmem_wait_ld();
+        reg_fence(m0);
+        reg_fence(r0);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+        if (my > 1) {
+          reg_fence(m1);
+          reg_fence(r1);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+        }
+        if (my > 2) {
+          reg_fence(m2);
+          reg_fence(r2);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[32 + t] += __uint_as_float(m2[t]) + __uint_as_float(r2[t]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0 && g + 2 < T) mbar_arrive(smem_u32(&full[(g + 2) % S]));
+      }
+      if (!(__all_sync(0xffffffffu, ok) && !*abort_flag)) break;
+      // the epilogue of this tile: the MMAs of the next one run meanwhile
 #pragma unroll
       for (int c = 0; c < CH * 16; ++c)
         if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
@@ -601,9 +898,9 @@ __global__ void k_kmu(float* __restrict__ kmu, const double* __restrict__ kpow,
 // Forward B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
 // (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
 __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
-                       const float4* __restrict__ gdf, const int* __restrict__ cls_of, int N_tr,
-                       int N_ell, int n_h, int l_lo, int n_l, int r, int NI, int n_cols, int NT,
-                       int n_nt, int n_kb) {
+                       const float4* __restrict__ gdf, const int* __restrict__ cls_of,
+                       const int2* __restrict__ cmap, int N_tr, int N_ell, int n_h, int l_lo,
+                       int n_l, int r, int NI, int n_cols, int NT, int n_nt, int n_kb) {
   const long total = (long)n_nt * n_kb * NT * 4;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
     long t = e;
@@ -618,8 +915,14 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
     if (live) {
       s = j % r;
       const int g = j / r;
-      l = g % n_l;
-      wi = g / n_l;
+      if (cmap) {
+        const int2 cm = cmap[g];
+        wi = cm.x;
+        l = cm.y;
+      } else {
+        l = g % n_l;
+        wi = g / n_l;
+      }
       i = wi % N_tr;
     }
     const float4* Fr = F + ((size_t)wi * NI + s) * n_h;
@@ -645,8 +948,8 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
 // Adjoint B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, s, l) (l fastest),
 // (j, q) = kmu[i][s][q] Dbar[w][l][i][q]
 __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
-                       const float* __restrict__ kmu, int N_tr, int N_k, int n_l, int r,
-                       int n_cols, int NT, int n_nt, int n_kb) {
+                       const float* __restrict__ kmu, const int2* __restrict__ cmap, int N_tr,
+                       int N_k, int n_l, int r, int n_cols, int NT, int n_nt, int n_kb) {
   const long total = (long)n_nt * n_kb * NT * 4;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
     long t = e;
@@ -658,8 +961,15 @@ __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar
     const bool live = j < n_cols;
     int l = 0, s = 0, i = 0, w = 0;
     if (live) {
-      l = j % n_l;
-      const int g = j / n_l;
+      int g;
+      if (cmap) {
+        const int2 cm = cmap[j];
+        g = cm.x;
+        l = cm.y;
+      } else {
+        l = j % n_l;
+        g = j / n_l;
+      }
       s = g % r;
       const int wi = g / r;
       i = wi % N_tr;
@@ -679,84 +989,6 @@ __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar
   }
 }
 
-// The reverse mode's Dbar (a5) fused with the adjoint GEMM's B image, for one multipole of one
-// walker and 128 k points per CTA (grid: k tiles, multipoles of the chunk, walkers):
-//   T_i = sum_j S_ij A_j Delta_j(l, q),   Dbar_i = 2 A_i u_q T_i  (FP32, S = (Cbar + Cbar^T)/2),
-//   image row ((w N_tr + i) r + s) n_l + l, column q:  kmu[i][s][q] Dbar_i, split into 3 bf16
-//   planes,
-// and the multipole's P_bar partial sum_i A_i Delta_i T_i (compensated FP32, written as FP64 to
-// pbar_part[l][w][q] for the ordered reduction).  The arithmetic is that of k_delta_bar followed
-// by k_dimg, without the round trip of Dbar through global memory.  The CTAs of the first
-// multipole and walker also write the zero rows that pad the last column tile.
-constexpr int kDT = 128;
-__global__ void __launch_bounds__(kDT)
-k_dbar_dimg(uint8_t* __restrict__ img, double* __restrict__ pbar_part, const float* __restrict__ delta,
-            const double* __restrict__ Cf, const double* __restrict__ amp,
-            const double* __restrict__ P, const double* __restrict__ wk2,
-            const float* __restrict__ kmu, int N_tr, int N_k, int N_ell, int n_walk, int l_lo,
-            int n_l, int r, int n_cols, int NT, int n_nt, int n_kb) {
-  extern __shared__ __align__(16) float dsm[];
-  float* St = dsm;                        // [N_tr][N_tr]  St[j][i] = S_ij A_j
-  float* Dl = St + N_tr * N_tr;           // [N_tr][kDT]
-  float* As = Dl + N_tr * kDT;            // [N_tr]
-  const int ll = blockIdx.y, w = blockIdx.z;
-  const int l = l_lo + ll;
-  const int q = blockIdx.x * kDT + threadIdx.x;
-  const bool in_img = q < n_kb * kK;      // inside the image's K range (zero past N_k)
-  const bool live = q < N_k;
-  const double* A = amp + (size_t)w * N_tr;
-  for (int e = threadIdx.x; e < N_tr * N_tr; e += kDT) {
-    const int j = e / N_tr, i = e - j * N_tr;
-    St[e] = (float)(Cf[((size_t)w * N_ell + l) * N_tr * N_tr + i * N_tr + j] * A[j]);
-  }
-  for (int e = threadIdx.x; e < N_tr; e += kDT) As[e] = (float)A[e];
-  const float* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
-#pragma unroll 8
-  for (int t = 0; t < N_tr; ++t) Dl[t * kDT + threadIdx.x] = live ? dl[(size_t)t * N_k + q] : 0.0f;
-  __syncthreads();
-  if (!in_img) return;
-  const float two_u = live ? (float)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : 0.0f;
-  const float* dq = Dl + threadIdx.x;
-  const int kb = q / kK;
-  const uint32_t kbyte = (uint32_t)(q % kK) * 2;
-  const size_t plane = (size_t)NT * kRow;
-  float ps = 0.0f, pc = 0.0f;
-  for (int i = 0; i < N_tr; ++i) {
-    float t = 0.0f;
-    for (int j = 0; j < N_tr; ++j) t = fmaf(St[j * N_tr + i], dq[j * kDT], t);
-    const float ai = As[i];
-    {
-      // P_bar partial: compensated sum (TwoSum)
-      const float x = ai * dq[i * kDT] * t;
-      const float sn = ps + x;
-      const float bp = sn - ps;
-      pc += (ps - (sn - bp)) + (x - bp);
-      ps = sn;
-    }
-    const float db = two_u * ai * t;
-    for (int s = 0; s < r; ++s) {
-      const int jrow = ((w * N_tr + i) * r + s) * n_l + ll;
-      const int nt = jrow / NT, row = jrow - nt * NT;
-      const float x = live ? kmu[((size_t)i * 4 + s) * N_k + q] * db : 0.0f;
-      __nv_bfloat16 v[3];
-      split_f32(x, v);
-      uint8_t* dst = img + ((size_t)nt * n_kb + kb) * kPlanes * plane + off64(row, kbyte);
-#pragma unroll
-      for (int p = 0; p < kPlanes; ++p) *reinterpret_cast<__nv_bfloat16*>(dst + p * plane) = v[p];
-    }
-  }
-  if (live) pbar_part[((size_t)l * n_walk + w) * N_k + q] = (double)ps + (double)pc;
-  if (ll == 0 && w == 0) {
-    // zero rows past the last column
-    for (int jrow = n_cols; jrow < n_nt * NT; ++jrow) {
-      const int nt = jrow / NT, row = jrow - nt * NT;
-      uint8_t* dst = img + ((size_t)nt * n_kb + kb) * kPlanes * plane + off64(row, kbyte);
-#pragma unroll
-      for (int p = 0; p < kPlanes; ++p) *reinterpret_cast<__nv_bfloat16*>(dst + p * plane) = __float2bfloat16_rn(0.0f);
-    }
-  }
-}
-
 unsigned grid_for(long total) {
   return (unsigned)std::max<long>(1, std::min<long>((total + 255) / 256, 152L * 32));
 }
@@ -765,6 +997,8 @@ unsigned grid_for(long total) {
 constexpr int kPair = 256;
 // bit 10 = two K-blocks per pipeline stage: one barrier round trip, commit and drain per 64 of K
 constexpr int kDeep = 1024;
+// bit 12 (with bit 10) = the persistent two-K-block GEMM (k_gemm_persist), tiles up to 96 columns
+constexpr int kPersist = 4096;
 
 template <class P>
 int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
@@ -773,13 +1007,21 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   const int KS = (code & kDeep) ? 2 : 1;
   const uint32_t cap = pair ? 113 * 1024 : 227 * 1024;
   int stages = kMaxStages;
-  Layout L = layout<P>(NT, stages, KS);
-  while (stages > 2 && L.total > cap) L = layout<P>(NT, --stages, KS);
+  const bool persist = code & kPersist;
+  if (persist && (!(code & kDeep) || NT > 96))
+    return fail(c, SWCL_ERR_INVALID_ARG, "persistent GEMM tiles: two K-blocks per stage, <= 96 columns");
+  auto lay = [&](int st) {
+    return persist ? layout_persist<P>(NT, st, 3) : layout<P>(NT, st, KS);
+  };
+  Layout L = lay(stages);
+  while (stages > 2 && L.total > cap) L = lay(--stages);
   if (L.total > cap) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
   while (cols < (uint32_t)(4 * stride)) cols <<= 1;
-  sh = GemmShape{n_mt, n_kb, NT, stages, cols};
+  int first_corr = 1;
+  while (first_corr < P::kProducts && !((c->bt_pmask >> first_corr) & 1u)) ++first_corr;
+  sh = GemmShape{n_mt, n_kb, NT, stages, cols, c->bt_pmask, first_corr};
   smem = L.total;
   return SWCL_OK;
 }
@@ -796,9 +1038,23 @@ cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, cons
 }
 
 template <class P, class Epi>
+cudaError_t launch_persist(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                           uint32_t smem, int n_nt, const Epi& epi) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_persist<P, Epi, 3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int n_tiles = sh.n_mt * n_nt;
+  const int grid = std::min(n_tiles, std::max(1, c->num_sms));
+  k_gemm_persist<P, Epi, 3><<<(unsigned)grid, threads_for(8), smem, c->stream>>>(
+      a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
+  return cudaGetLastError();
+}
+
+template <class P, class Epi>
 cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* b,
                         const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
   const int nch = sh.NT / 16;
+  if (code & kPersist) return launch_persist<P, Epi>(c, a, b, sh, smem, n_nt, epi);
   if (code & kPair)   // four drain warps: every chunk of a row in one thread
     return nch <= 3 ? launch_variant<P, Epi, 4, 3, 1>(c, a, b, sh, smem, n_nt, epi)
                     : launch_variant<P, Epi, 4, 4, 1>(c, a, b, sh, smem, n_nt, epi);
@@ -812,17 +1068,22 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
 // Candidate tile codes: column tiles that are multiples of 16; in forward tiles each drain
 // thread's column range (whole 16-column chunks; split in two halves with eight drain warps)
 // holds whole groups of r basis columns.
-std::vector<int> tile_candidates(int r, bool need_groups) {
+std::vector<int> tile_candidates(int r, bool need_groups, bool tuned_only = false) {
   std::vector<int> v;
-  for (int nt = 32; nt <= kMaxNT; nt += 16) {
-    const int half0 = 16 * ((nt / 16 + 1) / 2);
-    if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt);
+  if (!tuned_only) {
+    for (int nt = 32; nt <= kMaxNT; nt += 16) {
+      const int half0 = 16 * ((nt / 16 + 1) / 2);
+      if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt);
+    }
+    for (int nt = 32; nt <= 64; nt += 16)
+      if (!need_groups || nt % r == 0) v.push_back(nt | kPair);
   }
-  for (int nt = 32; nt <= 64; nt += 16)
-    if (!need_groups || nt % r == 0) v.push_back(nt | kPair);
   for (int nt = 64; nt <= kMaxNT; nt += 32) {
     const int half0 = 16 * ((nt / 16 + 1) / 2);
-    if (!need_groups || (nt % r == 0 && half0 % r == 0)) v.push_back(nt | kDeep);
+    if (!need_groups || (nt % r == 0 && half0 % r == 0)) {
+      v.push_back(nt | kDeep);
+      if (nt <= 96) v.push_back(nt | kDeep | kPersist);
+    }
   }
   return v;
 }
@@ -889,30 +1150,109 @@ int basis_prepare(swcl_ctx* c) {
 
 namespace {
 
-int build_h(swcl_ctx* c, int NT, int n_nt, int l_lo, int n_l) {
+// Columns of the two basis GEMMs for the multipoles [l_lo, l_lo + n_l).  Without ragged lists (or
+// when the multipoles run in several chunks) every (walker, tracer, multipole, profile) is a
+// column.  With ragged lists covered by one chunk, only the multipoles each walker lists are:
+// forward columns (w, i, listed l, s), adjoint columns (w, i, s, listed l), with the maps
+//   cmap_f[group of r columns] = {w N_tr + i, l},   cmap_a[column] = {(w N_tr + i) r + s, l},
+//   lpos[w][l] = position of l in walker w's list (-1 if unlisted),  wbase[w] = {first column,
+//   listed count},
+// built on the host once per configuration (outside graph capture).  Delta rows of unlisted
+// multipoles are then never written by the forward GEMM: they are cleared once, so that the
+// reductions over all multipoles (U, P_bar) read zeros there.
+struct ColPlan {
+  int n_cols = 0;
+  const int2* cmap_f = nullptr;
+  const int2* cmap_a = nullptr;
+  const int* lpos = nullptr;
+  const int2* wbase = nullptr;
+};
+
+int column_plan(swcl_ctx* c, int l_lo, int n_l, ColPlan& p) {
+  const int r = basis_rank(c);
+  p = ColPlan();
+  const bool compact = c->ragged && (int)c->off_h.size() == c->n_walk + 1 && l_lo == 0 &&
+                       n_l == c->N_ell;
+  c->bt_compact = compact;
+  if (!compact) {
+    p.n_cols = c->n_walk * c->N_tr * n_l * r;
+    c->bt_delta_clean = false;   // every row of Delta is written
+    return SWCL_OK;
+  }
+  const int nw = c->n_walk, N_tr = c->N_tr;
+  const int64_t n_listed = c->off_h.back();
+  int st;
+  if ((st = ensure(c, c->bt_cmap_f, sizeof(int2) * std::max<int64_t>(1, n_listed * N_tr)))) return st;
+  if ((st = ensure(c, c->bt_cmap_a, sizeof(int2) * std::max<int64_t>(1, n_listed * N_tr * r)))) return st;
+  if ((st = ensure(c, c->bt_lpos, sizeof(int) * (size_t)nw * n_l))) return st;
+  if ((st = ensure(c, c->bt_wbase, sizeof(int2) * (size_t)nw))) return st;
+  const int64_t key[7] = {c->lists_gen, nw, N_tr, n_l, r, (int64_t)(uintptr_t)c->ws_delta.p,
+                          (int64_t)c->ws_delta.bytes};
+  if (!std::equal(key, key + 7, c->bt_plan_key)) {
+    if (c->capturing) return fail(c, SWCL_ERR_STATE, "GEMM column plan built during capture");
+    std::vector<int2> cf, ca, wb(nw);
+    std::vector<int> lp((size_t)nw * n_l, -1);
+    cf.reserve(n_listed * N_tr);
+    ca.reserve(n_listed * N_tr * r);
+    int col = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int o0 = c->off_h[w], m = c->off_h[w + 1] - o0;
+      wb[w] = make_int2(col, m);
+      for (int u = 0; u < m; ++u) lp[(size_t)w * n_l + c->idx_h[o0 + u]] = u;
+      for (int i = 0; i < N_tr; ++i)
+        for (int u = 0; u < m; ++u) cf.push_back(make_int2(w * N_tr + i, c->idx_h[o0 + u]));
+      for (int i = 0; i < N_tr; ++i)
+        for (int s = 0; s < r; ++s)
+          for (int u = 0; u < m; ++u) ca.push_back(make_int2((w * N_tr + i) * r + s, c->idx_h[o0 + u]));
+      col += N_tr * m * r;
+    }
+    if (!cf.empty()) {
+      if ((st = copy_in(c, c->bt_cmap_f, cf.data(), sizeof(int2) * cf.size()))) return st;
+      if ((st = copy_in(c, c->bt_cmap_a, ca.data(), sizeof(int2) * ca.size()))) return st;
+    }
+    if ((st = copy_in(c, c->bt_lpos, lp.data(), sizeof(int) * lp.size()))) return st;
+    if ((st = copy_in(c, c->bt_wbase, wb.data(), sizeof(int2) * wb.size()))) return st;
+    std::copy(key, key + 7, c->bt_plan_key);
+    c->bt_plan_cols = col;
+    c->bt_delta_clean = false;
+  }
+  if (!c->bt_delta_clean) {
+    cudaError_t e = cudaMemsetAsync(c->ws_delta.p, 0, c->ws_delta.bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear Delta");
+    c->bt_delta_clean = true;
+  }
+  p.n_cols = c->bt_plan_cols;
+  p.cmap_f = (const int2*)c->bt_cmap_f.p;
+  p.cmap_a = (const int2*)c->bt_cmap_a.p;
+  p.lpos = (const int*)c->bt_lpos.p;
+  p.wbase = (const int2*)c->bt_wbase.p;
+  return SWCL_OK;
+}
+
+int build_h(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int l_lo, int n_l) {
   const Stencil sv = stencil(c);
   const int r = basis_rank(c);
-  const int n_cols = c->n_walk * c->N_tr * n_l * r;
+  const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * kPlanes * NT * kRow);
   if (st) return st;
   const long tot = (long)n_nt * c->bt_f_kb * NT * 4;
   k_himg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p,
                                                (const float4*)c->bt_gdf.p, (const int*)c->d_cls_of.p,
-                                               c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r, sv.NI,
-                                               n_cols, NT, n_nt, c->bt_f_kb);
+                                               cp.cmap_f, c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r,
+                                               sv.NI, n_cols, NT, n_nt, c->bt_f_kb);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward operand");
 }
 
-int build_d(swcl_ctx* c, int NT, int n_nt, int n_l) {
+int build_d(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int n_l) {
   const int r = basis_rank(c);
-  const int n_cols = c->n_walk * c->N_tr * r * n_l;
+  const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow);
   if (st) return st;
   const long tot = (long)n_nt * c->bt_a_kb * NT * 4;
   k_dimg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p,
-                                               (const float*)c->bt_kmu.p, c->N_tr, c->N_k, n_l, r,
-                                               n_cols, NT, n_nt, c->bt_a_kb);
+                                               (const float*)c->bt_kmu.p, cp.cmap_a, c->N_tr, c->N_k,
+                                               n_l, r, n_cols, NT, n_nt, c->bt_a_kb);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint operand");
 }
@@ -961,15 +1301,19 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
   int st = basis_prepare(c);
   if (st) return st;
   const int r = basis_rank(c);
-  const int n_cols = c->n_walk * c->N_tr * n_l * r;
+  ColPlan cp;
+  if ((st = column_plan(c, l_lo, n_l, cp))) return st;
+  const int n_cols = cp.n_cols;
+  if (n_cols == 0) return SWCL_OK;   // no walker lists a multipole of this chunk
   auto run = [&](int code, bool build) -> int {
     const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
-    if (build && (st = build_h(c, NT, n_nt, l_lo, n_l))) return st;
+    if (build && (st = build_h(c, cp, NT, n_nt, l_lo, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
     if ((st = shape_for<A3B3>(c, code, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
-    EpiFwd epi{(float*)c->ws_delta.p, (const float*)c->bt_kmu.p, c->N_k, c->N_tr, n_l, r, n_cols};
+    EpiFwd epi{(float*)c->ws_delta.p, (const float*)c->bt_kmu.p, cp.cmap_f, c->N_k, c->N_tr, n_l, r,
+               n_cols};
     cudaError_t e = launch_gemm<A3B3>(c, code, (const uint8_t*)c->bt_eimg_f.p,
                                       (const uint8_t*)c->bt_himg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward GEMM");
@@ -978,59 +1322,39 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
     return fail(c, SWCL_ERR_INVALID_ARG, "SWCL_BASIS_TILES: not a forward tile for this rank");
   if (c->bt_nt_fwd == 0) {
     if (c->capturing) c->bt_nt_fwd = 96 % r == 0 ? 96 : 64;
-    else if ((st = autotune(c, tile_candidates(r, true), run, c->bt_nt_fwd))) return st;
+    else if ((st = autotune(c, tile_candidates(r, true, true), run, c->bt_nt_fwd))) return st;
   }
   const int code = c->bt_nt_fwd, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
-  if ((st = counted(c, "basis operand fwd", [&] { return build_h(c, NT, n_nt, l_lo, n_l); })))
+  if ((st = counted(c, "basis operand fwd", [&] { return build_h(c, cp, NT, n_nt, l_lo, n_l); })))
     return st;
   return counted(c, "basis gemm fwd", [&] { return run(code, false); });
 }
 
 // ws_cbar (FP64 complex, [n_walk][N_tr][NI][n_h], zeroed here) from ws_dbar (FP32,
 // [n_walk][n_l][N_tr][N_k]) for multipoles [l_lo, l_lo + n_l); accumulate = keep ws_cbar.
-int basis_dbar_image(swcl_ctx* c, int l_lo, int n_l, double* pbar_part) {
-  int st = basis_prepare(c);
-  if (st) return st;
-  if (c->bt_nt_adj == 0) return fail(c, SWCL_ERR_STATE, "adjoint tile not chosen yet");
-  const int r = basis_rank(c);
-  const int n_cols = c->n_walk * c->N_tr * r * n_l;
-  const int NT = c->bt_nt_adj & 255;
-  const int n_nt = (n_cols + NT - 1) / NT;
-  if ((st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow))) return st;
-  const size_t smem = sizeof(float) * ((size_t)c->N_tr * c->N_tr + (size_t)c->N_tr * kDT + c->N_tr);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_dbar_dimg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(c, e, "dbar image attribute");
-  }
-  const dim3 grid((c->bt_a_kb * kK + kDT - 1) / kDT, n_l, c->n_walk);
-  return counted(c, "dbar + image adj", [&] {
-    k_dbar_dimg<<<grid, kDT, smem, c->stream>>>(
-        (uint8_t*)c->bt_dimg.p, pbar_part, (const float*)c->ws_delta.p, (const double*)c->ws_Cbar.p,
-        (const double*)c->d_amp.p, (const double*)c->d_P.p, (const double*)c->d_wk2.p,
-        (const float*)c->bt_kmu.p, c->N_tr, c->N_k, c->N_ell, c->n_walk, l_lo, n_l, r, n_cols, NT,
-        n_nt, c->bt_a_kb);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "dbar image");
-  });
-}
-
-int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_ready) {
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
   int st = basis_prepare(c);
   if (st) return st;
   const Stencil sv = stencil(c);
   const int r = basis_rank(c);
-  const int n_cols = c->n_walk * c->N_tr * r * n_l;
+  ColPlan cp;
+  if ((st = column_plan(c, l_lo, n_l, cp))) return st;
+  const int n_cols = cp.n_cols;
   const size_t cbytes = sizeof(cplx) * (size_t)c->n_walk * c->N_tr * sv.NI * c->n_h;
+  if (n_cols == 0) {   // no walker lists a multipole of this chunk
+    cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(c->ws_cbar.p, 0, cbytes, c->stream);
+    return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "clear cbar");
+  }
   auto run = [&](int code, bool build) -> int {
     const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
-    if (build && (st = build_d(c, NT, n_nt, n_l))) return st;
+    if (build && (st = build_d(c, cp, NT, n_nt, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
     if ((st = shape_for<A3B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
     EpiAdj epi{(cplx*)c->ws_cbar.p, (const float2*)c->bt_g32.p, (const int*)c->d_cls_of.p,
-               c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
+               cp.cmap_a, c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
     cudaError_t e = launch_gemm<A3B3>(c, code, (const uint8_t*)c->bt_eimg_a.p,
                                       (const uint8_t*)c->bt_dimg.p, sh, smem, n_nt, epi);
     return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint GEMM");
@@ -1042,7 +1366,7 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_re
       c->bt_nt_adj = 96;
     } else {
       // the tuning launches accumulate into ws_cbar, which is cleared below
-      if ((st = autotune(c, tile_candidates(r, false), run, c->bt_nt_adj))) return st;
+      if ((st = autotune(c, tile_candidates(r, false, true), run, c->bt_nt_adj))) return st;
       if (accumulate) return fail(c, SWCL_ERR_STATE, "basis adjoint tuned inside an accumulation");
     }
   }
@@ -1052,8 +1376,7 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_re
   }
   const int code = c->bt_nt_adj, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
-  if (!image_ready &&
-      (st = counted(c, "basis operand adj", [&] { return build_d(c, NT, n_nt, n_l); })))
+  if ((st = counted(c, "basis operand adj", [&] { return build_d(c, cp, NT, n_nt, n_l); })))
     return st;
   return counted(c, "basis gemm adj", [&] { return run(code, false); });
 }

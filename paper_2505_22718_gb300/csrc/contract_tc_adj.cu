@@ -197,30 +197,46 @@ k_contract_tc_adj(cplx* __restrict__ cpart, const uint8_t* __restrict__ aimg,
       const int a_hi = min(N_I - 1, tj0[q_last - q0] + 3);
       const int nk = a_hi - a_lo + 1;
       cplx* out = cpart + (size_t)(wi * n_qt + qt) * R * n_h;
-      for (int item = tid; item < nk * 64; item += kWarps * 32) {
-        const int ka = item / 64, m = item - ka * 64;
-        const int a = a_lo + ka;
+      // four consecutive knots per item: the rows whose stencil holds any of them are walked
+      // once, each row's V and weights are read once, and the four knots accumulate in
+      // independent double-float sums (a warp's 32 items share the knots, so the branches on the
+      // stencil offset are warp-uniform)
+      const int ngrp = (nk + 3) / 4;
+      for (int item = tid; item < ngrp * 64; item += kWarps * 32) {
+        const int gq = item / 64, m = item - gq * 64;
+        const int a0 = a_lo + 4 * gq;
         const int n = ct * (kCT / 2) + m;
         if (n >= n_h) continue;
-        float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
-        // first row whose stencil can hold knot a (j0 >= a - 3; j0 is nondecreasing in q)
+        float sr[4], srl[4], si[4], sil[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sr[u] = srl[u] = si[u] = sil[u] = 0.f;
+        // first row whose stencil can hold knot a0 (j0 >= a0 - 3; j0 is nondecreasing in q)
         int lo = 0, hi = kMTile;
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
-          if (tj0[mid] < a - 3) lo = mid + 1; else hi = mid;
+          if (tj0[mid] < a0 - 3) lo = mid + 1; else hi = mid;
         }
         for (int r = lo; r < kMTile; ++r) {
           const int jr = tj0[r];
-          if (jr > a) break;
-          const int d = a - jr;
+          if (jr > a0 + 3) break;
           const float4 lw = tlw[r], lwl = tlwl[r];
-          const float l = d == 0 ? lw.x : d == 1 ? lw.y : d == 2 ? lw.z : lw.w;
-          const float ll = d == 0 ? lwl.x : d == 1 ? lwl.y : d == 2 ? lwl.z : lwl.w;
           const float4 v = V[m * VS + r];
-          df_fma(l, ll, v.x, v.z, sr, srl);
-          df_fma(l, ll, v.y, v.w, si, sil);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int d = a0 + u - jr;
+            if (d >= 0 && d <= 3) {
+              const float l = d == 0 ? lw.x : d == 1 ? lw.y : d == 2 ? lw.z : lw.w;
+              const float ll = d == 0 ? lwl.x : d == 1 ? lwl.y : d == 2 ? lwl.z : lwl.w;
+              df_fma(l, ll, v.x, v.z, sr[u], srl[u]);
+              df_fma(l, ll, v.y, v.w, si[u], sil[u]);
+            }
+          }
         }
-        out[(size_t)ka * n_h + n] = cplx{(double)sr + (double)srl, (double)si + (double)sil};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (a0 + u <= a_hi)
+            out[(size_t)(4 * gq + u) * n_h + n] =
+                cplx{(double)sr[u] + (double)srl[u], (double)si[u] + (double)sil[u]};
       }
     }
   } else if (lane == 0) {

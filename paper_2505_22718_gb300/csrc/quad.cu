@@ -5,9 +5,10 @@
 //   Abar_i   = 2 sum_l sum_j S_ij A_j U_ij            (U = C at unit amplitudes),
 // with S = (Cbar + Cbar^T)/2 (zero for multipoles outside a walker's list).
 //
-// The unit-amplitude spectra U are formed by one CTA per (multipole, walker): partial sums of
-// each unordered pair (i <= j) over chunks of 256 k points, the chunks added in a fixed order and
-// written to both (i,j) and (j,i), so C is symmetric bit for bit and the same from run to run.  Delta in FP32 (mixed paths): the products are FP32, each thread's share of a
+// The unit-amplitude spectra U are formed in two passes: partial sums of each unordered pair
+// (i <= j) over chunks of 256 k points (one CTA per multipole and chunk), then the chunks added in
+// a fixed order and written to both (i,j) and (j,i), so C is symmetric bit for bit and the same
+// from run to run.  Delta in FP32 (mixed paths): the products are FP32, each thread's share of a
 // chunk is one compensated FP32 sum (TwoSum; the rounding of each addition is carried in a
 // second float), and everything above it is FP64.
 #include <algorithm>
@@ -23,102 +24,89 @@ constexpr int KS = KC + 1; // shared row stride: lanes reading rows j at the sam
                            // different banks
 static_assert(QT == KC, "k_quad_part stages one k point per thread");
 
-// U for one multipole of one walker per CTA: grid (multipole, walker).  The k range runs in
-// chunks of KC points; CP chunks at a time are staged in shared memory (all loads of a pass in
-// flight together), then each chunk's pair sums are formed: thread t handles pair
-// p = t % npair for the k points t / npair, t / npair + G, ... of the chunk (G = QT / npair
-// groups), the groups are combined in a fixed order in FP64, and the chunk sums are added in
-// ascending chunk order into tot[p] (FP64).  Finally U[i][j] = U[j][i] = tot[p].
+// Partial pair sums over one chunk of KC k points: part[w][l - l_lo][kc][p] for unordered pairs
+// p = (i <= j).  Grid (multipole, k chunk, walker).  Thread t handles pair p = t % npair for the
+// k points t / npair, t / npair + G, ... of the chunk (G = QT / npair groups); groups are combined
+// in shared memory in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(QT)
-k_quad_full(double* __restrict__ U, const T* __restrict__ delta, const double* __restrict__ P,
-            const double* __restrict__ wk2, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-            int n_kc, int CP) {
-  extern __shared__ __align__(16) unsigned char qraw[];
+k_quad_part(double* __restrict__ part, const T* __restrict__ delta, const double* __restrict__ P,
+            const double* __restrict__ wk2, int N_tr, int N_k, int n_l, int n_kc,
+            const int* __restrict__ listed) {
+  extern __shared__ double qsm[];
+  T* Ds = reinterpret_cast<T*>(qsm);              // [N_tr][KS]
+  __shared__ double us[KC];
+  __shared__ float usf[KC];
+  __shared__ double red[QT];
+  const int ll = blockIdx.x, kc = blockIdx.y, w = blockIdx.z;
+  const int q0 = kc * KC;
   const int npair = N_tr * (N_tr + 1) / 2;
-  double* tot = reinterpret_cast<double*>(qraw);           // [npair]
-  double* red = tot + ((npair + 1) & ~1);                   // [QT]
-  double* us = red + QT;                                    // [CP][KC]
-  float* usf = reinterpret_cast<float*>(us + (size_t)CP * KC);   // [CP][KC]
-  T* Ds = reinterpret_cast<T*>(usf + (size_t)CP * KC);     // [CP][N_tr][KS]
-  const int ll = blockIdx.x, w = blockIdx.y;
-  for (int p = threadIdx.x; p < npair; p += QT) tot[p] = 0.0;
+  if (listed && listed[w * n_l + ll] < 0) {
+    // a multipole the walker does not list: zero partials (its Delta rows are not read)
+    double* out = part + (((size_t)w * n_l + ll) * n_kc + kc) * npair;
+    for (int p = threadIdx.x; p < npair; p += QT) out[p] = 0.0;
+    return;
+  }
   const T* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k;
-  const int ngroups = max(1, QT / npair);
-  for (int kc0 = 0; kc0 < n_kc; kc0 += CP) {
-    const int ncp = min(CP, n_kc - kc0);
-    __syncthreads();   // the previous pass has finished reading the staged chunks
-    for (int c = 0; c < ncp; ++c) {
-      // one k point per thread (QT == KC); the rows' loads are unrolled so that several are in
-      // flight at once
-      const int qq = threadIdx.x, q = (kc0 + c) * KC + qq;
-      T* Dc = Ds + (size_t)c * N_tr * KS;
+  {
+    // one k point per thread (QT == KC); the rows' loads are unrolled so that several are in
+    // flight at once
+    const int qq = threadIdx.x, q = q0 + qq;
 #pragma unroll 8
-      for (int t = 0; t < N_tr; ++t) Dc[t * KS + qq] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
-      const double u = q < N_k ? wk2[q] * P[(size_t)w * N_k + q] : 0.0;
-      us[c * KC + qq] = u;
-      usf[c * KC + qq] = (float)u;
-    }
-    __syncthreads();
-    for (int c = 0; c < ncp; ++c) {
-      const T* Dc = Ds + (size_t)c * N_tr * KS;
-      const double* uc = us + c * KC;
-      const float* ucf = usf + c * KC;
-      for (int p0 = 0; p0 < npair; p0 += QT) {
-        const int p = p0 + (ngroups > 1 ? threadIdx.x % npair : threadIdx.x);
-        const int group = ngroups > 1 ? threadIdx.x / npair : 0;
-        const bool active = p < npair && group < ngroups;
-        double acc = 0.0;
-        if (active) {
-          int r = p, i = 0;                           // unordered pair index -> (i <= j)
-          while (r >= N_tr - i) { r -= N_tr - i; ++i; }
-          const int j = i + r;
-          const T* di = Dc + i * KS;
-          const T* dj = Dc + j * KS;
-          if (sizeof(T) == 4) {
-            // FP32 products in one compensated FP32 sum (the rounding error of each addition,
-            // from TwoSum, carried in a second float), widened to FP64 once: GB300 runs FP64 at
-            // a small fraction of its FP32 rate
-            float sum = 0.0f, comp = 0.0f;
-            for (int c0 = group * 32; c0 < KC; c0 += ngroups * 32) {
-#pragma unroll 8
-              for (int qq = c0; qq < c0 + 32; ++qq) {
-                const float t = ((float)di[qq] * ucf[qq]) * (float)dj[qq];
-                const float sn = sum + t;
-                const float bp = sn - sum;
-                comp += (sum - (sn - bp)) + (t - bp);
-                sum = sn;
-              }
-            }
-            acc = (double)sum + (double)comp;
-          } else {
-            for (int qq = group; qq < KC; qq += ngroups)
-              acc = fma((double)di[qq] * uc[qq], (double)dj[qq], acc);
-          }
-        }
-        if (ngroups > 1) {
-          red[threadIdx.x] = acc;
-          __syncthreads();
-          if (active && group == 0) {
-            double s2 = acc;
-            for (int g = 1; g < ngroups; ++g) s2 += red[g * npair + threadIdx.x];
-            tot[p] += s2;
-          }
-          __syncthreads();
-        } else if (active) {
-          tot[p] += acc;
-        }
-      }
-    }
+    for (int t = 0; t < N_tr; ++t) Ds[t * KS + qq] = q < N_k ? dl[(size_t)t * N_k + q] : T(0);
+  }
+  for (int e = threadIdx.x; e < KC; e += QT) {
+    const int q = q0 + e;
+    us[e] = q < N_k ? wk2[q] * P[(size_t)w * N_k + q] : 0.0;
+    usf[e] = (float)us[e];
   }
   __syncthreads();
-  double* u = U + ((size_t)w * N_ell + l_lo + ll) * N_tr * N_tr;
-  for (int p = threadIdx.x; p < npair; p += QT) {
-    int r = p, i = 0;
-    while (r >= N_tr - i) { r -= N_tr - i; ++i; }
-    const int j = i + r;
-    u[i * N_tr + j] = tot[p];
-    u[j * N_tr + i] = tot[p];
+  const int ngroups = max(1, QT / npair);
+  double* out = part + (((size_t)w * n_l + ll) * n_kc + kc) * npair;
+  for (int p0 = 0; p0 < npair; p0 += QT) {
+    const int p = p0 + (ngroups > 1 ? threadIdx.x % npair : threadIdx.x);
+    const int group = ngroups > 1 ? threadIdx.x / npair : 0;
+    const bool active = p < npair && group < ngroups;
+    double acc = 0.0;
+    if (active) {
+      int r = p, i = 0;                           // unordered pair index -> (i <= j)
+      while (r >= N_tr - i) { r -= N_tr - i; ++i; }
+      const int j = i + r;
+      const T* di = Ds + i * KS;
+      const T* dj = Ds + j * KS;
+      if (sizeof(T) == 4) {
+        // FP32 products in one compensated FP32 sum (the rounding error of each addition,
+        // from TwoSum, carried in a second float), widened to FP64 once: GB300 runs FP64 at a
+        // small fraction of its FP32 rate
+        float sum = 0.0f, comp = 0.0f;
+        for (int c0 = group * 32; c0 < KC; c0 += ngroups * 32) {
+#pragma unroll 8
+          for (int qq = c0; qq < c0 + 32; ++qq) {
+            const float t = ((float)di[qq] * usf[qq]) * (float)dj[qq];
+            const float sn = sum + t;
+            const float bp = sn - sum;
+            comp += (sum - (sn - bp)) + (t - bp);
+            sum = sn;
+          }
+        }
+        acc = (double)sum + (double)comp;
+      } else {
+        for (int qq = group; qq < KC; qq += ngroups)
+          acc = fma((double)di[qq] * us[qq], (double)dj[qq], acc);
+      }
+    }
+    if (ngroups > 1) {
+      red[threadIdx.x] = acc;
+      __syncthreads();
+      if (active && group == 0) {
+        double s2 = acc;
+        for (int g = 1; g < ngroups; ++g) s2 += red[g * npair + threadIdx.x];
+        out[p] = s2;
+      }
+      __syncthreads();
+    } else if (active) {
+      out[p] = acc;
+    }
   }
 }
 
@@ -262,7 +250,7 @@ __global__ void __launch_bounds__(DT)
 k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __restrict__ delta,
             const double* __restrict__ Cf, const double* __restrict__ amp,
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
-            int N_ell, int n_walk, int l_lo, int n_l) {
+            int N_ell, int n_walk, int l_lo, int n_l, const int* __restrict__ listed) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int NP = delta_bar_pitch(N_tr);
   T* St = reinterpret_cast<T*>(dsm_raw);           // [LC][N_tr][NP]  St[j][i] = S_ij A_j
@@ -274,6 +262,12 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
   const int q = blockIdx.x * DT + threadIdx.x;
   const int l0 = lc * LC;
   const int nl = min(LC, l_lo + n_l - l0);
+  if (listed && listed[w * n_l + (l0 - l_lo)] < 0) {
+    // a multipole the walker does not list (LC = 1): S = 0, so Dbar = 0 and the P_bar partial is
+    // 0; its Delta rows are not read and its Dbar rows are not used
+    if (q < N_k) pbar_part[((size_t)lc * n_walk + w) * N_k + q] = 0.0;
+    return;
+  }
   const double* A = amp + (size_t)w * N_tr;
   for (int e = threadIdx.x; e < nl * N_tr * NP; e += DT) {
     const int ll = e / (N_tr * NP), r = e - ll * N_tr * NP, j = r / NP, i = r - j * NP;
@@ -337,25 +331,27 @@ __global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restric
 
 template <typename T>
 cudaError_t launch_quad(double* U, const T* delta, const double* P, const double* wk2, int n_walk,
-                        int N_tr, int N_k, int N_ell, int l_lo, int n_l, cudaStream_t s) {
-  const int n_kc = (N_k + KC - 1) / KC;
-  const int npair = N_tr * (N_tr + 1) / 2;
-  const size_t fixed = sizeof(double) * (((npair + 1) & ~1) + QT);
-  const size_t per_chunk = (size_t)N_tr * KS * sizeof(T) + (size_t)KC * (sizeof(double) + sizeof(float));
-  // a grid of a few waves stages its whole k range (one load phase per CTA); a large grid keeps
-  // the shared memory per CTA small so that several CTAs share an SM and hide each other's loads
-  const size_t budget = (long)n_l * n_walk >= 2L * 152 ? 48 * 1024 : 200 * 1024;
-  int CP = (int)std::max<size_t>(1, budget > fixed ? (budget - fixed) / per_chunk : 1);
-  CP = std::min(CP, n_kc);
-  const size_t smem = fixed + CP * per_chunk;
+                        int N_tr, int N_k, int N_ell, int l_lo, int n_l, double* scratch,
+                        cudaStream_t s, const int* listed = nullptr) {
+  size_t smem = (size_t)N_tr * KS * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_quad_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_quad_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_quad_full<T><<<dim3(n_l, n_walk), QT, smem, s>>>(U, delta, P, wk2, N_tr, N_k, N_ell, l_lo, n_l,
-                                                      n_kc, CP);
+  const int n_kc = (N_k + KC - 1) / KC;
+  dim3 g(n_l, n_kc, n_walk);
+  k_quad_part<T><<<g, QT, smem, s>>>(scratch, delta, P, wk2, N_tr, N_k, n_l, n_kc, listed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long total = (long)n_walk * n_l * N_tr * (N_tr + 1) / 2;
+  const unsigned grid = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+  k_quad_reduce<<<grid, 256, 0, s>>>(U, scratch, N_tr, N_ell, l_lo, n_l, n_kc, n_walk);
   return cudaGetLastError();
+}
+
+size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l) {
+  return sizeof(double) * (size_t)n_walk * n_l * ((N_k + KC - 1) / KC) * (N_tr * (N_tr + 1) / 2);
 }
 
 cudaError_t launch_pair_reduce(double* U, const double* part, int n_walk, int N_tr, int N_ell,
@@ -368,14 +364,15 @@ cudaError_t launch_pair_reduce(double* U, const double* part, int n_walk, int N_
 
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                             cudaStream_t s) {
-  return launch_quad<double>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
+                             double* scratch, cudaStream_t s) {
+  return launch_quad<double>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, scratch, s);
 }
 
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                            cudaStream_t s) {
-  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, s);
+                            double* scratch, cudaStream_t s, const int* listed) {
+  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, scratch, s,
+                            listed);
 }
 
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,
@@ -405,7 +402,8 @@ cudaError_t launch_amp_bar(double* amp_bar, const double* Cf, const double* U, c
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
-                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s) {
+                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s,
+                             const int* listed) {
   const size_t smem = (size_t)(LC * N_tr * delta_bar_pitch(N_tr) + N_tr * DT + N_tr) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
@@ -414,7 +412,7 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const do
   }
   dim3 g((N_k + DT - 1) / DT, (n_l + LC - 1) / LC, n_walk);
   k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell,
-                                     n_walk, l_lo, n_l);
+                                     n_walk, l_lo, n_l, listed);
   return cudaGetLastError();
 }
 
@@ -433,9 +431,10 @@ size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell) {
 
 template cudaError_t launch_delta_bar<double>(double*, const double*, const double*,
                                               const double*, const double*, const double*, int,
-                                              int, int, int, int, int, double*, cudaStream_t);
+                                              int, int, int, int, int, double*, cudaStream_t,
+                                              const int*);
 template cudaError_t launch_delta_bar<float>(float*, const float*, const double*, const double*,
                                              const double*, const double*, int, int, int, int,
-                                             int, int, double*, cudaStream_t);
+                                             int, int, double*, cudaStream_t, const int*);
 
 }  // namespace swcl

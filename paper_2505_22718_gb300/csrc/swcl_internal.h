@@ -47,11 +47,7 @@ int contract_adj_tc(swcl_ctx* c, int precision);
 // a3 / a5 in basis mode as GEMMs against the constant phase operand (basis_tc.cu)
 int basis_prepare(swcl_ctx* c);
 int basis_forward(swcl_ctx* c, int l_lo, int n_l);
-// image_ready: the B image was built by basis_dbar_image (which also forms the P_bar partials)
-int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate, bool image_ready);
-// Dbar of the chunk straight into the adjoint GEMM's B image (at the chosen adjoint tile) with the
-// P_bar partials, in place of launch_delta_bar + the image build
-int basis_dbar_image(swcl_ctx* c, int l_lo, int n_l, double* pbar_part);
+int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate);
 size_t basis_fixed_bytes(const swcl_ctx* c);     // constant operands of basis mode
 size_t basis_bytes_per_ell(const swcl_ctx* c);   // per-call operand images per multipole
 
@@ -96,6 +92,7 @@ struct LimberTable {
 
 struct swcl_ctx {
   int device = 0;
+  int num_sms = 148;                        // multiprocessors of the device (persistent grids)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t aux = nullptr;               // second stream for independent VJP kernels
@@ -153,10 +150,18 @@ struct swcl_ctx {
   int bt_f_mt = 0, bt_f_kb = 0, bt_a_mt = 0, bt_a_kb = 0;
   int bt_nt_fwd = 0, bt_nt_adj = 0;   // autotuned column tiles (0 = not tuned yet)
   int bt_fixed_fwd = 0, bt_fixed_adj = 0;  // tiles fixed by the environment (0 = tune)
+  uint32_t bt_pmask = 0x3F;    // compensated products issued (all six unless a study narrows it)
   swcl::DevBuf bt_eimg_f, bt_eimg_a;  // phase images: forward A [q][(n,re/im)], adjoint A [(n,re/im)][q]
   swcl::DevBuf bt_gdf, bt_g32;        // Gamma-ratio table as double-float and FP32
   swcl::DevBuf bt_kmu;                // [N_tr][4][N_k] float kpow * mu
   swcl::DevBuf bt_himg, bt_dimg;      // per-call B images (forward H, adjoint kpow mu Dbar)
+  // ragged multipole lists: the GEMM columns of listed multipoles only (basis_tc.cu column_plan)
+  swcl::DevBuf bt_cmap_f, bt_cmap_a, bt_lpos, bt_wbase;
+  int64_t bt_plan_key[7] = {-1, -1, -1, -1, -1, -1, -1};
+  int64_t lists_gen = 0;              // bumped when the walkers' multipole lists may change
+  int bt_plan_cols = 0;
+  bool bt_delta_clean = false;        // Delta rows of unlisted multipoles hold zeros
+  bool bt_compact = false;            // the last column plan kept listed multipoles only
 
   // ragged ell lists
   bool ragged = false;
@@ -177,6 +182,7 @@ struct swcl_ctx {
   swcl::DevBuf ws_aimg;      // VJP: split Dbar image (tensor-core A operand)
   swcl::DevBuf ws_cpart;     // VJP: per-k-tile knot partial sums of cbar
   swcl::DevBuf ws_pbpart;    // VJP: per-multipole-chunk partial sums of P_bar
+  swcl::DevBuf ws_qpart;     // forward: per-k-chunk partial pair sums of the k-quadrature
   swcl::DevBuf ws_jin;       // JVP: windows [1 + n_dir][N_tr][N] (base first), P' [n_dir][N_k], A' [n_dir][N_tr]
   swcl::DevBuf ws_dU;        // JVP: [n_dir][N_ell][N_tr][N_tr] tangent of U
   swcl::DevBuf ws_jout;      // JVP output / Fisher input staging for host arrays
@@ -286,12 +292,16 @@ cudaError_t launch_contract_fp64_adj(cplx* cbar, const double* dbar, const cplx*
 
 // a4 k-quadrature and VJP reductions (quad.cu).  Delta and Dbar buffers hold the multipoles
 // l_lo .. l_lo + n_l - 1 ([n_walk][n_l][N_tr][N_k]); U and Cbar_full all N_ell.
+// scratch: quad_scratch_bytes(n_walk, N_tr, N_k, n_l) of per-k-chunk pair sums
 cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, const double* wk2,
                              int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                             cudaStream_t s);
+                             double* scratch, cudaStream_t s);
+// listed [n_walk][n_l] (may be null): negative entries mark multipoles a walker does not list,
+// whose U is written as zero without reading Delta
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
-                            cudaStream_t s);
+                            double* scratch, cudaStream_t s, const int* listed = nullptr);
+size_t quad_scratch_bytes(int n_walk, int N_tr, int N_k, int n_l);
 
 // self-test of the bounded waits (selftest.cu)
 cudaError_t launch_wait_nothing(int* status, long long* cycles, cudaStream_t s);
@@ -309,7 +319,8 @@ cudaError_t launch_amp_bar(double* amp_bar, const double* Cbar_full, const doubl
 template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
-                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s);
+                             int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s,
+                             const int* listed = nullptr);   // listed: as in launch_quad_f32
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
                                int n_walk, int N_k, int N_ell, cudaStream_t s,
                                int* status = nullptr);

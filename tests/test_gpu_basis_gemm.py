@@ -125,10 +125,12 @@ def test_rank_two_profiles():
     assert wbar_err(Wb[0], Wbo) < GATE_G
 
 
-@pytest.mark.parametrize("code", [96, 128, 48, 64 | 256, 32 | 256, 64 | 1024, 96 | 1024, 128 | 1024])
+@pytest.mark.parametrize("code", [96, 128, 48, 64 | 256, 32 | 256, 64 | 1024, 96 | 1024, 128 | 1024,
+                                  64 | 1024 | 4096, 96 | 1024 | 4096])
 def test_every_tile_variant_against_oracle(code):
     """Each GEMM variant, fixed through SWCL_BASIS_TILES: one CTA per SM (48, 96, 128 columns),
-    two CTAs per SM (| 256), two K-blocks per pipeline stage (| 1024); three walkers, a ragged k
+    two CTAs per SM (| 256), two K-blocks per pipeline stage (| 1024), the persistent two-K-block
+    form (| 1024 | 4096); three walkers, a ragged k
     tail (333 points), 17 K-blocks in the forward GEMM (an odd count: the last stage is short),
     against the oracle."""
     import paper_2505_22718_gb300 as S
