@@ -638,6 +638,7 @@ def run_ours(args, rank, world, device):
     if rank == 0 and world == 1 and args.workload == "n5k" and not args.no_extra:
         out["general_profile"] = run_general_profile(args, dev, stream, flush, timed, peaks, src)
         out["batched"] = run_batched(args, dev, stream, timed, peaks, src)
+        out["large"] = run_large(args, dev, stream, timed, peaks, src)
     return out, w, cbar
 
 
@@ -684,6 +685,31 @@ def run_general_profile(args, dev, stream, flush, timed, peaks, src):
         floor = 1e-3 * np.sqrt(dg[:, :, None] * dg[:, None, :])
         rec["accuracy"] = {"max_norm_err_vs_oracle": float(np.max(np.abs(C - Co) / np.maximum(np.abs(Co), floor))),
                            "gate": 1e-4}
+    return rec
+
+
+def run_large(args, dev, stream, timed, peaks, src):
+    """Sub-record for the large configuration (30 tracers, every ell in [2, 3000], N = N_k = 4096,
+    200 knots, B(k, z)): one evaluation per step, forward + VJP and forward only, under a 40 GiB
+    memory budget, and the roofline of the dominant kernel."""
+    import paper_2505_22718_gb300 as swcl
+    from workloads import make_workload
+    w = make_workload("large")
+    cbar = np.random.default_rng(31).standard_normal((1, len(w.ells), w.n_tr, w.n_tr))
+    prec = swcl.PRECISIONS[args.precision]
+    ctx = swcl.Context(dev.index, 40 << 30, stream.cuda_stream)
+    st = device_inputs(swcl, ctx, w, cbar, dev)
+    ms, _, _ = timed(lambda: st.full(prec), 5, 3)
+    msf, _, _ = timed(lambda: st.fwd(prec), 5, 2)
+    _, _, stats = timed(lambda: st.profiled(prec), 3, 1, profile_ctx=ctx)
+    rank_r = ctx.query(swcl.SWCL_Q_PROFILE_RANK)
+    rec = {"workload": WORKLOAD_LARGE, "budget_gb": 40, "delta_recomputed": bool(ctx.query(swcl.SWCL_Q_RECOMPUTE)),
+           "value": 1e3 * 5 / ms, "unit": "evals/s", "ms_per_step": ms / 5,
+           "fwd_only": {"value": 1e3 * 5 / msf, "ms_per_step": msf / 5},
+           "tiles": {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)},
+           "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in stats.items()},
+           "roofline": roofline(stats, w, 1, args.precision, peaks, src, rank_r, "large", 3)}
+    ctx.close()
     return rec
 
 
@@ -868,7 +894,8 @@ def main():
                 "accuracy": acc, "kernel_ms": out["kernel_ms"],
                 "kernels_per_step": out["kernels_per_step"],
                 "peaks_measured_here": out.get("peaks_measured_here"),
-                "general_profile": out.get("general_profile"), "batched": out.get("batched")}
+                "general_profile": out.get("general_profile"), "batched": out.get("batched"),
+                "large": out.get("large")}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -303,12 +303,13 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
   if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
-  // a subset of the six compensated products of the basis GEMMs, for accuracy studies (bit t =
-  // product t in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0); the leading product and at least
-  // one correction are kept)
+  // the accuracy study of the compensated products: a subset of the six products of the basis
+  // GEMMs (bit t = product t in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)); only the sets
+  // 0x2F, 0x37, 0x1F, 0x17 and 0x07 exist, at the 96-column two-K-block tile (SWCL_BASIS_TILES
+  // 1120,1120); they all miss the accuracy gate
   if (const char* v = std::getenv("SWCL_BASIS_PRODUCTS")) {
-    const unsigned m = (unsigned)std::strtoul(v, nullptr, 0) & 0x3Fu;
-    if ((m & 1u) && (m & 0x3Eu)) c->bt_pmask = m;
+    const unsigned m = (unsigned)std::strtoul(v, nullptr, 0);
+    if (m == 0x2Fu || m == 0x37u || m == 0x1Fu || m == 0x17u || m == 0x07u) c->bt_pmask = m;
   }
   // fixed basis-GEMM tiles "fwd,adj" (tile codes as reported by SWCL_Q_TILE_*) instead of tuning
   if (const char* v = std::getenv("SWCL_BASIS_TILES")) {

@@ -129,11 +129,14 @@ __host__ __device__ inline Layout layout(int NT, int stages, int KS) {
 struct GemmShape {
   int n_mt, n_kb, NT, stages;
   uint32_t tmem_cols;
-  // products issued (bit t = product t of A3B3; bit 0, the leading product, always set) and the
-  // first correction issued, whose MMA overwrites the correction slot of each stage
-  uint32_t pmask;
-  int first_corr;
 };
+
+// Products issued (bit t = product t of A3B3) and the first correction among them, whose MMA
+// overwrites the correction slot of each stage.  All six in production; the other sets exist for
+// the accuracy study of the compensated products (SWCL_BASIS_PRODUCTS).
+__host__ __device__ constexpr int first_correction(uint32_t pm) {
+  return (pm & 2u) ? 1 : (pm & 4u) ? 2 : (pm & 8u) ? 3 : (pm & 16u) ? 4 : 5;
+}
 
 // ------------------------------------------------------------------ epilogues ----
 
@@ -335,7 +338,7 @@ struct EpiAdj {
 
 // CH: 16-column chunks per drain thread at most (3 for tiles up to 96 columns with 8 drain
 // warps, 4 otherwise); it sizes the accumulator registers.
-template <class P, class Epi, int DW, int CH, int KS>
+template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu>
 __global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
@@ -445,12 +448,12 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
           for (int j = 0; j < kK / 16; ++j) {
 #pragma unroll
             for (int t = 0; t < P::kProducts; ++t) {
-              if (!((sh.pmask >> t) & 1u)) continue;
+              if (!((PM >> t) & 1u)) continue;
               // descriptor start addresses advance in 16-byte units
               const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
               const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
               const bool lead = (t == 0);
-              const bool first = (h == 0) && (j == 0) && (lead || t == sh.first_corr);
+              const bool first = (h == 0) && (j == 0) && (lead || t == first_correction(PM));
               mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
             }
           }
@@ -684,11 +687,10 @@ k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bim
           for (int j = 0; j < kK / 16; ++j) {
 #pragma unroll
             for (int t = 0; t < P::kProducts; ++t) {
-              if (!((sh.pmask >> t) & 1u)) continue;
               const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
               const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
               const bool lead = (t == 0);
-              const bool first = (h == 0) && (j == 0) && (lead || t == sh.first_corr);
+              const bool first = (h == 0) && (j == 0) && (t <= 1);
               mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
             }
           }
@@ -1019,22 +1021,34 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
   while (cols < (uint32_t)(4 * stride)) cols <<= 1;
-  int first_corr = 1;
-  while (first_corr < P::kProducts && !((c->bt_pmask >> first_corr) & 1u)) ++first_corr;
-  sh = GemmShape{n_mt, n_kb, NT, stages, cols, c->bt_pmask, first_corr};
+  sh = GemmShape{n_mt, n_kb, NT, stages, cols};
   smem = L.total;
   return SWCL_OK;
 }
 
-template <class P, class Epi, int DW, int CH, int KS>
+template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu>
 cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
                            uint32_t smem, int n_nt, const Epi& epi) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS>,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS, PM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi, DW, CH, KS><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
+  k_gemm_basis<P, Epi, DW, CH, KS, PM><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
       a, b, sh, epi, (int*)c->ws_status.p);
   return cudaGetLastError();
+}
+
+// The product subsets of the accuracy study, at the 96-column two-K-block tile only.
+template <class P, class Epi>
+cudaError_t launch_subset(swcl_ctx* c, uint32_t pm, const uint8_t* a, const uint8_t* b,
+                          const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
+  switch (pm) {
+    case 0x2Fu: return launch_variant<P, Epi, 8, 3, 2, 0x2Fu>(c, a, b, sh, smem, n_nt, epi);
+    case 0x37u: return launch_variant<P, Epi, 8, 3, 2, 0x37u>(c, a, b, sh, smem, n_nt, epi);
+    case 0x1Fu: return launch_variant<P, Epi, 8, 3, 2, 0x1Fu>(c, a, b, sh, smem, n_nt, epi);
+    case 0x17u: return launch_variant<P, Epi, 8, 3, 2, 0x17u>(c, a, b, sh, smem, n_nt, epi);
+    case 0x07u: return launch_variant<P, Epi, 8, 3, 2, 0x07u>(c, a, b, sh, smem, n_nt, epi);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class P, class Epi>
@@ -1054,6 +1068,10 @@ template <class P, class Epi>
 cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* b,
                         const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
   const int nch = sh.NT / 16;
+  if (c->bt_pmask != 0x3Fu) {
+    if (code != (96 | kDeep)) return cudaErrorInvalidValue;   // study subsets: tile 1120 only
+    return launch_subset<P, Epi>(c, c->bt_pmask, a, b, sh, smem, n_nt, epi);
+  }
   if (code & kPersist) return launch_persist<P, Epi>(c, a, b, sh, smem, n_nt, epi);
   if (code & kPair)   // four drain warps: every chunk of a row in one thread
     return nch <= 3 ? launch_variant<P, Epi, 4, 3, 1>(c, a, b, sh, smem, n_nt, epi)

@@ -48,3 +48,20 @@ def test_ell_blocks_on_replicas_match_full_evaluation(name, prec, wl):
     assert pbar_err(Pb[0], Pbo, ex["P_abs"]) < gate_g
     assert grad_err(Ab[0], Abo) < gate_g
     assert wbar_err(Wb[0], Wbo) < gate_g
+
+
+def test_evaluate_ell_split_through_the_library(wl):
+    """sharding.evaluate_ell_split without a process group: the whole multipole list is this
+    process's block, computed through the C ABI (library_block), equal to the oracle."""
+    import paper_2505_22718_gb300 as S
+    from paper_2505_22718_gb300.sharding import evaluate_ell_split
+    w = wl("tiny2")
+    Cb = np.random.default_rng(4).standard_normal((len(w.ells), w.n_tr, w.n_tr))
+    setup = dict(chi_min=w.chi_min, chi_max=w.chi_max, N=w.N, k=w.k, ells=w.ells, knots=w.knots,
+                 kind=w.kind, fft_bias=w.fft_bias, W=w.W, D=w.D, B=w.B, P=w.P, amp=w.amp)
+    C, Pb, Ab, Wb = evaluate_ell_split(setup, Cb, S.SWCL_FP64)
+    f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, C_bar=Cb)
+    assert norm_err(C.numpy(), f["C"]) < 1e-10
+    assert pbar_err(Pb.numpy(), Pbo, ex["P_abs"]) < 1e-10
+    assert grad_err(Ab.numpy(), Abo) < 1e-10
+    assert wbar_err(Wb.numpy(), Wbo) < 1e-9
