@@ -144,19 +144,24 @@ def algorithmic_work(w, walkers, rank, n_ell_useful=None):
 # benchmark workload (one walker), from the ncu capture summarised in profiles/, valid only for
 # the kernel source it was taken from (sha256 of the file; otherwise reported as null).
 TRAFFIC = {
-    # profiles/basis_gemm_n5k_bf16.md (tiles 1120/1120: 96 columns, two K-blocks per stage; one walker)
-    "basis gemm adj": {"bytes": 25438720 + 0, "walkers": 1, "workload": "n5k",
-                       "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
-    "basis gemm fwd": {"bytes": 33252096 + 0, "walkers": 1, "workload": "n5k",
-                       "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                       "sha256": "9b84500be7150163b7243effd9416f46cd16b3bd6481933a3a935ce4a9c59b02"},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture per (kernel, tile code), one
+    # walker, N5K-shaped workload (profiles/basis_gemm_n5k_bf16.md); valid while basis_tc.cu is
+    # the file whose sha256 is recorded
+    ("basis gemm adj", 1120): {"bytes": 25419776 + 256, "walkers": 1, "workload": "n5k",
+                               "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
+                               "sha256": "675501c90c3b8f0a1d82cafc91a73c90fb6746468f22f39238cb9b1400d69bfd"},
+    ("basis gemm fwd", 1120): {"bytes": 33254912 + 2048, "walkers": 1, "workload": "n5k",
+                               "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
+                               "sha256": "675501c90c3b8f0a1d82cafc91a73c90fb6746468f22f39238cb9b1400d69bfd"},
 }
 
 
-def traffic_for(name, walkers, workload="n5k"):
+def traffic_for(name, walkers, workload="n5k", tiles=None):
     import hashlib
-    t = TRAFFIC.get(name)
+    code = None
+    if tiles and name.startswith("basis gemm"):
+        code = tiles.get("adj" if name.endswith("adj") else "fwd")
+    t = TRAFFIC.get((name, code))
     if not t or t["walkers"] != walkers or t["workload"] != workload:
         return None
     try:
@@ -203,7 +208,7 @@ def measure_matmul_peaks(dev):
 
 
 def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", steps=None,
-             recompute=False, kernel=None, n_ell_useful=None):
+             recompute=False, kernel=None, n_ell_useful=None, tiles=None):
     """Roofline of one kernel of the profiled steps (default: the longest).  `achieved` is the
     method's useful work (algorithmic_work) per launch over the kernel's average CUDA-event time,
     and `frac` is that over the measured peak of the kernel's arithmetic (bf16 burst from
@@ -243,7 +248,7 @@ def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", ste
             peak, note = peaks["bf16_tflops"], "bf16 burst peak (%s)" % src
         return {"kernel": name, "bound": "tensor", "achieved": useful, "peak": peak, "unit": "TFLOP/s",
                 "frac": useful / peak, "pipe_occupancy": useful * products / peak,
-                "products": products, "traffic": traffic_for(name, walkers, workload),
+                "products": products, "traffic": traffic_for(name, walkers, workload, tiles),
                 "avg_ms": ms / launches, "launches": launches, "peak_source": note,
                 "work": "4 n_h N_tr N_k N_ell useful flops per evaluation (%.3g per launch)" % flops}
     if peaks.get("fp64_tflops"):
@@ -253,7 +258,7 @@ def roofline(stats, w, walkers, precision, peaks, src, rank, workload="n5k", ste
         peak = FP64_PEAK_TFLOPS
         note = "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"
     return {"kernel": name, "bound": "alu", "achieved": useful, "peak": peak, "unit": "TFLOP/s",
-            "frac": useful / peak, "traffic": traffic_for(name, walkers, workload),
+            "frac": useful / peak, "traffic": traffic_for(name, walkers, workload, tiles),
             "avg_ms": ms / launches, "launches": launches, "peak_source": note,
             "work": "%.3g useful flops per launch" % flops}
 
@@ -571,7 +576,7 @@ def run_ours(args, rank, world, device):
     out["tiles"] = {"fwd": ctx.query(swcl.SWCL_Q_TILE_FWD), "adj": ctx.query(swcl.SWCL_Q_TILE_ADJ)}
     out["recompute"] = ctx.query(swcl.SWCL_Q_RECOMPUTE)
     out["roofline"] = roofline(stats, w, nw, args.precision, peaks, src, rank_r, args.workload,
-                               k_prof, bool(out["recompute"]))
+                               k_prof, bool(out["recompute"]), tiles=out["tiles"])
     out["profile_rank"] = rank_r
     msf, _, _ = timed(lambda: st.fwd(prec), args.steps, max(3, args.warmup // 2))
     out["fwd_only"] = {"value": nw * world / (msf / args.steps / 1e3), "unit": "evals/s",

@@ -295,6 +295,7 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
       cudaEventCreateWithFlags(&c->ev_pre, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_unpack, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_pack, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_quad, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc((void**)&c->stage, swcl::kStageBytes, cudaHostAllocDefault) != cudaSuccess) {
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -369,6 +370,7 @@ int swcl_destroy(swcl_ctx* c) {
   if (c->ev_pre) cudaEventDestroy(c->ev_pre);
   if (c->ev_unpack) cudaEventDestroy(c->ev_unpack);
   if (c->ev_pack) cudaEventDestroy(c->ev_pack);
+  if (c->ev_quad) cudaEventDestroy(c->ev_quad);
   if (c->stage) cudaFreeHost(c->stage);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -884,19 +886,29 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                                (const double*)c->d_chipow.p, sv.D, sv.B,
                                                (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                                nw, N_tr, N_I, N, c->stream), "fftlog");
+  // In a batched forward + VJP with one multipole chunk and no Limber rows, U feeds only the
+  // packing of C and amp_bar, both on the auxiliary stream, while the VJP's Dbar needs Delta
+  // alone: the k-quadrature then runs on the auxiliary stream too, beside the reverse mode.
+  const bool quad_aside = c->overlap && n_lc >= n_fft && lim.n_lim == 0 && swcl::is_device_ptr(C_out);
   for (int l_lo = 0; l_lo < n_fft; l_lo += n_lc) {
     const int n_l = std::min(n_lc, n_fft - l_lo);
     SWCL_TRY(contract_chunk(c, precision, l_lo, n_l));
+    cudaStream_t qs = c->stream;
+    if (quad_aside) {
+      SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_quad, c->stream), "fork quadrature");
+      SWCL_TRY_CUDA(c, cudaStreamWaitEvent(c->aux, c->ev_quad, 0), "fork quadrature");
+      qs = c->aux;
+    }
     if (fp64)
       SWCL_LAUNCH(c, swcl::launch_quad_fp64((double*)c->ws_U.p, (const double*)c->ws_delta.p,
                                             (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
                                             N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
-                                            c->stream), "k-quadrature fp64");
+                                            qs), "k-quadrature fp64");
     else
       SWCL_LAUNCH(c, swcl::launch_quad_f32((double*)c->ws_U.p, (const float*)c->ws_delta.p,
                                            (const double*)c->d_P.p, (const double*)c->d_wk2.p, nw,
                                            N_tr, N_k, N_ell, l_lo, n_l, (double*)c->ws_qpart.p,
-                                           c->stream,
+                                           qs,
                                            use_basis_gemm(c, precision) && c->bt_compact
                                                ? (const int*)c->bt_lpos.p : nullptr),
                   "k-quadrature f32");

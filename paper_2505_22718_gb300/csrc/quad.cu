@@ -5,12 +5,12 @@
 //   Abar_i   = 2 sum_l sum_j S_ij A_j U_ij            (U = C at unit amplitudes),
 // with S = (Cbar + Cbar^T)/2 (zero for multipoles outside a walker's list).
 //
-// The unit-amplitude spectra U are formed in two passes: partial sums of each unordered pair
-// (i <= j) over chunks of 256 k points (one CTA per multipole and chunk), then the chunks added in
-// a fixed order and written to both (i,j) and (j,i), so C is symmetric bit for bit and the same
-// from run to run.  Delta in FP32 (mixed paths): the products are FP32, each thread's share of a
-// chunk is one compensated FP32 sum (TwoSum; the rounding of each addition is carried in a
-// second float), and everything above it is FP64.
+// The unit-amplitude spectra U of the FP64 form are formed in two passes: partial sums of each
+// unordered pair (i <= j) over chunks of 256 k points (one CTA per multipole and chunk), then the
+// chunks added in a fixed order and written to both (i,j) and (j,i), so C is symmetric bit for
+// bit and the same from run to run.  Delta in FP32 (mixed paths) goes through k_quad_blocks
+// below: FP32 products, compensated FP32 sums (TwoSum; the rounding of each addition carried in
+// a second float), FP64 above them, in one pass when a multipole's k range fits one CTA.
 #include <algorithm>
 
 #include "swcl_internal.h"
@@ -128,6 +128,181 @@ __global__ void k_quad_reduce(double* __restrict__ U, const double* __restrict__
     double* u = U + ((size_t)w * N_ell + l_lo + ll) * N_tr * N_tr;
     u[i * N_tr + j] = s;
     u[j * N_tr + i] = s;
+  }
+}
+
+// ---- FP32 form: register blocks of 4 x 4 tracer pairs ----
+//
+// One CTA per (multipole, k chunk, walker) copies the chunk's Delta rows into shared memory as
+// they lie in global memory ([tracer][k], rows padded to a multiple of four tracers with zeros)
+// with asynchronous 16-byte copies, all in flight at once, and u = wk2 P in FP32.  Warp b takes
+// the block of pairs (4 ib .. 4 ib + 3) x (4 jb .. 4 jb + 3), ib <= jb; lane l takes the k points
+// l, l + 32, ... (consecutive lanes read consecutive words: no bank conflicts).  Per k point a lane
+// forms a_i = Delta_i u (four products, rounded as in the two-pass form) and sixteen FMAs a_i
+// Delta_j into block sums; every QB_GROUP points the block sums are added into compensated
+// (TwoSum) accumulators.  The 32 lanes are then combined by a butterfly that halves the pairs
+// each lane holds at every step (each combination a TwoSum), so lane pair (2p, 2p + 1) ends with
+// pair p of the block.  The order of every addition is fixed: the result is the same from run to
+// run.  With one chunk the sum, widened to FP64, is U itself (both triangles); with several, the
+// per-chunk sums go through the chunk reduction of the other form.
+constexpr int QB_MAX_WARPS = 20;
+constexpr int QB_GROUP = 4;                  // k points per lane between compensated additions
+constexpr int QB_SMEM = 100 * 1024;          // staged rows per CTA at most (2 CTAs per SM)
+
+__device__ __forceinline__ void qb_two_sum(float& s, float& c, float b) {
+  const float sn = s + b;
+  const float bp = sn - s;
+  c += (s - (sn - bp)) + (b - bp);
+  s = sn;
+}
+
+// (s, c) += (rs, rc): the sums' rounding error from TwoSum, the compensations added
+__device__ __forceinline__ void qb_combine(float& s, float& c, float rs, float rc) {
+  const float sn = s + rs;
+  const float bp = sn - s;
+  const float e = (s - (sn - bp)) + (rs - bp);
+  c = (c + rc) + e;
+  s = sn;
+}
+
+// one butterfly step: lanes with (lane & OFF) keep the upper half of their H pairs
+template <int H, int OFF>
+__device__ __forceinline__ void qb_scatter_step(float* s, float* c, int lane) {
+  const bool up = lane & OFF;
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const float keep_s = up ? s[p + H] : s[p], keep_c = up ? c[p + H] : c[p];
+    const float ss = up ? s[p] : s[p + H], sc = up ? c[p] : c[p + H];
+    const float rs = __shfl_xor_sync(0xffffffffu, ss, OFF);
+    const float rc = __shfl_xor_sync(0xffffffffu, sc, OFF);
+    s[p] = keep_s;
+    c[p] = keep_c;
+    qb_combine(s[p], c[p], rs, rc);
+  }
+}
+
+__global__ void __launch_bounds__(QB_MAX_WARPS * 32, 1)
+k_quad_blocks(double* __restrict__ U, double* __restrict__ part, const float* __restrict__ delta,
+              const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
+              int N_ell, int l_lo, int n_l, int kcap, int n_kc, int ks, bool vec4,
+              const int* __restrict__ listed) {
+  extern __shared__ float4 qb_smv[];
+  float* qb_sm = reinterpret_cast<float*>(qb_smv);
+  const int ll = blockIdx.x, kc = blockIdx.y, w = blockIdx.z;
+  const int n_ib = (N_tr + 3) / 4, nb = n_ib * (n_ib + 1) / 2;
+  const int npair = N_tr * (N_tr + 1) / 2;
+  const int q0 = kc * kcap;
+  const int nk = min(kcap, N_k - q0);
+  const int nk32 = (nk + 31) & ~31;
+  double* Uw = U + ((size_t)w * N_ell + l_lo + ll) * N_tr * N_tr;
+  double* pw = part + (((size_t)w * n_l + ll) * n_kc + kc) * npair;
+  if (listed && listed[w * n_l + ll] < 0) {
+    // a multipole the walker does not list: zero sums (its Delta rows are not read)
+    if (n_kc == 1)
+      for (int e = threadIdx.x; e < N_tr * N_tr; e += blockDim.x) Uw[e] = 0.0;
+    else
+      for (int e = threadIdx.x; e < npair; e += blockDim.x) pw[e] = 0.0;
+    return;
+  }
+  const int rows = 4 * n_ib;
+  float* Ds = qb_sm;                                            // [rows][kcap]
+  float* us = qb_sm + (size_t)rows * kcap;                      // [kcap]
+  const float* dl = delta + ((size_t)w * n_l + ll) * N_tr * N_k + q0;
+  if (vec4) {
+    // rows start on 16-byte boundaries (N_k and q0 multiples of 4): 16-byte copies, the part of
+    // a group past the chunk's end (and every padding row) filled with zeros by the copy itself
+    const int ng = nk32 >> 2;
+    for (int e = threadIdx.x; e < rows * ng; e += blockDim.x) {
+      const int t = e / ng, gq = e - t * ng;
+      const int left = nk - 4 * gq;
+      const int bytes = t < N_tr ? (left >= 4 ? 16 : left > 0 ? 4 * left : 0) : 0;
+      const float* src = bytes ? dl + (size_t)t * N_k + 4 * gq : dl;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(Ds + (size_t)t * kcap + 4 * gq);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(bytes) : "memory");
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * nk32; e += blockDim.x) {
+      const int t = e / nk32, kk = e - t * nk32;
+      const int bytes = t < N_tr && kk < nk ? 4 : 0;
+      const float* src = bytes ? dl + (size_t)t * N_k + kk : dl;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(Ds + (size_t)t * kcap + kk);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src),
+                   "r"(bytes) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int kk = threadIdx.x; kk < nk32; kk += blockDim.x)
+    us[kk] = kk < nk ? (float)(wk2[q0 + kk] * P[(size_t)w * N_k + q0 + kk]) : 0.0f;
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  // warp wi: k part h = wi / wb of ks, blocks bw, bw + wb, ... (bw = wi % wb); part h takes the
+  // 32-point groups [h n32 / ks, (h + 1) n32 / ks) of the chunk
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int wb = (blockDim.x >> 5) / ks, h = wi / wb, bw = wi - h * wb;
+  const int n32 = nk32 >> 5;
+  const int k_lo = 32 * (h * n32 / ks), k_hi = 32 * ((h + 1) * n32 / ks);
+  float2* red = reinterpret_cast<float2*>(us + kcap);         // [ks][nb][16] (sum, compensation)
+  for (int b = bw; b < nb && h < ks; b += wb) {
+    int ib = 0, r = b;                                          // block b -> (ib <= jb)
+    while (r >= n_ib - ib) { r -= n_ib - ib; ++ib; }
+    const int jb = ib + r;
+    const float* ra = Ds + (size_t)(4 * ib) * kcap;
+    const float* rb = Ds + (size_t)(4 * jb) * kcap;
+    float s[16], c[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) s[p] = c[p] = 0.0f;
+    for (int g0 = k_lo; g0 < k_hi; g0 += 32 * QB_GROUP) {
+      float bs[16];
+#pragma unroll
+      for (int p = 0; p < 16; ++p) bs[p] = 0.0f;
+      const int g1 = min(k_hi, g0 + 32 * QB_GROUP);
+#pragma unroll 2
+      for (int kk = g0 + lane; kk < g1; kk += 32) {
+        const float u = us[kk];
+        float ai[4], dj[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          ai[x] = ra[(size_t)x * kcap + kk] * u;
+          dj[x] = rb[(size_t)x * kcap + kk];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) bs[4 * x + y] = fmaf(ai[x], dj[y], bs[4 * x + y]);
+      }
+#pragma unroll
+      for (int p = 0; p < 16; ++p) qb_two_sum(s[p], c[p], bs[p]);
+    }
+    qb_scatter_step<8, 16>(s, c, lane);
+    qb_scatter_step<4, 8>(s, c, lane);
+    qb_scatter_step<2, 4>(s, c, lane);
+    qb_scatter_step<1, 2>(s, c, lane);
+    qb_combine(s[0], c[0], __shfl_xor_sync(0xffffffffu, s[0], 1),
+               __shfl_xor_sync(0xffffffffu, c[0], 1));
+    if (!(lane & 1)) red[((size_t)h * nb + b) * 16 + (lane >> 1)] = make_float2(s[0], c[0]);
+  }
+  __syncthreads();
+  // the k parts of each pair, added in order; pair p of block b is (4 ib + p / 4, 4 jb + p % 4)
+  for (int e = threadIdx.x; e < nb * 16; e += blockDim.x) {
+    const int b = e >> 4, p = e & 15;
+    int ib = 0, r = b;
+    while (r >= n_ib - ib) { r -= n_ib - ib; ++ib; }
+    const int jb = ib + r;
+    const int i = 4 * ib + (p >> 2), j = 4 * jb + (p & 3);
+    if (i >= N_tr || j >= N_tr || i > j) continue;
+    float2 t = red[e];
+    for (int hh = 1; hh < ks; ++hh) {
+      const float2 o = red[(size_t)hh * nb * 16 + e];
+      qb_combine(t.x, t.y, o.x, o.y);
+    }
+    const double v = (double)t.x + (double)t.y;
+    if (n_kc == 1) {
+      Uw[i * N_tr + j] = v;
+      Uw[j * N_tr + i] = v;
+    } else {
+      pw[i * N_tr - i * (i - 1) / 2 + (j - i)] = v;
+    }
   }
 }
 
@@ -371,8 +546,34 @@ cudaError_t launch_quad_fp64(double* U, const double* delta, const double* P, co
 cudaError_t launch_quad_f32(double* U, const float* delta, const double* P, const double* wk2,
                             int n_walk, int N_tr, int N_k, int N_ell, int l_lo, int n_l,
                             double* scratch, cudaStream_t s, const int* listed) {
-  return launch_quad<float>(U, delta, P, wk2, n_walk, N_tr, N_k, N_ell, l_lo, n_l, scratch, s,
-                            listed);
+  if (n_walk <= 0 || n_l <= 0) return cudaSuccess;
+  const int n_ib = (N_tr + 3) / 4, nb = n_ib * (n_ib + 1) / 2;
+  // k parts per block: with few CTAs (one walker), enough warps per CTA to hide the shared-load
+  // and FMA latencies; with many, one part (each further part repeats the lane combination)
+  const long n_cta0 = (long)n_walk * n_l * ((N_k + 1023) / 1024);
+  const int ks = n_cta0 >= 2 * 152 ? 1 : std::max(1, std::min(4, QB_MAX_WARPS / nb));
+  const int warps = ks * std::min(nb, QB_MAX_WARPS / ks);
+  const size_t red_bytes = sizeof(float2) * (size_t)ks * nb * 16;
+  // k points per CTA: the largest power of two up to 1024 whose rows fit QB_SMEM
+  int kcap = 1024;
+  while (kcap > 32 && (size_t)kcap * (16 * n_ib + 4) + red_bytes > (size_t)QB_SMEM) kcap >>= 1;
+  const int n_kc = (N_k + kcap - 1) / kcap;
+  const size_t smem = (size_t)kcap * (16 * n_ib + 4) + red_bytes;
+  const bool vec4 = N_k % 4 == 0 && ((uintptr_t)delta & 15) == 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_quad_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g(n_l, n_kc, n_walk);
+  k_quad_blocks<<<g, warps * 32, smem, s>>>(U, scratch, delta, P, wk2, N_tr, N_k, N_ell, l_lo,
+                                            n_l, kcap, n_kc, ks, vec4, listed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_kc == 1) return e;
+  const long total = (long)n_walk * n_l * N_tr * (N_tr + 1) / 2;
+  const unsigned grid = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+  k_quad_reduce<<<grid, 256, 0, s>>>(U, scratch, N_tr, N_ell, l_lo, n_l, n_kc, n_walk);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scale_pack(double* C, const double* U, const double* amp, const int* off,

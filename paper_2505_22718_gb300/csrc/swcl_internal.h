@@ -197,7 +197,7 @@ struct swcl_ctx {
   // swcl_compute_batched with a cotangent: the cotangent is unpacked on the auxiliary stream beside
   // the forward pass, and C is packed there beside the VJP (joined at the end of the VJP)
   bool overlap = false;
-  cudaEvent_t ev_pre = nullptr, ev_unpack = nullptr, ev_pack = nullptr;
+  cudaEvent_t ev_pre = nullptr, ev_unpack = nullptr, ev_pack = nullptr, ev_quad = nullptr;
   // pinned staging for small host inputs: copied on the host, then sent without a wait
   unsigned char* stage = nullptr;
   size_t stage_off = 0;

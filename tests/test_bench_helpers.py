@@ -85,10 +85,13 @@ def test_named_kernel_roofline(n5k):
     assert bench.roofline(stats, n5k, 1, "bf16x9", PEAKS, "m", 0, "n5k", 10, kernel="nope") is None
 
 
-def test_stored_traffic_applies_only_to_its_workload_and_source():
-    t = bench.TRAFFIC["basis gemm adj"]
-    got = bench.traffic_for("basis gemm adj", 1, "n5k")
+def test_stored_traffic_applies_only_to_its_workload_source_and_tiles():
+    t = bench.TRAFFIC[("basis gemm adj", 1120)]
+    tiles = {"fwd": 1120, "adj": 1120}
+    got = bench.traffic_for("basis gemm adj", 1, "n5k", tiles)
     assert got in (t["bytes"], None)     # None once the kernel source has changed
-    assert bench.traffic_for("basis gemm adj", 1, "large") is None
-    assert bench.traffic_for("basis gemm adj", 256, "n5k") is None
-    assert bench.traffic_for("fftlog", 1, "n5k") is None
+    assert bench.traffic_for("basis gemm adj", 1, "n5k") is None                       # tiles unknown
+    assert bench.traffic_for("basis gemm adj", 1, "n5k", {"fwd": 1120, "adj": 96}) is None
+    assert bench.traffic_for("basis gemm adj", 1, "large", tiles) is None
+    assert bench.traffic_for("basis gemm adj", 256, "n5k", tiles) is None
+    assert bench.traffic_for("fftlog", 1, "n5k", tiles) is None
