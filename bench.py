@@ -147,12 +147,9 @@ TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture per (kernel, tile code), one
     # walker, N5K-shaped workload (profiles/basis_gemm_n5k_bf16.md); valid while basis_tc.cu is
     # the file whose sha256 is recorded
-    ("basis gemm adj", 1120): {"bytes": 25419776 + 256, "walkers": 1, "workload": "n5k",
+    ("basis gemm adj", 1120): {"bytes": 25427456 + 256, "walkers": 1, "workload": "n5k",
                                "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                               "sha256": "675501c90c3b8f0a1d82cafc91a73c90fb6746468f22f39238cb9b1400d69bfd"},
-    ("basis gemm fwd", 1120): {"bytes": 33254912 + 2048, "walkers": 1, "workload": "n5k",
-                               "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                               "sha256": "675501c90c3b8f0a1d82cafc91a73c90fb6746468f22f39238cb9b1400d69bfd"},
+                               "sha256": "0dca7de8644e260b90d1f5634a7880c1ad4d9efd4588512751e7659983e58604"},
 }
 
 

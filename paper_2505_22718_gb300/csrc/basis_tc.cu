@@ -129,6 +129,7 @@ __host__ __device__ inline Layout layout(int NT, int stages, int KS) {
 struct GemmShape {
   int n_mt, n_kb, NT, stages;
   uint32_t tmem_cols;
+  uint32_t pre_off;     // offset of the epilogue's staged table rows (0: none), k_gemm_basis only
 };
 
 // Products issued (bit t = product t of A3B3) and the first correction among them, whose MMA
@@ -140,6 +141,20 @@ __host__ __device__ constexpr int first_correction(uint32_t pm) {
 
 // ------------------------------------------------------------------ epilogues ----
 
+// 8-byte asynchronous copy global -> shared; bytes = 0 fills the destination with zeros (src is
+// then not read, but stays a valid address)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+// the drain warps' own barrier (barrier 1; barrier 0 is the CTA's)
+__device__ __forceinline__ void drain_bar(int nthreads) {
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
+
 // The epilogues read this thread's accumulator column c at acc[c * stride] (shared memory; see
 // the drain), in loops that are not unrolled: the kernel runs them once per CTA, so a compact
 // body keeps the cold instruction fetch short.
@@ -150,6 +165,9 @@ struct EpiFwd {
   const float* kmu;     // [N_tr][4][N_k]
   const int2* cmap;     // ragged lists: column group -> {w N_tr + i, l}; null: every multipole
   int N_k, N_tr, n_l, r, n_cols;
+  static constexpr bool kGamma = false;   // no table rows staged in shared memory
+  __device__ __forceinline__ void prefetch(float2*, int, int, int, int, int) const {}
+  __device__ __forceinline__ void set_stage(const float2*, int) {}
   // row m, this thread's columns j0 .. j0 + nc - 1 (j0 is a multiple of r)
   __device__ __forceinline__ void operator()(int m, int j0, const float* acc, int stride, int nc) const {
     if (m >= N_k) return;
@@ -226,6 +244,49 @@ struct EpiAdj {
   const int* cls_of;
   const int2* cmap;     // ragged lists: column -> {(w N_tr + i) r + s, l}; null: every multipole
   int n_h, N_tr, N_ell, l_lo, n_l, r, NI, n_cols;
+  // Gamma rows of the tile staged in shared memory during the main loop: gs[c][n - 64 mt] for the
+  // tile's columns c = j - gs_j0 (null: read from L2 in the epilogue)
+  const float2* gs = nullptr;
+  int gs_j0 = 0;
+  static constexpr bool kGamma = true;
+  __device__ __forceinline__ void set_stage(const float2* p, int j0) { gs = p; gs_j0 = j0; }
+  // Issue the copies of the tile's NT x 64 Gamma values (threads tid, tid + nthr, ... of the
+  // nthr drain threads, which all call it).  The row offset of each column (its class needs a
+  // table load) goes to shared memory first, after dst's NT x 64 values, so that no copy waits
+  // on a load.
+  __device__ __forceinline__ void prefetch(float2* dst, int mt, int nt, int NT, int tid,
+                                           int nthr) const {
+    constexpr int kN = kM / 2;
+    long long* rowoff = reinterpret_cast<long long*>(dst + (size_t)NT * kN);
+    const int n0 = mt * kN, j0 = nt * NT;
+    for (int cc = tid; cc < NT; cc += nthr) {
+      const int j = j0 + cc;
+      long long o = -1;
+      if (j < n_cols) {
+        int g, l;
+        if (cmap) {
+          const int2 cm = __ldg(cmap + j);
+          g = cm.x;
+          l = cm.y;
+        } else {
+          g = j / n_l;
+          l = j - g * n_l;
+        }
+        o = ((long long)__ldg(cls_of + (g / r) % N_tr) * N_ell + l_lo + l) * n_h;
+      }
+      rowoff[cc] = o;
+    }
+    drain_bar(nthr);
+    for (int e = tid; e < NT * kN; e += nthr) {
+      const long long o = rowoff[e / kN];
+      const int n = n0 + e % kN;
+      const bool ok = o >= 0 && n < n_h;
+      cp_async8(dst + e, ok ? g32 + o + n : g32, ok ? 8 : 0);
+    }
+  }
+  static constexpr uint32_t stage_bytes(int NT) {
+    return (uint32_t)(NT * (kM / 2) * sizeof(float2) + NT * sizeof(long long));
+  }
   __device__ __forceinline__ void flush(int g, int n, int t, float are, float aim) const {
     const float re = are + __shfl_xor_sync(0xffffffffu, are, 1);
     const float im = aim + __shfl_xor_sync(0xffffffffu, aim, 1);
@@ -245,7 +306,11 @@ struct EpiAdj {
     const int ncols = min(nc, n_cols - j0);
     if (ncols <= 0) return;
     if (cmap) {
-      ragged(n, t, live, nn, j0, acc, stride, ncols);
+      ragged(n, t, live, nn, j0, acc, stride, ncols, (m >> 1) & (kM / 2 - 1));
+      return;
+    }
+    if (gs) {
+      staged(n, t, live, j0, acc, stride, ncols, (m >> 1) & (kM / 2 - 1));
       return;
     }
     int l = j0 % n_l, g = j0 / n_l;
@@ -290,10 +355,33 @@ struct EpiAdj {
     }
     if (l != 0) flush(g, n, t, are, aim);
   }
+  // Every multipole, Gamma from the staged rows (nl = n - 64 mt)
+  __device__ __noinline__ void staged(int n, int t, bool live, int j0, const float* acc,
+                                      int stride, int ncols, int nl) const {
+    int l = j0 % n_l, g = j0 / n_l;
+    const float2* gcol = gs + (size_t)(j0 - gs_j0) * (kM / 2) + nl;
+    float are = 0.0f, aim = 0.0f;
+#pragma unroll 4
+    for (int cc = 0; cc < ncols; ++cc) {
+      const float2 G = gcol[(size_t)cc * (kM / 2)];
+      const float y = live ? acc[cc * stride] : 0.0f;
+      // t = 0 (Re row): (Gx, -Gy); t = 1 (Im row): (Gy, Gx)
+      are = fmaf(t ? G.y : G.x, y, are);
+      aim = fmaf(t ? G.x : -G.y, y, aim);
+      if (++l == n_l) {
+        flush(g, n, t, are, aim);
+        are = 0.0f;
+        aim = 0.0f;
+        l = 0;
+        ++g;
+      }
+    }
+    if (l != 0) flush(g, n, t, are, aim);
+  }
   // The same with the column map: a group (w, i, s) is a run of columns with equal map.x, which
   // is the same for every lane (the group changes and their shuffles stay warp-uniform).
   __device__ __noinline__ void ragged(int n, int t, bool live, int nn, int j0, const float* acc,
-                                      int stride, int ncols) const {
+                                      int stride, int ncols, int nl) const {
     int g = __ldg(&cmap[j0].x);
     float are = 0.0f, aim = 0.0f;
 #pragma unroll 1
@@ -307,7 +395,8 @@ struct EpiAdj {
         if (c0 + u < ncols) {
           const int2 cm = __ldg(cmap + j0 + c0 + u);
           gg[u] = cm.x;
-          G[u] = __ldg(g32 + ((size_t)__ldg(cls_of + (cm.x / r) % N_tr) * N_ell + l_lo + cm.y) * n_h + nn);
+          G[u] = gs ? gs[(size_t)(j0 + c0 + u - gs_j0) * (kM / 2) + nl]
+                    : __ldg(g32 + ((size_t)__ldg(cls_of + (cm.x / r) % N_tr) * N_ell + l_lo + cm.y) * n_h + nn);
         }
       }
 #pragma unroll
@@ -478,6 +567,14 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
 #pragma unroll
     for (int t = 0; t < CH * 16; ++t) acc[t] = 0.0f;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    // the epilogue's table rows: copies issued now, waited for after the main loop
+    float2* gstage = nullptr;
+    if constexpr (Epi::kGamma) {
+      if (sh.pre_off) {
+        gstage = reinterpret_cast<float2*>(base + sh.pre_off);
+        epi.prefetch(gstage, mt, nt, NT, tid - 64, 32 * DW);
+      }
+    }
     // the first two K-blocks find their accumulator buffers empty
     if (lane == 0) {
       mbar_arrive(smem_u32(&full[0]));
@@ -548,6 +645,12 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       // buffer b is free for K-block kb + 2: every lane of the warp has finished its loads
       if (lane == 0 && kb + 2 < n_kb) mbar_arrive(smem_u32(&full[(kb + 2) % S]));
     }
+    // every drain thread's staged copies have landed and are visible to the others (every drain
+    // warp reaches this barrier once, whether its loop completed or stopped early)
+    if (gstage) {
+      cp_async_commit_wait_all();
+      drain_bar(32 * DW);
+    }
     // every lane of a drain warp reaches the epilogue (its shuffles need the full warp)
     const bool all_ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
     if (all_ok) {
@@ -559,7 +662,9 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
 #pragma unroll
       for (int c = 0; c < CH * 16; ++c)
         if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
-      epi(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+      Epi e = epi;
+      e.set_stage(gstage, nt * NT);
+      e(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
     }
   }
   tc_fence_before();
@@ -1002,8 +1107,12 @@ constexpr int kDeep = 1024;
 // bit 12 (with bit 10) = the persistent two-K-block GEMM (k_gemm_persist), tiles up to 96 columns
 constexpr int kPersist = 4096;
 
+// extra: bytes of table rows the epilogue stages in shared memory during the main loop; they are
+// added only where they fit beside the stage count the tile has without them, and only in the
+// one-CTA-per-SM non-persistent form
 template <class P>
-int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem) {
+int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t& smem,
+              uint32_t extra = 0) {
   const int NT = code & 255;
   const bool pair = code & kPair;
   const int KS = (code & kDeep) ? 2 : 1;
@@ -1021,8 +1130,15 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
   while (cols < (uint32_t)(4 * stride)) cols <<= 1;
-  sh = GemmShape{n_mt, n_kb, NT, stages, cols};
+  sh = GemmShape{n_mt, n_kb, NT, stages, cols, 0};
   smem = L.total;
+  if (extra && !persist && !pair) {
+    const uint32_t pre_off = (L.bar_off + 8 * (3 * stages + 1) + 16 + 127) & ~127u;
+    if (pre_off + extra + 1024 <= cap) {
+      sh.pre_off = pre_off;
+      smem = pre_off + extra + 1024;
+    }
+  }
   return SWCL_OK;
 }
 
@@ -1370,7 +1486,9 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
     if (build && (st = build_d(c, cp, NT, n_nt, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
-    if ((st = shape_for<A3B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem))) return st;
+    if ((st = shape_for<A3B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem,
+                              EpiAdj::stage_bytes(code & 255))))
+      return st;
     EpiAdj epi{(cplx*)c->ws_cbar.p, (const float2*)c->bt_g32.p, (const int*)c->d_cls_of.p,
                cp.cmap_a, c->n_h, c->N_tr, c->N_ell, l_lo, n_l, r, sv.NI, n_cols};
     cudaError_t e = launch_gemm<A3B3>(c, code, (const uint8_t*)c->bt_eimg_a.p,

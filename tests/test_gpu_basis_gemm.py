@@ -47,7 +47,8 @@ def test_n5k_against_oracle_and_stencil_kernels(wl):
     code_f, code_a = ctx.query(S.SWCL_Q_TILE_FWD), ctx.query(S.SWCL_Q_TILE_ADJ)
     nt_f, nt_a = code_f & 255, code_a & 255
     assert nt_f in range(32, 129, 16) and nt_a in range(32, 129, 16)
-    assert code_f >> 8 in (0, 1, 4) and code_a >> 8 in (0, 1, 4)
+    # plain, two-CTA (bit 8), two-K-block (bit 10) or persistent two-K-block (bits 10 and 12)
+    assert code_f >> 8 in (0, 1, 4, 20) and code_a >> 8 in (0, 1, 4, 20)
     assert (not code_f & 256 or nt_f <= 64) and (not code_a & 256 or nt_a <= 64)
     f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, C_bar=w.C_bar)
     e = (norm_err(C, f["C"]), pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0], Abo), wbar_err(Wb[0], Wbo))
