@@ -232,21 +232,48 @@ constexpr int kClThreads = 128;
 
 __device__ __forceinline__ cplx tw_mod(const cplx* tw, long x, int N) { return tw[x & (N - 1)]; }
 
-// kCl-point DFTs of step 2 for this CTA's slice of k2: Xo[e kCl + k1] (e = k2 - rank kq)
-__device__ __forceinline__ void step2(cg::cluster_group& cl, cplx* Xo, cplx* Y, int L, int N,
-                                      const cplx* __restrict__ tw) {
+// 4-point DFT of (y0, y1, y2, y3) stored at o[off], o[off + 2], o[off + 4], o[off + 6]
+__device__ __forceinline__ void dft4_strided(cplx y0, cplx y1, cplx y2, cplx y3, cplx* o, int off) {
+  const cplx s02 = cadd(y0, y2), d02 = csub(y0, y2);
+  const cplx s13 = cadd(y1, y3), d13 = csub(y1, y3);
+  const cplx md13 = {d13.y, -d13.x};  // -i * d13
+  o[off] = cadd(s02, s13);
+  o[off + 2] = cadd(d02, md13);
+  o[off + 4] = csub(s02, s13);
+  o[off + 6] = csub(d02, md13);
+}
+
+// kCl-point DFTs of step 2 for this CTA's slice of k2: Xo[e kCl + k1] (e = k2 - rank kq),
+// X_{k1} = sum_{n1} w_8^{n1 k1} Y_{n1}[k2], as one radix-2 split into two 4-point DFTs (the
+// twiddles w_8^j are 1, (1 - i)/sqrt 2, -i, -(1 + i)/sqrt 2)
+__device__ __forceinline__ void step2(cg::cluster_group& cl, cplx* Xo, cplx* Y, int L) {
+  static_assert(kCl == 8, "step 2 is an 8-point DFT");
+  constexpr double h = 0.70710678118654752440;   // 1/sqrt 2
   const int kq = L / kCl;
   const int c = cl.block_rank();
-  for (int o = threadIdx.x; o < L; o += blockDim.x) {
-    const int e = o / kCl, k1 = o - e * kCl;
+  for (int e = threadIdx.x; e < kq; e += blockDim.x) {
     const int k2 = c * kq + e;
-    cplx s = {0.0, 0.0};
+    cplx x[kCl];
 #pragma unroll
-    for (int n1 = 0; n1 < kCl; ++n1) {
-      const cplx* Yr = cl.map_shared_rank(Y, n1);
-      s = cadd(s, cmul(Yr[k2], tw_mod(tw, (long)((n1 * k1) % kCl) * (N / kCl), N)));
-    }
-    Xo[o] = s;
+    for (int n1 = 0; n1 < kCl; ++n1) x[n1] = cl.map_shared_rank(Y, n1)[k2];
+    const cplx d1 = csub(x[1], x[5]), d2 = csub(x[2], x[6]), d3 = csub(x[3], x[7]);
+    const cplx b1 = {(d1.x + d1.y) * h, (d1.y - d1.x) * h};
+    const cplx b2 = {d2.y, -d2.x};
+    const cplx b3 = {(d3.y - d3.x) * h, -(d3.x + d3.y) * h};
+    cplx* o = Xo + e * kCl;
+    dft4_strided(cadd(x[0], x[4]), cadd(x[1], x[5]), cadd(x[2], x[6]), cadd(x[3], x[7]), o, 0);
+    dft4_strided(csub(x[0], x[4]), b1, b2, b3, o, 1);
+  }
+}
+
+// Twiddle tables of one cluster CTA in shared memory, loaded before the first transform:
+// tws[m] = tw[m N / L] (the L-point Stockham's own table: the same values it would read from
+// tw) and twc[k2] = w_M^{c k2}
+__device__ __forceinline__ void load_cluster_twiddles(cplx* tws, cplx* twc, const cplx* tw, int L,
+                                                      int N, int c) {
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    tws[m] = tw[(size_t)m * (N / L)];
+    twc[m] = tw_mod(tw, 2L * c * m, N);
   }
 }
 
@@ -263,6 +290,10 @@ k_fftlog_fwd_cl(CT* __restrict__ coef, const double* __restrict__ W,
   cplx* a = smem;
   cplx* b = smem + L;
   cplx* Xo = smem + 2 * L;
+  cplx* tws = smem + 3 * L;
+  cplx* twc = smem + 4 * L;
+  cplx* twn = smem + 5 * L;        // [L + 1]: tw[n] and psi_i[n] of this CTA's unpack outputs
+  cplx* psn = smem + 6 * L + 1;    // [L + 1]
   const long row = blockIdx.x / kCl;
   const int ka = (int)(row % N_I);
   const long wi = row / N_I;
@@ -278,12 +309,22 @@ k_fftlog_fwd_cl(CT* __restrict__ coef, const double* __restrict__ W,
     if (bb) { g0 *= bb[m]; g1 *= bb[m + 1]; }
     a[t] = {g0, g1};
   }
+  load_cluster_twiddles(tws, twc, tw, L, N, c);
+  for (int o = threadIdx.x; o <= L; o += blockDim.x) {
+    int n = M;                                                     // o = L: the Nyquist point
+    if (o < L) {
+      const int e = o / kCl, k1 = o - e * kCl;
+      n = c * kq + e + L * k1;
+    }
+    twn[o] = tw[n];
+    psn[o] = psi[(size_t)i * n_h + n];
+  }
   __syncthreads();
-  cplx* Y = stockham(a, b, L, 1, tw, N);
+  cplx* Y = stockham(a, b, L, 1, tws, L);
   for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x)
-    Y[k2] = cmul(Y[k2], tw_mod(tw, 2L * c * k2, N));            // w_M^{c k2}
+    Y[k2] = cmul(Y[k2], twc[k2]);                                  // w_M^{c k2}
   cl.sync();
-  step2(cl, Xo, Y, L, N, tw);
+  step2(cl, Xo, Y, L);
   cl.sync();
   // unpack X_n = E_n + e^{-2 pi i n/N} O_n with Z_{M-n} from the CTA that holds it
   for (int o = threadIdx.x; o <= L; o += blockDim.x) {
@@ -307,8 +348,8 @@ k_fftlog_fwd_cl(CT* __restrict__ coef, const double* __restrict__ W,
     const cplx e = {0.5 * (zn.x + zc.x), 0.5 * (zn.y + zc.y)};
     const cplx dl = {0.5 * (zn.x - zc.x), 0.5 * (zn.y - zc.y)};
     const cplx od = {dl.y, -dl.x};
-    const cplx x = cadd(e, cmul(tw[n], od));
-    store_coef(coef + row * n_h + n, cmul(psi[(size_t)i * n_h + n], x));
+    const cplx x = cadd(e, cmul(twn[o], od));
+    store_coef(coef + row * n_h + n, cmul(psn[o], x));
   }
   cl.sync();   // the other CTAs may still read this CTA's shared memory until here
 }
@@ -328,9 +369,22 @@ k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
   cplx* a = smem;
   cplx* b = smem + L;
   cplx* Xo = smem + 2 * L;
+  cplx* tws = smem + 3 * L;
+  cplx* twc = smem + 4 * L;
+  cplx* twn = smem + 5 * L;       // [L]: tw[n], psi_i[n] and psi_i[M - n] of n = c + kCl t
+  cplx* psn = smem + 6 * L;
+  cplx* psm = smem + 7 * L;
   const long wi = blockIdx.x / kCl;
   const int i = (int)(wi % N_tr);
   const cplx* ps = psi + (size_t)i * n_h;
+  load_cluster_twiddles(tws, twc, tw, L, N, c);
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    const int n = c + kCl * t;
+    twn[t] = tw[n];
+    psn[t] = ps[n];
+    psm[t] = ps[M - n];
+  }
+  __syncthreads();
   const double* cp = chipow + (size_t)i * N;
   constexpr int kOut = 2;                  // outputs per thread (L <= 2 kClThreads)
   double acc0[kOut], acc1[kOut];
@@ -340,24 +394,25 @@ k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
     const cplx* cb = cbar + ((size_t)wi * N_I + ka) * n_h;
     for (int t = threadIdx.x; t < L; t += blockDim.x) {
       const int n = c + kCl * t;               // < M
-      cplx y = cmulc(cb[n], ps[n]);
+      cplx y = cmulc(cb[n], psn[t]);
       cplx h = (n == 0) ? cplx{y.x, 0.0} : cplx{0.5 * y.x, 0.5 * y.y};
       const int m = M - n;
-      cplx ym = cmulc(cb[m], ps[m]);
+      cplx ym = cmulc(cb[m], psm[t]);
       cplx hm = (m == M) ? cplx{ym.x, 0.0} : cplx{0.5 * ym.x, 0.5 * ym.y};
       cplx hmc = cconj(hm);
       cplx e = cadd(h, hmc);
       cplx dd = csub(h, hmc);
-      cplx od = cmulc(dd, tw[n]);
+      cplx od = cmulc(dd, twn[t]);
       cplx z = {e.x - od.y, e.y + od.x};
       a[t] = cconj(z);
     }
     __syncthreads();
-    cplx* Y = stockham(a, b, L, 1, tw, N);
+    cplx* Y = stockham(a, b, L, 1, tws, L);
     for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x)
-      Y[k2] = cmul(Y[k2], tw_mod(tw, 2L * c * k2, N));
+      Y[k2] = cmul(Y[k2], twc[k2]);
     cl.sync();
-    step2(cl, Xo, Y, L, N, tw);
+    step2(cl, Xo, Y, L);
+    __syncthreads();   // step 2 writes each k2's eight outputs from one thread
     // x_{2j} + i x_{2j+1} = conj(Z_j), j = k2 + L k1 of this CTA's outputs
     const double* d = D + (size_t)ka * N;
     const double* bb = B ? B + ((size_t)i * N_I + ka) * N : nullptr;
@@ -405,7 +460,7 @@ static cudaError_t fftlog_fwd(CT* coef, const double* W, const double* chipow, c
                               int N_tr, int N_I, int N, cudaStream_t s) {
   long rows = (long)n_walk * N_tr * N_I;
   if (use_cluster(rows, N)) {
-    const size_t smem = (size_t)3 * (N / 2 / kCl) * sizeof(cplx);
+    const size_t smem = ((size_t)7 * (N / 2 / kCl) + 2) * sizeof(cplx);
     k_fftlog_fwd_cl<CT><<<(unsigned)(rows * kCl), kClThreads, smem, s>>>(coef, W, chipow, D, B, psi,
                                                                         twiddle, N_tr, N_I, N);
     return cudaGetLastError();
@@ -453,7 +508,7 @@ cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chi
   int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
   if (nchunk == 1 && use_cluster((long)n_walk * N_tr, N)) {
     // one chunk: the cluster kernel writes W_bar directly
-    const size_t csm = (size_t)3 * (N / 2 / kCl) * sizeof(cplx);
+    const size_t csm = (size_t)8 * (N / 2 / kCl) * sizeof(cplx);
     k_fftlog_adj_cl<<<(unsigned)((long)n_walk * N_tr * kCl), kClThreads, csm, s>>>(
         W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I, N, status);
     return cudaGetLastError();
