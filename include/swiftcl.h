@@ -185,6 +185,28 @@ int swcl_vjp(swcl_ctx* ctx, int precision, const double* C_bar,
 int swcl_compute_batched(swcl_ctx* ctx, int precision, double* C_out, const double* C_bar,
                          double* P_bar, double* amp_bar, double* W_bar);
 
+/* One step of a sampler that keeps its parameter points in host memory (Sec. 4.3: every step
+ * evaluates C_l and its gradient at new parameters).  The step's inputs go host -> device, the
+ * kernels of swcl_compute_batched run, and the results come back device -> host, all inside one
+ * CUDA-graph replay on the context stream; the call returns when the host outputs are written.
+ * Inputs (NULL keeps the values of the last set call or step):
+ *   W[n_walk][N_tr][N] window samples (as swcl_set_window_samples: D, B and the profile
+ *   factorisation stay), P[n_walk][N_k] and amp[n_walk][N_tr] (as swcl_set_power; both or
+ *   neither), C_bar (layout of C_out; NULL = forward only).
+ * Outputs: C_out (required), P_bar, amp_bar, W_bar (NULL to skip; they need C_bar), laid out as
+ * in swcl_compute_cl / swcl_vjp.
+ * Every non-NULL pointer must be page-locked host memory (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor): the copies are graph nodes that read and write it directly.  The
+ * library-owned device side of the outputs and cotangent is sized at the first call.  The first
+ * call of a configuration (pointers, precision, sizes) runs the step once outside the graph and
+ * captures it; later calls replay it.  Needs set_grids, set_tracers, set_windows and set_power
+ * first.  Errors: SWCL_ERR_INVALID_ARG (a pointer that is not page-locked host memory, P without
+ * amp, gradients without C_bar), SWCL_ERR_STATE, and SWCL_ERR_NONFINITE / SWCL_ERR_TIMEOUT from
+ * the device status word of this step (then cleared). */
+int swcl_step_host(swcl_ctx* ctx, int precision, const double* W, const double* P,
+                   const double* amp, const double* C_bar, double* C_out, double* P_bar,
+                   double* amp_bar, double* W_bar);
+
 /* Forward-mode derivative (JVP) of a1-a4 at one parameter point (Sec. 4.3: the Fisher forecasts
  * differentiate C_l along the parameters).  The context must hold one walker (n_walk = 1).  For
  * n_dir tangents (1..256) of the inputs

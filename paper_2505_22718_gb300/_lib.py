@@ -33,6 +33,7 @@ SIGNATURES = {
     "swcl_sync": (c_int, [c_void_p]),
     "swcl_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
     "swcl_compute_batched": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "swcl_step_host": (c_int, [c_void_p, c_int] + [c_void_p] * 8),
     "swcl_debug_read": (c_int, [c_void_p, c_int, c_void_p, ctypes.POINTER(c_int64)]),
     "swcl_fftlog_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -163,6 +163,18 @@ def swcl_compute_batched(ctx, precision, C_out, C_bar=None, P_bar=None, amp_bar=
     _check(ctx, _lib.load().swcl_compute_batched(ctx, precision, *ptrs))
 
 
+def swcl_step_host(ctx, precision, C_out, W=None, P=None, amp=None, C_bar=None, P_bar=None,
+                   amp_bar=None, W_bar=None):
+    """One sampler step with page-locked host arrays (pinned torch tensors): inputs in, forward
+    (+ VJP when C_bar is given), results out, in one CUDA-graph replay; returns when the host
+    outputs are written."""
+    ptrs = []
+    for a in (W, P, amp, C_bar, C_out, P_bar, amp_bar, W_bar):
+        p, _k = _ptr(a, np.float64)
+        ptrs.append(p)
+    _check(ctx, _lib.load().swcl_step_host(ctx, precision, *ptrs))
+
+
 def swcl_profile_enable(ctx, enable=True):
     _check(ctx, _lib.load().swcl_profile_enable(ctx, 1 if enable else 0))
 

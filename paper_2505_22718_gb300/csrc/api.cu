@@ -69,6 +69,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool is_pinned_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes) {
   int st = ensure(c, dst, bytes);
   if (st) return st;
@@ -349,7 +358,7 @@ int swcl_destroy(swcl_ctx* c) {
                     &c->bt_g32, &c->bt_kmu, &c->bt_himg, &c->bt_dimg, &c->ws_qpart, &c->bt_cmap_f,
                     &c->bt_cmap_a, &c->bt_lpos, &c->bt_wbase,
                     &c->ws_jin, &c->ws_dU, &c->ws_jout, &c->ws_fz, &c->ws_fsmall, &c->ws_lq,
-                    &c->ws_ltab};
+                    &c->ws_ltab, &c->hs_C, &c->hs_Cb, &c->hs_Pb, &c->hs_Ab, &c->hs_Wb};
   for (DevBuf* b : bufs) swcl::release(c, *b);
   for (auto& t : c->tc) {
     swcl::release(c, t.bfwd);
@@ -362,6 +371,8 @@ int swcl_destroy(swcl_ctx* c) {
   for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->hgraph_exec) cudaGraphExecDestroy(c->hgraph_exec);
+  if (c->hs_status) cudaFreeHost(c->hs_status);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -1099,6 +1110,75 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
   return SWCL_OK;
 }
 
+}  // extern "C"
+
+// The kernels of one batched step (forward, and the VJP when C_bar is given) on the context
+// stream, device pointers only; swcl_compute_batched and swcl_step_host capture it in graphs.
+static int batched_body(swcl_ctx* c, int precision, double* C_out, const double* C_bar,
+                        double* P_bar, double* amp_bar, double* W_bar) {
+  // the cotangent's unpacking depends on C_bar alone: on the auxiliary stream, beside the
+  // forward pass (not while profiling, which times kernels one by one)
+  const bool overlap = C_bar && !c->prof;
+  if (overlap) {
+    const size_t n = (size_t)c->n_walk * c->N_ell * c->N_tr * c->N_tr;
+    int st0 = swcl::ensure(c, c->ws_Cbar, sizeof(double) * n);
+    if (st0) return st0;
+    cudaError_t e = cudaEventRecord(c->ev_pre, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_pre, 0);
+    if (e == cudaSuccess)
+      e = swcl::launch_unpack_sym((double*)c->ws_Cbar.p, C_bar,
+                                  c->ragged ? (const int*)c->d_off.p : nullptr,
+                                  c->ragged ? (const int*)c->d_idx.p : nullptr, c->n_walk,
+                                  c->N_tr, c->N_ell, out_count(c), c->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_unpack, c->aux);
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "unpack cotangent");
+  }
+  c->overlap = overlap;
+  int st = swcl_compute_cl(c, precision, C_out);
+  const int64_t n_fwd = c->last_launches;
+  if (st == SWCL_OK && C_bar) {
+    st = swcl_vjp(c, precision, C_bar, P_bar, amp_bar, W_bar);
+    c->last_launches += n_fwd + (overlap ? 1 : 0);   // forward and unpack kernels too
+  }
+  c->overlap = false;
+  return st;
+}
+
+// Captures run() into a graph on the context stream (after one run outside it, which builds
+// tables and sizes every buffer); on failure the partial graph is dropped.
+template <class Run>
+static int capture_graph(swcl_ctx* c, Run run, cudaGraphExec_t* exec, int64_t* gen_out) {
+  SWCL_TRY(run());
+  *gen_out = c->alloc_gen;
+  cudaGraph_t graph = nullptr;
+  SWCL_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  c->capturing = true;
+  int st = run();
+  c->capturing = false;
+  if (st != SWCL_OK) {
+    // a failed capture: join the auxiliary stream so that the capture can end, then drop the
+    // partial graph and the capture error it leaves behind
+    cudaEventRecord(c->ev_join, c->aux);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  }
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st != SWCL_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st;
+  }
+  if (e != cudaSuccess) return swcl::cuda_fail(c, e, "end capture");
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return swcl::cuda_fail(c, e, "graph instantiate");
+  }
+  return SWCL_OK;
+}
+
+extern "C" {
+
 int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double* C_bar,
                          double* P_bar, double* amp_bar, double* W_bar) {
   if (!c) return SWCL_ERR_INVALID_ARG;
@@ -1110,34 +1190,7 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
     if (p && !swcl::is_device_ptr(p))
       return swcl::fail(c, SWCL_ERR_INVALID_ARG, "swcl_compute_batched takes device pointers only");
   if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
-  auto run = [&]() -> int {
-    // the cotangent's unpacking depends on C_bar alone: on the auxiliary stream, beside the
-    // forward pass (not while profiling, which times kernels one by one)
-    const bool overlap = C_bar && !c->prof;
-    if (overlap) {
-      const size_t n = (size_t)c->n_walk * c->N_ell * c->N_tr * c->N_tr;
-      int st0 = swcl::ensure(c, c->ws_Cbar, sizeof(double) * n);
-      if (st0) return st0;
-      cudaError_t e = cudaEventRecord(c->ev_pre, c->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_pre, 0);
-      if (e == cudaSuccess)
-        e = swcl::launch_unpack_sym((double*)c->ws_Cbar.p, C_bar,
-                                    c->ragged ? (const int*)c->d_off.p : nullptr,
-                                    c->ragged ? (const int*)c->d_idx.p : nullptr, c->n_walk,
-                                    c->N_tr, c->N_ell, out_count(c), c->aux);
-      if (e == cudaSuccess) e = cudaEventRecord(c->ev_unpack, c->aux);
-      if (e != cudaSuccess) return swcl::cuda_fail(c, e, "unpack cotangent");
-    }
-    c->overlap = overlap;
-    int st = swcl_compute_cl(c, precision, C_out);
-    const int64_t n_fwd = c->last_launches;
-    if (st == SWCL_OK && C_bar) {
-      st = swcl_vjp(c, precision, C_bar, P_bar, amp_bar, W_bar);
-      c->last_launches += n_fwd + (overlap ? 1 : 0);   // forward and unpack kernels too
-    }
-    c->overlap = false;
-    return st;
-  };
+  auto run = [&]() -> int { return batched_body(c, precision, C_out, C_bar, P_bar, amp_bar, W_bar); };
   bool same = c->graph_exec && c->graph_key.precision == precision &&
               c->graph_key.alloc_gen == c->alloc_gen;
   for (int t = 0; t < 5 && same; ++t) same = c->graph_key.ptrs[t] == ptrs[t];
@@ -1146,35 +1199,8 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
       cudaGraphExecDestroy(c->graph_exec);
       c->graph_exec = nullptr;
     }
-    // run once outside the graph: builds tables, sizes every buffer
-    SWCL_TRY(run());
-    const int64_t gen = c->alloc_gen;
-    cudaGraph_t graph = nullptr;
-    SWCL_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    c->capturing = true;
-    const int64_t launches_before = c->last_launches;
-    int st = run();
-    c->capturing = false;
-    if (st != SWCL_OK) {
-      // a failed capture: join the auxiliary stream so that the capture can end, then drop the
-      // partial graph and the capture error it leaves behind
-      cudaEventRecord(c->ev_join, c->aux);
-      cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    }
-    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-    if (st != SWCL_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return st;
-    }
-    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "end capture");
-    (void)launches_before;
-    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      c->graph_exec = nullptr;
-      return swcl::cuda_fail(c, e, "graph instantiate");
-    }
+    int64_t gen = 0;
+    SWCL_TRY(capture_graph(c, run, &c->graph_exec, &gen));
     c->graph_key.precision = precision;
     c->graph_key.alloc_gen = gen;
     for (int t = 0; t < 5; ++t) c->graph_key.ptrs[t] = ptrs[t];
@@ -1182,6 +1208,97 @@ int swcl_compute_batched(swcl_ctx* c, int precision, double* C_out, const double
   }
   SWCL_TRY_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
   c->last_launches = c->graph_launches;
+  return SWCL_OK;
+}
+
+int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P, const double* amp,
+                   const double* C_bar, double* C_out, double* P_bar, double* amp_bar,
+                   double* W_bar) {
+  if (!c) return SWCL_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->err.clear();
+  SWCL_TRY(check_ready(c, precision));
+  if (!C_out) return swcl::fail(c, SWCL_ERR_INVALID_ARG, "C_out is NULL");
+  if ((P == nullptr) != (amp == nullptr))
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "P and amp go together (both or neither)");
+  if (!C_bar && (P_bar || amp_bar || W_bar))
+    return swcl::fail(c, SWCL_ERR_INVALID_ARG, "gradients need C_bar");
+  const void* ptrs[8] = {W, P, amp, C_bar, C_out, P_bar, amp_bar, W_bar};
+  for (const void* p : ptrs)
+    if (p && !swcl::is_pinned_host_ptr(p))
+      return swcl::fail(c, SWCL_ERR_INVALID_ARG,
+                        "swcl_step_host takes page-locked host arrays only (cudaHostAlloc / cudaHostRegister)");
+  const size_t nC = (size_t)out_count(c) * c->N_tr * c->N_tr;
+  const size_t nW = (size_t)c->n_walk * c->N_tr * c->N, nP = (size_t)c->n_walk * c->N_k;
+  const size_t nA = (size_t)c->n_walk * c->N_tr;
+  SWCL_TRY(swcl::ensure(c, c->hs_C, sizeof(double) * nC));
+  if (C_bar) SWCL_TRY(swcl::ensure(c, c->hs_Cb, sizeof(double) * nC));
+  if (P_bar) SWCL_TRY(swcl::ensure(c, c->hs_Pb, sizeof(double) * nP));
+  if (amp_bar) SWCL_TRY(swcl::ensure(c, c->hs_Ab, sizeof(double) * nA));
+  if (W_bar) SWCL_TRY(swcl::ensure(c, c->hs_Wb, sizeof(double) * nW));
+  if (!c->hs_status) {
+    SWCL_TRY_CUDA(c, cudaHostAlloc((void**)&c->hs_status, sizeof(int), cudaHostAllocDefault),
+                  "cudaHostAlloc (status word)");
+  }
+  // the input buffers exist with these sizes since swcl_set_windows / swcl_set_power
+  if (c->d_W.bytes < sizeof(double) * nW || c->d_P.bytes < sizeof(double) * nP ||
+      c->d_amp.bytes < sizeof(double) * nA)
+    return swcl::fail(c, SWCL_ERR_STATE, "set_windows and set_power for this n_walk first");
+  double* dC = (double*)c->hs_C.p;
+  double* dCb = C_bar ? (double*)c->hs_Cb.p : nullptr;
+  double* dPb = P_bar ? (double*)c->hs_Pb.p : nullptr;
+  double* dAb = amp_bar ? (double*)c->hs_Ab.p : nullptr;
+  double* dWb = W_bar ? (double*)c->hs_Wb.p : nullptr;
+  auto run = [&]() -> int {
+    auto h2d = [&](void* dst, const void* src, size_t bytes) {
+      return src ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
+    };
+    auto d2h = [&](void* dst, const void* src, size_t bytes) {
+      return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream) : cudaSuccess;
+    };
+    cudaError_t e = h2d(c->d_W.p, W, sizeof(double) * nW);
+    if (e == cudaSuccess) e = h2d(c->d_P.p, P, sizeof(double) * nP);
+    if (e == cudaSuccess) e = h2d(c->d_amp.p, amp, sizeof(double) * nA);
+    if (e == cudaSuccess) e = h2d(dCb, C_bar, sizeof(double) * nC);
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step inputs host -> device");
+    int st = batched_body(c, precision, dC, dCb, dPb, dAb, dWb);
+    if (st) return st;
+    e = d2h(C_out, dC, sizeof(double) * nC);
+    if (e == cudaSuccess) e = d2h(P_bar, dPb, sizeof(double) * nP);
+    if (e == cudaSuccess) e = d2h(amp_bar, dAb, sizeof(double) * nA);
+    if (e == cudaSuccess) e = d2h(W_bar, dWb, sizeof(double) * nW);
+    if (e == cudaSuccess) e = d2h(c->hs_status, c->ws_status.p, sizeof(int));
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step results device -> host");
+    return SWCL_OK;
+  };
+  bool same = c->hgraph_exec && c->hgraph_key.precision == precision &&
+              c->hgraph_key.alloc_gen == c->alloc_gen;
+  for (int t = 0; t < 8 && same; ++t) same = c->hgraph_key.ptrs[t] == ptrs[t];
+  if (!same) {
+    if (c->hgraph_exec) {
+      cudaGraphExecDestroy(c->hgraph_exec);
+      c->hgraph_exec = nullptr;
+    }
+    int64_t gen = 0;
+    SWCL_TRY(capture_graph(c, run, &c->hgraph_exec, &gen));
+    c->hgraph_key.precision = precision;
+    c->hgraph_key.alloc_gen = gen;
+    for (int t = 0; t < 8; ++t) c->hgraph_key.ptrs[t] = ptrs[t];
+    c->hgraph_launches = c->last_launches;
+  }
+  SWCL_TRY_CUDA(c, cudaGraphLaunch(c->hgraph_exec, c->stream), "graph launch");
+  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  c->last_launches = c->hgraph_launches;
+  c->last_fwd_precision = precision;
+  const int h = *c->hs_status;
+  if (h) {
+    *c->hs_status = 0;
+    SWCL_TRY_CUDA(c, cudaMemset(c->ws_status.p, 0, sizeof(int)), "status clear");
+    if (h & swcl::kStatusTimeout)
+      return swcl::fail(c, SWCL_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on an mbarrier");
+    return swcl::fail(c, SWCL_ERR_NONFINITE,
+                      "an output (C, P_bar, amp_bar or W_bar) holds a NaN or Inf");
+  }
   return SWCL_OK;
 }
 

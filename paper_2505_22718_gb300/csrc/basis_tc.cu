@@ -106,6 +106,72 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
+// Cluster helpers (the two-SM tile and the split-K tile)
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cl_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test_wait_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+// every thread of both CTAs
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMEM of both CTAs, allocated and released by one warp in each of them together
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(dst_slot), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                              uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// arrive on the barrier at cluster address `bar` once every MMA issued so far has completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
 // A stage holds KS consecutive K-blocks (contiguous in both images): KS A-blocks of a1 bytes,
 // then KS B-blocks of b1 bytes.
 struct Layout {
@@ -427,14 +493,31 @@ struct EpiAdj {
 
 // CH: 16-column chunks per drain thread at most (3 for tiles up to 96 columns with 8 drain
 // warps, 4 otherwise); it sizes the accumulator registers.
-template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu>
+// MG: one accumulator slot per TMEM buffer instead of two.  Each stage issues its correction
+// products first and the leading products last, so the slot holds the small corrections when
+// the leading terms arrive: the leading sum is rounded as often as in its own slot, and the
+// correction bits below the FP32 resolution of the sum are the ones that would be lost in the
+// drain's addition anyway.  Half the TMEM per tile allows tiles up to 240 columns.
+//
+// SK = 2: split K in two.  A cluster of two CTAs computes one tile, each over its half of the
+// stages (the first CTA the first half); each drains its partial sums into registers as usual and
+// stages them in its shared memory; the first CTA then adds the second's through distributed
+// shared memory (two FP32 terms: the same sum in any order) and runs the epilogue.  Launched with
+// a cluster dimension of 2 (cudaLaunchKernelEx), grid = 2 x tiles.
+template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu, bool MG = false, int SK = 1>
 __global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // n_kb counts the stages' worth of K (KS K-blocks each, the last one possibly short)
-  const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
+  // n_kb counts the stages' worth of K (KS K-blocks each, the last one possibly short); with a
+  // split, this CTA's stages are kb_lo .. kb_lo + n_kb - 1 of the n_all stages of the tile
+  const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_all = (n_kb1 + KS - 1) / KS;
+  const int rank = SK == 2 ? (int)cluster_ctarank() : 0;
+  const int half_kb = (n_all + 1) / 2;
+  const int kb_lo = SK == 2 ? rank * half_kb : 0;
+  const int n_kb = SK == 2 ? (rank == 0 ? half_kb : n_all - half_kb) : n_all;
+  const int tile = SK == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const Layout L = layout<P>(NT, S, KS);
   // Barriers per stage: ready[s] completes when the stage's copies have landed (transaction
   // count only); full[s] when the copy warp has seen ready[s] AND the drain warps have emptied
@@ -454,8 +537,8 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x % sh.n_mt;
-  const int nt = blockIdx.x / sh.n_mt;
+  const int mt = tile % sh.n_mt;
+  const int nt = tile / sh.n_mt;
   const int stride = (NT + 31) & ~31;   // TMEM columns per accumulator slot
 
   if (tid == 0) {
@@ -474,6 +557,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  bool drain_ok = false;   // the split-K reduction: this drain warp's partial sums are valid
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- copies ----
@@ -481,8 +565,8 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       // K-blocks (ready -> full) in order.  Both conditions are polled without suspending
       // (test_wait): a thread suspended on "stage free" would hold back the forward of a landed
       // K-block until the tensor core had finished the previous one, a bubble per K-block.
-      const uint8_t* asrc = aimg + (size_t)mt * n_kb1 * L.a1;
-      const uint8_t* bsrc = bimg + (size_t)nt * n_kb1 * L.b1;
+      const uint8_t* asrc = aimg + ((size_t)mt * n_kb1 + (size_t)kb_lo * KS) * L.a1;
+      const uint8_t* bsrc = bimg + ((size_t)nt * n_kb1 + (size_t)kb_lo * KS) * L.b1;
       int next = 0, fwd = 0;
       long idle = 0;
       while (fwd < n_kb) {
@@ -491,7 +575,7 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
           const int s = next % S, r = next / S;
           if (r == 0 || mbar_test_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
             uint8_t* st = base + s * L.stage;
-            const int nk = min(KS, n_kb1 - next * KS);      // K-blocks in this stage
+            const int nk = min(KS, n_kb1 - (kb_lo + next) * KS);      // K-blocks in this stage
             mbar_arrive_tx(smem_u32(&ready[s]), nk * (L.a1 + L.b1));
             bulk_g2s(smem_u32(st), asrc + (size_t)next * KS * L.a1, nk * L.a1, smem_u32(&ready[s]));
             bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)next * KS * L.b1, nk * L.b1,
@@ -526,24 +610,45 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
         if (!mbar_wait(smem_u32(&full[s]), r & 1, abort_flag)) break;
         tc_fence_after();
         const uint32_t a0 = smem_u32(base + s * L.stage);
-        const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
-        const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
-        const int nk = min(KS, n_kb1 - kb * KS);
+        const int nk = min(KS, n_kb1 - (kb_lo + kb) * KS);
+        if constexpr (MG) {
+          const uint32_t d = tmem + (uint32_t)(b * stride);
+          // corrections first (the first of them overwrites the slot), the leading products last
 #pragma unroll
-        for (int h = 0; h < KS; ++h) {
-          if (h >= nk) break;
-          const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
+          for (int t = 1; t <= P::kProducts; ++t) {
+            const int tt = t % P::kProducts;
 #pragma unroll
-          for (int j = 0; j < kK / 16; ++j) {
+            for (int h = 0; h < KS; ++h) {
+              if (h >= nk) break;
+              const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
 #pragma unroll
-            for (int t = 0; t < P::kProducts; ++t) {
-              if (!((PM >> t) & 1u)) continue;
-              // descriptor start addresses advance in 16-byte units
-              const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
-              const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
-              const bool lead = (t == 0);
-              const bool first = (h == 0) && (j == 0) && (lead || t == first_correction(PM));
-              mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+              for (int j = 0; j < kK / 16; ++j) {
+                const uint64_t ad = da + (uint64_t)((P::pa(tt) * kPlaneM + j * 256) >> 4);
+                const uint64_t bd = db + (uint64_t)((P::pb(tt) * b_plane + j * 256) >> 4);
+                const bool first = (t == 1) && (h == 0) && (j == 0);
+                mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
+              }
+            }
+          }
+        } else {
+          const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
+          const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+#pragma unroll
+          for (int h = 0; h < KS; ++h) {
+            if (h >= nk) break;
+            const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
+#pragma unroll
+            for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+              for (int t = 0; t < P::kProducts; ++t) {
+                if (!((PM >> t) & 1u)) continue;
+                // descriptor start addresses advance in 16-byte units
+                const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+                const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+                const bool lead = (t == 0);
+                const bool first = (h == 0) && (j == 0) && (lead || t == first_correction(PM));
+                mma_bf16(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+              }
             }
           }
         }
@@ -587,9 +692,28 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
       const bool got = mbar_wait(smem_u32(&mmadone[kb % S]), (kb / S) & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
       tc_fence_after();
-      const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
+      const uint32_t slot_m = lane_base + (MG ? b : 2 * b) * stride + c_begin * 16;
       const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
-      if constexpr (CH <= 3) {
+      if constexpr (MG) {
+        // one slot: up to four chunks in flight per wait (two with eight chunks per thread)
+        constexpr int kF = CH > 4 ? 2 : 4;
+#pragma unroll
+        for (int g = 0; g < CH; g += kF) {
+          uint32_t m[kF][16];
+#pragma unroll
+          for (int u = 0; u < kF; ++u)
+            if (g + u < my) tmem_ld16_async(slot_m + (g + u) * 16, m[u]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < kF; ++u) {
+            if (g + u < my) {
+              reg_fence(m[u]);
+#pragma unroll
+              for (int t = 0; t < 16; ++t) acc[(g + u) * 16 + t] += __uint_as_float(m[u][t]);
+            }
+          }
+        }
+      } else if constexpr (CH <= 3) {
         // up to three chunks: every load of the K-block in flight behind one wait
         uint32_t m0[16], r0[16], m1[16], r1[16], m2[16], r2[16];
         tmem_ld16_async(slot_m, m0);
@@ -662,10 +786,47 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
 #pragma unroll
       for (int c = 0; c < CH * 16; ++c)
         if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
-      Epi e = epi;
-      e.set_stage(gstage, nt * NT);
-      e(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+      if constexpr (SK == 1) {
+        Epi e = epi;
+        e.set_stage(gstage, nt * NT);
+        e(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+      }
     }
+    if constexpr (SK == 2) drain_ok = all_ok;
+  }
+  if constexpr (SK == 2) {
+    // both CTAs' partial sums are staged (every thread of the cluster takes part)
+    cluster_sync_all();
+    if (rank == 0 && warp >= 2) {
+      const uint32_t peer_abort = cluster_addr(smem_u32((const void*)abort_flag), 1);
+      int pa;
+      asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(pa) : "r"(peer_abort) : "memory");
+      const bool go = __all_sync(0xffffffffu, drain_ok && pa == 0);
+      if (go) {
+        const int quarter = warp & 3, half = (warp - 2) >> 2, row = quarter * 32 + lane;
+        const int nch = NT / 16, nch0 = (nch + 1) / 2;
+        const int c_begin = half ? nch0 : 0, my = half ? nch - nch0 : nch0;
+        const int dt = tid - 64;
+        float* ep = reinterpret_cast<float*>(base);
+        const uint32_t rep = cluster_addr(smem_u32(ep), 1);
+        for (int c0 = 0; c0 < my * 16; c0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            asm volatile("ld.shared::cluster.f32 %0, [%1];"
+                         : "=f"(v[u]) : "r"(rep + 4u * (uint32_t)((c0 + u) * (32 * DW) + dt)) : "memory");
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ep[(c0 + u) * (32 * DW) + dt] += v[u];
+        }
+        Epi e = epi;
+        e.set_stage(nullptr, nt * NT);
+        e(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+      } else if (lane == 0) {
+        *abort_flag = 1;
+      }
+    }
+    // the second CTA's shared memory is read until here
+    cluster_sync_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -881,6 +1042,258 @@ k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bim
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, sh.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------- two-SM tile (cta_group::2) ----
+
+// A cluster of two CTAs on two SMs computes one 256 x NT tile with tcgen05.mma.cta_group::2:
+// each MMA instruction, issued by one thread of the first CTA, multiplies 256 rows of A (128 in
+// each CTA's shared memory) by NT columns of B (NT / 2 in each CTA's shared memory) into both
+// CTAs' TMEM (each holds its own 128 rows x NT columns).  Against the one-SM tile of the same
+// width this halves the MMA instructions and the B bytes each SM copies per K-block, so a stage
+// is smaller and three of them fit.
+//
+// Handshakes: each CTA copies its own halves and relays "landed" to the first CTA's full[s]
+// (a remote arrive); the drain warps of both CTAs relay "buffer drained" there too, so full[s]
+// takes 2 (1 + DW) arrivals.  The MMA thread commits each stage to mmadone[s] in both CTAs (one
+// commit per barrier; a commit tracks every MMA the thread issued before it).  Waits on barriers
+// that the other CTA or the tensor core signals use acquire at cluster scope.
+
+
+// Grid: 2 CTAs per (row-tile pair, column tile); sh.n_mt is the number of 128-row tiles (the A
+// image holds an even count, the last one zero when n_mt is odd), sh.NT the tile's columns; the
+// B image is laid out in half tiles of NT / 2 columns ([2 nt + rank][kb][planes][NT / 2 x 64 B]).
+template <class P, class Epi, int CH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(threads_for(8), 1)
+k_gemm_2sm(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
+           Epi epi, int* __restrict__ status) {
+  constexpr int DW = 8, KS = 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int NT = sh.NT, H = NT / 2, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
+  const Layout L = layout<P>(H, S, KS);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
+  uint64_t* full = bars;              // used in CTA 0 only
+  uint64_t* mmadone = bars + S;
+  uint64_t* ready = bars + 2 * S;
+  uint64_t* done = bars + 3 * S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int n_mt2 = (sh.n_mt + 1) / 2;
+  const int pair = blockIdx.x >> 1;
+  const int mt = 2 * (pair % n_mt2) + (int)rank;   // this CTA's 128-row tile of A
+  const int nt = pair / n_mt2;                      // the pair's column tile
+  const int stride = (NT + 31) & ~31;
+  const uint32_t full0 = cluster_addr(smem_u32(&full[0]), 0);   // CTA 0's full[0]
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 2 * (1 + DW));
+      mbar_init(smem_u32(&mmadone[s]), 1);
+      mbar_init(smem_u32(&ready[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc_pair(smem_u32(tmem_slot), sh.tmem_cols);
+  tc_fence_before();
+  cluster_sync_all();   // barriers of both CTAs initialised, TMEM of both allocated
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (rank == 1 && tid == 0) {
+    // the MMA thread addresses both CTAs' accumulators through CTA 0's TMEM address
+    uint32_t lead;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(lead) : "r"(cluster_addr(smem_u32(tmem_slot), 0)) : "memory");
+    if (lead != tmem) *abort_flag = 1;
+  }
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- copies ----
+      const uint8_t* asrc = aimg + (size_t)mt * n_kb1 * L.a1;
+      const uint8_t* bsrc = bimg + (size_t)(2 * nt + (int)rank) * n_kb1 * L.b1;
+      int next = 0, fwd = 0;
+      long idle = 0;
+      while (fwd < n_kb) {
+        bool progress = false;
+        if (next < n_kb) {
+          const int s = next % S, r = next / S;
+          if (r == 0 || mbar_test_wait_cl(smem_u32(&mmadone[s]), (r - 1) & 1)) {
+            uint8_t* st = base + s * L.stage;
+            const int nk = min(KS, n_kb1 - next * KS);
+            mbar_arrive_tx(smem_u32(&ready[s]), nk * (L.a1 + L.b1));
+            bulk_g2s(smem_u32(st), asrc + (size_t)next * KS * L.a1, nk * L.a1, smem_u32(&ready[s]));
+            bulk_g2s(smem_u32(st + L.a_bytes), bsrc + (size_t)next * KS * L.b1, nk * L.b1,
+                     smem_u32(&ready[s]));
+            ++next;
+            progress = true;
+          }
+        }
+        if (fwd < next && mbar_test_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
+          mbar_arrive_remote(full0 + 8u * (uint32_t)(fwd % S));
+          ++fwd;
+          progress = true;
+        }
+        if (progress) {
+          idle = 0;
+        } else if (++idle > (kSpinLimit << 6) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      for (int kb = fwd; kb < next; ++kb) mbar_wait_drain(smem_u32(&ready[kb % S]), (kb / S) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ------------------------------------------------------------- MMA ----
+      const uint32_t idesc = idesc_bf16(2 * kM, NT);
+      const uint32_t b_plane = H * kRow;
+      const uint32_t peer_done0 = cluster_addr(smem_u32(&mmadone[0]), 1);
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int s = kb % S, r = kb / S, b = kb & 1;
+        if (!mbar_wait_cl(smem_u32(&full[s]), r & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(base + s * L.stage);
+        const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
+        const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+        const int nk = min(KS, n_kb1 - kb * KS);
+#pragma unroll
+        for (int h = 0; h < KS; ++h) {
+          if (h >= nk) break;
+          const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
+#pragma unroll
+          for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+            for (int t = 0; t < P::kProducts; ++t) {
+              const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+              const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+              const bool lead = (t == 0);
+              const bool first = (h == 0) && (j == 0) && (t <= 1);
+              mma_bf16_pair(lead ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit_pair(smem_u32(&mmadone[s]));
+        mma_commit_pair(peer_done0 + 8u * (uint32_t)s);
+      }
+      mma_commit_pair(smem_u32(done));
+      mbar_wait_drain(smem_u32(done), 0);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ drain ----
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+    const int nch = NT / 16;
+    const int nch0 = (nch + 1) / 2;
+    const int c_begin = half ? nch0 : 0;
+    const int my = half ? nch - nch0 : nch0;
+    float acc[CH * 16];
+#pragma unroll
+    for (int t = 0; t < CH * 16; ++t) acc[t] = 0.0f;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    float2* gstage = nullptr;
+    if constexpr (Epi::kGamma) {
+      if (sh.pre_off) {
+        gstage = reinterpret_cast<float2*>(base + sh.pre_off);
+        epi.prefetch(gstage, mt, nt, NT, tid - 64, 32 * DW);
+      }
+    }
+    if (lane == 0) {
+      mbar_arrive_remote(full0);
+      if (n_kb > 1) mbar_arrive_remote(full0 + 8u * (uint32_t)(1 % S));
+    }
+    bool ok = true;
+    for (int kb = 0; kb < n_kb && ok; ++kb) {
+      const int b = kb & 1;
+      const bool got = mbar_wait_cl(smem_u32(&mmadone[kb % S]), (kb / S) & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
+      const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
+      if constexpr (CH <= 3) {
+        uint32_t m0[16], r0[16], m1[16], r1[16], m2[16], r2[16];
+        tmem_ld16_async(slot_m, m0);
+        tmem_ld16_async(slot_c, r0);
+        if (my > 1) {
+          tmem_ld16_async(slot_m + 16, m1);
+          tmem_ld16_async(slot_c + 16, r1);
+        }
+        if (my > 2) {
+          tmem_ld16_async(slot_m + 32, m2);
+          tmem_ld16_async(slot_c + 32, r2);
+        }
+        tmem_wait_ld();
+        reg_fence(m0);
+        reg_fence(r0);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+        if (my > 1) {
+          reg_fence(m1);
+          reg_fence(r1);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+        }
+        if (my > 2) {
+          reg_fence(m2);
+          reg_fence(r2);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) acc[32 + t] += __uint_as_float(m2[t]) + __uint_as_float(r2[t]);
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < CH; g += 2) {
+          uint32_t m0[16], r0[16], m1[16], r1[16];
+          tmem_ld16_async(slot_m + g * 16, m0);
+          tmem_ld16_async(slot_c + g * 16, r0);
+          tmem_ld16_async(slot_m + (g + 1) * 16, m1);
+          tmem_ld16_async(slot_c + (g + 1) * 16, r1);
+          tmem_wait_ld();
+          reg_fence(m0);
+          reg_fence(r0);
+          reg_fence(m1);
+          reg_fence(r1);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            acc[g * 16 + t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+            acc[(g + 1) * 16 + t] += __uint_as_float(m1[t]) + __uint_as_float(r1[t]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0 && kb + 2 < n_kb) mbar_arrive_remote(full0 + 8u * (uint32_t)((kb + 2) % S));
+    }
+    if (gstage) {
+      cp_async_commit_wait_all();
+      drain_bar(32 * DW);
+    }
+    const bool all_ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+    if (all_ok) {
+      const int dt = tid - 64;
+      float* ep = reinterpret_cast<float*>(base);
+#pragma unroll
+      for (int c = 0; c < CH * 16; ++c)
+        if (c < my * 16) ep[c * (32 * DW) + dt] = acc[c];
+      Epi e = epi;
+      e.set_stage(gstage, nt * NT);
+      e(mt * kM + row, nt * NT + c_begin * 16, ep + dt, 32 * DW, my * 16);
+    }
+  }
+  tc_fence_before();
+  // both CTAs are past their last TMEM access and CTA 0's MMAs have completed
+  cluster_sync_all();
+  if (tid == 0 && *abort_flag) atomicExch(status, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, sh.tmem_cols);
   }
 }
 
@@ -1106,6 +1519,22 @@ constexpr int kPair = 256;
 constexpr int kDeep = 1024;
 // bit 12 (with bit 10) = the persistent two-K-block GEMM (k_gemm_persist), tiles up to 96 columns
 constexpr int kPersist = 4096;
+// bit 13 (with bit 10) = the two-SM tile (k_gemm_2sm): 256 rows x NT columns per CTA pair,
+// NT in {64, 96, 128}; bit 11 with it = stage the adjoint epilogue's table rows in shared memory
+// even where that leaves room for two pipeline stages only
+constexpr int kTwoSM = 8192;
+constexpr int kTableFirst = 2048;
+// bit 14 = one accumulator slot per TMEM buffer (k_gemm_basis<..., MG = true>): column tiles up to
+// kMaxNTWide; tiles wider than 128 take one K-block per stage except 160 with bit 10
+constexpr int kMerged = 16384;
+constexpr int kMaxNTWide = 240;
+// bit 15 (with bit 14, one K-block per stage, 160 columns or more) = K split over a cluster of
+// two CTAs (k_gemm_basis<..., SK = 2>): twice the CTAs of the wide tiles for few walkers
+constexpr int kSplitK = 32768;
+
+// columns per tile of the B operand image: a two-SM tile's image holds half tiles
+inline int img_cols(int code) { return (code & kTwoSM) ? (code & 255) / 2 : (code & 255); }
+inline int img_tiles(int code, int n_nt) { return (code & kTwoSM) ? 2 * n_nt : n_nt; }
 
 // extra: bytes of table rows the epilogue stages in shared memory during the main loop; they are
 // added only where they fit beside the stage count the tile has without them, and only in the
@@ -1119,36 +1548,57 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   const uint32_t cap = pair ? 113 * 1024 : 227 * 1024;
   int stages = kMaxStages;
   const bool persist = code & kPersist;
+  const bool two_sm = code & kTwoSM;
   if (persist && (!(code & kDeep) || NT > 96))
     return fail(c, SWCL_ERR_INVALID_ARG, "persistent GEMM tiles: two K-blocks per stage, <= 96 columns");
+  if (two_sm && (!(code & kDeep) || persist || pair || NT % 32 || NT < 64 || NT > 128))
+    return fail(c, SWCL_ERR_INVALID_ARG, "two-SM GEMM tiles: two K-blocks per stage, 64, 96 or 128 columns");
+  if ((code & kTableFirst) && !two_sm)
+    return fail(c, SWCL_ERR_INVALID_ARG, "GEMM tile code: bit 11 needs the two-SM tile");
+  const bool merged = code & kMerged;
+  if (merged && (persist || pair || two_sm || NT % 16 || NT < 64 || NT > kMaxNTWide ||
+                 (NT > 160 && KS == 2)))
+    return fail(c, SWCL_ERR_INVALID_ARG, "one-slot GEMM tiles: 64..240 columns (<= 160 with two K-blocks)");
+  if (!merged && NT > kMaxNT)
+    return fail(c, SWCL_ERR_INVALID_ARG, "GEMM tiles wider than 128 columns need bit 14");
+  const bool splitk = code & kSplitK;
+  if (splitk && (!merged || KS != 1 || NT < 160 || n_kb < 2))
+    return fail(c, SWCL_ERR_INVALID_ARG, "split-K GEMM tiles: bit 14, one K-block per stage, >= 160 columns");
   auto lay = [&](int st) {
-    return persist ? layout_persist<P>(NT, st, 3) : layout<P>(NT, st, KS);
+    return persist ? layout_persist<P>(NT, st, 3) : layout<P>(two_sm ? NT / 2 : NT, st, KS);
+  };
+  // the table rows the epilogue stages sit after the barriers
+  auto with_extra = [&](const Layout& L) {
+    return ((L.bar_off + 8 * (3 * L.stages + 1) + 16 + 127) & ~127u) + extra + 1024;
   };
   Layout L = lay(stages);
   while (stages > 2 && L.total > cap) L = lay(--stages);
+  if (extra && (code & kTableFirst))
+    while (stages > 2 && with_extra(L) > cap) L = lay(--stages);
   if (L.total > cap) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit shared memory");
   const int stride = (NT + 31) & ~31;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(4 * stride)) cols <<= 1;
+  while (cols < (uint32_t)((merged ? 2 : 4) * stride)) cols <<= 1;
+  if (cols > 512) return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile does not fit TMEM");
+  // the epilogue stages the accumulators of the 256 drain threads in the stage ring
+  if (!persist && !pair && L.stages * L.stage < (uint32_t)(16 * ((NT / 16 + 1) / 2) * 256 * 4))
+    return fail(c, SWCL_ERR_UNSUPPORTED, "basis GEMM tile: stage ring smaller than the epilogue");
   sh = GemmShape{n_mt, n_kb, NT, stages, cols, 0};
   smem = L.total;
-  if (extra && !persist && !pair) {
-    const uint32_t pre_off = (L.bar_off + 8 * (3 * stages + 1) + 16 + 127) & ~127u;
-    if (pre_off + extra + 1024 <= cap) {
-      sh.pre_off = pre_off;
-      smem = pre_off + extra + 1024;
-    }
+  if (extra && !persist && !pair && !splitk && with_extra(L) <= cap) {
+    sh.pre_off = (L.bar_off + 8 * (3 * stages + 1) + 16 + 127) & ~127u;
+    smem = with_extra(L);
   }
   return SWCL_OK;
 }
 
-template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu>
+template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu, bool MG = false>
 cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
                            uint32_t smem, int n_nt, const Epi& epi) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS, PM>,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS, PM, MG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi, DW, CH, KS, PM><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
+  k_gemm_basis<P, Epi, DW, CH, KS, PM, MG><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
       a, b, sh, epi, (int*)c->ws_status.p);
   return cudaGetLastError();
 }
@@ -1180,6 +1630,42 @@ cudaError_t launch_persist(swcl_ctx* c, const uint8_t* a, const uint8_t* b, cons
   return cudaGetLastError();
 }
 
+// one K-block per stage, one accumulator slot, 8 chunks per drain thread, K split over a
+// cluster of two CTAs
+template <class P, class Epi>
+cudaError_t launch_splitk(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                          uint32_t smem, int n_nt, const Epi& epi) {
+  auto kern = k_gemm_basis<P, Epi, 8, 8, 1, 0x3Fu, true, 2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * sh.n_mt * n_nt));
+  cfg.blockDim = dim3(threads_for(8));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a, b, sh, epi, (int*)c->ws_status.p);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+template <class P, class Epi, int CH>
+cudaError_t launch_2sm(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                       uint32_t smem, int n_nt, const Epi& epi) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_2sm<P, Epi, CH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int n_mt2 = (sh.n_mt + 1) / 2;
+  k_gemm_2sm<P, Epi, CH><<<(unsigned)(2 * n_mt2 * n_nt), threads_for(8), smem, c->stream>>>(
+      a, b, sh, epi, (int*)c->ws_status.p);
+  return cudaGetLastError();
+}
+
 template <class P, class Epi>
 cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* b,
                         const GemmShape& sh, uint32_t smem, int n_nt, const Epi& epi) {
@@ -1187,6 +1673,17 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
   if (c->bt_pmask != 0x3Fu) {
     if (code != (96 | kDeep)) return cudaErrorInvalidValue;   // study subsets: tile 1120 only
     return launch_subset<P, Epi>(c, c->bt_pmask, a, b, sh, smem, n_nt, epi);
+  }
+  if (code & kTwoSM)
+    return (nch + 1) / 2 <= 3 ? launch_2sm<P, Epi, 3>(c, a, b, sh, smem, n_nt, epi)
+                              : launch_2sm<P, Epi, 4>(c, a, b, sh, smem, n_nt, epi);
+  if (code & kSplitK) return launch_splitk<P, Epi>(c, a, b, sh, smem, n_nt, epi);
+  if (code & kMerged) {
+    const int ch = (nch + 1) / 2;
+    if (!(code & kDeep)) return launch_variant<P, Epi, 8, 8, 1, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi);
+    return ch <= 3 ? launch_variant<P, Epi, 8, 3, 2, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi)
+         : ch <= 4 ? launch_variant<P, Epi, 8, 4, 2, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi)
+                   : launch_variant<P, Epi, 8, 8, 2, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi);
   }
   if (code & kPersist) return launch_persist<P, Epi>(c, a, b, sh, smem, n_nt, epi);
   if (code & kPair)   // four drain warps: every chunk of a row in one thread
@@ -1204,6 +1701,27 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
 // holds whole groups of r basis columns.
 std::vector<int> tile_candidates(int r, bool need_groups, bool tuned_only = false) {
   std::vector<int> v;
+  // one-slot tiles: two K-blocks per stage up to 160 columns, one beyond.  Tuned in the adjoint
+  // only: in the forward their C error (4.4e-5 of the oracle at N5K shape, against 3.1e-5 with
+  // two slots) took a mixed-precision JVP over its gate
+  for (int nt = 64; nt <= kMaxNTWide && !(tuned_only && need_groups); nt += 16) {
+    const int half0 = 16 * ((nt / 16 + 1) / 2);
+    if (need_groups && (nt % r != 0 || half0 % r != 0)) continue;
+    if (nt <= 160 && nt % 32 == 0) v.push_back(nt | kDeep | kMerged);
+    if (nt >= 160 && (nt % 32 == 0 || nt == 208 || nt == 240)) {
+      v.push_back(nt | kMerged);
+      if (need_groups) v.push_back(nt | kMerged | kSplitK);   // forward
+    }
+  }
+  // two-SM tiles, in the adjoint also with the table rows staged at two stages: selectable, not
+  // tuned (measured no faster than the one-SM tiles of the same width)
+  for (int nt = 64; nt <= kMaxNT && !tuned_only; nt += 32) {
+    const int half0 = 16 * ((nt / 16 + 1) / 2);
+    if (!need_groups || (nt % r == 0 && half0 % r == 0)) {
+      v.push_back(nt | kDeep | kTwoSM);
+      if (!need_groups) v.push_back(nt | kDeep | kTwoSM | kTableFirst);
+    }
+  }
   if (!tuned_only) {
     for (int nt = 32; nt <= kMaxNT; nt += 16) {
       const int half0 = 16 * ((nt / 16 + 1) / 2);
@@ -1231,12 +1749,13 @@ bool valid_tile(int code, const std::vector<int>& cands) {
 }  // namespace
 
 size_t basis_fixed_bytes(const swcl_ctx* c) {
-  const size_t f_mt = (c->N_k + kM - 1) / kM, f_kb = (2 * c->n_h + kK - 1) / kK;
-  const size_t a_mt = (2 * c->n_h + kM - 1) / kM, a_kb = (c->N_k + kK - 1) / kK;
+  // row tiles rounded up to an even count, as in basis_prepare
+  const size_t f_mt = (((c->N_k + kM - 1) / kM) + 1) & ~1, f_kb = (2 * c->n_h + kK - 1) / kK;
+  const size_t a_mt = (((2 * c->n_h + kM - 1) / kM) + 1) & ~1, a_kb = (c->N_k + kK - 1) / kK;
   const size_t ng = (size_t)c->n_cls * c->N_ell * c->n_h;
   return (f_mt * f_kb + a_mt * a_kb) * kPlanes * kPlaneM + ng * (sizeof(float4) + sizeof(float2)) +
          sizeof(float) * (size_t)c->N_tr * 4 * c->N_k +
-         (size_t)kMaxNT * (f_kb + a_kb) * kPlanes * kRow;   // column padding of the last tile
+         (size_t)kMaxNTWide * (f_kb + a_kb) * kPlanes * kRow;   // column padding of the last tile
 }
 
 size_t basis_bytes_per_ell(const swcl_ctx* c) {
@@ -1255,20 +1774,23 @@ int basis_prepare(swcl_ctx* c) {
   c->bt_f_kb = (2 * n_h + kK - 1) / kK;
   c->bt_a_mt = (2 * n_h + kM - 1) / kM;
   c->bt_a_kb = (N_k + kK - 1) / kK;
-  const size_t ef = (size_t)c->bt_f_mt * c->bt_f_kb * kPlanes * kPlaneM;
-  const size_t ea = (size_t)c->bt_a_mt * c->bt_a_kb * kPlanes * kPlaneM;
+  // the images hold an even number of row tiles (the last one zero when the count is odd), so
+  // that the two-SM tiles take rows in pairs of tiles
+  const int f_mt2 = (c->bt_f_mt + 1) & ~1, a_mt2 = (c->bt_a_mt + 1) & ~1;
+  const size_t ef = (size_t)f_mt2 * c->bt_f_kb * kPlanes * kPlaneM;
+  const size_t ea = (size_t)a_mt2 * c->bt_a_kb * kPlanes * kPlaneM;
   if ((st = ensure(c, c->bt_eimg_f, ef))) return st;
   if ((st = ensure(c, c->bt_eimg_a, ea))) return st;
   const long ng = (long)c->n_cls * c->N_ell * n_h;
   if ((st = ensure(c, c->bt_gdf, sizeof(float4) * ng))) return st;
   if ((st = ensure(c, c->bt_g32, sizeof(float2) * ng))) return st;
   if ((st = ensure(c, c->bt_kmu, sizeof(float) * (size_t)c->N_tr * 4 * N_k))) return st;
-  long tot = (long)c->bt_f_mt * c->bt_f_kb * kM * 4;
+  long tot = (long)f_mt2 * c->bt_f_kb * kM * 4;
   k_eimg_fwd<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_eimg_f.p, (const cplx*)c->d_phase.p,
-                                                   N_k, n_h, c->bt_f_mt, c->bt_f_kb);
-  tot = (long)c->bt_a_mt * c->bt_a_kb * kM * 4;
+                                                   N_k, n_h, f_mt2, c->bt_f_kb);
+  tot = (long)a_mt2 * c->bt_a_kb * kM * 4;
   k_eimg_adj<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_eimg_a.p, (const cplx*)c->d_phase.p,
-                                                   N_k, n_h, c->bt_a_mt, c->bt_a_kb);
+                                                   N_k, n_h, a_mt2, c->bt_a_kb);
   k_gtab_split<<<grid_for(ng), 256, 0, c->stream>>>((float4*)c->bt_gdf.p, (float2*)c->bt_g32.p,
                                                     (const cplx*)c->d_gtab.p, ng);
   k_kmu<<<grid_for((long)c->N_tr * 4 * N_k), 256, 0, c->stream>>>(
@@ -1442,7 +1964,7 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
   auto run = [&](int code, bool build) -> int {
     const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
-    if (build && (st = build_h(c, cp, NT, n_nt, l_lo, n_l))) return st;
+    if (build && (st = build_h(c, cp, img_cols(code), img_tiles(code, n_nt), l_lo, n_l))) return st;
     GemmShape sh;
     uint32_t smem;
     if ((st = shape_for<A3B3>(c, code, c->bt_f_mt, c->bt_f_kb, sh, smem))) return st;
@@ -1460,7 +1982,9 @@ int basis_forward(swcl_ctx* c, int l_lo, int n_l) {
   }
   const int code = c->bt_nt_fwd, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
-  if ((st = counted(c, "basis operand fwd", [&] { return build_h(c, cp, NT, n_nt, l_lo, n_l); })))
+  if ((st = counted(c, "basis operand fwd", [&] {
+         return build_h(c, cp, img_cols(code), img_tiles(code, n_nt), l_lo, n_l);
+       })))
     return st;
   return counted(c, "basis gemm fwd", [&] { return run(code, false); });
 }
@@ -1483,7 +2007,7 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
   auto run = [&](int code, bool build) -> int {
     const int NT = code & 255;
     const int n_nt = (n_cols + NT - 1) / NT;
-    if (build && (st = build_d(c, cp, NT, n_nt, n_l))) return st;
+    if (build && (st = build_d(c, cp, img_cols(code), img_tiles(code, n_nt), n_l))) return st;
     GemmShape sh;
     uint32_t smem;
     if ((st = shape_for<A3B3>(c, code, c->bt_a_mt, c->bt_a_kb, sh, smem,
@@ -1512,7 +2036,9 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
   }
   const int code = c->bt_nt_adj, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
-  if ((st = counted(c, "basis operand adj", [&] { return build_d(c, cp, NT, n_nt, n_l); })))
+  if ((st = counted(c, "basis operand adj", [&] {
+         return build_d(c, cp, img_cols(code), img_tiles(code, n_nt), n_l);
+       })))
     return st;
   return counted(c, "basis gemm adj", [&] { return run(code, false); });
 }

@@ -217,6 +217,18 @@ struct swcl_ctx {
   bool capturing = false;
   int64_t graph_launches = 0; // kernels in the captured graph
 
+  // CUDA graph of swcl_step_host: host -> device copies of the step's inputs, the batched
+  // kernels, device -> host copies of the results and of the status word
+  cudaGraphExec_t hgraph_exec = nullptr;
+  struct HostKey {
+    int precision = -1;
+    const void* ptrs[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t alloc_gen = -1;
+  } hgraph_key;
+  int64_t hgraph_launches = 0;
+  swcl::DevBuf hs_C, hs_Cb, hs_Pb, hs_Ab, hs_Wb;   // device side of the step's arrays
+  int* hs_status = nullptr;                        // page-locked copy of the status word
+
   // per-kernel timing (swcl_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -235,6 +247,7 @@ int cuda_fail(swcl_ctx* c, cudaError_t e, const char* what);
 int ensure(swcl_ctx* c, DevBuf& b, size_t bytes);
 void release(swcl_ctx* c, DevBuf& b);
 bool is_device_ptr(const void* p);
+bool is_pinned_host_ptr(const void* p);   // page-locked host memory known to CUDA
 int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes);
 int copy_in_queued(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes, bool* host_src);
 int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes);

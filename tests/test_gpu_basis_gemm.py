@@ -46,10 +46,14 @@ def test_n5k_against_oracle_and_stencil_kernels(wl):
     assert ctx.query(S.SWCL_Q_PROFILE_RANK) == 1
     code_f, code_a = ctx.query(S.SWCL_Q_TILE_FWD), ctx.query(S.SWCL_Q_TILE_ADJ)
     nt_f, nt_a = code_f & 255, code_a & 255
-    assert nt_f in range(32, 129, 16) and nt_a in range(32, 129, 16)
-    # plain, two-CTA (bit 8), two-K-block (bit 10) or persistent two-K-block (bits 10 and 12)
-    assert code_f >> 8 in (0, 1, 4, 20) and code_a >> 8 in (0, 1, 4, 20)
+    assert nt_f in range(32, 241, 16) and nt_a in range(32, 241, 16)
+    # plain, two-CTA (bit 8), two-K-block (bit 10), persistent two-K-block (bits 10 and 12),
+    # two-SM tile (bits 10 and 13, with bit 11 in the adjoint: table rows staged first), one
+    # accumulator slot per buffer (bit 14, with or without bit 10; in the forward also with bit 15,
+    # K split over two CTAs)
+    assert code_f >> 8 in (0, 1, 4, 20, 36, 64, 68, 192) and code_a >> 8 in (0, 1, 4, 20, 36, 44, 64, 68)
     assert (not code_f & 256 or nt_f <= 64) and (not code_a & 256 or nt_a <= 64)
+    assert (nt_f <= 128 or code_f & 16384) and (nt_a <= 128 or code_a & 16384)
     f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, C_bar=w.C_bar)
     e = (norm_err(C, f["C"]), pbar_err(Pb[0], Pbo, ex["P_abs"]), grad_err(Ab[0], Abo), wbar_err(Wb[0], Wbo))
     print("basis GEMM n5k: C %.2e  Pbar %.2e  Abar %.2e  Wbar %.2e  tile codes %d/%d" % (e + (code_f, code_a)))
@@ -127,17 +131,25 @@ def test_rank_two_profiles():
 
 
 @pytest.mark.parametrize("code", [96, 128, 48, 64 | 256, 32 | 256, 64 | 1024, 96 | 1024, 128 | 1024,
-                                  64 | 1024 | 4096, 96 | 1024 | 4096])
+                                  64 | 1024 | 4096, 96 | 1024 | 4096, 64 | 1024 | 8192,
+                                  96 | 1024 | 8192, 128 | 1024 | 8192, 96 | 1024 | 8192 | 2048,
+                                  96 | 1024 | 16384, 128 | 1024 | 16384, 160 | 1024 | 16384,
+                                  192 | 16384, 208 | 16384, 240 | 16384, 160 | 16384 | 32768,
+                                  192 | 16384 | 32768, 240 | 16384 | 32768])
 def test_every_tile_variant_against_oracle(code):
     """Each GEMM variant, fixed through SWCL_BASIS_TILES: one CTA per SM (48, 96, 128 columns),
     two CTAs per SM (| 256), two K-blocks per pipeline stage (| 1024), the persistent two-K-block
-    form (| 1024 | 4096); three walkers, a ragged k
+    form (| 1024 | 4096), the two-SM tile (| 1024 | 8192; | 2048: the adjoint's table rows staged
+    at two stages), one accumulator slot per buffer (| 16384: up to 240 columns; | 32768: K split
+    over a cluster of two CTAs, forward only, with the 208-column one-slot adjoint); three walkers,
+    a ragged k
     tail (333 points), 17 K-blocks in the forward GEMM (an odd count: the last stage is short),
     against the oracle."""
     import paper_2505_22718_gb300 as S
     w, tapers = make_ragged_case(n_walk=3, seed=51)
     old = os.environ.get("SWCL_BASIS_TILES")
-    os.environ["SWCL_BASIS_TILES"] = "%d,%d" % (code, code)
+    code_a = 208 | 16384 if code & 32768 else code
+    os.environ["SWCL_BASIS_TILES"] = "%d,%d" % (code, code_a)
     try:
         ctx = _context(w, tapers)
     finally:
@@ -154,7 +166,7 @@ def test_every_tile_variant_against_oracle(code):
         # a forward tile must hold whole groups of r basis columns
         assert "not a forward tile" in str(e)
         pytest.skip("tile %d does not hold whole basis groups at this rank" % code)
-    assert ctx.query(S.SWCL_Q_TILE_FWD) == code and ctx.query(S.SWCL_Q_TILE_ADJ) == code
+    assert ctx.query(S.SWCL_Q_TILE_FWD) == code and ctx.query(S.SWCL_Q_TILE_ADJ) == code_a
     C = C.reshape(3, len(w.ells), w.n_tr, w.n_tr)
     Cb = Cb.reshape(3, len(w.ells), w.n_tr, w.n_tr)
     for wk in range(3):
