@@ -954,6 +954,9 @@ int swcl_compute_cl(swcl_ctx* c, int precision, double* C_out) {
                                          c->ragged ? (const int*)c->d_idx.p : nullptr, nw, N_tr,
                                          N_ell, n_out, pack_stream, (int*)c->ws_status.p),
               "scale/pack");
+  if (c->early_C && dev_out)
+    SWCL_TRY_CUDA(c, cudaMemcpyAsync(c->early_C, dst, cbytes, cudaMemcpyDeviceToHost, pack_stream),
+                  "C device -> host");
   c->last_fwd_precision = precision;
   c->u_valid = true;
   if (!dev_out) {
@@ -1097,6 +1100,14 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
     c->last_launches += W_bar ? 3 : 2;  // W_bar reduction, P_bar gather and reduction
   }
   if (W_bar) SWCL_TRY(swcl::copy_out(c, W_bar, Wb, wbytes));
+  // swcl_step_host: P_bar and amp_bar are final here on the side stream; their copies to the host
+  // run beside the rest of the reverse mode
+  if (c->early_Pb)
+    SWCL_TRY_CUDA(c, cudaMemcpyAsync(c->early_Pb, Pb, sizeof(double) * nw * (size_t)N_k,
+                                     cudaMemcpyDeviceToHost, side), "P_bar device -> host");
+  if (c->early_Ab)
+    SWCL_TRY_CUDA(c, cudaMemcpyAsync(c->early_Ab, Ab, sizeof(double) * nrow, cudaMemcpyDeviceToHost,
+                                     side), "amp_bar device -> host");
   if (fork) {
     // join: the main stream (and the caller's later work on it) sees the auxiliary kernels
     SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_join, c->aux), "join");
@@ -1256,17 +1267,29 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
     auto d2h = [&](void* dst, const void* src, size_t bytes) {
       return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream) : cudaSuccess;
     };
-    cudaError_t e = h2d(c->d_W.p, W, sizeof(double) * nW);
+    // the cotangent is first read by its unpacking on the auxiliary stream (batched_body), so
+    // its copy goes there and runs beside the window copy and the forward pass
+    const bool aside = C_bar && !c->prof;
+    cudaError_t e = cudaSuccess;
+    if (aside) {
+      e = cudaEventRecord(c->ev_fork, c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dCb, C_bar, sizeof(double) * nC, cudaMemcpyHostToDevice, c->aux);
+    }
+    if (e == cudaSuccess) e = h2d(c->d_W.p, W, sizeof(double) * nW);
     if (e == cudaSuccess) e = h2d(c->d_P.p, P, sizeof(double) * nP);
     if (e == cudaSuccess) e = h2d(c->d_amp.p, amp, sizeof(double) * nA);
-    if (e == cudaSuccess) e = h2d(dCb, C_bar, sizeof(double) * nC);
+    if (e == cudaSuccess && !aside) e = h2d(dCb, C_bar, sizeof(double) * nC);
     if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step inputs host -> device");
+    // C, P_bar and amp_bar are copied out by the kernels' own streams as soon as they are final
+    c->early_C = C_out;
+    c->early_Pb = P_bar;
+    c->early_Ab = amp_bar;
     int st = batched_body(c, precision, dC, dCb, dPb, dAb, dWb);
+    c->early_C = c->early_Pb = c->early_Ab = nullptr;
     if (st) return st;
-    e = d2h(C_out, dC, sizeof(double) * nC);
-    if (e == cudaSuccess) e = d2h(P_bar, dPb, sizeof(double) * nP);
-    if (e == cudaSuccess) e = d2h(amp_bar, dAb, sizeof(double) * nA);
-    if (e == cudaSuccess) e = d2h(W_bar, dWb, sizeof(double) * nW);
+    e = d2h(W_bar, dWb, sizeof(double) * nW);
     if (e == cudaSuccess) e = d2h(c->hs_status, c->ws_status.p, sizeof(int));
     if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step results device -> host");
     return SWCL_OK;

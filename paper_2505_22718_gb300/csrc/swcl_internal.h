@@ -228,6 +228,11 @@ struct swcl_ctx {
   int64_t hgraph_launches = 0;
   swcl::DevBuf hs_C, hs_Cb, hs_Pb, hs_Ab, hs_Wb;   // device side of the step's arrays
   int* hs_status = nullptr;                        // page-locked copy of the status word
+  // host destinations that swcl_step_host sets for the duration of one capture: C, P_bar and
+  // amp_bar go device -> host on the stream that produced them, as soon as they are final
+  double* early_C = nullptr;
+  double* early_Pb = nullptr;
+  double* early_Ab = nullptr;
 
   // per-kernel timing (swcl_profile_*)
   bool prof = false;

@@ -86,8 +86,8 @@ def test_named_kernel_roofline(n5k):
 
 
 def test_stored_traffic_applies_only_to_its_workload_source_and_tiles():
-    t = bench.TRAFFIC[("basis gemm adj", 1120)]
-    tiles = {"fwd": 1120, "adj": 1120}
+    t = bench.TRAFFIC[("basis gemm adj", 16608)]
+    tiles = {"fwd": 1120, "adj": 16608}
     got = bench.traffic_for("basis gemm adj", 1, "n5k", tiles)
     assert got in (t["bytes"], None)     # None once the kernel source has changed
     assert bench.traffic_for("basis gemm adj", 1, "n5k") is None                       # tiles unknown
