@@ -1556,9 +1556,11 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   if ((code & kTableFirst) && !two_sm)
     return fail(c, SWCL_ERR_INVALID_ARG, "GEMM tile code: bit 11 needs the two-SM tile");
   const bool merged = code & kMerged;
-  if (merged && (persist || pair || two_sm || NT % 16 || NT < 64 || NT > kMaxNTWide ||
-                 (NT > 160 && KS == 2)))
-    return fail(c, SWCL_ERR_INVALID_ARG, "one-slot GEMM tiles: 64..240 columns (<= 160 with two K-blocks)");
+  if (merged && (persist || two_sm || NT % 16 || NT < 64 || NT > kMaxNTWide ||
+                 (NT > 160 && KS == 2) || (pair && (KS != 1 || NT % 32 || NT > 128))))
+    return fail(c, SWCL_ERR_INVALID_ARG,
+                "one-slot GEMM tiles: 64..240 columns (<= 160 with two K-blocks; 64, 96 or 128 "
+                "with one K-block at two CTAs per SM)");
   if (!merged && NT > kMaxNT)
     return fail(c, SWCL_ERR_INVALID_ARG, "GEMM tiles wider than 128 columns need bit 14");
   const bool splitk = code & kSplitK;
@@ -1678,6 +1680,10 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
     return (nch + 1) / 2 <= 3 ? launch_2sm<P, Epi, 3>(c, a, b, sh, smem, n_nt, epi)
                               : launch_2sm<P, Epi, 4>(c, a, b, sh, smem, n_nt, epi);
   if (code & kSplitK) return launch_splitk<P, Epi>(c, a, b, sh, smem, n_nt, epi);
+  if ((code & kMerged) && (code & kPair))   // two CTAs per SM, four drain warps: whole rows
+    return nch <= 4 ? launch_variant<P, Epi, 4, 4, 1, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi)
+         : nch <= 6 ? launch_variant<P, Epi, 4, 6, 1, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi)
+                    : launch_variant<P, Epi, 4, 8, 1, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi);
   if (code & kMerged) {
     const int ch = (nch + 1) / 2;
     if (!(code & kDeep)) return launch_variant<P, Epi, 8, 8, 1, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi);
@@ -1712,6 +1718,7 @@ std::vector<int> tile_candidates(int r, bool need_groups, bool tuned_only = fals
       v.push_back(nt | kMerged);
       if (need_groups) v.push_back(nt | kMerged | kSplitK);   // forward
     }
+    if (nt <= 128 && nt % 32 == 0) v.push_back(nt | kMerged | kPair);   // two CTAs per SM
   }
   // two-SM tiles, in the adjoint also with the table rows staged at two stages: selectable, not
   // tuned (measured no faster than the one-SM tiles of the same width)
