@@ -1417,96 +1417,100 @@ __global__ void k_kmu(float* __restrict__ kmu, const double* __restrict__ kpow,
 
 // Forward B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
 // (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
+// Grid (n_kb, n_nt), NT * 4 threads: thread (row, ch) writes 16 bytes of each plane (four n).
 __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
                        const float4* __restrict__ gdf, const int* __restrict__ cls_of,
                        const int2* __restrict__ cmap, int N_tr, int N_ell, int n_h, int l_lo,
-                       int n_l, int r, int NI, int n_cols, int NT, int n_nt, int n_kb) {
-  const long total = (long)n_nt * n_kb * NT * 4;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    long t = e;
-    const int ch = (int)(t % 4); t /= 4;
-    const int row = (int)(t % NT); t /= NT;
-    const int kb = (int)(t % n_kb); t /= n_kb;
-    const int nt = (int)t;
-    const int j = nt * NT + row;
-    __nv_bfloat16 v[8][kPlanes];
-    const bool live = j < n_cols;
-    int s = 0, l = 0, wi = 0, i = 0;
-    if (live) {
-      s = j % r;
-      const int g = j / r;
-      if (cmap) {
-        const int2 cm = cmap[g];
-        wi = cm.x;
-        l = cm.y;
-      } else {
-        l = g % n_l;
-        wi = g / n_l;
-      }
-      i = wi % N_tr;
+                       int n_l, int r, int NI, int n_cols, int NT, int n_kb) {
+  const int kb = blockIdx.x, nt = blockIdx.y;
+  const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;
+  const int j = nt * NT + row;
+  __nv_bfloat16 v[8][kPlanes];
+  const bool live = j < n_cols;
+  int s = 0, l = 0, wi = 0, i = 0;
+  if (live) {
+    s = j % r;
+    const int g = j / r;
+    if (cmap) {
+      const int2 cm = cmap[g];
+      wi = cm.x;
+      l = cm.y;
+    } else {
+      l = g % n_l;
+      wi = g / n_l;
     }
-    const float4* Fr = F + ((size_t)wi * NI + s) * n_h;
-    const float4* Gr = gdf + ((size_t)(live ? cls_of[i] : 0) * N_ell + l_lo + l) * n_h;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int n = (kb * kK + ch * 8) / 2 + u;
-      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-      if (live && n < n_h) {
-        const float4 f = Fr[n], g = Gr[n];
-        // Re = fr gr - fi gi, Im = fr gi + fi gr
-        df_dot2(f.x, f.z, g.x, g.z, f.y, f.w, g.y, g.w, -1.0f, rh, rl);
-        df_dot2(f.x, f.z, g.y, g.w, f.y, f.w, g.x, g.z, 1.0f, ih, il);
-      }
-      split_df(rh, rl, v[2 * u]);
-      split_df(-ih, -il, v[2 * u + 1]);
-    }
-    store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
-                          off64(row, ch * 16), v);
+    i = wi % N_tr;
   }
+  const float4* Fr = F + ((size_t)wi * NI + s) * n_h;
+  const float4* Gr = gdf + ((size_t)(live ? cls_of[i] : 0) * N_ell + l_lo + l) * n_h;
+  const int n0 = (kb * kK + ch * 8) / 2;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int n = n0 + u;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (live && n < n_h) {
+      const float4 f = Fr[n], g = Gr[n];
+      // Re = fr gr - fi gi, Im = fr gi + fi gr
+      df_dot2(f.x, f.z, g.x, g.z, f.y, f.w, g.y, g.w, -1.0f, rh, rl);
+      df_dot2(f.x, f.z, g.y, g.w, f.y, f.w, g.x, g.z, 1.0f, ih, il);
+    }
+    split_df(rh, rl, v[2 * u]);
+    split_df(-ih, -il, v[2 * u + 1]);
+  }
+  store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
+                        off64(row, ch * 16), v);
 }
 
 // Adjoint B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, s, l) (l fastest),
-// (j, q) = kmu[i][s][q] Dbar[w][l][i][q]
+// (j, q) = kmu[i][s][q] Dbar[w][l][i][q].  Grid (n_kb, n_nt), NT * 4 threads: thread (row, ch)
+// writes eight q; vec4: N_k % 4 == 0, so that the rows of Dbar and kmu hold 16-byte aligned
+// groups of four.
 __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
                        const float* __restrict__ kmu, const int2* __restrict__ cmap, int N_tr,
-                       int N_k, int n_l, int r, int n_cols, int NT, int n_nt, int n_kb) {
-  const long total = (long)n_nt * n_kb * NT * 4;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    long t = e;
-    const int ch = (int)(t % 4); t /= 4;
-    const int row = (int)(t % NT); t /= NT;
-    const int kb = (int)(t % n_kb); t /= n_kb;
-    const int nt = (int)t;
-    const int j = nt * NT + row;
-    const bool live = j < n_cols;
-    int l = 0, s = 0, i = 0, w = 0;
-    if (live) {
-      int g;
-      if (cmap) {
-        const int2 cm = cmap[j];
-        g = cm.x;
-        l = cm.y;
-      } else {
-        l = j % n_l;
-        g = j / n_l;
-      }
-      s = g % r;
-      const int wi = g / r;
-      i = wi % N_tr;
-      w = wi / N_tr;
+                       int N_k, int n_l, int r, int n_cols, int NT, int n_kb, int vec4) {
+  const int kb = blockIdx.x, nt = blockIdx.y;
+  const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;
+  const int j = nt * NT + row;
+  const bool live = j < n_cols;
+  int l = 0, s = 0, i = 0, w = 0;
+  if (live) {
+    int g;
+    if (cmap) {
+      const int2 cm = cmap[j];
+      g = cm.x;
+      l = cm.y;
+    } else {
+      l = j % n_l;
+      g = j / n_l;
     }
-    const float* drow = dbar + (((size_t)w * n_l + l) * N_tr + i) * N_k;
-    const float* krow = kmu + ((size_t)i * 4 + s) * N_k;
-    __nv_bfloat16 v[8][3];
+    s = g % r;
+    const int wi = g / r;
+    i = wi % N_tr;
+    w = wi / N_tr;
+  }
+  const float* drow = dbar + (((size_t)w * n_l + l) * N_tr + i) * N_k;
+  const float* krow = kmu + ((size_t)i * 4 + s) * N_k;
+  const int q0 = kb * kK + ch * 8;
+  float x[8];
+  if (vec4 && live && q0 + 8 <= N_k) {
+    const float4 d0 = *reinterpret_cast<const float4*>(drow + q0);
+    const float4 d1 = *reinterpret_cast<const float4*>(drow + q0 + 4);
+    const float4 k0 = *reinterpret_cast<const float4*>(krow + q0);
+    const float4 k1 = *reinterpret_cast<const float4*>(krow + q0 + 4);
+    x[0] = k0.x * d0.x; x[1] = k0.y * d0.y; x[2] = k0.z * d0.z; x[3] = k0.w * d0.w;
+    x[4] = k1.x * d1.x; x[5] = k1.y * d1.y; x[6] = k1.z * d1.z; x[7] = k1.w * d1.w;
+  } else {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int q = kb * kK + ch * 8 + u;
-      const float x = (live && q < N_k) ? krow[q] * drow[q] : 0.0f;
-      split_f32(x, v[u]);
+      const int q = q0 + u;
+      x[u] = (live && q < N_k) ? krow[q] * drow[q] : 0.0f;
     }
-    store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
-                          off64(row, ch * 16), v);
   }
+  __nv_bfloat16 v[8][3];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) split_f32(x[u], v[u]);
+  store_planes<kPlanes>(img + ((size_t)nt * n_kb + kb) * kPlanes * NT * kRow, NT * kRow,
+                        off64(row, ch * 16), v);
 }
 
 unsigned grid_for(long total) {
@@ -1898,11 +1902,10 @@ int build_h(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int l_lo, int n_l)
   const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * kPlanes * NT * kRow);
   if (st) return st;
-  const long tot = (long)n_nt * c->bt_f_kb * NT * 4;
-  k_himg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p,
-                                               (const float4*)c->bt_gdf.p, (const int*)c->d_cls_of.p,
-                                               cp.cmap_f, c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r,
-                                               sv.NI, n_cols, NT, n_nt, c->bt_f_kb);
+  k_himg<<<dim3((unsigned)c->bt_f_kb, (unsigned)n_nt), NT * 4, 0, c->stream>>>(
+      (uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p, (const float4*)c->bt_gdf.p,
+      (const int*)c->d_cls_of.p, cp.cmap_f, c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r, sv.NI, n_cols,
+      NT, c->bt_f_kb);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward operand");
 }
@@ -1912,10 +1915,9 @@ int build_d(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int n_l) {
   const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow);
   if (st) return st;
-  const long tot = (long)n_nt * c->bt_a_kb * NT * 4;
-  k_dimg<<<grid_for(tot), 256, 0, c->stream>>>((uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p,
-                                               (const float*)c->bt_kmu.p, cp.cmap_a, c->N_tr, c->N_k,
-                                               n_l, r, n_cols, NT, n_nt, c->bt_a_kb);
+  k_dimg<<<dim3((unsigned)c->bt_a_kb, (unsigned)n_nt), NT * 4, 0, c->stream>>>(
+      (uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p, (const float*)c->bt_kmu.p, cp.cmap_a,
+      c->N_tr, c->N_k, n_l, r, n_cols, NT, c->bt_a_kb, c->N_k % 4 == 0 ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint operand");
 }
