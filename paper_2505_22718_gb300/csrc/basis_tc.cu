@@ -1045,6 +1045,227 @@ k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bim
   }
 }
 
+// Persistent form with epilogue warps (tile-code bits 10 + 12 + 16, k_gemm_persist_ep).  As
+// k_gemm_persist, one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  with
+// the barriers, TMEM and stage ring live across tiles, but the epilogue has four warps of its
+// own: at the end of a tile the drain warps write their sums into a row-major hand-off region
+// (pitch NT + 1 words: conflict-free in both directions) and go on draining the next tile, while
+// the epilogue warps (one row and all NT columns per thread) run the epilogue from there.  The
+// epilogue of tile t thus runs beside the main loop of tile t + 1.  Barriers of the hand-off:
+// epi_full (one arrival per drain warp) and epi_free (one per epilogue warp).  The epilogue's
+// table rows come from L2 (no staging).
+constexpr int kEpiWarps = 4;   // one per TMEM lane quarter, all of a row's columns
+__host__ __device__ constexpr int threads_persist_ep() { return 64 + 32 * 8 + 32 * kEpiWarps; }
+
+template <class P>
+__host__ __device__ inline Layout layout_persist_ep(int NT, int stages) {
+  Layout L = layout<P>(NT, stages, 2);
+  const uint32_t hb_bytes = (uint32_t)kM * (NT + 1) * sizeof(float);
+  L.bar_off = (stages * L.stage + hb_bytes + 7) & ~7u;
+  L.total = L.bar_off + 8 * (3 * stages + 3) + 16 + 1024;
+  return L;
+}
+
+template <class P, class Epi, int CH>
+__global__ void __launch_bounds__(threads_persist_ep(), 1)
+k_gemm_persist_ep(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
+                  int n_tiles, Epi epi, int* __restrict__ status) {
+  constexpr int DW = 8, KS = 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
+  const Layout L = layout_persist_ep<P>(NT, S);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar_off);
+  uint64_t* full = bars;
+  uint64_t* mmadone = bars + S;
+  uint64_t* ready = bars + 2 * S;
+  uint64_t* done = bars + 3 * S;
+  uint64_t* epi_full = bars + 3 * S + 1;
+  uint64_t* epi_free = bars + 3 * S + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* hb = reinterpret_cast<float*>(base + S * L.stage);   // [kM][NT + 1]
+  const int hp = NT + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_my = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int T = n_my * n_kb;
+  const int stride = (NT + 31) & ~31;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1 + DW);
+      mbar_init(smem_u32(&mmadone[s]), 1);
+      mbar_init(smem_u32(&ready[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    mbar_init(smem_u32(epi_full), DW);
+    mbar_init(smem_u32(epi_free), kEpiWarps);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), sh.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- copies ----
+      int next = 0, fwd = 0;
+      long idle = 0;
+      while (fwd < T) {
+        bool progress = false;
+        if (next < T) {
+          const int s = next % S, r = next / S;
+          if (r == 0 || mbar_test_wait(smem_u32(&mmadone[s]), (r - 1) & 1)) {
+            const int tile = blockIdx.x + (next / n_kb) * gridDim.x, kb = next % n_kb;
+            const int mt = tile % sh.n_mt, nt = tile / sh.n_mt;
+            uint8_t* st = base + s * L.stage;
+            const int nk = min(KS, n_kb1 - kb * KS);
+            mbar_arrive_tx(smem_u32(&ready[s]), nk * (L.a1 + L.b1));
+            bulk_g2s(smem_u32(st), aimg + ((size_t)mt * n_kb1 + kb * KS) * L.a1, nk * L.a1,
+                     smem_u32(&ready[s]));
+            bulk_g2s(smem_u32(st + L.a_bytes), bimg + ((size_t)nt * n_kb1 + kb * KS) * L.b1,
+                     nk * L.b1, smem_u32(&ready[s]));
+            ++next;
+            progress = true;
+          }
+        }
+        if (fwd < next && mbar_test_wait(smem_u32(&ready[fwd % S]), (fwd / S) & 1)) {
+          mbar_arrive(smem_u32(&full[fwd % S]));
+          ++fwd;
+          progress = true;
+        }
+        if (progress) {
+          idle = 0;
+        } else if (++idle > (kSpinLimit << 6) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      for (int g = fwd; g < next; ++g) mbar_wait_drain(smem_u32(&ready[g % S]), (g / S) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA ----
+      const uint32_t idesc = idesc_bf16(kM, NT);
+      const uint32_t b_plane = NT * kRow;
+      for (int g = 0; g < T; ++g) {
+        const int s = g % S, r = g / S, b = g & 1, kb = g % n_kb;
+        if (!mbar_wait(smem_u32(&full[s]), r & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(base + s * L.stage);
+        const uint32_t d_main = tmem + (uint32_t)((2 * b) * stride);
+        const uint32_t d_corr = tmem + (uint32_t)((2 * b + 1) * stride);
+        const int nk = min(KS, n_kb1 - kb * KS);
+#pragma unroll
+        for (int h = 0; h < KS; ++h) {
+          if (h >= nk) break;
+          const uint64_t da = desc64(a0 + h * L.a1), db = desc64(a0 + L.a_bytes + h * L.b1);
+#pragma unroll
+          for (int j = 0; j < kK / 16; ++j) {
+#pragma unroll
+            for (int t = 0; t < P::kProducts; ++t) {
+              const uint64_t ad = da + (uint64_t)((P::pa(t) * kPlaneM + j * 256) >> 4);
+              const uint64_t bd = db + (uint64_t)((P::pb(t) * b_plane + j * 256) >> 4);
+              const bool first = (h == 0) && (j == 0) && (t <= 1);
+              mma_bf16(t == 0 ? d_main : d_corr, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(smem_u32(&mmadone[s]));
+      }
+      mma_commit(smem_u32(done));
+      mbar_wait_drain(smem_u32(done), 0);
+    }
+    __syncwarp();
+  } else if (warp < 2 + DW) {
+    // ------------------------------------------------------------ drain ----
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+    const int nch = NT / 16;
+    const int nch0 = (nch + 1) / 2;
+    const int c_begin = half ? nch0 : 0;
+    const int my = half ? nch - nch0 : nch0;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    if (lane == 0) {
+      mbar_arrive(smem_u32(&full[0]));
+      if (T > 1) mbar_arrive(smem_u32(&full[1 % S]));
+    }
+    bool ok = true;
+    for (int it = 0; it < n_my && ok; ++it) {
+      float acc[CH * 16];
+#pragma unroll
+      for (int t = 0; t < CH * 16; ++t) acc[t] = 0.0f;
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int g = it * n_kb + kb, b = g & 1;
+        const bool got = mbar_wait(smem_u32(&mmadone[g % S]), (g / S) & 1, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t slot_m = lane_base + (2 * b) * stride + c_begin * 16;
+        const uint32_t slot_c = lane_base + (2 * b + 1) * stride + c_begin * 16;
+        // one 16-column chunk (leading and correction slots) in flight per wait: the registers
+        // are shared with the epilogue warps
+#pragma unroll
+        for (int cc = 0; cc < CH; ++cc) {
+          if (cc < my) {
+            uint32_t m0[16], r0[16];
+            tmem_ld16_async(slot_m + cc * 16, m0);
+            tmem_ld16_async(slot_c + cc * 16, r0);
+            tmem_wait_ld();
+            reg_fence(m0);
+            reg_fence(r0);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) acc[cc * 16 + t] += __uint_as_float(m0[t]) + __uint_as_float(r0[t]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0 && g + 2 < T) mbar_arrive(smem_u32(&full[(g + 2) % S]));
+      }
+      if (!ok) break;
+      // hand the tile's sums to the epilogue warps once they have read the previous tile's
+      if (it > 0) {
+        const bool fr = mbar_wait(smem_u32(epi_free), (it - 1) & 1, abort_flag);
+        if (!__all_sync(0xffffffffu, fr)) { ok = false; break; }
+      }
+      float* hr = hb + (size_t)row * hp + c_begin * 16;
+#pragma unroll
+      for (int c = 0; c < CH * 16; ++c)
+        if (c < my * 16) hr[c] = acc[c];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(epi_full));
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue ----
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int c0 = 0, nc = NT;
+    for (int it = 0; it < n_my; ++it) {
+      const bool got = mbar_wait(smem_u32(epi_full), it & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) break;
+      const int tile = blockIdx.x + it * gridDim.x;
+      const int mt = tile % sh.n_mt, nt = tile / sh.n_mt;
+      Epi e = epi;
+      e.set_stage(nullptr, nt * NT);
+      e(mt * kM + row, nt * NT + c0, hb + (size_t)row * hp + c0, 1, nc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(epi_free));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(status, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, sh.tmem_cols);
+  }
+}
+
 // ------------------------------------------------------- two-SM tile (cta_group::2) ----
 
 // A cluster of two CTAs on two SMs computes one 256 x NT tile with tcgen05.mma.cta_group::2:
@@ -1523,6 +1744,8 @@ constexpr int kPair = 256;
 constexpr int kDeep = 1024;
 // bit 12 (with bit 10) = the persistent two-K-block GEMM (k_gemm_persist), tiles up to 96 columns
 constexpr int kPersist = 4096;
+// bit 16 (with bits 10 and 12) = the persistent GEMM with epilogue warps (k_gemm_persist_ep)
+constexpr int kPersistEp = 65536;
 // bit 13 (with bit 10) = the two-SM tile (k_gemm_2sm): 256 rows x NT columns per CTA pair,
 // NT in {64, 96, 128}; bit 11 with it = stage the adjoint epilogue's table rows in shared memory
 // even where that leaves room for two pipeline stages only
@@ -1570,8 +1793,12 @@ int shape_for(swcl_ctx* c, int code, int n_mt, int n_kb, GemmShape& sh, uint32_t
   const bool splitk = code & kSplitK;
   if (splitk && (!merged || KS != 1 || NT < 160 || n_kb < 2))
     return fail(c, SWCL_ERR_INVALID_ARG, "split-K GEMM tiles: bit 14, one K-block per stage, >= 160 columns");
+  const bool persist_ep = code & kPersistEp;
+  if (persist_ep && !persist)
+    return fail(c, SWCL_ERR_INVALID_ARG, "GEMM tile code: bit 16 needs bits 10 and 12");
   auto lay = [&](int st) {
-    return persist ? layout_persist<P>(NT, st, 3) : layout<P>(two_sm ? NT / 2 : NT, st, KS);
+    return persist_ep ? layout_persist_ep<P>(NT, st)
+         : persist ? layout_persist<P>(NT, st, 3) : layout<P>(two_sm ? NT / 2 : NT, st, KS);
   };
   // the table rows the epilogue stages sit after the barriers
   auto with_extra = [&](const Layout& L) {
@@ -1621,6 +1848,19 @@ cudaError_t launch_subset(swcl_ctx* c, uint32_t pm, const uint8_t* a, const uint
     case 0x07u: return launch_variant<P, Epi, 8, 3, 2, 0x07u>(c, a, b, sh, smem, n_nt, epi);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <class P, class Epi>
+cudaError_t launch_persist_ep(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const GemmShape& sh,
+                              uint32_t smem, int n_nt, const Epi& epi) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_persist_ep<P, Epi, 3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int n_tiles = sh.n_mt * n_nt;
+  const int grid = std::min(n_tiles, std::max(1, c->num_sms));
+  k_gemm_persist_ep<P, Epi, 3><<<(unsigned)grid, threads_persist_ep(), smem, c->stream>>>(
+      a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
+  return cudaGetLastError();
 }
 
 template <class P, class Epi>
@@ -1695,6 +1935,7 @@ cudaError_t launch_gemm(swcl_ctx* c, int code, const uint8_t* a, const uint8_t* 
          : ch <= 4 ? launch_variant<P, Epi, 8, 4, 2, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi)
                    : launch_variant<P, Epi, 8, 8, 2, 0x3Fu, true>(c, a, b, sh, smem, n_nt, epi);
   }
+  if (code & kPersistEp) return launch_persist_ep<P, Epi>(c, a, b, sh, smem, n_nt, epi);
   if (code & kPersist) return launch_persist<P, Epi>(c, a, b, sh, smem, n_nt, epi);
   if (code & kPair)   // four drain warps: every chunk of a row in one thread
     return nch <= 3 ? launch_variant<P, Epi, 4, 3, 1>(c, a, b, sh, smem, n_nt, epi)
@@ -1745,7 +1986,10 @@ std::vector<int> tile_candidates(int r, bool need_groups, bool tuned_only = fals
     const int half0 = 16 * ((nt / 16 + 1) / 2);
     if (!need_groups || (nt % r == 0 && half0 % r == 0)) {
       v.push_back(nt | kDeep);
-      if (nt <= 96) v.push_back(nt | kDeep | kPersist);
+      if (nt <= 96) {
+        v.push_back(nt | kDeep | kPersist);
+        v.push_back(nt | kDeep | kPersist | kPersistEp);
+      }
     }
   }
   return v;

@@ -50,9 +50,9 @@ def test_n5k_against_oracle_and_stencil_kernels(wl):
     # plain, two-CTA (bit 8), two-K-block (bit 10), persistent two-K-block (bits 10 and 12),
     # two-SM tile (bits 10 and 13, with bit 11 in the adjoint: table rows staged first), one
     # accumulator slot per buffer (bit 14, with or without bit 10; in the forward also with bit 15,
-    # K split over two CTAs)
-    assert code_f >> 8 in (0, 1, 4, 20, 36, 64, 65, 68, 192)
-    assert code_a >> 8 in (0, 1, 4, 20, 36, 44, 64, 65, 68)
+    # K split over two CTAs) or the persistent form with epilogue warps (bits 10, 12 and 16)
+    assert code_f >> 8 in (0, 1, 4, 20, 36, 64, 65, 68, 192, 276)
+    assert code_a >> 8 in (0, 1, 4, 20, 36, 44, 64, 65, 68, 276)
     assert (not code_f & 256 or nt_f <= (128 if code_f & 16384 else 64))
     assert (not code_a & 256 or nt_a <= (128 if code_a & 16384 else 64))
     assert (nt_f <= 128 or code_f & 16384) and (nt_a <= 128 or code_a & 16384)
@@ -138,14 +138,15 @@ def test_rank_two_profiles():
                                   96 | 1024 | 16384, 128 | 1024 | 16384, 160 | 1024 | 16384,
                                   192 | 16384, 208 | 16384, 240 | 16384, 160 | 16384 | 32768,
                                   192 | 16384 | 32768, 240 | 16384 | 32768, 64 | 256 | 16384,
-                                  96 | 256 | 16384, 128 | 256 | 16384])
+                                  96 | 256 | 16384, 128 | 256 | 16384, 64 | 1024 | 4096 | 65536,
+                                  96 | 1024 | 4096 | 65536])
 def test_every_tile_variant_against_oracle(code):
     """Each GEMM variant, fixed through SWCL_BASIS_TILES: one CTA per SM (48, 96, 128 columns),
     two CTAs per SM (| 256), two K-blocks per pipeline stage (| 1024), the persistent two-K-block
     form (| 1024 | 4096), the two-SM tile (| 1024 | 8192; | 2048: the adjoint's table rows staged
     at two stages), one accumulator slot per buffer (| 16384: up to 240 columns; | 32768: K split
     over a cluster of two CTAs, forward only, with the 208-column one-slot adjoint; | 256: two CTAs
-    per SM); three walkers,
+    per SM; | 1024 | 4096 | 65536: persistent with epilogue warps); three walkers,
     a ragged k
     tail (333 points), 17 K-blocks in the forward GEMM (an odd count: the last stage is short),
     against the oracle."""
