@@ -386,8 +386,8 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
   }
 }
 
-// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT points, LC multipoles,
-// walker); one thread per k point.  S_ij A_j is staged per multipole chunk in shared memory,
+// Delta_bar and the P_bar partial sums.  Grid: (k tile of DT QT points, one multipole, walker);
+// QT consecutive k points per thread.  S_ij A_j is staged per multipole chunk in shared memory,
 // transposed (St[j][i], rows padded to a multiple of DG with zeros) so that DG consecutive rows i
 // load as one vector, in the arithmetic type T (FP32 for the mixed paths, FP64 for the FP64 path);
 // Delta_j(l, q) sits in a per-thread shared column.  Each thread forms T_i for DG rows i at a time,
@@ -420,74 +420,108 @@ __device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {
   s = sn;
 }
 
+// QT consecutive k points per thread (2 for FP32: every shared load of S feeds 2 DG FMAs, and
+// Delta and Dbar move as 8-byte pairs); the sums of each k point are those of one thread per
+// point, in the same order.
+template <typename T> struct DbarQ { static constexpr int QT = 1; };
+template <> struct DbarQ<float> { static constexpr int QT = 2; };
+
 template <typename T>
 __global__ void __launch_bounds__(DT)
 k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __restrict__ delta,
             const double* __restrict__ Cf, const double* __restrict__ amp,
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
             int N_ell, int n_walk, int l_lo, int n_l, const int* __restrict__ listed) {
+  constexpr int QT = DbarQ<T>::QT, DQ = DT * QT;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int NP = delta_bar_pitch(N_tr);
-  T* St = reinterpret_cast<T*>(dsm_raw);           // [LC][N_tr][NP]  St[j][i] = S_ij A_j
-  T* Dl = St + LC * N_tr * NP;                     // [N_tr][DT]
-  T* As = Dl + N_tr * DT;                          // [N_tr] A_i
+  T* St = reinterpret_cast<T*>(dsm_raw);           // [N_tr][NP]  St[j][i] = S_ij A_j
+  T* Dl = St + N_tr * NP;                          // [N_tr][DQ]
+  T* As = Dl + N_tr * DQ;                          // [N_tr] A_i
   const int w = blockIdx.z;
-  // Delta and Dbar hold multipoles [l_lo, l_lo + n_l) (l_lo a multiple of LC); Cf all N_ell
-  const int lc = l_lo / LC + blockIdx.y;
-  const int q = blockIdx.x * DT + threadIdx.x;
-  const int l0 = lc * LC;
-  const int nl = min(LC, l_lo + n_l - l0);
+  // Delta and Dbar hold multipoles [l_lo, l_lo + n_l); Cf all N_ell (LC = 1 multipole per CTA)
+  const int l0 = l_lo + blockIdx.y;
+  const int qt = threadIdx.x * QT;                 // this thread's first column of Dl
+  const int q0 = blockIdx.x * DQ + qt;
   if (listed && listed[w * n_l + (l0 - l_lo)] < 0) {
-    // a multipole the walker does not list (LC = 1): S = 0, so Dbar = 0 and the P_bar partial is
-    // 0; its Delta rows are not read and its Dbar rows are not used
-    if (q < N_k) pbar_part[((size_t)lc * n_walk + w) * N_k + q] = 0.0;
+    // a multipole the walker does not list: S = 0, so Dbar = 0 and the P_bar partial is 0; its
+    // Delta rows are not read and its Dbar rows are not used
+#pragma unroll
+    for (int u = 0; u < QT; ++u)
+      if (q0 + u < N_k) pbar_part[((size_t)l0 * n_walk + w) * N_k + q0 + u] = 0.0;
     return;
   }
   const double* A = amp + (size_t)w * N_tr;
-  for (int e = threadIdx.x; e < nl * N_tr * NP; e += DT) {
-    const int ll = e / (N_tr * NP), r = e - ll * N_tr * NP, j = r / NP, i = r - j * NP;
-    St[e] = i < N_tr ? (T)(Cf[((size_t)w * N_ell + l0 + ll) * N_tr * N_tr + i * N_tr + j] * A[j])
-                     : T(0);
+  const double* Cl = Cf + ((size_t)w * N_ell + l0) * N_tr * N_tr;
+  for (int e = threadIdx.x; e < N_tr * NP; e += DT) {
+    const int j = e / NP, i = e - j * NP;
+    St[e] = i < N_tr ? (T)(Cl[i * N_tr + j] * A[j]) : T(0);
   }
   for (int e = threadIdx.x; e < N_tr; e += DT) As[e] = (T)A[e];
-  const T two_u = (q < N_k) ? (T)(2.0 * wk2[q] * P[(size_t)w * N_k + q]) : T(0);
-  const T* dq = Dl + threadIdx.x;
-  T ps = 0, pc = 0;
-  for (int ll = 0; ll < nl; ++ll) {
-    __syncthreads();
-    const T* dl = delta + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
-#pragma unroll 8
-    for (int t = 0; t < N_tr; ++t)
-      Dl[t * DT + threadIdx.x] = (q < N_k) ? dl[(size_t)t * N_k + q] : T(0);
-    __syncthreads();
-    if (q < N_k) {
-      const T* Sl = St + ll * N_tr * NP;
-      T* db = dbar + ((size_t)w * n_l + l0 - l_lo + ll) * N_tr * N_k;
-      for (int i0 = 0; i0 < N_tr; i0 += DG) {
-        T t[DG];
+  T two_u[QT];
 #pragma unroll
-        for (int g = 0; g < DG; ++g) t[g] = 0;
-#pragma unroll 4
-        for (int j = 0; j < N_tr; ++j) {
-          T sv[DG];
-          lds4(Sl + j * NP + i0, sv);
-          const T d = dq[j * DT];
+  for (int u = 0; u < QT; ++u)
+    two_u[u] = (q0 + u < N_k) ? (T)(2.0 * wk2[q0 + u] * P[(size_t)w * N_k + q0 + u]) : T(0);
+  const T* dl = delta + ((size_t)w * n_l + l0 - l_lo) * N_tr * N_k;
+  const bool pair = QT == 2 && (N_k & 1) == 0 && q0 + 1 < N_k;   // 8-byte aligned pair
+#pragma unroll 5
+  for (int t = 0; t < N_tr; ++t) {
+    if (pair) {
+      *reinterpret_cast<float2*>(Dl + t * DQ + qt) = *reinterpret_cast<const float2*>(dl + (size_t)t * N_k + q0);
+    } else {
 #pragma unroll
-          for (int g = 0; g < DG; ++g) t[g] = fma(sv[g], d, t[g]);
+      for (int u = 0; u < QT; ++u) Dl[t * DQ + qt + u] = (q0 + u < N_k) ? dl[(size_t)t * N_k + q0 + u] : T(0);
+    }
+  }
+  __syncthreads();
+  if (q0 >= N_k) return;
+  T ps[QT], pc[QT];
+#pragma unroll
+  for (int u = 0; u < QT; ++u) ps[u] = pc[u] = T(0);
+  const T* dq = Dl + qt;
+  T* db = dbar + ((size_t)w * n_l + l0 - l_lo) * N_tr * N_k + q0;
+  for (int i0 = 0; i0 < N_tr; i0 += DG) {
+    T t[DG][QT];
+#pragma unroll
+    for (int g = 0; g < DG; ++g)
+#pragma unroll
+      for (int u = 0; u < QT; ++u) t[g][u] = 0;
+#pragma unroll 5
+    for (int j = 0; j < N_tr; ++j) {
+      T sv[DG];
+      lds4(St + j * NP + i0, sv);
+      T d[QT];
+#pragma unroll
+      for (int u = 0; u < QT; ++u) d[u] = dq[j * DQ + u];
+#pragma unroll
+      for (int g = 0; g < DG; ++g)
+#pragma unroll
+        for (int u = 0; u < QT; ++u) t[g][u] = fma(sv[g], d[u], t[g][u]);
+    }
+#pragma unroll
+    for (int g = 0; g < DG; ++g) {
+      const int ii = i0 + g;
+      if (ii < N_tr) {
+        const T ai = As[ii];
+        T o[QT];
+#pragma unroll
+        for (int u = 0; u < QT; ++u) {
+          two_sum_acc(ps[u], pc[u], ai * dq[ii * DQ + u] * t[g][u]);
+          o[u] = two_u[u] * ai * t[g][u];
         }
+        if (pair) {
+          *reinterpret_cast<float2*>(db + (size_t)ii * N_k) = make_float2((float)o[0], (float)o[QT - 1]);
+        } else {
 #pragma unroll
-        for (int g = 0; g < DG; ++g) {
-          const int ii = i0 + g;
-          if (ii < N_tr) {
-            const T ai = As[ii];
-            two_sum_acc(ps, pc, ai * dq[ii * DT] * t[g]);
-            db[(size_t)ii * N_k + q] = two_u * ai * t[g];
-          }
+          for (int u = 0; u < QT; ++u)
+            if (q0 + u < N_k) db[(size_t)ii * N_k + u] = o[u];
         }
       }
     }
   }
-  if (q < N_k) pbar_part[((size_t)lc * n_walk + w) * N_k + q] = (double)ps + (double)pc;
+#pragma unroll
+  for (int u = 0; u < QT; ++u)
+    if (q0 + u < N_k) pbar_part[((size_t)l0 * n_walk + w) * N_k + q0 + u] = (double)ps[u] + (double)pc[u];
 }
 
 __global__ void k_pbar_reduce(double* __restrict__ Pbar, const double* __restrict__ part,
@@ -605,13 +639,14 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const do
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s,
                              const int* listed) {
-  const size_t smem = (size_t)(LC * N_tr * delta_bar_pitch(N_tr) + N_tr * DT + N_tr) * sizeof(T);
+  constexpr int DQ = DT * DbarQ<T>::QT;
+  const size_t smem = (size_t)(N_tr * delta_bar_pitch(N_tr) + N_tr * DQ + N_tr) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_delta_bar<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 g((N_k + DT - 1) / DT, (n_l + LC - 1) / LC, n_walk);
+  dim3 g((N_k + DQ - 1) / DQ, n_l, n_walk);
   k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell,
                                      n_walk, l_lo, n_l, listed);
   return cudaGetLastError();
