@@ -196,7 +196,9 @@ int swcl_compute_batched(swcl_ctx* ctx, int precision, double* C_out, const doub
  * Outputs: C_out (required), P_bar, amp_bar, W_bar (NULL to skip; they need C_bar), laid out as
  * in swcl_compute_cl / swcl_vjp.
  * Every non-NULL pointer must be page-locked host memory (cudaHostAlloc, cudaHostRegister, a
- * pinned torch tensor): the copies are graph nodes that read and write it directly.  The
+ * pinned torch tensor): two kernels of the graph read and write it directly (copy nodes where
+ * the device cannot address it).  Pointers equal to those of the captured graph are not checked
+ * again.  The
  * library-owned device side of the outputs and cotangent is sized at the first call.  The first
  * call of a configuration (pointers, precision, sizes) runs the step once outside the graph and
  * captures it; later calls replay it.  Needs set_grids, set_tracers, set_windows and set_power

@@ -69,6 +69,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+void* host_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool is_pinned_host_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -373,6 +382,7 @@ int swcl_destroy(swcl_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->hgraph_exec) cudaGraphExecDestroy(c->hgraph_exec);
   if (c->hs_status) cudaFreeHost(c->hs_status);
+  if (c->ev_host) cudaEventDestroy(c->ev_host);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -1235,8 +1245,11 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
   if (!C_bar && (P_bar || amp_bar || W_bar))
     return swcl::fail(c, SWCL_ERR_INVALID_ARG, "gradients need C_bar");
   const void* ptrs[8] = {W, P, amp, C_bar, C_out, P_bar, amp_bar, W_bar};
+  // the pointers of the captured graph were checked when it was captured
+  bool known = c->hgraph_exec != nullptr;
+  for (int t = 0; t < 8 && known; ++t) known = c->hgraph_key.ptrs[t] == ptrs[t];
   for (const void* p : ptrs)
-    if (p && !swcl::is_pinned_host_ptr(p))
+    if (!known && p && !swcl::is_pinned_host_ptr(p))
       return swcl::fail(c, SWCL_ERR_INVALID_ARG,
                         "swcl_step_host takes page-locked host arrays only (cudaHostAlloc / cudaHostRegister)");
   const size_t nC = (size_t)out_count(c) * c->N_tr * c->N_tr;
@@ -1248,8 +1261,12 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
   if (amp_bar) SWCL_TRY(swcl::ensure(c, c->hs_Ab, sizeof(double) * nA));
   if (W_bar) SWCL_TRY(swcl::ensure(c, c->hs_Wb, sizeof(double) * nW));
   if (!c->hs_status) {
-    SWCL_TRY_CUDA(c, cudaHostAlloc((void**)&c->hs_status, sizeof(int), cudaHostAllocDefault),
+    SWCL_TRY_CUDA(c, cudaHostAlloc((void**)&c->hs_status, sizeof(int), cudaHostAllocMapped),
                   "cudaHostAlloc (status word)");
+    if (cudaHostGetDevicePointer((void**)&c->hs_status_dev, c->hs_status, 0) != cudaSuccess) {
+      cudaGetLastError();
+      c->hs_status_dev = nullptr;
+    }
   }
   // the input buffers exist with these sizes since swcl_set_windows / swcl_set_power
   if (c->d_W.bytes < sizeof(double) * nW || c->d_P.bytes < sizeof(double) * nP ||
@@ -1260,7 +1277,39 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
   double* dPb = P_bar ? (double*)c->hs_Pb.p : nullptr;
   double* dAb = amp_bar ? (double*)c->hs_Ab.p : nullptr;
   double* dWb = W_bar ? (double*)c->hs_Wb.p : nullptr;
+  // The copies run as two kernels that address the host arrays directly, when the device can
+  // (page-locked memory mapped into its address space); else as copy nodes.
+  // (resolved when the graph is captured)
+  const void* dptr[8] = {};
+  bool direct = false;
+  auto resolve = [&]() {
+    direct = c->hs_status_dev != nullptr;
+    for (int t = 0; t < 8 && direct; ++t)
+      if (ptrs[t]) direct = (dptr[t] = swcl::host_device_ptr(ptrs[t])) != nullptr;
+  };
+  auto run_direct = [&]() -> int {
+    swcl::CopyList in;
+    in.add(c->d_W.p, dptr[0], sizeof(double) * nW);
+    in.add(c->d_P.p, dptr[1], sizeof(double) * nP);
+    in.add(c->d_amp.p, dptr[2], sizeof(double) * nA);
+    in.add(dCb, dptr[3], sizeof(double) * nC);
+    cudaError_t e = swcl::launch_copy_list(in, c->stream);
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step inputs host -> device");
+    int st = batched_body(c, precision, dC, dCb, dPb, dAb, dWb);
+    if (st) return st;
+    c->last_launches += 2;   // the two copy kernels
+    swcl::CopyList out;
+    out.add(const_cast<void*>(dptr[4]), dC, sizeof(double) * nC);
+    out.add(const_cast<void*>(dptr[5]), dPb, sizeof(double) * nP);
+    out.add(const_cast<void*>(dptr[6]), dAb, sizeof(double) * nA);
+    out.add(const_cast<void*>(dptr[7]), dWb, sizeof(double) * nW);
+    out.add(c->hs_status_dev, c->ws_status.p, sizeof(int));
+    e = swcl::launch_copy_list(out, c->stream);
+    if (e != cudaSuccess) return swcl::cuda_fail(c, e, "step results device -> host");
+    return SWCL_OK;
+  };
   auto run = [&]() -> int {
+    if (direct) return run_direct();
     auto h2d = [&](void* dst, const void* src, size_t bytes) {
       return src ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
     };
@@ -1303,6 +1352,7 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
       c->hgraph_exec = nullptr;
     }
     int64_t gen = 0;
+    resolve();
     SWCL_TRY(capture_graph(c, run, &c->hgraph_exec, &gen));
     c->hgraph_key.precision = precision;
     c->hgraph_key.alloc_gen = gen;
@@ -1310,7 +1360,16 @@ int swcl_step_host(swcl_ctx* c, int precision, const double* W, const double* P,
     c->hgraph_launches = c->last_launches;
   }
   SWCL_TRY_CUDA(c, cudaGraphLaunch(c->hgraph_exec, c->stream), "graph launch");
-  SWCL_TRY_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  // wait by polling an event: a sampler's step is short (a fraction of a millisecond), and a
+  // polling thread sees the end of the graph sooner than one woken from a blocking wait
+  if (!c->ev_host)
+    SWCL_TRY_CUDA(c, cudaEventCreateWithFlags(&c->ev_host, cudaEventDisableTiming), "event");
+  SWCL_TRY_CUDA(c, cudaEventRecord(c->ev_host, c->stream), "event record");
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(c->ev_host);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return swcl::cuda_fail(c, q, "step wait");
+  }
   c->last_launches = c->hgraph_launches;
   c->last_fwd_precision = precision;
   const int h = *c->hs_status;

@@ -228,6 +228,8 @@ struct swcl_ctx {
   int64_t hgraph_launches = 0;
   swcl::DevBuf hs_C, hs_Cb, hs_Pb, hs_Ab, hs_Wb;   // device side of the step's arrays
   int* hs_status = nullptr;                        // page-locked copy of the status word
+  cudaEvent_t ev_host = nullptr;                   // end of the step, polled by the host
+  int* hs_status_dev = nullptr;                    // its device-side address
   // host destinations that swcl_step_host sets for the duration of one capture: C, P_bar and
   // amp_bar go device -> host on the stream that produced them, as soon as they are final
   double* early_C = nullptr;
@@ -253,6 +255,21 @@ int ensure(swcl_ctx* c, DevBuf& b, size_t bytes);
 void release(swcl_ctx* c, DevBuf& b);
 bool is_device_ptr(const void* p);
 bool is_pinned_host_ptr(const void* p);   // page-locked host memory known to CUDA
+// device-side address of page-locked host memory (null when the device cannot address it)
+void* host_device_ptr(const void* p);
+
+// Up to eight copies as one kernel (hostio.cu): segment s moves bytes[s] from src[s] to dst[s];
+// either side may be page-locked host memory given by its device-side address.
+struct CopyList {
+  const void* src[8] = {};
+  void* dst[8] = {};
+  size_t bytes[8] = {};
+  int n = 0;
+  void add(void* d, const void* s, size_t b) {
+    if (d && s && b) { src[n] = s; dst[n] = d; bytes[n] = b; ++n; }
+  }
+};
+cudaError_t launch_copy_list(const CopyList& L, cudaStream_t s);
 int copy_in(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes);
 int copy_in_queued(swcl_ctx* c, DevBuf& dst, const void* src, size_t bytes, bool* host_src);
 int copy_out(swcl_ctx* c, void* dst, const void* src, size_t bytes);
