@@ -321,6 +321,7 @@ int swcl_create(swcl_ctx** out, int device, size_t mem_budget_bytes, void* strea
   }
   // SWCL_PER_KNOT_FFT=1 keeps the paper's one FFT per knot (no low-rank profiles)
   if (const char* v = std::getenv("SWCL_PER_KNOT_FFT")) c->lr_disabled = std::atoi(v) != 0;
+  if (const char* v = std::getenv("SWCL_PDL")) c->pdl = std::atoi(v) != 0;
   if (const char* v = std::getenv("SWCL_BASIS_GEMM")) c->bt_disabled = std::atoi(v) == 0;
   // the accuracy study of the compensated products: a subset of the six products of the basis
   // GEMMs (bit t = product t in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)); only the sets
@@ -1057,7 +1058,8 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                                    (const double*)c->d_wk2.p, nw, N_tr, N_k, N_ell,
                                                    l_lo, n_l, (double*)c->ws_pbpart.p, c->stream,
                                                    use_basis_gemm(c, precision) && c->bt_compact
-                                                       ? (const int*)c->bt_lpos.p : nullptr),
+                                                       ? (const int*)c->bt_lpos.p : nullptr,
+                                                   c->pdl && !c->prof),
                   "delta_bar f32");
     if (!W_bar) continue;
     if (fp64) {
@@ -1093,7 +1095,7 @@ int swcl_vjp(swcl_ctx* c, int precision, const double* C_bar, double* P_bar, dou
                                              (const double*)c->d_chipow.p, sv.D, sv.B,
                                              (const cplx*)c->d_psi.p, (const cplx*)c->d_twiddle.p,
                                              nw, N_tr, N_I, N, scratch, c->stream,
-                                             (int*)c->ws_status.p), "fftlog adj");
+                                             (int*)c->ws_status.p, c->pdl && !c->prof), "fftlog adj");
       if (!swcl::fftlog_adj_single_launch(nw, N_tr, N_I, N)) ++c->last_launches;  // chunk reduction
     } else {
       SWCL_TRY_CUDA(c, cudaMemsetAsync(Wb, 0, wbytes, c->stream), "clear W_bar");

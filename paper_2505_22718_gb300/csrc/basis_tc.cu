@@ -508,6 +508,7 @@ template <class P, class Epi, int DW, int CH, int KS, uint32_t PM = 0x3Fu, bool 
 __global__ void __launch_bounds__(threads_for(DW), DW == 4 ? 2 : 1)
 k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
              Epi epi, int* __restrict__ status) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // n_kb counts the stages' worth of K (KS K-blocks each, the last one possibly short); with a
@@ -556,6 +557,8 @@ k_gemm_basis(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg,
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // barriers and TMEM are set up; the operands and outputs belong to the kernels before
+  pdl_wait();
 
   bool drain_ok = false;   // the split-K reduction: this drain warp's partial sums are valid
   if (warp == 0) {
@@ -858,6 +861,7 @@ __global__ void __launch_bounds__(threads_for(8), 1)
 k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
                int n_tiles, Epi epi, int* __restrict__ status) {
   constexpr int DW = 8, KS = 2;
+  pdl_trigger();   // the next kernel of the step may be scheduled
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
@@ -893,6 +897,8 @@ k_gemm_persist(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bim
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // barriers and TMEM are set up; the operands and outputs belong to the kernels before
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1071,6 +1077,7 @@ __global__ void __launch_bounds__(threads_persist_ep(), 1)
 k_gemm_persist_ep(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
                   int n_tiles, Epi epi, int* __restrict__ status) {
   constexpr int DW = 8, KS = 2;
+  pdl_trigger();   // the next kernel of the step may be scheduled
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NT = sh.NT, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
@@ -1109,6 +1116,8 @@ k_gemm_persist_ep(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // barriers and TMEM are set up; the operands and outputs belong to the kernels before
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1290,6 +1299,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(threads_for(8), 1)
 k_gemm_2sm(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, GemmShape sh,
            Epi epi, int* __restrict__ status) {
   constexpr int DW = 8, KS = 2;
+  pdl_trigger();   // the next kernel of the step may be scheduled
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NT = sh.NT, H = NT / 2, S = sh.stages, n_kb1 = sh.n_kb, n_kb = (n_kb1 + KS - 1) / KS;
@@ -1326,6 +1336,8 @@ k_gemm_2sm(const uint8_t* __restrict__ aimg, const uint8_t* __restrict__ bimg, G
   cluster_sync_all();   // barriers of both CTAs initialised, TMEM of both allocated
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // barriers and TMEM are set up; the operands and outputs belong to the kernels before
+  pdl_wait();
   if (rank == 1 && tid == 0) {
     // the MMA thread addresses both CTAs' accumulators through CTA 0's TMEM address
     uint32_t lead;
@@ -1643,6 +1655,7 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
                        const float4* __restrict__ gdf, const int* __restrict__ cls_of,
                        const int2* __restrict__ cmap, int N_tr, int N_ell, int n_h, int l_lo,
                        int n_l, int r, int NI, int n_cols, int NT, int n_kb) {
+  pdl_trigger();
   const int kb = blockIdx.x, nt = blockIdx.y;
   const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;
   const int j = nt * NT + row;
@@ -1665,12 +1678,17 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
   const float4* Fr = F + ((size_t)wi * NI + s) * n_h;
   const float4* Gr = gdf + ((size_t)(live ? cls_of[i] : 0) * N_ell + l_lo + l) * n_h;
   const int n0 = (kb * kK + ch * 8) / 2;
+  // the Gamma table and the column maps are the grid's; F comes from the FFTLog before
+  float4 gv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) gv[u] = (live && n0 + u < n_h) ? Gr[n0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+  pdl_wait();
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int n = n0 + u;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     if (live && n < n_h) {
-      const float4 f = Fr[n], g = Gr[n];
+      const float4 f = Fr[n], g = gv[u];
       // Re = fr gr - fi gi, Im = fr gi + fi gr
       df_dot2(f.x, f.z, g.x, g.z, f.y, f.w, g.y, g.w, -1.0f, rh, rl);
       df_dot2(f.x, f.z, g.y, g.w, f.y, f.w, g.x, g.z, 1.0f, ih, il);
@@ -1688,7 +1706,9 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
 // groups of four.
 __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
                        const float* __restrict__ kmu, const int2* __restrict__ cmap, int N_tr,
-                       int N_k, int n_l, int r, int n_cols, int NT, int n_kb, int vec4) {
+                       int N_k, int n_l, int r, int n_cols, int NT, int n_kb, int vec4,
+                       double* __restrict__ zero, long n_zero) {
+  pdl_trigger();
   const int kb = blockIdx.x, nt = blockIdx.y;
   const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;
   const int j = nt * NT + row;
@@ -1712,6 +1732,14 @@ __global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar
   const float* drow = dbar + (((size_t)w * n_l + l) * N_tr + i) * N_k;
   const float* krow = kmu + ((size_t)i * 4 + s) * N_k;
   const int q0 = kb * kK + ch * 8;
+  // Dbar comes from the kernel before; zero[0 .. n_zero) (the adjoint GEMM's accumulator, which
+  // the adjoint of the step before read last) is cleared here for the GEMM that follows
+  pdl_wait();
+  if (zero) {
+    const long nthr = (long)gridDim.x * gridDim.y * blockDim.x;
+    const long t0 = ((long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    for (long e = t0; e < n_zero; e += nthr) zero[e] = 0.0;
+  }
   float x[8];
   if (vec4 && live && q0 + 8 <= N_k) {
     const float4 d0 = *reinterpret_cast<const float4*>(drow + q0);
@@ -1831,9 +1859,8 @@ cudaError_t launch_variant(swcl_ctx* c, const uint8_t* a, const uint8_t* b, cons
   cudaError_t e = cudaFuncSetAttribute(k_gemm_basis<P, Epi, DW, CH, KS, PM, MG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_basis<P, Epi, DW, CH, KS, PM, MG><<<(unsigned)(sh.n_mt * n_nt), threads_for(DW), smem, c->stream>>>(
-      a, b, sh, epi, (int*)c->ws_status.p);
-  return cudaGetLastError();
+  return launch_k(c->pdl && !c->prof, k_gemm_basis<P, Epi, DW, CH, KS, PM, MG>, dim3((unsigned)(sh.n_mt * n_nt)),
+                  dim3(threads_for(DW)), smem, c->stream, a, b, sh, epi, (int*)c->ws_status.p);
 }
 
 // The product subsets of the accuracy study, at the 96-column two-K-block tile only.
@@ -1858,9 +1885,8 @@ cudaError_t launch_persist_ep(swcl_ctx* c, const uint8_t* a, const uint8_t* b, c
   if (e != cudaSuccess) return e;
   const int n_tiles = sh.n_mt * n_nt;
   const int grid = std::min(n_tiles, std::max(1, c->num_sms));
-  k_gemm_persist_ep<P, Epi, 3><<<(unsigned)grid, threads_persist_ep(), smem, c->stream>>>(
-      a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
-  return cudaGetLastError();
+  return launch_k(c->pdl && !c->prof, k_gemm_persist_ep<P, Epi, 3>, dim3((unsigned)grid), dim3(threads_persist_ep()),
+                  smem, c->stream, a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
 }
 
 template <class P, class Epi>
@@ -1871,9 +1897,8 @@ cudaError_t launch_persist(swcl_ctx* c, const uint8_t* a, const uint8_t* b, cons
   if (e != cudaSuccess) return e;
   const int n_tiles = sh.n_mt * n_nt;
   const int grid = std::min(n_tiles, std::max(1, c->num_sms));
-  k_gemm_persist<P, Epi, 3><<<(unsigned)grid, threads_for(8), smem, c->stream>>>(
-      a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
-  return cudaGetLastError();
+  return launch_k(c->pdl && !c->prof, k_gemm_persist<P, Epi, 3>, dim3((unsigned)grid), dim3(threads_for(8)), smem,
+                  c->stream, a, b, sh, n_tiles, epi, (int*)c->ws_status.p);
 }
 
 // one K-block per stage, one accumulator slot, 8 chunks per drain thread, K split over a
@@ -1889,13 +1914,15 @@ cudaError_t launch_splitk(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const
   cfg.blockDim = dim3(threads_for(8));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = 2;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = c->pdl && !c->prof ? 2 : 1;
   e = cudaLaunchKernelEx(&cfg, kern, a, b, sh, epi, (int*)c->ws_status.p);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
@@ -1907,9 +1934,8 @@ cudaError_t launch_2sm(swcl_ctx* c, const uint8_t* a, const uint8_t* b, const Ge
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n_mt2 = (sh.n_mt + 1) / 2;
-  k_gemm_2sm<P, Epi, CH><<<(unsigned)(2 * n_mt2 * n_nt), threads_for(8), smem, c->stream>>>(
-      a, b, sh, epi, (int*)c->ws_status.p);
-  return cudaGetLastError();
+  return launch_k(c->pdl && !c->prof, k_gemm_2sm<P, Epi, CH>, dim3((unsigned)(2 * n_mt2 * n_nt)), dim3(threads_for(8)),
+                  smem, c->stream, a, b, sh, epi, (int*)c->ws_status.p);
 }
 
 template <class P, class Epi>
@@ -2146,23 +2172,23 @@ int build_h(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int l_lo, int n_l)
   const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_himg, (size_t)n_nt * c->bt_f_kb * kPlanes * NT * kRow);
   if (st) return st;
-  k_himg<<<dim3((unsigned)c->bt_f_kb, (unsigned)n_nt), NT * 4, 0, c->stream>>>(
-      (uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p, (const float4*)c->bt_gdf.p,
-      (const int*)c->d_cls_of.p, cp.cmap_f, c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r, sv.NI, n_cols,
-      NT, c->bt_f_kb);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(c->pdl && !c->prof, k_himg, dim3((unsigned)c->bt_f_kb, (unsigned)n_nt), dim3(NT * 4),
+                           0, c->stream, (uint8_t*)c->bt_himg.p, (const float4*)c->ws_coef.p,
+                           (const float4*)c->bt_gdf.p, (const int*)c->d_cls_of.p, cp.cmap_f,
+                           c->N_tr, c->N_ell, c->n_h, l_lo, n_l, r, sv.NI, n_cols, NT, c->bt_f_kb);
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis forward operand");
 }
 
-int build_d(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int n_l) {
+int build_d(swcl_ctx* c, const ColPlan& cp, int NT, int n_nt, int n_l, double* zero = nullptr,
+            long n_zero = 0) {
   const int r = basis_rank(c);
   const int n_cols = cp.n_cols;
   int st = ensure(c, c->bt_dimg, (size_t)n_nt * c->bt_a_kb * kPlanes * NT * kRow);
   if (st) return st;
-  k_dimg<<<dim3((unsigned)c->bt_a_kb, (unsigned)n_nt), NT * 4, 0, c->stream>>>(
-      (uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p, (const float*)c->bt_kmu.p, cp.cmap_a,
-      c->N_tr, c->N_k, n_l, r, n_cols, NT, c->bt_a_kb, c->N_k % 4 == 0 ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(c->pdl && !c->prof, k_dimg, dim3((unsigned)c->bt_a_kb, (unsigned)n_nt), dim3(NT * 4),
+                           0, c->stream, (uint8_t*)c->bt_dimg.p, (const float*)c->ws_dbar.p,
+                           (const float*)c->bt_kmu.p, cp.cmap_a, c->N_tr, c->N_k, n_l, r, n_cols,
+                           NT, c->bt_a_kb, c->N_k % 4 == 0 ? 1 : 0, zero, n_zero);
   return e == cudaSuccess ? SWCL_OK : cuda_fail(c, e, "basis adjoint operand");
 }
 
@@ -2283,14 +2309,14 @@ int basis_adjoint(swcl_ctx* c, int l_lo, int n_l, bool accumulate) {
       if (accumulate) return fail(c, SWCL_ERR_STATE, "basis adjoint tuned inside an accumulation");
     }
   }
-  if (!accumulate) {
-    cudaError_t e = cudaMemsetAsync(c->ws_cbar.p, 0, cbytes, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "clear cbar");
-  }
+  // the adjoint image's builder clears the GEMM's accumulator (one launch less than a memset
+  // between them, which would also break the programmatic launch of the GEMM)
+  double* zero = accumulate ? nullptr : (double*)c->ws_cbar.p;
+  const long n_zero = (long)(cbytes / sizeof(double));
   const int code = c->bt_nt_adj, NT = code & 255;
   const int n_nt = (n_cols + NT - 1) / NT;
   if ((st = counted(c, "basis operand adj", [&] {
-         return build_d(c, cp, img_cols(code), img_tiles(code, n_nt), n_l);
+         return build_d(c, cp, img_cols(code), img_tiles(code, n_nt), n_l, zero, n_zero);
        })))
     return st;
   return counted(c, "basis gemm adj", [&] { return run(code, false); });

@@ -102,6 +102,8 @@ k_fftlog_fwd(CT* __restrict__ coef, const double* __restrict__ W,
              const double* __restrict__ chipow, const double* __restrict__ D,
              const double* __restrict__ B, const cplx* __restrict__ psi,
              const cplx* __restrict__ tw, int n_walk, int N_tr, int N_I, int N) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
+  pdl_wait();      // every earlier kernel of the step has completed
   extern __shared__ cplx smem[];
   const int n2 = N / 2, n_h = N / 2 + 1;
   const int R = rows_per_cta(N);
@@ -161,6 +163,8 @@ k_fftlog_adj(double* __restrict__ scratch, const cplx* __restrict__ cbar,
              const double* __restrict__ chipow, const double* __restrict__ D,
              const double* __restrict__ B, const cplx* __restrict__ psi,
              const cplx* __restrict__ tw, int n_walk, int N_tr, int N_I, int N) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
+  pdl_wait();      // every earlier kernel of the step has completed
   extern __shared__ cplx smem[];
   const int n2 = N / 2, n_h = N / 2 + 1;
   cplx* a = smem;
@@ -211,6 +215,8 @@ k_fftlog_adj(double* __restrict__ scratch, const cplx* __restrict__ cbar,
 
 __global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restrict__ scratch,
                              long per_chunk, int nchunk, int* __restrict__ status) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
+  pdl_wait();      // every earlier kernel of the step has completed
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per_chunk) return;
   double s = 0.0;
@@ -283,6 +289,8 @@ k_fftlog_fwd_cl(CT* __restrict__ coef, const double* __restrict__ W,
                 const double* __restrict__ chipow, const double* __restrict__ D,
                 const double* __restrict__ B, const cplx* __restrict__ psi,
                 const cplx* __restrict__ tw, int N_tr, int N_I, int N) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
+  pdl_wait();      // every earlier kernel of the step has completed
   extern __shared__ cplx smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
@@ -362,6 +370,7 @@ k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
                 const double* __restrict__ chipow, const double* __restrict__ D,
                 const double* __restrict__ B, const cplx* __restrict__ psi,
                 const cplx* __restrict__ tw, int N_tr, int N_I, int N, int* __restrict__ status) {
+  pdl_trigger();   // the next kernel of the step may be scheduled
   extern __shared__ cplx smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
@@ -384,6 +393,8 @@ k_fftlog_adj_cl(double* __restrict__ scratch, const cplx* __restrict__ cbar,
     psn[t] = ps[n];
     psm[t] = ps[M - n];
   }
+  // the tables above are the grid's; the coefficient cotangents come from the kernels before
+  pdl_wait();
   __syncthreads();
   const double* cp = chipow + (size_t)i * N;
   constexpr int kOut = 2;                  // outputs per thread (L <= 2 kClThreads)
@@ -504,14 +515,14 @@ size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N) {
 cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
-                              double* scratch, cudaStream_t s, int* status) {
+                              double* scratch, cudaStream_t s, int* status, bool pdl) {
   int nchunk = (N_I + kKnotChunk - 1) / kKnotChunk;
   if (nchunk == 1 && use_cluster((long)n_walk * N_tr, N)) {
     // one chunk: the cluster kernel writes W_bar directly
     const size_t csm = (size_t)8 * (N / 2 / kCl) * sizeof(cplx);
-    k_fftlog_adj_cl<<<(unsigned)((long)n_walk * N_tr * kCl), kClThreads, csm, s>>>(
-        W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I, N, status);
-    return cudaGetLastError();
+    return launch_k(pdl, k_fftlog_adj_cl, dim3((unsigned)((long)n_walk * N_tr * kCl)),
+                    dim3(kClThreads), csm, s, W_bar, cbar, chipow, D, B, psi, twiddle, N_tr, N_I,
+                    N, status);
   }
   size_t smem = (size_t)(N / 2) * 2 * sizeof(cplx) + (size_t)N * sizeof(double);
   if (smem > 48 * 1024) {

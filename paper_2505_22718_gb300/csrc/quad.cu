@@ -433,6 +433,8 @@ k_delta_bar(T* __restrict__ dbar, double* __restrict__ pbar_part, const T* __res
             const double* __restrict__ P, const double* __restrict__ wk2, int N_tr, int N_k,
             int N_ell, int n_walk, int l_lo, int n_l, const int* __restrict__ listed) {
   constexpr int QT = DbarQ<T>::QT, DQ = DT * QT;
+  pdl_trigger();   // the next kernel of the step may be scheduled
+  pdl_wait();      // Delta and the cotangent come from the kernels before
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   const int NP = delta_bar_pitch(N_tr);
   T* St = reinterpret_cast<T*>(dsm_raw);           // [N_tr][NP]  St[j][i] = S_ij A_j
@@ -638,7 +640,7 @@ template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s,
-                             const int* listed) {
+                             const int* listed, bool pdl) {
   constexpr int DQ = DT * DbarQ<T>::QT;
   const size_t smem = (size_t)(N_tr * delta_bar_pitch(N_tr) + N_tr * DQ + N_tr) * sizeof(T);
   if (smem > 48 * 1024) {
@@ -647,9 +649,8 @@ cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cf, const do
     if (e != cudaSuccess) return e;
   }
   dim3 g((N_k + DQ - 1) / DQ, n_l, n_walk);
-  k_delta_bar<T><<<g, DT, smem, s>>>(dbar, scratch, delta, Cf, amp, P, wk2, N_tr, N_k, N_ell,
-                                     n_walk, l_lo, n_l, listed);
-  return cudaGetLastError();
+  return launch_k(pdl, k_delta_bar<T>, g, dim3(DT), smem, s, dbar, scratch, delta, Cf, amp, P, wk2,
+                  N_tr, N_k, N_ell, n_walk, l_lo, n_l, listed);
 }
 
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
@@ -668,9 +669,9 @@ size_t delta_bar_scratch_bytes(int n_walk, int N_k, int N_ell) {
 template cudaError_t launch_delta_bar<double>(double*, const double*, const double*,
                                               const double*, const double*, const double*, int,
                                               int, int, int, int, int, double*, cudaStream_t,
-                                              const int*);
+                                              const int*, bool);
 template cudaError_t launch_delta_bar<float>(float*, const float*, const double*, const double*,
                                              const double*, const double*, int, int, int, int,
-                                             int, int, double*, cudaStream_t, const int*);
+                                             int, int, double*, cudaStream_t, const int*, bool);
 
 }  // namespace swcl

@@ -22,6 +22,33 @@ __device__ __forceinline__ void flag_nonfinite(int* status, double v) {
   if (status && !isfinite(v)) atomicOr(status, kStatusNonfinite);
 }
 
+// Programmatic dependent launch.  A kernel launched with pdl = true (launch_k) may start while
+// the kernel before it in the stream is still running: it calls pdl_wait() before it touches any
+// memory that an earlier kernel of the step writes (after the wait, every earlier kernel of the
+// stream has completed and its writes are visible), and pdl_trigger() early, so that the next
+// kernel can be scheduled once every CTA of this one has started.  Both are no-ops in a kernel
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 // Device buffer with a byte count, owned by the context.
 struct DevBuf {
   void* p = nullptr;
@@ -197,6 +224,9 @@ struct swcl_ctx {
   // swcl_compute_batched with a cotangent: the cotangent is unpacked on the auxiliary stream beside
   // the forward pass, and C is packed there beside the VJP (joined at the end of the VJP)
   bool overlap = false;
+  // the kernels of the critical path start with programmatic dependent launch (launch_k) when
+  // SWCL_PDL=1 at context creation; off by default (measured no faster inside the step's graph)
+  bool pdl = false;
   cudaEvent_t ev_pre = nullptr, ev_unpack = nullptr, ev_pack = nullptr, ev_quad = nullptr;
   // pinned staging for small host inputs: copied on the host, then sent without a wait
   unsigned char* stage = nullptr;
@@ -309,7 +339,8 @@ cudaError_t launch_fftlog_fwd_df(float4* coef, const double* W, const double* ch
 cudaError_t launch_fftlog_adj(double* W_bar, const cplx* cbar, const double* chipow,
                               const double* D, const double* B, const cplx* psi,
                               const cplx* twiddle, int n_walk, int N_tr, int N_I, int N,
-                              double* scratch, cudaStream_t s, int* status = nullptr);
+                              double* scratch, cudaStream_t s, int* status = nullptr,
+                              bool pdl = false);
 size_t fftlog_adj_scratch_bytes(int n_walk, int N_tr, int N_I, int N);
 bool fftlog_adj_single_launch(int n_walk, int N_tr, int N_I, int N);   // no chunk reduction
 
@@ -355,7 +386,8 @@ template <typename T>
 cudaError_t launch_delta_bar(T* dbar, const T* delta, const double* Cbar_full, const double* amp,
                              const double* P, const double* wk2, int n_walk, int N_tr, int N_k,
                              int N_ell, int l_lo, int n_l, double* scratch, cudaStream_t s,
-                             const int* listed = nullptr);   // listed: as in launch_quad_f32
+                             const int* listed = nullptr,   // listed: as in launch_quad_f32
+                             bool pdl = false);
 cudaError_t launch_pbar_reduce(double* P_bar, const double* scratch, const double* wk2,
                                int n_walk, int N_k, int N_ell, cudaStream_t s,
                                int* status = nullptr);
