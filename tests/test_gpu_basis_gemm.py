@@ -178,3 +178,28 @@ def test_every_tile_variant_against_oracle(code):
         f, (Pbo, Abo, Wbo, ex) = oracle_walker(w, wk, tapers, C_bar=Cb[wk])
         assert norm_err(C[wk], f["C"]) < GATE_C
         assert max(pbar_err(Pb[wk], Pbo, ex["P_abs"]), grad_err(Ab[wk], Abo), wbar_err(Wb[wk], Wbo)) < GATE_G
+
+
+def test_programmatic_dependent_launch_gives_the_same_results(wl):
+    """SWCL_PDL=1: the critical-path kernels start before their predecessors finish and wait with
+    griddepcontrol.wait; C must be bit for bit that of the ordinary launches (the same kernels,
+    the same sums) and the gradients equal up to the order of the adjoint's FP64 atomics."""
+    w = wl("n5k_vjp")
+    old_pdl, old_tiles = os.environ.get("SWCL_PDL"), os.environ.get("SWCL_BASIS_TILES")
+    os.environ["SWCL_BASIS_TILES"] = "1120,16736"
+    try:
+        os.environ["SWCL_PDL"] = "1"
+        ctx_p = _context(w)
+        os.environ["SWCL_PDL"] = "0"
+        ctx_0 = _context(w)
+    finally:
+        for k, v in (("SWCL_PDL", old_pdl), ("SWCL_BASIS_TILES", old_tiles)):
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    Cp, gp = _fwd_vjp(ctx_p, w.C_bar)
+    C0, g0 = _fwd_vjp(ctx_0, w.C_bar)
+    assert np.array_equal(Cp, C0)
+    for a, b in zip(gp, g0):
+        assert max_rel(a, b) < 1e-12
