@@ -69,11 +69,12 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the sub-records (general profile, 256-walker batch) and the TF32/FP64 "
                          "peak measurement")
-    ap.add_argument("--sweep", default="none", choices=["none", "nell", "cpu", "cpu-child"],
+    ap.add_argument("--sweep", default="none", choices=["none", "nell", "cpu", "cpu-child", "e2e"],
                     help="nell: time per evaluation against the number of multipoles (one JSON "
                          "line per point and a linear fit), instead of the headline line; cpu: the "
                          "oracle on the host cores for each workload size, with the BLAS thread "
-                         "count pinned to one and to all cores")
+                         "count pinned to one and to all cores; e2e: one step's host wall time "
+                         "through the device-pointer graph and through swcl_step_host")
     ap.add_argument("--limber", type=int, default=0,
                     help="Limber branch for multipoles >= this (0: off, the paper's setting)")
     ap.add_argument("--workload", default="n5k", choices=["n5k", "large"],
@@ -812,6 +813,58 @@ def run_sweep_nell(args, device):
     return 0
 
 
+def run_sweep_e2e(args, device):
+    """Where the end-to-end step's time goes, one parameter point of the N5K-shaped workload, one
+    process: per step (host wall time over the timed steps, no L2 flush), the device-pointer graph
+    followed by a host synchronisation; swcl_step_host through the Python binding; and the same
+    C entry point called through ctypes with its arguments prepared once."""
+    import ctypes
+    import torch
+    import paper_2505_22718_gb300 as swcl
+    from paper_2505_22718_gb300 import _lib
+    torch.cuda.set_device(device)
+    dev = torch.device("cuda", device)
+    prec = swcl.PRECISIONS[args.precision]
+    w, cbar = make_inputs(1, 0, 1)
+    ctx = swcl.Context(device)
+    st = device_inputs(swcl, ctx, w, cbar, dev)
+
+    def pinned(a, shape):
+        h = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        h.numpy()[...] = np.asarray(a).reshape(shape)
+        return h
+    W_h, P_h, A_h = pinned(w.W, st.Wb.shape), pinned(w.P, st.Pb.shape), pinned(w.amp, st.Ab.shape)
+    Cb_h = pinned(cbar, st.C.shape)
+    C_h, Pb_h, Ab_h, Wb_h = (torch.empty(x.shape, dtype=torch.float64, pin_memory=True)
+                             for x in (st.C, st.Pb, st.Ab, st.Wb))
+    lib = _lib.load()
+    args_c = [ctypes.c_void_p(t.data_ptr()) for t in (W_h, P_h, A_h, Cb_h, C_h, Pb_h, Ab_h, Wb_h)]
+
+    def device_graph():
+        st.full(prec)
+        ctx.sync()
+
+    def step_binding():
+        swcl.swcl_step_host(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
+
+    def step_ctypes():
+        if lib.swcl_step_host(ctx.ptr, prec, *args_c) != 0:
+            raise RuntimeError("swcl_step_host failed")
+    steps = max(100, args.steps)
+    out = {"sweep": "e2e", "workload": WORKLOAD, "precision": args.precision, "steps": steps}
+    for name, fn in (("device_graph_and_sync_us", device_graph), ("step_host_binding_us", step_binding),
+                     ("step_host_ctypes_us", step_ctypes)):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        out[name] = (time.perf_counter() - t0) / steps * 1e6
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -854,6 +907,12 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         return run_sweep_nell(args, local)
+    if args.sweep == "e2e":
+        if rank != 0:
+            return 0
+        import __graft_entry__
+        __graft_entry__.build()
+        return run_sweep_e2e(args, local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
