@@ -198,10 +198,10 @@ int swcl_compute_batched(swcl_ctx* ctx, int precision, double* C_out, const doub
  * Every non-NULL pointer must be page-locked host memory (cudaHostAlloc, cudaHostRegister, a
  * pinned torch tensor): two kernels of the graph read and write it directly (copy nodes where
  * the device cannot address it).  Pointers equal to those of the captured graph are not checked
- * again.  The
- * library-owned device side of the outputs and cotangent is sized at the first call.  The first
- * call of a configuration (pointers, precision, sizes) runs the step once outside the graph and
- * captures it; later calls replay it.  Needs set_grids, set_tracers, set_windows and set_power
+ * again.  The library-owned device side of the outputs and cotangent is sized at the first call.
+ * The first call of a configuration (pointers, precision, sizes) runs the step once outside the
+ * graph and captures it; later calls replay it.  The call waits for the replay by polling (it
+ * keeps one host thread busy for the step's duration).  Needs set_grids, set_tracers, set_windows and set_power
  * first.  Errors: SWCL_ERR_INVALID_ARG (a pointer that is not page-locked host memory, P without
  * amp, gradients without C_bar), SWCL_ERR_STATE, and SWCL_ERR_NONFINITE / SWCL_ERR_TIMEOUT from
  * the device status word of this step (then cleared). */
