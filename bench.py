@@ -613,10 +613,9 @@ def run_ours(args, rank, world, device):
         Ab_h = torch.empty(st.Ab.shape, dtype=torch.float64, pin_memory=True)
         Wb_h = torch.empty(st.Wb.shape, dtype=torch.float64, pin_memory=True)
 
-        def e2e_step():
-            # one call: inputs host -> device, forward + VJP, results device -> host, in one
-            # graph replay; returns when the host outputs are written
-            swcl.swcl_step_host(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
+        # one call per step: inputs host -> device, forward + VJP, results device -> host, in
+        # one graph replay; returns when the host outputs are written
+        e2e_step = swcl.HostStep(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
 
         for _ in range(max(3, args.warmup // 2)):
             e2e_step()
@@ -634,9 +633,10 @@ def run_ours(args, rank, world, device):
         d2h = sum(x.numel() * 8 for x in (C_h, Pb_h, Ab_h, Wb_h))
         out["e2e"] = {"value": nw * world * args.steps / el, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h,
-                      "calls": "swcl_step_host: window samples, P, amplitudes and cotangent "
+                      "calls": "swcl_step_host (HostStep, arguments prepared once): window "
+                               "samples, P, amplitudes and cotangent "
                                "host -> device, forward + VJP, C and the gradients device -> host, "
-                               "one graph replay and one stream sync per step"}
+                               "one graph replay and one wait per step"}
     ctx.close()
     del st
     if rank == 0 and world == 1 and args.workload == "n5k" and not args.no_extra:
@@ -852,8 +852,9 @@ def run_sweep_e2e(args, device):
             raise RuntimeError("swcl_step_host failed")
     steps = max(100, args.steps)
     out = {"sweep": "e2e", "workload": WORKLOAD, "precision": args.precision, "steps": steps}
+    step_prepared = swcl.HostStep(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
     for name, fn in (("device_graph_and_sync_us", device_graph), ("step_host_binding_us", step_binding),
-                     ("step_host_ctypes_us", step_ctypes)):
+                     ("step_host_ctypes_us", step_ctypes), ("host_step_object_us", step_prepared)):
         for _ in range(max(3, args.warmup)):
             fn()
         t0 = time.perf_counter()

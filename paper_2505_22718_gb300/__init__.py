@@ -17,7 +17,7 @@ from .api import (  # noqa: F401
     swcl_selftest_wait_timeout, swcl_jvp, swcl_gaussian_fisher, swcl_set_limber,
     swcl_profile_enable, swcl_profile_read, swcl_profile_reset, swcl_debug_read,
     SWCL_DBG_COEF, SWCL_DBG_DELTA, SWCL_DBG_GTAB, SWCL_DBG_PHASE, SWCL_DBG_UNIT,
-    swcl_last_error, strerror, swcl_fftlog_noalloc, swcl_compute_batched, swcl_step_host,
+    swcl_last_error, strerror, swcl_fftlog_noalloc, swcl_compute_batched, swcl_step_host, HostStep,
 )
 
 

@@ -175,6 +175,30 @@ def swcl_step_host(ctx, precision, C_out, W=None, P=None, amp=None, C_bar=None, 
     _check(ctx, _lib.load().swcl_step_host(ctx, precision, *ptrs))
 
 
+class HostStep:
+    """swcl_step_host with its arguments prepared once: the page-locked host tensors are checked
+    and their addresses taken at construction, and each call of the object runs one step (inputs
+    in, forward + VJP, results out) without re-marshalling.  The tensors must stay alive and in
+    place; write new parameters into them between steps."""
+
+    def __init__(self, ctx, precision, C_out, W=None, P=None, amp=None, C_bar=None, P_bar=None,
+                 amp_bar=None, W_bar=None):
+        self._keep = []
+        self._args = []
+        for a in (W, P, amp, C_bar, C_out, P_bar, amp_bar, W_bar):
+            p, k = _ptr(a, np.float64)
+            self._keep.append(k)
+            self._args.append(p)
+        self._ctx = ctx
+        self._precision = precision
+        self._fn = _lib.load().swcl_step_host
+
+    def __call__(self):
+        st = self._fn(self._ctx, self._precision, *self._args)
+        if st != SWCL_OK:
+            _check(self._ctx, st)
+
+
 def swcl_profile_enable(ctx, enable=True):
     _check(ctx, _lib.load().swcl_profile_enable(ctx, 1 if enable else 0))
 

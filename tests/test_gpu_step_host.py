@@ -137,3 +137,28 @@ def test_step_host_rejects_pageable_arrays_and_reports_nonfinite(walkers):
     W_h.numpy()[...] = w.W
     S.swcl_step_host(ctx.ptr, prec, C_h, W_h, P_h, A_h)
     assert np.all(np.isfinite(C_h.numpy()))
+
+
+def test_host_step_object_matches_the_call(walkers):
+    """HostStep (arguments prepared once) runs the same graph as swcl_step_host, and each call
+    reads the host arrays as they are then."""
+    import paper_2505_22718_gb300 as S
+    w = walkers
+    ctx = lib_context(w)
+    prec = S.SWCL_SPLIT_BF16
+    n_out = sum(len(l) for l in w.ell_lists)
+    Cb = np.random.default_rng(6).standard_normal((n_out, w.n_tr, w.n_tr))
+    W_h, P_h, A_h, Cb_h = _pinned(w.W), _pinned(w.P), _pinned(w.amp), _pinned(Cb)
+    C_h, Pb_h, Ab_h, Wb_h = _outputs(w, n_out)
+    S.swcl_step_host(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
+    ref = [t.numpy().copy() for t in (C_h, Pb_h, Ab_h, Wb_h)]
+    step = S.HostStep(ctx.ptr, prec, C_h, W_h, P_h, A_h, Cb_h, Pb_h, Ab_h, Wb_h)
+    for t in (C_h, Pb_h, Ab_h, Wb_h):
+        t.zero_()
+    step()
+    assert np.array_equal(C_h.numpy(), ref[0])
+    for a, b in zip((Pb_h, Ab_h, Wb_h), ref[1:]):
+        assert np.max(np.abs(a.numpy() - b)) <= 1e-12 * np.max(np.abs(b))
+    A_h.numpy()[...] = w.amp * 2.0       # C is quadratic in the amplitudes
+    step()
+    assert np.max(np.abs(C_h.numpy() - 4.0 * ref[0])) <= 1e-12 * np.max(np.abs(ref[0]))
