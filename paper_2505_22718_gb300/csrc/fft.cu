@@ -234,7 +234,7 @@ __global__ void k_sum_chunks(double* __restrict__ W_bar, const double* __restric
 // Step 1 runs in each CTA (Stockham in shared memory), step 2 (the kCl-point DFTs, each CTA a
 // slice of k2) reads the other CTAs' Y through distributed shared memory.
 constexpr int kCl = 8;
-constexpr int kClThreads = 128;
+constexpr int kClThreads = 256;
 
 __device__ __forceinline__ cplx tw_mod(const cplx* tw, long x, int N) { return tw[x & (N - 1)]; }
 
