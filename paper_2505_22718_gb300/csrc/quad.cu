@@ -396,7 +396,7 @@ __global__ void k_amp_bar(double* __restrict__ abar, const double* __restrict__ 
 // chunks.  A launch covers the multipoles [l_lo, l_lo + n_l) of the Delta buffer it is given (a
 // multipole chunk when Delta is recomputed chunk by chunk); the reduction runs once after the last
 // chunk.
-constexpr int DT = 128;
+constexpr int DT = 256;   // threads per CTA
 constexpr int LC = 1;   // multipoles per CTA: one, for enough CTAs to hide the load latency
 constexpr int DG = 4;   // rows i per pass
 
@@ -420,11 +420,12 @@ __device__ __forceinline__ void two_sum_acc(T& s, T& c, T x) {
   s = sn;
 }
 
-// QT consecutive k points per thread (2 for FP32: every shared load of S feeds 2 DG FMAs, and
-// Delta and Dbar move as 8-byte pairs); the sums of each k point are those of one thread per
-// point, in the same order.
+// QT consecutive k points per thread: with QT = 2 every shared load of S feeds 2 DG FMAs and
+// Delta and Dbar move as 8-byte pairs, but one point per thread at 256 threads per CTA measured
+// faster (more warps to hide the load latency), so both types use QT = 1; the sums of each k
+// point are the same in either form.
 template <typename T> struct DbarQ { static constexpr int QT = 1; };
-template <> struct DbarQ<float> { static constexpr int QT = 2; };
+template <> struct DbarQ<float> { static constexpr int QT = 1; };
 
 template <typename T>
 __global__ void __launch_bounds__(DT)
