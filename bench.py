@@ -150,13 +150,13 @@ TRAFFIC = {
     # the file whose sha256 is recorded
     ("basis gemm adj", 16736): {"bytes": 25439232, "walkers": 1, "workload": "n5k",
                                "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                               "sha256": "4891ced3c538ae140537ef4aeeab2f038494dea763e55cb271944e0a021f48fc"},
-    ("basis gemm adj", 16592): {"bytes": 25639168, "walkers": 1, "workload": "n5k",
+                               "sha256": "0e9f3ff4655bc6f91d9ef2dae84baf3ebf09bfb862c184be3b5fec9aa3aae851"},
+    ("basis gemm adj", 16592): {"bytes": 25639936, "walkers": 1, "workload": "n5k",
                                "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                               "sha256": "4891ced3c538ae140537ef4aeeab2f038494dea763e55cb271944e0a021f48fc"},
-    ("basis gemm adj", 16608): {"bytes": 25050112, "walkers": 1, "workload": "n5k",
+                               "sha256": "0e9f3ff4655bc6f91d9ef2dae84baf3ebf09bfb862c184be3b5fec9aa3aae851"},
+    ("basis gemm adj", 16608): {"bytes": 25048576, "walkers": 1, "workload": "n5k",
                                "src": "paper_2505_22718_gb300/csrc/basis_tc.cu",
-                               "sha256": "4891ced3c538ae140537ef4aeeab2f038494dea763e55cb271944e0a021f48fc"},
+                               "sha256": "0e9f3ff4655bc6f91d9ef2dae84baf3ebf09bfb862c184be3b5fec9aa3aae851"},
 }
 
 

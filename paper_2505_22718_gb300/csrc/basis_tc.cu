@@ -1651,7 +1651,8 @@ __global__ void k_kmu(float* __restrict__ kmu, const double* __restrict__ kpow,
 // Forward B image [nt][kb][3 planes][NT rows x 64 B]: row j = (w, i, l, s) (s fastest),
 // (j, 2n) = Re H, (j, 2n+1) = -Im H, H = F_{w,i,s,n} G_{cls(i)}[l_lo + l][n] in double-float.
 // Grid (n_kb, n_nt), NT * 4 threads: thread (row, ch) writes 16 bytes of each plane (four n).
-__global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
+// at most 40 registers (no spills): four blocks of 384 threads (96-column tiles) per SM
+__global__ void __maxnreg__(40) k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
                        const float4* __restrict__ gdf, const int* __restrict__ cls_of,
                        const int2* __restrict__ cmap, int N_tr, int N_ell, int n_h, int l_lo,
                        int n_l, int r, int NI, int n_cols, int NT, int n_kb) {
@@ -1704,7 +1705,8 @@ __global__ void k_himg(uint8_t* __restrict__ img, const float4* __restrict__ F,
 // (j, q) = kmu[i][s][q] Dbar[w][l][i][q].  Grid (n_kb, n_nt), NT * 4 threads: thread (row, ch)
 // writes eight q; vec4: N_k % 4 == 0, so that the rows of Dbar and kmu hold 16-byte aligned
 // groups of four.
-__global__ void k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
+// at most 32 registers (no spills): five blocks of 384 threads per SM
+__global__ void __maxnreg__(32) k_dimg(uint8_t* __restrict__ img, const float* __restrict__ dbar,
                        const float* __restrict__ kmu, const int2* __restrict__ cmap, int N_tr,
                        int N_k, int n_l, int r, int n_cols, int NT, int n_kb, int vec4,
                        double* __restrict__ zero, long n_zero) {
